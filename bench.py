@@ -1,0 +1,294 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 RMT per-step update: FSI cell-updates/s.
+
+Default workload: the 256^3 triply periodic active-swimmer scene (8 ellipsoids with an active
+bending stress, FP32 bulk with FP64 multigrid residual refinement).  One "step" is one full
+timestep of the 13-step algorithm over the whole grid.  Inputs (fields of 256^3 cells, several
+GB) are far larger than the 129 MB L2, so no cache flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
+
+N > 1 runs one independent replica per GPU (launched with torch.distributed.run); value is the
+cell-updates/s of all replicas together, timed between barriers, max over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
+scene (the same bodies and constants on a 48^3 grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FSI cell-updates/s"
+CONFIGS = {
+    # name: (scene factory kwargs, description)
+    "swimmers256": dict(kind="swimmers", n=256, precision="fp32",
+                        desc="256^3 triply periodic unit box, 8 active-stress ellipsoid swimmers "
+                             "(0.15,0.04,0.04), G=1, mu=mu_a=0.01, A=0.5, omega=2pi; FP32 bulk + FP64 "
+                             "multigrid residual refinement"),
+    "swimmers256_fp64": dict(kind="swimmers", n=256, precision="fp64",
+                             desc="the same 256^3 swimmer scene on the plain FP64 path"),
+    "settling128": dict(kind="settling", n=128, precision="fp64",
+                        desc="128^3 no-slip box, 20 settling ellipsoids (10 at 1.5, 10 at 0.5), FP64"),
+    "cavity32": dict(kind="cavity", n=32, precision="fp64", desc="32^3 lid-driven cavity, one soft sphere, FP64"),
+}
+CPU_SAMPLE_N = 48
+
+
+def make_scene(cfg: dict, n: int | None = None):
+    from paper_2104_00095_gb300 import scenes as S
+
+    n = n or cfg["n"]
+    if cfg["kind"] == "swimmers":
+        return S.swimmers(n=n, precision=cfg["precision"])
+    if cfg["kind"] == "settling":
+        return S.settling(n=n, precision=cfg["precision"])
+    return S.cavity_sphere(n, precision=cfg["precision"])
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+                pw.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_rate(cfg: dict, steps: int, warmup: int):
+    """cell-updates/s of the FP64 oracle on the CPU_SAMPLE_N^3 copy of the scene (single thread)."""
+    import oracle as O
+
+    sc = make_scene(cfg, CPU_SAMPLE_N)
+    sc["precision"] = "fp64"
+    o = O.Oracle(sc)
+    o.read(O.F_RHO)  # initialisation outside the timed region
+    for _ in range(warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    rc = o.step(steps)
+    dt = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed: {o.error()}")
+    return CPU_SAMPLE_N**3 * steps / dt, dt
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    rate, dt = cpu_oracle_rate(cfg, args.steps, args.warmup)
+    sample = (f"{args.steps} timed steps (after {args.warmup} warm-up) of the same scene on a "
+              f"{CPU_SAMPLE_N}^3 grid, FP64 oracle, one host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.config + f" (sampled at {CPU_SAMPLE_N}^3)"},
+            "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
+    ap.add_argument("--mg-cycles", type=int, default=4, help="V-cycles per Poisson solve (fixed, no host sync)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2104_00095_gb300 import rmt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    scene = make_scene(cfg)
+    scene["mg_fixed_cycles"] = args.mg_cycles
+    g = rmt.Grid(scene, stream=stream.cuda_stream)
+    N = int(np.prod(scene["n"]))
+    for _ in range(args.warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = str(local)
+    clk = Clocks(uuid)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = rmt.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = rmt.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * args.steps / (ms / 1e3)
+
+    # the same steps again with the library's CUDA-event profiler on: per-stage times and the
+    # per-launch duration of the finest-level multigrid kernels
+    g.profile(True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        g.step(1)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof = g.profile_read()
+    g.profile(False)
+    prof_ms = p0.elapsed_time(p1)
+    kern = [p for p in prof if p[3] > 0 and p[2] > 0]
+    peak, peak_kind = peaks()
+    roofline = None
+    if kern:
+        name, tot, nl, byt = max(kern, key=lambda p: p[1])
+        per = tot / nl
+        ach = byt / (per / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                    "bytes_per_launch": byt, "launches": nl, "avg_launch_ms": per,
+                    "share_of_step": tot / prof_ms, "profiled_ms_per_step": prof_ms / args.steps}
+    stages = {p[0]: round(p[1] / args.steps, 4) for p in prof if p[1] > 0}
+
+    # end to end through the C ABI with host buffers: every step uploads u from pinned host
+    # memory, advances one step and reads u back
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+        g.read(rmt.RMT_F_U, out=host_in.numpy())
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.write_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * 8, 0)
+            g.step(1)
+            g.read(rmt.RMT_F_U, out=host_out.numpy())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        et = t1 - t0
+        if world > 1:
+            t = torch.tensor([et], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": world * N * args.steps / et, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
+               "ms_per_step": 1e3 * et / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(cfg, 2, 0)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"2 steps of the same scene on a {CPU_SAMPLE_N}^3 grid, FP64 oracle, one host thread "
+                         f"({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": args.config, "description": cfg["desc"], "grid": list(scene["n"]),
+                           "bodies": len(scene["solids"]), "mg_cycles_per_solve": args.mg_cycles,
+                           "dt": g.dt, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (no flush needed)"},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,
+                "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,681 @@
+// C ABI of the RMT per-step update (declared in include/rmt.h).  Owns the device state of
+// one simulation and sequences the kernels of one timestep in the order of the paper's
+// SI "Timestepping algorithm" (13 steps) on the grid's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <atomic>
+
+#include "rmt.h"
+#include "rmt_kernels.h"
+
+static std::atomic<long> g_launches{0};
+void rmt_count_launches(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+struct BodyMem {
+  void* X[2] = {nullptr, nullptr};
+  void* PHI[2] = {nullptr, nullptr};
+  int8_t* LAY[2] = {nullptr, nullptr};
+  void* XH = nullptr;
+  void* PHIH = nullptr;
+};
+
+}  // namespace
+
+namespace {
+enum {
+  P_STRESS_N, P_GODUNOV, P_MAC_SETUP, P_MAC_SOLVE, P_MAC_CORR_ADV, P_XI_PRED, P_EXTRAP, P_CORR, P_STRESS_H,
+  P_USTAR, P_FE_SETUP, P_FE_SOLVE, P_FE_UPDATE, P_MAC_SMOOTH, P_MAC_RESID, P_FE_SMOOTH, P_FE_RESID, P_NUM
+};
+const char* const kProfNames[P_NUM] = {
+    "stress_n", "godunov_velocity", "mac_setup", "mac_solve", "mac_correct_advect", "xi_predict", "extrapolate",
+    "corrector", "stress_half", "density_ustar", "fe_setup", "fe_solve", "fe_update_density",
+    "k_smooth(mac,level0,colour)", "k_resid64(mac)", "k_smooth(fe,level0,colour)", "k_resid64(fe)"};
+struct Prof {
+  int on = 0;
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int e;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  cudaEvent_t open[P_NUM] = {};
+  double ms[P_NUM] = {};
+  long n[P_NUM] = {};
+};
+struct HookCtx {
+  rmt_grid* g;
+  int kind;
+};
+}  // namespace
+
+struct rmt_grid {
+  rmt_grid_desc desc;
+  Geo g;
+  int fp32 = 0;
+  size_t esz = 8;
+  cudaStream_t s = nullptr;
+  int inited = 0;
+  rmt_status sticky = RMT_OK;
+  char msg[512] = {0};
+  std::vector<rmt_solid_desc> solids;
+  std::vector<Body> bodies;
+  std::vector<BodyMem> bm;
+  Body* bodies_d = nullptr;
+  void* views_d = nullptr;  // BodyView<T>[2 parities][3 levels][nb]
+  int par = 0;
+  void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
+  void *adv = nullptr, *ustar = nullptr, *psi = nullptr;
+  void* ub[3][3] = {};
+  void* vadv[3] = {};
+  void* uf[3][3] = {};
+  void* umac[3] = {};
+  MGSolver* mac = nullptr;
+  MGSolver* fe = nullptr;
+  int* err_d = nullptr;
+  int* err_h = nullptr;
+  double* stage = nullptr;
+  long stage_len = 0;
+  int cycles[2] = {0, 0};
+  double t = 0.0;
+  long step = 0;
+  std::vector<void*> allocs;
+  Prof prof;
+  HookCtx hctx[2];
+};
+
+namespace {
+
+rmt_status fail(rmt_grid* g, rmt_status st, const char* fmt, ...) {
+  if (g) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g->msg, sizeof g->msg, fmt, ap);
+    va_end(ap);
+    if (st != RMT_EINVAL) g->sticky = st;
+  }
+  return st;
+}
+
+#define CK(g, call)                                                                           \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(g, RMT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaEvent_t prof_event(rmt_grid* g) {
+  cudaEvent_t e = nullptr;
+  if (!g->prof.pool.empty()) {
+    e = g->prof.pool.back();
+    g->prof.pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+void pb(rmt_grid* g, int e) {
+  if (!g->prof.on) return;
+  g->prof.open[e] = prof_event(g);
+  cudaEventRecord(g->prof.open[e], g->s);
+}
+void pe(rmt_grid* g, int e) {
+  if (!g->prof.on || !g->prof.open[e]) return;
+  cudaEvent_t b = prof_event(g);
+  cudaEventRecord(b, g->s);
+  g->prof.recs.push_back({e, g->prof.open[e], b});
+  g->prof.open[e] = nullptr;
+  g->prof.n[e]++;
+}
+void prof_flush(rmt_grid* g) {
+  if (g->prof.recs.empty()) return;
+  cudaStreamSynchronize(g->s);
+  for (auto& r : g->prof.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) g->prof.ms[r.e] += ms;
+    g->prof.pool.push_back(r.a);
+    g->prof.pool.push_back(r.b);
+  }
+  g->prof.recs.clear();
+}
+void mg_hook(void* ctx, int which, int begin, cudaStream_t) {
+  HookCtx* h = (HookCtx*)ctx;
+  const int e = h->kind == 0 ? (which == 0 ? P_MAC_SMOOTH : P_MAC_RESID) : (which == 0 ? P_FE_SMOOTH : P_FE_RESID);
+  if (begin) pb(h->g, e);
+  else pe(h->g, e);
+}
+// algorithmic bytes of one launch of the profiled multigrid kernels (w = bytes per word):
+// smoother colour (7-point): x 1, b 1/2, three face coefficients 3, x written 1/2 words per cell;
+// smoother colour (27-point): x 1 + b 1/8 + written 1/8 words per node, beta 1 word per cell;
+// FP64 residual: x and b 8 bytes each, coefficients (3 or 1 words), residual copy 1 word.
+double prof_bytes(const rmt_grid* g, int e) {
+  const double w = (double)g->esz, N = (double)g->g.N, NN = (double)g->g.NN;
+  switch (e) {
+    case P_MAC_SMOOTH: return 5.0 * N * w;
+    case P_MAC_RESID: return 16.0 * N + 4.0 * N * w;
+    case P_FE_SMOOTH: return 1.25 * NN * w + N * w;
+    case P_FE_RESID: return 16.0 * NN + N * w + NN * w;
+  }
+  return 0.0;
+}
+
+rmt_status dalloc(rmt_grid* g, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) return fail(g, RMT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  g->allocs.push_back(*p);
+  e = cudaMemsetAsync(*p, 0, bytes < 16 ? 16 : bytes, g->s);
+  if (e != cudaSuccess) return fail(g, RMT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  return RMT_OK;
+}
+
+// Reading of the time step when the caller gives none: explicit viscous and elastic-wave
+// limits, dt = min(0.2 h, 0.8 rho_min h^2/(6 mu_max), 0.5 h/sqrt(G_max/rho_min)).
+double pick_dt(const rmt_grid* g) {
+  if (g->desc.dt > 0.0) return g->desc.dt;
+  const double h = g->g.h;
+  double rmin = g->desc.rho_f, mumax = g->desc.mu, gmax = 0.0;
+  for (const auto& s : g->solids) {
+    if (s.rho_s < rmin) rmin = s.rho_s;
+    const double ma = s.mu_a * (1.0 + s.gamma_t);
+    if (ma > mumax) mumax = ma;
+    if (s.G > gmax) gmax = s.G;
+  }
+  double dt = 0.2 * h;
+  const double dv = 0.8 * rmin * h * h / (6.0 * mumax);
+  if (dv < dt) dt = dv;
+  if (gmax > 0.0) {
+    const double de = 0.5 * h / sqrt(gmax / rmin);
+    if (de < dt) dt = de;
+  }
+  return dt;
+}
+
+template <typename T>
+__global__ void k_cvt(const T* __restrict__ a, double* __restrict__ b, long n) {
+  GRID_LOOP(i, n) b[i] = (double)a[i];
+}
+template <typename T>
+__global__ void k_cvt_back(const double* __restrict__ a, T* __restrict__ b, long n) {
+  GRID_LOOP(i, n) b[i] = (T)a[i];
+}
+__global__ void k_cvt_i8(const int8_t* __restrict__ a, double* __restrict__ b, long n) {
+  GRID_LOOP(i, n) b[i] = (double)a[i];
+}
+inline int nbk(long n) {
+  long b = (n + 255) / 256;
+  if (b > 152L * 32) b = 152L * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+BodyView<T>* views(rmt_grid* g, int par, int level) {
+  return (BodyView<T>*)g->views_d + ((size_t)(par * 3 + level) * g->bodies.size());
+}
+
+template <typename T>
+rmt_status build_views(rmt_grid* g) {
+  const int nb = (int)g->bodies.size();
+  std::vector<BodyView<T>> hv((size_t)6 * (nb > 0 ? nb : 1));
+  for (int par = 0; par < 2; par++)
+    for (int m = 0; m < nb; m++) {
+      BodyMem& b = g->bm[m];
+      hv[(par * 3 + 0) * nb + m] = {(const T*)b.X[par], (const T*)b.PHI[par], b.LAY[par]};
+      hv[(par * 3 + 1) * nb + m] = {(const T*)b.XH, (const T*)b.PHIH, b.LAY[1 - par]};
+      hv[(par * 3 + 2) * nb + m] = {(const T*)b.X[1 - par], (const T*)b.PHI[1 - par], b.LAY[1 - par]};
+    }
+  if (nb > 0) {
+    CK(g, cudaMemcpyAsync(g->views_d, hv.data(), hv.size() * sizeof(BodyView<T>), cudaMemcpyHostToDevice, g->s));
+    CK(g, cudaMemcpyAsync(g->bodies_d, g->bodies.data(), nb * sizeof(Body), cudaMemcpyHostToDevice, g->s));
+    CK(g, cudaStreamSynchronize(g->s));
+  }
+  return RMT_OK;
+}
+
+template <typename T>
+rmt_status init_t(rmt_grid* g) {
+  const Geo& G = g->g;
+  const long N = G.N;
+  rmt_status st;
+#define AL(ptr, bytes) \
+  if ((st = dalloc(g, (void**)&(ptr), (bytes))) != RMT_OK) return st;
+  const size_t e = sizeof(T);
+  AL(g->u, 3 * N * e);
+  AL(g->p, G.NN * e);
+  AL(g->rho, N * e);
+  AL(g->rho_h, N * e);
+  AL(g->divn, 3 * N * e);
+  AL(g->divh, 3 * N * e);
+  AL(g->adv, 3 * N * e);
+  AL(g->ustar, 3 * N * e);
+  AL(g->psi, G.NN * e);
+  for (int d = 0; d < 3; d++) {
+    const long nf = nfaces(G, d);
+    for (int a = 0; a < 3; a++) {
+      AL(g->ub[d][a], nf * e);
+      AL(g->uf[d][a], nf * e);
+    }
+    AL(g->vadv[d], nf * e);
+    AL(g->umac[d], nf * e);
+  }
+  const int nb = (int)g->bodies.size();
+  g->bm.assign(nb, BodyMem());
+  for (int m = 0; m < nb; m++) {
+    BodyMem& b = g->bm[m];
+    for (int q = 0; q < 2; q++) {
+      AL(b.X[q], 3 * N * e);
+      AL(b.PHI[q], N * e);
+      AL(b.LAY[q], N);
+    }
+    AL(b.XH, 3 * N * e);
+    AL(b.PHIH, N * e);
+  }
+  AL(g->bodies_d, (nb > 0 ? nb : 1) * sizeof(Body));
+  AL(g->views_d, (size_t)6 * (nb > 0 ? nb : 1) * sizeof(BodyView<T>));
+  AL(g->err_d, 16);
+  CK(g, cudaMallocHost((void**)&g->err_h, 16));
+  long sl = 3 * N;
+  for (int d = 0; d < 3; d++)
+    if (3 * nfaces(G, d) > sl) sl = 3 * nfaces(G, d);
+  if (G.NN > sl) sl = G.NN;
+  AL(g->stage, sl * sizeof(double));
+  g->stage_len = sl;
+#undef AL
+  cudaError_t ce = cudaSuccess;
+  g->mac = mg_create(G, 0, g->fp32, &ce);
+  if (ce != cudaSuccess) return fail(g, RMT_ENOMEM, "multigrid (MAC) allocation: %s", cudaGetErrorString(ce));
+  g->fe = mg_create(G, 1, g->fp32, &ce);
+  if (ce != cudaSuccess) return fail(g, RMT_ENOMEM, "multigrid (FE) allocation: %s", cudaGetErrorString(ce));
+  g->hctx[0] = {g, 0};
+  g->hctx[1] = {g, 1};
+  mg_set_hook(g->mac, mg_hook, &g->hctx[0]);
+  mg_set_hook(g->fe, mg_hook, &g->hctx[1]);
+  for (int m = 0; m < nb; m++) launch_fill<int8_t>(g->bm[m].LAY[1], (int8_t)-1, N, g->s);
+  if ((st = build_views<T>(g)) != RMT_OK) return st;
+  // SI "Initialization": u^0 = 0, p = 0, xi^0 = x, extrapolation, phi, rho^0
+  for (int m = 0; m < nb; m++) {
+    BodyMem& b = g->bm[m];
+    launch_init_xi<T>(G, g->bodies[m], (T*)b.X[0], g->s);
+    launch_extrapolate<T>(G, g->bodies_d + m, g->bodies[m], (T*)b.X[0], (T*)b.PHI[0], b.LAY[0], g->err_d, g->s);
+  }
+  launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, (T*)g->rho, g->s);
+  CK(g, cudaGetLastError());
+  CK(g, cudaStreamSynchronize(g->s));
+  return RMT_OK;
+}
+
+template <typename T>
+rmt_status step_t(rmt_grid* g) {
+  const Geo& G = g->g;
+  cudaStream_t s = g->s;
+  const int nb = (int)g->bodies.size();
+  const int cur = g->par, nxt = 1 - g->par;
+  T* ub[3][3];
+  T* vadv[3];
+  T* uf[3][3];
+  T* umac[3];
+  for (int d = 0; d < 3; d++) {
+    for (int a = 0; a < 3; a++) {
+      ub[d][a] = (T*)g->ub[d][a];
+      uf[d][a] = (T*)g->uf[d][a];
+    }
+    vadv[d] = (T*)g->vadv[d];
+    umac[d] = (T*)g->umac[d];
+  }
+  T* u = (T*)g->u;
+  // 1. tau^n and its divergence
+  pb(g, P_STRESS_N);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->t, (T*)g->divn, s);
+  pe(g, P_STRESS_N);
+  // 2. Godunov face states of u (transverse bar states first)
+  pb(g, P_GODUNOV);
+  launch_bar_states<T>(G, u, ub, vadv, s);
+  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, ub, vadv, uf, s);
+  pe(g, P_GODUNOV);
+  // 3. MAC projection of the normal face velocities
+  T* mbeta[3] = {(T*)mg_coef0(g->mac, 0), (T*)mg_coef0(g->mac, 1), (T*)mg_coef0(g->mac, 2)};
+  pb(g, P_MAC_SETUP);
+  launch_mac_setup<T>(G, uf, (const T*)g->rho, mg_rhs(g->mac), mbeta, s);
+  pe(g, P_MAC_SETUP);
+  cudaError_t ce = cudaSuccess;
+  const double rtol = g->desc.mg_rtol > 0 ? g->desc.mg_rtol : 1e-12;
+  const int maxc = g->desc.mg_max_cycles > 0 ? g->desc.mg_max_cycles : 60;
+  pb(g, P_MAC_SOLVE);
+  int cyc = mg_solve(g->mac, rtol, maxc, g->desc.mg_fixed_cycles, s, &ce);
+  pe(g, P_MAC_SOLVE);
+  if (ce != cudaSuccess) return fail(g, RMT_ECUDA, "MAC solve: %s", cudaGetErrorString(ce));
+  if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "MAC multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  g->cycles[0] = cyc;
+  pb(g, P_MAC_CORR_ADV);
+  launch_mac_correct<T>(G, uf, mbeta, mg_solution(g->mac), umac, s);
+  // 4. advective term
+  launch_advect<T>(G, uf, umac, (T*)g->adv, s);
+  pe(g, P_MAC_CORR_ADV);
+  // 5.-7. predictor, re-extrapolation, corrector for every body
+  for (int m = 0; m < nb; m++) {
+    BodyMem& b = g->bm[m];
+    pb(g, P_XI_PRED);
+    launch_xi_predict<T>(G, u, vadv, uf, umac, (const T*)b.X[cur], b.LAY[cur], (T*)b.X[nxt], s);
+    pe(g, P_XI_PRED);
+    pb(g, P_EXTRAP);
+    launch_extrapolate<T>(G, g->bodies_d + m, g->bodies[m], (T*)b.X[nxt], (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, s);
+    pe(g, P_EXTRAP);
+    pb(g, P_CORR);
+    launch_corrector<T>(G, g->bodies_d + m, g->bodies[m], (const T*)b.X[cur], b.LAY[cur], (const T*)b.X[nxt],
+                        b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, s);
+    pe(g, P_CORR);
+  }
+  // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
+  pb(g, P_STRESS_H);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->t + 0.5 * G.dt, (T*)g->divh, s);
+  pe(g, P_STRESS_H);
+  pb(g, P_USTAR);
+  launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, (T*)g->rho_h, s);
+  launch_ustar<T>(G, u, (const T*)g->adv, (const T*)g->p, (const T*)g->rho_h, (const T*)g->divh, (T*)g->ustar, s);
+  pe(g, P_USTAR);
+  // 11. approximate projection, u^{n+1}, p^{n+1/2}
+  pb(g, P_FE_SETUP);
+  launch_fe_setup<T>(G, u, (const T*)g->ustar, (const T*)g->rho_h, mg_rhs(g->fe), (T*)mg_coef0(g->fe, 0), s);
+  pe(g, P_FE_SETUP);
+  pb(g, P_FE_SOLVE);
+  cyc = mg_solve(g->fe, rtol, maxc, g->desc.mg_fixed_cycles, s, &ce);
+  pe(g, P_FE_SOLVE);
+  if (ce != cudaSuccess) return fail(g, RMT_ECUDA, "FE solve: %s", cudaGetErrorString(ce));
+  if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "FE multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  g->cycles[1] = cyc;
+  pb(g, P_FE_UPDATE);
+  launch_fe_update<T>(G, (const T*)g->ustar, (const T*)g->rho_h, mg_solution(g->fe), u, (T*)g->p, (T*)g->psi, s);
+  // 12. xi <- xi^{n+1} (parity flip); 13. rho^{n+1}
+  g->par = nxt;
+  launch_density<T>(G, g->bodies_d, views<T>(g, nxt, 0), nb, (T*)g->rho, s);
+  pe(g, P_FE_UPDATE);
+  CK(g, cudaGetLastError());
+  g->t += G.dt;
+  g->step++;
+  return RMT_OK;
+}
+
+rmt_status ensure_init(rmt_grid* g) {
+  if (g->inited) return RMT_OK;
+  g->g.dt = pick_dt(g);
+  g->bodies.clear();
+  for (const auto& s : g->solids) {
+    Body b;
+    b.shape = s.shape;
+    for (int d = 0; d < 3; d++) {
+      b.c[d] = s.center[d];
+      b.a[d] = s.semi_axes[d];
+    }
+    for (int q = 0; q < 9; q++) b.R[q] = s.rot[q];
+    b.rho_s = s.rho_s;
+    b.G = s.G;
+    b.mu_a = s.mu_a;
+    b.gamma_t = s.gamma_t;
+    b.actA = s.active_A;
+    b.actW = s.active_omega;
+    b.actL = s.active_len;
+    g->bodies.push_back(b);
+  }
+  g->inited = 1;
+  rmt_status st = g->fp32 ? init_t<float>(g) : init_t<double>(g);
+  if (st != RMT_OK) return st;
+  return RMT_OK;
+}
+
+rmt_status check_err(rmt_grid* g) {
+  CK(g, cudaMemcpyAsync(g->err_h, g->err_d, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  if (g->err_h[0] != 0)
+    return fail(g, RMT_EDEGENERATE, "%d least-squares extrapolations stayed degenerate up to r_s = 4", g->err_h[0]);
+  return RMT_OK;
+}
+
+}  // namespace
+
+namespace {
+template <typename T>
+rmt_status gather_t(rmt_grid* g, int field, int sid, double* out) {
+  const Geo& G = g->g;
+  const long N = G.N;
+  cudaStream_t s = g->s;
+  auto cvt = [&](const void* src, long n, long off) { k_cvt<T><<<nbk(n), 256, 0, s>>>((const T*)src, out + off, n); rmt_count_launches(1); };
+  switch (field) {
+    case RMT_F_U: cvt(g->u, 3 * N, 0); break;
+    case RMT_F_P: cvt(g->p, G.NN, 0); break;
+    case RMT_F_RHO: cvt(g->rho, N, 0); break;
+    case RMT_F_XI: cvt(g->bm[sid].X[g->par], 3 * N, 0); break;
+    case RMT_F_PHI: cvt(g->bm[sid].PHI[g->par], N, 0); break;
+    case RMT_F_LAYER: k_cvt_i8<<<nbk(N), 256, 0, s>>>(g->bm[sid].LAY[g->par], out, N); rmt_count_launches(1); break;
+    case RMT_F_XI_HALF: cvt(g->bm[sid].XH, 3 * N, 0); break;
+    case RMT_F_DIVTAU_N: cvt(g->divn, 3 * N, 0); break;
+    case RMT_F_DIVTAU_H: cvt(g->divh, 3 * N, 0); break;
+    case RMT_F_ADV_U: cvt(g->adv, 3 * N, 0); break;
+    case RMT_F_USTAR: cvt(g->ustar, 3 * N, 0); break;
+    case RMT_F_RHO_HALF: cvt(g->rho_h, N, 0); break;
+    case RMT_F_MAC_Q:
+      CK(g, cudaMemcpyAsync(out, mg_solution(g->mac), N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      break;
+    case RMT_F_PSI:
+      CK(g, cudaMemcpyAsync(out, mg_solution(g->fe), G.NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      break;
+    case RMT_F_UFACE_X: case RMT_F_UFACE_Y: case RMT_F_UFACE_Z: {
+      const int d = field - RMT_F_UFACE_X;
+      const long nf = nfaces(G, d);
+      for (int a = 0; a < 3; a++) cvt(g->uf[d][a], nf, a * nf);
+      break;
+    }
+    case RMT_F_UMAC_X: case RMT_F_UMAC_Y: case RMT_F_UMAC_Z: {
+      const int d = field - RMT_F_UMAC_X;
+      cvt(g->umac[d], nfaces(G, d), 0);
+      break;
+    }
+    default: return fail(g, RMT_EINVAL, "unknown field %d", field);
+  }
+  CK(g, cudaGetLastError());
+  return RMT_OK;
+}
+
+template <typename T>
+rmt_status scatter_t(rmt_grid* g, int field, int sid) {
+  const Geo& G = g->g;
+  cudaStream_t s = g->s;
+  if (field == RMT_F_U) {
+    k_cvt_back<T><<<nbk(3 * G.N), 256, 0, s>>>(g->stage, (T*)g->u, 3 * G.N); rmt_count_launches(1);
+  } else if (field == RMT_F_P) {
+    k_cvt_back<T><<<nbk(G.NN), 256, 0, s>>>(g->stage, (T*)g->p, G.NN); rmt_count_launches(1);
+  } else {
+    BodyMem& b = g->bm[sid];
+    k_cvt_back<T><<<nbk(3 * G.N), 256, 0, s>>>(g->stage, (T*)b.X[g->par], 3 * G.N); rmt_count_launches(1);
+    launch_extrapolate<T>(G, g->bodies_d + sid, g->bodies[sid], (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par],
+                          g->err_d, s);
+    launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), (T*)g->rho, s);
+  }
+  CK(g, cudaGetLastError());
+  return RMT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+rmt_status rmt_create_grid(const rmt_grid_desc* d, rmt_grid** out) {
+  if (!d || !out) return RMT_EINVAL;
+  *out = nullptr;
+  for (int a = 0; a < 3; a++) {
+    if (d->n[a] < 4 || !(d->hi[a] > d->lo[a])) return RMT_EINVAL;
+    const int p0 = d->bc[2 * a] == RMT_BC_PERIODIC, p1 = d->bc[2 * a + 1] == RMT_BC_PERIODIC;
+    if (p0 != p1) return RMT_EINVAL;
+    if (!p0 && (d->bc[2 * a] != RMT_BC_NOSLIP || d->bc[2 * a + 1] != RMT_BC_NOSLIP)) return RMT_EINVAL;
+    if (p0 && (d->n[a] & 1)) return RMT_EINVAL;  // red-black colouring needs an even period
+    if (d->wall_u[2 * a][a] != 0.0 || d->wall_u[2 * a + 1][a] != 0.0) return RMT_EINVAL;
+  }
+  const double h = (d->hi[0] - d->lo[0]) / d->n[0];
+  for (int a = 1; a < 3; a++)
+    if (fabs((d->hi[a] - d->lo[a]) / d->n[a] - h) > 1e-12 * h) return RMT_EINVAL;
+  if (!(d->rho_f > 0) || !(d->mu >= 0) || !(d->eps_h > 0) || d->band_layers < 1 || d->band_layers > 8)
+    return RMT_EINVAL;
+  if (d->precision != RMT_PREC_FP64 && d->precision != RMT_PREC_FP32_REFINE) return RMT_EINVAL;
+  rmt_grid* g = new (std::nothrow) rmt_grid();
+  if (!g) return RMT_ENOMEM;
+  g->desc = *d;
+  g->s = (cudaStream_t)d->cuda_stream;
+  g->fp32 = d->precision == RMT_PREC_FP32_REFINE;
+  g->esz = g->fp32 ? 4 : 8;
+  Geo& G = g->g;
+  for (int a = 0; a < 3; a++) {
+    G.n[a] = d->n[a];
+    G.per[a] = d->bc[2 * a] == RMT_BC_PERIODIC;
+    G.nn[a] = G.per[a] ? G.n[a] : G.n[a] + 1;
+    G.lo[a] = d->lo[a];
+    G.len[a] = d->hi[a] - d->lo[a];
+    G.grav[a] = d->gravity[a];
+  }
+  for (int f = 0; f < 6; f++)
+    for (int a = 0; a < 3; a++) G.wall[f][a] = d->wall_u[f][a];
+  G.N = (long)G.n[0] * G.n[1] * G.n[2];
+  G.NN = (long)G.nn[0] * G.nn[1] * G.nn[2];
+  G.h = h;
+  G.eps = d->eps_h * h;
+  G.rho_f = d->rho_f;
+  G.mu = d->mu;
+  G.layers = d->band_layers;
+  G.dt = 0.0;
+  *out = g;
+  return RMT_OK;
+}
+
+rmt_status rmt_add_solid(rmt_grid* g, const rmt_solid_desc* s, int* solid_id) {
+  if (!g || !s) return RMT_EINVAL;
+  if (g->inited) return fail(g, RMT_ESTATE, "bodies must be added before the first step, read or write");
+  if (g->solids.size() >= RMT_MAX_BODIES) return fail(g, RMT_EINVAL, "at most %d bodies", RMT_MAX_BODIES);
+  if (s->shape != RMT_SHAPE_SPHERE && s->shape != RMT_SHAPE_ELLIPSOID) return fail(g, RMT_EINVAL, "unknown shape");
+  for (int a = 0; a < 3; a++)
+    if (!(s->semi_axes[a] > 0) && !(s->shape == RMT_SHAPE_SPHERE && a > 0)) return fail(g, RMT_EINVAL, "semi-axes must be positive");
+  if (!(s->rho_s > 0) || !(s->G >= 0) || !(s->mu_a >= 0)) return fail(g, RMT_EINVAL, "bad material constants");
+  if (s->active_A != 0.0 && !(s->active_len > 0)) return fail(g, RMT_EINVAL, "active_len must be positive");
+  g->solids.push_back(*s);
+  if (solid_id) *solid_id = (int)g->solids.size() - 1;
+  return RMT_OK;
+}
+
+rmt_status rmt_step(rmt_grid* g, int nsteps) {
+  if (!g || nsteps < 0) return RMT_EINVAL;
+  if (g->sticky != RMT_OK) return RMT_ESTATE;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  for (int k = 0; k < nsteps; k++) {
+    st = g->fp32 ? step_t<float>(g) : step_t<double>(g);
+    if (st != RMT_OK) return st;
+  }
+  if (g->desc.mg_fixed_cycles <= 0) return check_err(g);
+  return RMT_OK;
+}
+
+long rmt_field_len(rmt_grid* g, int field) {
+  if (!g) return -1;
+  const Geo& G = g->g;
+  switch (field) {
+    case RMT_F_U: case RMT_F_XI: case RMT_F_DIVTAU_N: case RMT_F_DIVTAU_H: case RMT_F_ADV_U:
+    case RMT_F_USTAR: case RMT_F_XI_HALF: return 3 * G.N;
+    case RMT_F_P: case RMT_F_PSI: return G.NN;
+    case RMT_F_RHO: case RMT_F_PHI: case RMT_F_LAYER: case RMT_F_MAC_Q: case RMT_F_RHO_HALF: return G.N;
+    case RMT_F_UFACE_X: case RMT_F_UFACE_Y: case RMT_F_UFACE_Z: return 3 * nfaces(G, field - RMT_F_UFACE_X);
+    case RMT_F_UMAC_X: case RMT_F_UMAC_Y: case RMT_F_UMAC_Z: return nfaces(G, field - RMT_F_UMAC_X);
+  }
+  return -1;
+}
+
+
+rmt_status rmt_read_fields(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes, int dst_is_device) {
+  if (!g || !dst) return RMT_EINVAL;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  const long n = rmt_field_len(g, field);
+  if (n < 0) return fail(g, RMT_EINVAL, "unknown field %d", field);
+  if (dst_bytes < (size_t)n * sizeof(double)) return fail(g, RMT_EINVAL, "destination too small");
+  if ((field == RMT_F_XI || field == RMT_F_PHI || field == RMT_F_LAYER || field == RMT_F_XI_HALF) &&
+      (solid_id < 0 || solid_id >= (int)g->bodies.size()))
+    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  double* out = dst_is_device ? (double*)dst : g->stage;
+  st = g->fp32 ? gather_t<float>(g, field, solid_id, out) : gather_t<double>(g, field, solid_id, out);
+  if (st != RMT_OK) return st;
+  if (!dst_is_device)
+    CK(g, cudaMemcpyAsync(dst, g->stage, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaStreamSynchronize(g->s));
+  return RMT_OK;
+}
+
+rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* src, size_t src_bytes, int src_is_device) {
+  if (!g || !src) return RMT_EINVAL;
+  if (g->sticky != RMT_OK) return RMT_ESTATE;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  if (field != RMT_F_U && field != RMT_F_P && field != RMT_F_XI) return fail(g, RMT_EINVAL, "field %d is not writable", field);
+  if (field == RMT_F_XI && (solid_id < 0 || solid_id >= (int)g->bodies.size()))
+    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  const long n = rmt_field_len(g, field);
+  if (src_bytes < (size_t)n * sizeof(double)) return fail(g, RMT_EINVAL, "source too small");
+  CK(g, cudaMemcpyAsync(g->stage, src, (size_t)n * sizeof(double),
+                        src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
+  st = g->fp32 ? scatter_t<float>(g, field, solid_id) : scatter_t<double>(g, field, solid_id);
+  if (st != RMT_OK) return st;
+  if (field == RMT_F_XI) return check_err(g);
+  if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
+  return RMT_OK;
+}
+
+int rmt_last_cycles(rmt_grid* g, int which) { return g ? g->cycles[which ? 1 : 0] : -1; }
+double rmt_dt(rmt_grid* g) { return g ? g->g.dt : 0.0; }
+
+rmt_status rmt_destroy_grid(rmt_grid* g) {
+  if (!g) return RMT_EINVAL;
+  if (g->s) cudaStreamSynchronize(g->s);
+  else cudaDeviceSynchronize();
+  for (void* p : g->allocs) cudaFree(p);
+  if (g->err_h) cudaFreeHost(g->err_h);
+  mg_destroy(g->mac);
+  mg_destroy(g->fe);
+  for (auto& r : g->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : g->prof.pool) cudaEventDestroy(e);
+  delete g;
+  return RMT_OK;
+}
+
+const char* rmt_last_error(const rmt_grid* g) { return g ? g->msg : "null grid"; }
+
+long rmt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rmt_status rmt_profile(rmt_grid* g, int enable) {
+  if (!g) return RMT_EINVAL;
+  prof_flush(g);
+  if (enable) {
+    for (int e = 0; e < P_NUM; e++) {
+      g->prof.ms[e] = 0.0;
+      g->prof.n[e] = 0;
+    }
+  }
+  g->prof.on = enable ? 1 : 0;
+  return RMT_OK;
+}
+
+int rmt_profile_entries(void) { return P_NUM; }
+
+const char* rmt_profile_name(int entry) { return (entry >= 0 && entry < P_NUM) ? kProfNames[entry] : ""; }
+
+rmt_status rmt_profile_read(rmt_grid* g, int entry, double* total_ms, long* launches, double* bytes_per_launch) {
+  if (!g || entry < 0 || entry >= P_NUM) return RMT_EINVAL;
+  prof_flush(g);
+  if (total_ms) *total_ms = g->prof.ms[entry];
+  if (launches) *launches = g->prof.n[entry];
+  if (bytes_per_launch) *bytes_per_launch = prof_bytes(g, entry);
+  return RMT_OK;
+}
+
+}  // extern "C"

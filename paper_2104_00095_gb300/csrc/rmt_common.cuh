@@ -1,0 +1,241 @@
+// Device-side building blocks of the RMT per-step update (arXiv 2104.00095).
+// Everything here is templated on the compute type T (double: FP64 path; float: FP32 bulk).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RMT_MAX_BODIES 64
+
+// process-wide count of kernels launched by this library (defined in rmt_api.cu)
+void rmt_count_launches(long n);
+#define RMT_PI 3.14159265358979323846
+
+// Grid geometry and the fluid constants, passed by value to every kernel.
+struct Geo {
+  int n[3];        // cells per axis
+  int per[3];      // 1 on a periodic axis
+  int nn[3];       // nodes per axis (n+1 walled, n periodic)
+  long N, NN;      // cells, nodes
+  double h, dt, eps, rho_f, mu;
+  double lo[3], len[3];
+  double wall[6][3];
+  double grav[3];
+  int layers;      // extrapolation layers
+};
+
+// One body's constants (Table pars + shape + active stress).
+struct Body {
+  int shape;
+  double c[3], a[3], R[9];
+  double rho_s, G, mu_a, gamma_t, actA, actW, actL;
+};
+
+// The reference-map fields of one body at one time level.
+template <typename T>
+struct BodyView {
+  const T* x;        // [3][N]
+  const T* phi;      // [N]
+  const int8_t* lay; // [N], -1 = absent
+};
+
+__host__ __device__ __forceinline__ long cidx(const Geo& g, int i, int j, int k) {
+  return i + (long)g.n[0] * (j + (long)g.n[1] * (long)k);
+}
+__host__ __device__ __forceinline__ long nidx(const Geo& g, int i, int j, int k) {
+  return i + (long)g.nn[0] * (j + (long)g.nn[1] * (long)k);
+}
+// d-face whose d-index is the face index f in [0, n_d] (between cells f-1 and f)
+__host__ __device__ __forceinline__ long fidx(const Geo& g, int d, int i, int j, int k) {
+  long e0 = g.n[0] + (d == 0), e1 = g.n[1] + (d == 1);
+  return i + e0 * (j + e1 * (long)k);
+}
+__host__ __device__ __forceinline__ long nfaces(const Geo& g, int d) {
+  return g.N / g.n[d] * (g.n[d] + 1);
+}
+
+// wraps a cell coordinate on a periodic axis; false outside a wall
+__device__ __forceinline__ bool wrap_axis(const Geo& g, int d, int& i) {
+  const int n = g.n[d];
+  if (i >= 0 && i < n) return true;
+  if (!g.per[d]) return false;
+  i %= n;
+  if (i < 0) i += n;
+  return true;
+}
+__device__ __forceinline__ bool cell_at(const Geo& g, int i, int j, int k, long& c) {
+  if (!wrap_axis(g, 0, i) || !wrap_axis(g, 1, j) || !wrap_axis(g, 2, k)) return false;
+  c = cidx(g, i, j, k);
+  return true;
+}
+__device__ __forceinline__ long node_at(const Geo& g, int i, int j, int k) {
+  if (g.per[0] && i >= g.nn[0]) i -= g.nn[0];
+  if (g.per[1] && j >= g.nn[1]) j -= g.nn[1];
+  if (g.per[2] && k >= g.nn[2]) k -= g.nn[2];
+  return nidx(g, i, j, k);
+}
+
+// Velocity component a at any cell coordinate: periodic wrap, or the mirrored ghost
+// 2 u_wall - u_mirror across a no-slip wall (applied axis by axis).
+template <typename T>
+__device__ __forceinline__ T uval(const Geo& g, const T* __restrict__ u, int a, int i, int j, int k) {
+  T add = T(0), s = T(1);
+  int ii[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const int n = g.n[d];
+    if (ii[d] < 0 || ii[d] >= n) {
+      if (g.per[d]) {
+        ii[d] %= n;
+        if (ii[d] < 0) ii[d] += n;
+      } else {
+        const int f = ii[d] < 0 ? 2 * d : 2 * d + 1;
+        add += s * T(2.0 * g.wall[f][a]);
+        s = -s;
+        ii[d] = ii[d] < 0 ? -1 - ii[d] : 2 * n - 1 - ii[d];
+      }
+    }
+  }
+  return add + s * u[a * g.N + cidx(g, ii[0], ii[1], ii[2])];
+}
+
+// -------------------------------------------------------------------------------------
+// explicitly rounded arithmetic (no contraction), used where a sign decides an integer
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+
+// Level set phi_0 of a body's reference shape (main text "Blurred interface method").
+// Sphere: exact signed distance.  Ellipsoid: (g-1)/|grad g| with g = |D^-1 R^T (X-c)|.
+template <typename T>
+__device__ T phi0(const Body& b, T X0, T X1, T X2) {
+  const T r0 = sub_rn(X0, T(b.c[0])), r1 = sub_rn(X1, T(b.c[1])), r2 = sub_rn(X2, T(b.c[2]));
+  if (b.shape == 0)
+    return sub_rn(sqrt_rn(add_rn(add_rn(mul_rn(r0, r0), mul_rn(r1, r1)), mul_rn(r2, r2))), T(b.a[0]));
+  const T z0 = add_rn(add_rn(mul_rn(T(b.R[0]), r0), mul_rn(T(b.R[3]), r1)), mul_rn(T(b.R[6]), r2));
+  const T z1 = add_rn(add_rn(mul_rn(T(b.R[1]), r0), mul_rn(T(b.R[4]), r1)), mul_rn(T(b.R[7]), r2));
+  const T z2 = add_rn(add_rn(mul_rn(T(b.R[2]), r0), mul_rn(T(b.R[5]), r1)), mul_rn(T(b.R[8]), r2));
+  const T y0 = div_rn(z0, T(b.a[0])), y1 = div_rn(z1, T(b.a[1])), y2 = div_rn(z2, T(b.a[2]));
+  const T gg = sqrt_rn(add_rn(add_rn(mul_rn(y0, y0), mul_rn(y1, y1)), mul_rn(y2, y2)));
+  if (gg < T(1e-12)) {
+    double m = b.a[0];
+    if (b.a[1] < m) m = b.a[1];
+    if (b.a[2] < m) m = b.a[2];
+    return T(-m);
+  }
+  const T w0 = div_rn(y0, T(b.a[0])), w1 = div_rn(y1, T(b.a[1])), w2 = div_rn(y2, T(b.a[2]));
+  const T wn = sqrt_rn(add_rn(add_rn(mul_rn(w0, w0), mul_rn(w1, w1)), mul_rn(w2, w2)));
+  return div_rn(mul_rn(sub_rn(gg, T(1)), gg), wn);
+}
+
+// direction of grad_X phi_0 (the WLS weights use its direction only)
+template <typename T>
+__device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
+  const T r[3] = {X[0] - T(b.c[0]), X[1] - T(b.c[1]), X[2] - T(b.c[2])};
+  if (b.shape == 0) {
+    gd[0] = r[0]; gd[1] = r[1]; gd[2] = r[2];
+    return;
+  }
+  T w[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const T z = T(b.R[a]) * r[0] + T(b.R[3 + a]) * r[1] + T(b.R[6 + a]) * r[2];
+    w[a] = z / T(b.a[a] * b.a[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) gd[a] = T(b.R[3 * a]) * w[0] + T(b.R[3 * a + 1]) * w[1] + T(b.R[3 * a + 2]) * w[2];
+}
+
+// smoothed Heaviside (eq. sm_heavi) and its derivative
+template <typename T>
+__device__ __forceinline__ T heavi(T phi, T eps) {
+  if (phi <= -eps) return T(0);
+  if (phi >= eps) return T(1);
+  return T(0.5) * (T(1) + phi / eps + sin(T(RMT_PI) * phi / eps) / T(RMT_PI));
+}
+template <typename T>
+__device__ __forceinline__ T dheavi(T phi, T eps) {
+  if (phi <= -eps || phi >= eps) return T(0);
+  return T(0.5) / eps * (T(1) + cos(T(RMT_PI) * phi / eps));
+}
+
+// Fourth-order monotonicity-limited slope (after Colella 1990); q[0..4] = q_{i-2..i+2}.
+// Missing outer values fall back to the second-order limited slope, a missing inner
+// neighbour gives zero.
+template <typename T>
+__device__ __forceinline__ T mc_lim(T qm, T q0, T qp) {
+  const T a = qp - q0, b = q0 - qm;
+  return (a * b > T(0)) ? T(2) * fmin(fabs(a), fabs(b)) : T(0);
+}
+template <typename T>
+__device__ __forceinline__ T sgnv(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+template <typename T>
+__device__ __forceinline__ T dflim(T qm, T q0, T qp) {
+  const T dc = T(0.5) * (qp - qm);
+  return sgnv(dc) * fmin(fabs(dc), mc_lim(qm, q0, qp));
+}
+template <typename T>
+__device__ __forceinline__ T lim_slope(const T q[5], unsigned okmask, T inv_h) {
+  // okmask bit s set when q[s] is present
+  if ((okmask & 0xE) != 0xE) return T(0);
+  const T dc = T(0.5) * (q[3] - q[1]);
+  const T dl = mc_lim(q[1], q[2], q[3]);
+  if ((okmask & 0x11) != 0x11) return sgnv(dc) * fmin(fabs(dc), dl) * inv_h;
+  const T dfp = dflim(q[2], q[3], q[4]);
+  const T dfm = dflim(q[0], q[1], q[2]);
+  const T d4 = T(4.0 / 3.0) * dc - (dfp + dfm) / T(6);
+  return sgnv(dc) * fmin(fabs(d4), dl) * inv_h;
+}
+
+// Godunov choice of the normal velocity and upwinding of other quantities
+// (SI "Godunov-type upwinding scheme")
+template <typename T>
+__device__ __forceinline__ T god_normal(T L, T R) {
+  if (L > T(0) && L + R > T(0)) return L;
+  if (R < T(0) && L + R < T(0)) return R;
+  return T(0);
+}
+template <typename T>
+__device__ __forceinline__ T upwind(T L, T R, T un) {
+  return un > T(0) ? L : (un < T(0) ? R : T(0.5) * (L + R));
+}
+
+// Multi-body mixing (SI eq. mod_heaviside): in place, w[m] = 1 - H_m on entry, the
+// (normalised) solid weights on exit; returns the fluid fraction.
+template <typename T>
+__device__ __forceinline__ T mix_weights(int cnt, T* w) {
+  T sum = T(0);
+  for (int m = 0; m < cnt; m++) sum += w[m];
+  if (sum > T(1))
+    for (int m = 0; m < cnt; m++) w[m] = w[m] / sum;
+  const T H = T(1) - sum;
+  return H > T(0) ? H : T(0);
+}
+
+// 3x3 inverse by the adjugate; false when singular
+template <typename T>
+__device__ __forceinline__ bool inv3(const T A[9], T F[9]) {
+  const T det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (det == T(0) || !isfinite(det)) return false;
+  F[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  F[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  F[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  F[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  F[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  F[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  F[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  F[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  F[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  return true;
+}
+
+// grid-stride helper
+#define GRID_LOOP(idx, total) \
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (total); idx += (long)gridDim.x * blockDim.x)

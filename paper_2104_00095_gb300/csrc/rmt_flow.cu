@@ -1,0 +1,449 @@
+// Flow kernels of the RMT per-step update (arXiv 2104.00095, SI sections "Evaluating the
+// advective term", "MAC projection", "Approximate pressure-Poisson projection"): Godunov
+// velocity states, projection glue, advective term, density mixing and u*.  One thread per
+// cell, face or node; templated on T.
+#include "rmt_kernels.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int nblocks(long n) {
+  long b = (n + TPB - 1) / TPB;
+  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) {
+  i = (int)(c % nx);
+  long r = c / nx;
+  j = (int)(r % ny);
+  k = (int)(r / ny);
+}
+
+
+template <typename T>
+__device__ __forceinline__ void cell_faces(const Geo& g, int e, int i, int j, int k, long& lo, long& hi) {
+  lo = fidx(g, e, i, j, k);
+  int ii[3] = {i, j, k};
+  ii[e] += 1;
+  hi = fidx(g, e, ii[0], ii[1], ii[2]);
+}
+// ---------------------------------------------------------------------------------
+// Godunov predictor
+
+template <typename T>
+__device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int a, int d, int i, int j, int k) {
+  T q[5];
+#pragma unroll
+  for (int s = -2; s <= 2; s++) {
+    int ii[3] = {i, j, k};
+    ii[d] += s;
+    q[s + 2] = uval(g, u, a, ii[0], ii[1], ii[2]);
+  }
+  return lim_slope(q, 0x1Fu, T(1.0 / g.h));
+}
+
+__device__ __forceinline__ bool is_wall_face(const Geo& g, int d, int f) {
+  return !g.per[d] && (f == 0 || f == g.n[d]);
+}
+
+// transverse bar states at every e-face (SI "Tangential derivatives")
+template <typename T>
+__global__ void k_bar(Geo g, int e, const T* __restrict__ u, T* __restrict__ ub0, T* __restrict__ ub1,
+                      T* __restrict__ ub2, T* __restrict__ vadv) {
+  const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1);
+  const long nf = nfaces(g, e);
+  const T h = T(g.h), dt = T(g.dt);
+  T* ub[3] = {ub0, ub1, ub2};
+  GRID_LOOP(f, nf) {
+    int i, j, k;
+    decode(f, ex, ey, i, j, k);
+    const int fi = e == 0 ? i : (e == 1 ? j : k);
+    if (is_wall_face(g, e, fi)) {
+      const int face = fi == 0 ? 2 * e : 2 * e + 1;
+#pragma unroll
+      for (int a = 0; a < 3; a++) ub[a][f] = T(g.wall[face][a]);
+      vadv[f] = T(g.wall[face][e]);
+      continue;
+    }
+    int lo[3] = {i, j, k};
+    lo[e] -= 1;
+    const T uD = uval(g, u, e, lo[0], lo[1], lo[2]);
+    const T uU = uval(g, u, e, i, j, k);
+    T qD[3], qU[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      qD[a] = uval(g, u, a, lo[0], lo[1], lo[2]) + (T(0.5) * h - T(0.5) * dt * uD) * slope_u(g, u, a, e, lo[0], lo[1], lo[2]);
+      qU[a] = uval(g, u, a, i, j, k) - (T(0.5) * h + T(0.5) * dt * uU) * slope_u(g, u, a, e, i, j, k);
+    }
+    const T va = god_normal(qD[e], qU[e]);
+    vadv[f] = va;
+#pragma unroll
+    for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va);
+  }
+}
+
+
+struct BarPtrs {
+  const void* ub[3][3];
+  const void* vadv[3];
+  void* uf[3];
+};
+
+// normal-face states of the velocity (eqs. left_final, right_final) + Godunov choice
+template <typename T>
+__global__ void k_face(Geo g, int d, const T* __restrict__ u, const T* __restrict__ p, const T* __restrict__ rho,
+                       const T* __restrict__ divtau, BarPtrs bp) {
+  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+  const long nf = nfaces(g, d);
+  const T h = T(g.h), dt = T(g.dt), ih = T(1.0 / g.h);
+  T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
+  GRID_LOOP(f, nf) {
+    int i, j, k;
+    decode(f, ex, ey, i, j, k);
+    const int fi = d == 0 ? i : (d == 1 ? j : k);
+    if (is_wall_face(g, d, fi)) {
+      const int face = fi == 0 ? 2 * d : 2 * d + 1;
+#pragma unroll
+      for (int a = 0; a < 3; a++) uf[a][f] = T(g.wall[face][a]);
+      continue;
+    }
+    T st[2][3];
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+      int cc[3] = {i, j, k};
+      if (side == 0) cc[d] -= 1;
+      wrap_axis(g, 0, cc[0]);
+      wrap_axis(g, 1, cc[1]);
+      wrap_axis(g, 2, cc[2]);
+      const long c = cidx(g, cc[0], cc[1], cc[2]);
+      // forcing -grad p^{n-1/2} + div tau^n + b^n, b = (rho - rho_f) g
+      T gp[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
+        const T pv = p[node_at(g, cc[0] + sa, cc[1] + sb, cc[2] + sc)];
+        gp[0] += sa ? pv : -pv;
+        gp[1] += sb ? pv : -pv;
+        gp[2] += sc ? pv : -pv;
+      }
+      const T r = rho[c];
+      const T ud = u[d * g.N + c];
+      const T coef = side == 0 ? (T(0.5) * h - T(0.5) * dt * ud) : -(T(0.5) * h + T(0.5) * dt * ud);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] + (r - T(g.rho_f)) * T(g.grav[a]);
+        T tr = T(0);
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+          if (e == d) continue;
+          long lo, hi;
+          cell_faces<T>(g, e, cc[0], cc[1], cc[2], lo, hi);
+          const T* vad = (const T*)bp.vadv[e];
+          const T* ube = (const T*)bp.ub[e][a];
+          tr += T(0.5) * (vad[lo] + vad[hi]) * (ube[hi] - ube[lo]) * ih;
+        }
+        st[side][a] = u[a * g.N + c] + coef * slope_u(g, u, a, d, cc[0], cc[1], cc[2]) - T(0.5) * dt * tr +
+                      T(0.5) * dt / r * F;
+      }
+    }
+    const T un = god_normal(st[0][d], st[1][d]);
+#pragma unroll
+    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// MAC projection glue: right-hand side, face coefficients, correction
+
+struct FacePtrs3 {
+  void* p[3];
+};
+
+template <typename T>
+__global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
+  const T ih = T(1.0 / g.h);
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    T dv = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      long lo, hi;
+      cell_faces<T>(g, d, i, j, k, lo, hi);
+      const T* U = (const T*)un.p[d];
+      dv += (U[hi] - U[lo]) * ih;
+    }
+    // positive operator A = -div(beta grad): A q = -div(u)/(dt/2)
+    b[c] = -(double)dv / (0.5 * g.dt);
+  }
+}
+
+template <typename T>
+__global__ void k_mac_beta(Geo g, int d, const T* __restrict__ rho, T* __restrict__ beta) {
+  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+  GRID_LOOP(f, nfaces(g, d)) {
+    int i, j, k;
+    decode(f, ex, ey, i, j, k);
+    const int fi = d == 0 ? i : (d == 1 ? j : k);
+    if (is_wall_face(g, d, fi)) {
+      beta[f] = T(0);
+      continue;
+    }
+    int a[3] = {i, j, k};
+    a[d] -= 1;
+    long ca, cb;
+    cell_at(g, a[0], a[1], a[2], ca);
+    cell_at(g, i, j, k, cb);
+    beta[f] = T(2) / (rho[ca] + rho[cb]);
+  }
+}
+
+template <typename T>
+__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ beta,
+                              const double* __restrict__ q, T* __restrict__ umac) {
+  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+  const T fac = T(0.5 * g.dt / g.h);
+  GRID_LOOP(f, nfaces(g, d)) {
+    int i, j, k;
+    decode(f, ex, ey, i, j, k);
+    const int fi = d == 0 ? i : (d == 1 ? j : k);
+    if (is_wall_face(g, d, fi)) {
+      umac[f] = un[f];
+      continue;
+    }
+    int a[3] = {i, j, k};
+    a[d] -= 1;
+    long ca, cb;
+    cell_at(g, a[0], a[1], a[2], ca);
+    cell_at(g, i, j, k, cb);
+    umac[f] = un[f] - fac * beta[f] * (T)(q[cb] - q[ca]);
+  }
+}
+
+// advective term (eq. adv_terms) with the MAC-corrected normal velocities
+struct AdvPtrs {
+  const void* uf[3][3];
+  const void* umac[3];
+};
+
+template <typename T>
+__global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
+  const T ih = T(1.0 / g.h);
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      long lo, hi;
+      cell_faces<T>(g, d, i, j, k, lo, hi);
+      const T* U = (const T*)ap.umac[d];
+      const T va = T(0.5) * (U[lo] + U[hi]);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const T* Q = (a == d) ? U : (const T*)ap.uf[d][a];
+        acc[a] += va * (Q[hi] - Q[lo]) * ih;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) adv[a * g.N + c] = acc[a];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// density by mixing (eq. mod_heaviside) and u*
+
+template <typename T>
+__global__ void k_density(Geo g, const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb,
+                          T* __restrict__ rho) {
+  const T eps = T(g.eps);
+  GRID_LOOP(c, g.N) {
+    T wsum = T(0), acc = T(0);
+    for (int m = 0; m < nb; m++) {
+      if (views[m].lay[c] < 0) continue;
+      const T w = T(1) - heavi(views[m].phi[c], eps);
+      acc += w * T(bodies[m].rho_s);
+      wsum += w;
+    }
+    const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
+    const T sc = wsum > T(1) ? T(1) / wsum : T(1);
+    rho[c] = Hf * T(g.rho_f) + acc * sc;
+  }
+}
+
+template <typename T>
+__global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ adv, const T* __restrict__ p,
+                        const T* __restrict__ rho_h, const T* __restrict__ divtau_h, T* __restrict__ ustar) {
+  const T dt = T(g.dt), q4 = T(0.25 / g.h);
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    T gp[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
+      const T pv = p[node_at(g, i + sa, j + sb, k + sc)];
+      gp[0] += sa ? pv : -pv;
+      gp[1] += sb ? pv : -pv;
+      gp[2] += sc ? pv : -pv;
+    }
+    const T r = rho_h[c];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      ustar[a * g.N + c] = u[a * g.N + c] - dt * adv[a * g.N + c] +
+                           dt / r * (divtau_h[a * g.N + c] - gp[a] * q4 + (r - T(g.rho_f)) * T(g.grav[a]));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// approximate FE projection glue
+
+// weak divergence of V = (u* - u^n)/dt at every node: sum over adjacent cells of
+// (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d
+template <typename T>
+__global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ ustar, double* __restrict__ b) {
+  const double s = g.h * g.h / 4.0 / g.dt;
+  GRID_LOOP(nd, g.NN) {
+    int i, j, k;
+    decode(nd, g.nn[0], g.nn[1], i, j, k);
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
+      long c;
+      if (!cell_at(g, i - 1 + sx, j - 1 + sy, k - 1 + sz, c)) continue;
+      const T v0 = ustar[c] - u[c], v1 = ustar[g.N + c] - u[g.N + c], v2 = ustar[2 * g.N + c] - u[2 * g.N + c];
+      acc += (sx ? -v0 : v0) + (sy ? -v1 : v1) + (sz ? -v2 : v2);
+    }
+    b[nd] = (double)acc * s;
+  }
+}
+
+template <typename T>
+__global__ void k_inv(long n, const T* __restrict__ rho, T* __restrict__ beta) {
+  GRID_LOOP(c, n) beta[c] = T(1) / rho[c];
+}
+
+template <typename T>
+__global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h,
+                              const double* __restrict__ psi, T* __restrict__ u) {
+  const double q4 = 0.25 / g.h;
+  const T dt = T(g.dt);
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    double gp[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
+      const double pv = psi[node_at(g, i + sa, j + sb, k + sc)];
+      gp[0] += sa ? pv : -pv;
+      gp[1] += sb ? pv : -pv;
+      gp[2] += sc ? pv : -pv;
+    }
+    const T r = rho_h[c];
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a * g.N + c] = ustar[a * g.N + c] - dt / r * (T)(gp[a] * q4);
+  }
+}
+
+template <typename T>
+__global__ void k_fe_update_p(long nn, const double* __restrict__ psi, T* __restrict__ p, T* __restrict__ psi_out) {
+  GRID_LOOP(i, nn) {
+    const T v = (T)psi[i];
+    p[i] += v;
+    psi_out[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_fill(T* a, T v, long n) {
+  GRID_LOOP(i, n) a[i] = v;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_bar_states(const Geo& g, const T* u, T* const ubar[3][3], T* const vadv[3], cudaStream_t s) {
+  for (int e = 0; e < 3; e++) {
+    k_bar<T><<<nblocks(nfaces(g, e)), TPB, 0, s>>>(g, e, u, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]); rmt_count_launches(1); }
+}
+template <typename T>
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const ubar[3][3],
+                        T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
+  BarPtrs bp;
+  for (int e = 0; e < 3; e++) {
+    for (int a = 0; a < 3; a++) bp.ub[e][a] = ubar[e][a];
+    bp.vadv[e] = vadv[e];
+  }
+  for (int d = 0; d < 3; d++) {
+    for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
+    k_face<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, u, p, rho, divtau, bp); rmt_count_launches(1);
+  }
+}
+template <typename T>
+void launch_mac_setup(const Geo& g, T* const uf[3][3], const T* rho, double* b64, T* const beta[3], cudaStream_t s) {
+  FacePtrs3 un;
+  for (int d = 0; d < 3; d++) un.p[d] = uf[d][d];
+  k_mac_rhs<T><<<nblocks(g.N), TPB, 0, s>>>(g, un, b64); rmt_count_launches(1);
+  for (int d = 0; d < 3; d++) { k_mac_beta<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, rho, beta[d]); rmt_count_launches(1); }
+}
+template <typename T>
+void launch_mac_correct(const Geo& g, T* const uf[3][3], T* const beta[3], const double* q, T* const umac[3],
+                        cudaStream_t s) {
+  for (int d = 0; d < 3; d++) {
+    k_mac_correct<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, uf[d][d], beta[d], q, umac[d]); rmt_count_launches(1); }
+}
+template <typename T>
+void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s) {
+  AdvPtrs ap;
+  for (int d = 0; d < 3; d++) {
+    ap.umac[d] = umac[d];
+    for (int a = 0; a < 3; a++) ap.uf[d][a] = uf[d][a];
+  }
+  k_adv<T><<<nblocks(g.N), TPB, 0, s>>>(g, ap, adv); rmt_count_launches(1);
+}
+template <typename T>
+void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho, cudaStream_t s) {
+  k_density<T><<<nblocks(g.N), TPB, 0, s>>>(g, bodies, views, nb, rho); rmt_count_launches(1);
+}
+template <typename T>
+void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h, T* ustar,
+                  cudaStream_t s) {
+  k_ustar<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, adv, p, rho_h, divtau_h, ustar); rmt_count_launches(1);
+}
+template <typename T>
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, const T* rho_h, double* b64, T* beta, cudaStream_t s) {
+  k_fe_rhs<T><<<nblocks(g.NN), TPB, 0, s>>>(g, u, ustar, b64); rmt_count_launches(1);
+  k_inv<T><<<nblocks(g.N), TPB, 0, s>>>(g.N, rho_h, beta); rmt_count_launches(1);
+}
+template <typename T>
+void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p, T* psi_out,
+                      cudaStream_t s) {
+  k_fe_update_u<T><<<nblocks(g.N), TPB, 0, s>>>(g, ustar, rho_h, psi, u); rmt_count_launches(1);
+  k_fe_update_p<T><<<nblocks(g.NN), TPB, 0, s>>>(g.NN, psi, p, psi_out); rmt_count_launches(1);
+}
+template <typename T>
+void launch_fill(T* a, T v, long n, cudaStream_t s) {
+  k_fill<T><<<nblocks(n), TPB, 0, s>>>(a, v, n); rmt_count_launches(1);
+}
+
+#define INST(T)                                                                                                   \
+  template void launch_bar_states<T>(const Geo&, const T*, T* const[3][3], T* const[3], cudaStream_t);            \
+  template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[3][3],        \
+                                      T* const[3], T* const[3][3], cudaStream_t);                                \
+  template void launch_mac_setup<T>(const Geo&, T* const[3][3], const T*, double*, T* const[3], cudaStream_t);    \
+  template void launch_mac_correct<T>(const Geo&, T* const[3][3], T* const[3], const double*, T* const[3],       \
+                                      cudaStream_t);                                                             \
+  template void launch_advect<T>(const Geo&, T* const[3][3], T* const[3], T*, cudaStream_t);                      \
+  template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, T*, cudaStream_t);          \
+  template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void launch_fe_setup<T>(const Geo&, const T*, const T*, const T*, double*, T*, cudaStream_t);         \
+  template void launch_fe_update<T>(const Geo&, const T*, const T*, const double*, T*, T*, T*, cudaStream_t);    \
+  template void launch_fill<T>(T*, T, long, cudaStream_t);
+
+INST(float)
+INST(double)
+template void launch_fill<int8_t>(int8_t*, int8_t, long, cudaStream_t);

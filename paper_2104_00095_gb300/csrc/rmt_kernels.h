@@ -1,0 +1,72 @@
+// Host-side launchers of the RMT kernels (explicitly instantiated for float and double).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rmt_common.cuh"
+
+// face-array bundle: vector value at every d-face (3 comps) for d = 0..2
+template <typename T>
+struct Faces3 {
+  T* v[3][3];  // v[d][a]
+};
+
+// ---- flow (rmt_flow.cu) -------------------------------------------------------------
+template <typename T>
+void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
+                       double t, T* out, cudaStream_t s);
+template <typename T>
+void launch_bar_states(const Geo& g, const T* u, T* const ubar[3][3], T* const vadv[3], cudaStream_t s);
+template <typename T>
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau,
+                        T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
+template <typename T>
+void launch_mac_setup(const Geo& g, T* const uf[3][3], const T* rho, double* b64, T* const beta[3],
+                      cudaStream_t s);
+template <typename T>
+void launch_mac_correct(const Geo& g, T* const uf[3][3], T* const beta[3], const double* q, T* const umac[3],
+                        cudaStream_t s);
+template <typename T>
+void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s);
+template <typename T>
+void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3],
+                       const T* x, const int8_t* lay, T* xn, cudaStream_t s);
+template <typename T>
+void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho,
+                    cudaStream_t s);
+template <typename T>
+void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h,
+                  T* ustar, cudaStream_t s);
+template <typename T>
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, const T* rho_h, double* b64, T* beta,
+                     cudaStream_t s);
+template <typename T>
+void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p,
+                      T* psi_out, cudaStream_t s);
+template <typename T>
+void launch_fill(T* a, T v, long n, cudaStream_t s);
+
+// ---- extrapolation (rmt_extrap.cu) ------------------------------------------------
+template <typename T>
+void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s);
+template <typename T>
+void launch_extrapolate(const Geo& g, const Body* bdev, const Body& b, T* x, T* phi, int8_t* lay,
+                        int* err, cudaStream_t s);
+template <typename T>
+void launch_corrector(const Geo& g, const Body* bdev, const Body& b, const T* x, const int8_t* lay,
+                      const T* xn, const int8_t* layn, T* xh, T* phih, int* err, cudaStream_t s);
+
+// ---- multigrid (rmt_mg.cu) ----------------------------------------------------------
+struct MGSolver;  // opaque
+// kind 0: cell-centred 7-point (MAC), kind 1: nodal trilinear FE (27-point)
+MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err);
+void mg_destroy(MGSolver* m);
+double* mg_rhs(MGSolver* m);        // level-0 FP64 right-hand side (fill before solve)
+double* mg_solution(MGSolver* m);   // level-0 FP64 solution
+void* mg_coef0(MGSolver* m, int d); // level-0 coefficients: MAC d=0..2 face beta; FE d=0 cell beta
+// Optional timing hook around the finest-level smoother and FP64-residual launches:
+// hook(ctx, which, begin, stream) with which = 0 (smoother colour) or 1 (FP64 residual).
+typedef void (*mg_hook_fn)(void* ctx, int which, int begin, cudaStream_t s);
+void mg_set_hook(MGSolver* m, mg_hook_fn fn, void* ctx);
+// Solves to rtol (or a fixed cycle count); returns cycles used, -1 on non-convergence.
+int mg_solve(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStream_t s, cudaError_t* err);

@@ -1,0 +1,162 @@
+// Stress kernel of the RMT per-step update (arXiv 2104.00095, SI "Stress calculations",
+// eq. mixed_stresses and the multi-body rule; main text "Swimming" for the active stress).
+// One thread per cell computes the face-normal rows of the blended stress at its six faces
+// and their divergence; templated on T.
+#include "rmt_kernels.h"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int nblocks(long n) {
+  long b = (n + TPB - 1) / TPB;
+  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) {
+  i = (int)(c % nx);
+  long r = c / nx;
+  j = (int)(r % ny);
+  k = (int)(r / ny);
+}
+
+// ---------------------------------------------------------------------------------
+// stress: face-normal row of the blended deviatoric stress, then its divergence
+
+template <typename T>
+__device__ __forceinline__ bool xget(const Geo& g, const BodyView<T>& v, int i, int j, int k, T x[3]) {
+  long c;
+  if (!cell_at(g, i, j, k, c)) return false;
+  if (v.lay[c] < 0) return false;
+  x[0] = v.x[c];
+  x[1] = v.x[g.N + c];
+  x[2] = v.x[2 * g.N + c];
+  return true;
+}
+
+// Row tau . e_d at the d-face below cell (i,j,k) (cell a = (i,j,k) - e_d, b = (i,j,k)).
+// bmask: bodies that may have xi at a or b.
+template <typename T>
+__device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, const Body* __restrict__ bodies,
+                         const BodyView<T>* __restrict__ views, uint64_t bmask, int d, int i, int j, int k,
+                         T tt, T row[3]) {
+  const T ih = T(1.0 / g.h);
+  int ia[3] = {i, j, k};
+  ia[d] -= 1;
+  T du[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) du[a] = (uval(g, u, a, i, j, k) - uval(g, u, a, ia[0], ia[1], ia[2])) * ih;
+  T acc[3] = {T(0), T(0), T(0)};
+  T wsum = T(0);
+  const T eps = T(g.eps);
+  while (bmask) {
+    const int m = __ffsll((long long)bmask) - 1;
+    bmask &= bmask - 1;
+    const BodyView<T> v = views[m];
+    T xa[3], xb[3];
+    if (!xget(g, v, ia[0], ia[1], ia[2], xa) || !xget(g, v, i, j, k, xb)) continue;
+    T A[9];
+#pragma unroll
+    for (int a = 0; a < 3; a++) A[3 * a + d] = (xb[a] - xa[a]) * ih;
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      if (e == d) continue;
+      int ap[3] = {ia[0], ia[1], ia[2]}, am[3] = {ia[0], ia[1], ia[2]};
+      int bp[3] = {i, j, k}, bm[3] = {i, j, k};
+      ap[e]++; am[e]--; bp[e]++; bm[e]--;
+      T v1[3], v2[3], v3[3], v4[3];
+      if (!xget(g, v, ap[0], ap[1], ap[2], v1) || !xget(g, v, bp[0], bp[1], bp[2], v2) ||
+          !xget(g, v, am[0], am[1], am[2], v3) || !xget(g, v, bm[0], bm[1], bm[2], v4)) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; a++) A[3 * a + e] = (v1[a] + v2[a] - v3[a] - v4[a]) * (T(0.25) * ih);
+    }
+    if (!ok) continue;
+    const Body& B = bodies[m];
+    const T xf[3] = {T(0.5) * (xa[0] + xb[0]), T(0.5) * (xa[1] + xb[1]), T(0.5) * (xa[2] + xb[2])};
+    const T ph = phi0(B, xf[0], xf[1], xf[2]);
+    const T w = T(1) - heavi(ph, eps);
+    if (!(w > T(0))) continue;
+    T F[9];
+    if (!inv3(A, F)) continue;
+    // neo-Hookean: tau = G (F F^T - tr/3 I); only row d is needed (tau is symmetric)
+    T Bd[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) Bd[a] = F[3 * a] * F[3 * d] + F[3 * a + 1] * F[3 * d + 1] + F[3 * a + 2] * F[3 * d + 2];
+    const T tr3 = (F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + F[4] * F[4] + F[5] * F[5] +
+                   F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) / T(3);
+    const T G = T(B.G);
+    T tau[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) tau[a] = G * (Bd[a] - (a == d ? tr3 : T(0)));
+    if (B.actA != 0.0) {
+      // active stress (3 Z s0 / 2)(e e^T - I/3), e = F E_X / |F E_X|, s0 = A sin(2 pi X/l - w t)
+      const T r[3] = {xf[0] - T(B.c[0]), xf[1] - T(B.c[1]), xf[2] - T(B.c[2])};
+      const T Xb = T(B.R[0]) * r[0] + T(B.R[3]) * r[1] + T(B.R[6]) * r[2];
+      const T Zb = T(B.R[2]) * r[0] + T(B.R[5]) * r[1] + T(B.R[8]) * r[2];
+      const T s0 = T(B.actA) * sin(T(2.0 * RMT_PI) * Xb / T(B.actL) - T(B.actW) * tt);
+      const T EX[3] = {T(B.R[0]), T(B.R[3]), T(B.R[6])};
+      T f[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) f[a] = F[3 * a] * EX[0] + F[3 * a + 1] * EX[1] + F[3 * a + 2] * EX[2];
+      const T fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+      const T amp = T(1.5) * Zb * s0;
+      const T ed = f[d] / fn;
+#pragma unroll
+      for (int a = 0; a < 3; a++) tau[a] += amp * ((f[a] / fn) * ed - (a == d ? T(1.0 / 3.0) : T(0)));
+    }
+    const T visc = T(B.mu_a) * (T(1) + T(B.gamma_t) * eps * dheavi(ph, eps));
+#pragma unroll
+    for (int a = 0; a < 3; a++) acc[a] += w * (tau[a] + visc * du[a]);
+    wsum += w;
+  }
+  const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
+  const T sc = wsum > T(1) ? T(1) / wsum : T(1);
+  const T mu = T(g.mu);
+#pragma unroll
+  for (int a = 0; a < 3; a++) row[a] = Hf * mu * du[a] + acc[a] * sc;
+}
+
+template <typename T>
+__global__ void k_stress_div(Geo g, const T* __restrict__ u, const Body* __restrict__ bodies,
+                             const BodyView<T>* __restrict__ views, int nb, T tt, T* __restrict__ out) {
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    // bodies that have xi at this cell: only they can contribute at its six faces
+    uint64_t bm = 0;
+    for (int m = 0; m < nb; m++)
+      if (views[m].lay[c] >= 0) bm |= (1ull << m);
+    T acc[3] = {T(0), T(0), T(0)};
+    const T ih = T(1.0 / g.h);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      int ip[3] = {i, j, k};
+      ip[d] += 1;
+      T rp[3], rm[3];
+      face_row(g, u, bodies, views, bm, d, ip[0], ip[1], ip[2], tt, rp);
+      face_row(g, u, bodies, views, bm, d, i, j, k, tt, rm);
+#pragma unroll
+      for (int a = 0; a < 3; a++) acc[a] += (rp[a] - rm[a]) * ih;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb, double t,
+                       T* out, cudaStream_t s) {
+  k_stress_div<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, bodies, views, nb, T(t), out); rmt_count_launches(1);
+}
+
+template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, double,
+                                       float*, cudaStream_t);
+template void launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int, double,
+                                        double*, cudaStream_t);

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of librmt.so (C ABI in include/rmt.h), same names as the C calls.
+
+Argument marshalling only: every step of the method runs in the CUDA library.  Loading
+fails loudly when the library cannot be built or loaded; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RMT_OK, RMT_EINVAL, RMT_ENOMEM, RMT_ECUDA, RMT_ESTATE = 0, 1, 2, 3, 4
+RMT_ENOCONVERGE, RMT_EDIVERGED, RMT_ETIMEOUT, RMT_EDEGENERATE = 5, 6, 7, 8
+RMT_BC_NOSLIP, RMT_BC_PERIODIC = 0, 1
+RMT_PREC_FP64, RMT_PREC_FP32_REFINE = 0, 1
+RMT_SHAPE_SPHERE, RMT_SHAPE_ELLIPSOID = 0, 1
+RMT_F_U, RMT_F_P, RMT_F_RHO, RMT_F_XI, RMT_F_PHI, RMT_F_LAYER = 1, 2, 3, 4, 5, 6
+RMT_F_DIVTAU_N, RMT_F_DIVTAU_H, RMT_F_UFACE_X, RMT_F_UFACE_Y, RMT_F_UFACE_Z = 20, 21, 22, 23, 24
+RMT_F_MAC_Q, RMT_F_ADV_U, RMT_F_USTAR, RMT_F_PSI, RMT_F_RHO_HALF, RMT_F_XI_HALF = 25, 26, 27, 28, 29, 30
+RMT_F_UMAC_X, RMT_F_UMAC_Y, RMT_F_UMAC_Z = 31, 32, 33
+
+EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt_read_fields",
+           "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_kernel_launches", "rmt_profile",
+           "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_destroy_grid", "rmt_last_error")
+
+
+class rmt_grid_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("bc", C.c_int * 6),
+        ("wall_u", (C.c_double * 3) * 6), ("rho_f", C.c_double), ("mu", C.c_double),
+        ("eps_h", C.c_double), ("band_layers", C.c_int), ("dt", C.c_double),
+        ("gravity", C.c_double * 3), ("precision", C.c_int), ("mg_rtol", C.c_double),
+        ("mg_max_cycles", C.c_int), ("mg_fixed_cycles", C.c_int), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class rmt_solid_desc(C.Structure):
+    _fields_ = [
+        ("shape", C.c_int), ("center", C.c_double * 3), ("semi_axes", C.c_double * 3),
+        ("rot", C.c_double * 9), ("rho_s", C.c_double), ("G", C.c_double), ("mu_a", C.c_double),
+        ("gamma_t", C.c_double), ("active_A", C.c_double), ("active_omega", C.c_double),
+        ("active_len", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(build: bool = True):
+    """Loads librmt.so (building it in-tree with nvcc first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"librmt.so not found at {path}; build it with paper_2104_00095_gb300.build")
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.rmt_create_grid.argtypes = [C.POINTER(rmt_grid_desc), C.POINTER(C.c_void_p)]
+    L.rmt_add_solid.argtypes = [vp, C.POINTER(rmt_solid_desc), C.POINTER(C.c_int)]
+    L.rmt_step.argtypes = [vp, C.c_int]
+    L.rmt_field_len.argtypes = [vp, C.c_int]
+    L.rmt_field_len.restype = C.c_long
+    L.rmt_read_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+    L.rmt_write_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+    L.rmt_last_cycles.argtypes = [vp, C.c_int]
+    L.rmt_dt.argtypes = [vp]
+    L.rmt_dt.restype = C.c_double
+    L.rmt_kernel_launches.argtypes = []
+    L.rmt_kernel_launches.restype = C.c_long
+    L.rmt_profile.argtypes = [vp, C.c_int]
+    L.rmt_profile.restype = C.c_int
+    L.rmt_profile_entries.argtypes = []
+    L.rmt_profile_entries.restype = C.c_int
+    L.rmt_profile_name.argtypes = [C.c_int]
+    L.rmt_profile_name.restype = C.c_char_p
+    L.rmt_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long), dp]
+    L.rmt_profile_read.restype = C.c_int
+    L.rmt_destroy_grid.argtypes = [vp]
+    L.rmt_last_error.argtypes = [vp]
+    L.rmt_last_error.restype = C.c_char_p
+    for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
+              "rmt_destroy_grid"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def kernel_launches() -> int:
+    """Kernels launched by librmt.so so far in this process."""
+    return load().rmt_kernel_launches()
+
+
+def make_grid_desc(scene: dict, stream: int = 0) -> rmt_grid_desc:
+    d = rmt_grid_desc()
+    d.n[:] = list(scene["n"])
+    d.lo[:] = list(scene.get("lo", (0.0, 0.0, 0.0)))
+    d.hi[:] = list(scene.get("hi", (1.0, 1.0, 1.0)))
+    d.bc[:] = list(scene["bc"])
+    wu = scene.get("wall_u", [[0.0] * 3] * 6)
+    for f in range(6):
+        d.wall_u[f][:] = list(wu[f])
+    d.rho_f, d.mu = scene["rho_f"], scene["mu"]
+    d.eps_h, d.band_layers = scene.get("eps_h", 1.5), scene.get("band_layers", 4)
+    d.dt = scene.get("dt", 0.0)
+    d.gravity[:] = list(scene.get("gravity", (0.0, 0.0, 0.0)))
+    d.precision = RMT_PREC_FP32_REFINE if scene.get("precision", "fp64") == "fp32" else RMT_PREC_FP64
+    d.mg_rtol = scene.get("mg_rtol", 0.0)
+    d.mg_max_cycles = scene.get("mg_max_cycles", 0)
+    d.mg_fixed_cycles = scene.get("mg_fixed_cycles", 0)
+    d.cuda_stream = stream or None
+    return d
+
+
+def make_solid_desc(s: dict) -> rmt_solid_desc:
+    o = rmt_solid_desc()
+    o.shape = s["shape"]
+    o.center[:] = list(s["center"])
+    o.semi_axes[:] = list(s["semi_axes"])
+    o.rot[:] = list(np.asarray(s.get("rot", np.eye(3)), dtype=np.float64).reshape(9))
+    o.rho_s, o.G, o.mu_a, o.gamma_t = s["rho_s"], s["G"], s["mu_a"], s.get("gamma_t", 0.0)
+    o.active_A = s.get("active_A", 0.0)
+    o.active_omega = s.get("active_omega", 0.0)
+    o.active_len = s.get("active_len", 1.0)
+    return o
+
+
+class RMTError(RuntimeError):
+    def __init__(self, call: str, status: int, msg: str):
+        super().__init__(f"{call} failed with status {status}: {msg}")
+        self.status = status
+
+
+class Grid:
+    """One simulation on the GPU; wraps the opaque rmt_grid handle."""
+
+    def __init__(self, scene: dict, stream: int = 0):
+        self._L = load()
+        self.scene = scene
+        self.n = tuple(scene["n"])
+        self._g = C.c_void_p()
+        self._check("rmt_create_grid", self._L.rmt_create_grid(C.byref(make_grid_desc(scene, stream)),
+                                                              C.byref(self._g)))
+        self.nsolids = 0
+        for s in scene.get("solids", []):
+            sid = C.c_int()
+            self._check("rmt_add_solid", self._L.rmt_add_solid(self._g, C.byref(make_solid_desc(s)),
+                                                              C.byref(sid)))
+            self.nsolids += 1
+
+    def _check(self, call: str, rc: int):
+        if rc != RMT_OK:
+            msg = self._L.rmt_last_error(self._g).decode() if self._g else ""
+            raise RMTError(call, rc, msg)
+
+    def close(self):
+        if getattr(self, "_g", None) and self._g.value:
+            self._L.rmt_destroy_grid(self._g)
+            self._g = C.c_void_p()
+
+    def __del__(self):
+        self.close()
+
+    def step(self, nsteps: int = 1):
+        self._check("rmt_step", self._L.rmt_step(self._g, nsteps))
+
+    def field_len(self, field: int) -> int:
+        return self._L.rmt_field_len(self._g, field)
+
+    def read(self, field: int, solid: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        n = self.field_len(field)
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        self._check("rmt_read_fields", self._L.rmt_read_fields(self._g, field, solid, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def read_device(self, field: int, ptr: int, nbytes: int, solid: int = 0):
+        self._check("rmt_read_fields", self._L.rmt_read_fields(self._g, field, solid, C.c_void_p(ptr), nbytes, 1))
+
+    def write(self, field: int, data: np.ndarray, solid: int = 0):
+        a = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)
+        self._check("rmt_write_fields", self._L.rmt_write_fields(self._g, field, solid, a.ctypes.data, a.nbytes, 0))
+
+    def write_ptr(self, field: int, ptr: int, nbytes: int, is_device: int, solid: int = 0):
+        self._check("rmt_write_fields",
+                    self._L.rmt_write_fields(self._g, field, solid, C.c_void_p(ptr), nbytes, is_device))
+
+    @property
+    def dt(self) -> float:
+        self.read(RMT_F_RHO)
+        return self._L.rmt_dt(self._g)
+
+    def profile(self, enable: bool):
+        self._check("rmt_profile", self._L.rmt_profile(self._g, 1 if enable else 0))
+
+    def profile_read(self) -> list:
+        """[(name, total_ms, launches, bytes_per_launch)] for every profile entry."""
+        out = []
+        for e in range(self._L.rmt_profile_entries()):
+            ms, n, b = C.c_double(), C.c_long(), C.c_double()
+            self._check("rmt_profile_read", self._L.rmt_profile_read(self._g, e, C.byref(ms), C.byref(n), C.byref(b)))
+            out.append((self._L.rmt_profile_name(e).decode(), ms.value, n.value, b.value))
+        return out
+
+    def cycles(self):
+        return self._L.rmt_last_cycles(self._g, 0), self._L.rmt_last_cycles(self._g, 1)
