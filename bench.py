@@ -155,7 +155,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
-    ap.add_argument("--mg-cycles", type=int, default=4, help="V-cycles per Poisson solve (fixed, no host sync)")
+    ap.add_argument("--mg-cycles-mac", type=int, default=7,
+                    help="V-cycles per MAC solve (fixed, no host sync; 7 reach ~1e-6 relative residual)")
+    ap.add_argument("--mg-cycles-fe", type=int, default=4,
+                    help="V-cycles per FE solve (fixed; 4 reach ~1e-6 relative residual)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -183,7 +186,8 @@ def main():
 
     stream = torch.cuda.current_stream()
     scene = make_scene(cfg)
-    scene["mg_fixed_cycles"] = args.mg_cycles
+    scene["mg_fixed_cycles"] = args.mg_cycles_mac
+    scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
     g = rmt.Grid(scene, stream=stream.cuda_stream)
     N = int(np.prod(scene["n"]))
     for _ in range(args.warmup):
@@ -279,7 +283,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": args.config, "description": cfg["desc"], "grid": list(scene["n"]),
-                           "bodies": len(scene["solids"]), "mg_cycles_per_solve": args.mg_cycles,
+                           "bodies": len(scene["solids"]),
+                           "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe},
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,

@@ -58,8 +58,9 @@ typedef struct {
   int precision;          /* RMT_PREC_FP64, or FP32 bulk with FP64 multigrid refinement      */
   double mg_rtol;         /* relative residual target of both Poisson solves (<=0: 1e-12)    */
   int mg_max_cycles;      /* cap on V-cycles per solve (<=0: 60)                              */
-  int mg_fixed_cycles;    /* > 0: run exactly this many cycles, no residual checks (no host
+  int mg_fixed_cycles;    /* > 0: run exactly this many MAC cycles, no residual checks (no host
                              synchronisation inside rmt_step)                                 */
+  int mg_fixed_cycles_fe; /* the same for the FE solve (<= 0: mg_fixed_cycles)                */
   void* cuda_stream;      /* cudaStream_t all work is ordered on (NULL: legacy stream)        */
 } rmt_grid_desc;
 

@@ -78,6 +78,8 @@ def lib():
         L.orc_dt.argtypes = [C.c_void_p]
         L.orc_dt.restype = C.c_double
         L.orc_last_iters.argtypes = [C.c_void_p, C.c_int]
+        L.orc_last_true_residual.argtypes = [C.c_void_p, C.c_int]
+        L.orc_last_true_residual.restype = C.c_double
         L.orc_error.argtypes = [C.c_void_p]
         L.orc_error.restype = C.c_char_p
         for fn in ("orc_heaviside", "orc_dheaviside"):
@@ -85,9 +87,9 @@ def lib():
             getattr(L, fn).restype = C.c_double
         L.orc_limited_slope.argtypes = [dp, ip, C.c_double]
         L.orc_limited_slope.restype = C.c_double
-        L.orc_godunov_normal.argtypes = [C.c_double, C.c_double]
+        L.orc_godunov_normal.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_godunov_normal.restype = C.c_double
-        L.orc_upwind.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_upwind.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_upwind.restype = C.c_double
         L.orc_phi0.argtypes = [C.POINTER(SolidDesc), dp]
         L.orc_phi0.restype = C.c_double
@@ -175,6 +177,9 @@ class Oracle:
 
     def iters(self):
         return self._L.orc_last_iters(self._g, 0), self._L.orc_last_iters(self._g, 1)
+
+    def true_residuals(self):
+        return self._L.orc_last_true_residual(self._g, 0), self._L.orc_last_true_residual(self._g, 1)
 
     def read(self, field: int, solid: int = 0) -> np.ndarray:
         n = self._L.orc_field_len(self._g, field)

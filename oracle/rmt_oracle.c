@@ -33,7 +33,7 @@ struct orc_grid {
   orc_grid_desc d;
   int n[3], per[3], nn[3];
   long N, NN, NF[3];
-  double h, dt, t, eps;
+  double h, dt, t, eps, utol;
   long step;
   int inited;
   double *u[3], *p, *rho;
@@ -43,6 +43,7 @@ struct orc_grid {
   int nsol;
   solid* sol;
   int iters[2];
+  double true_rel[2], last_true_rel;
   int degenerate;
   char err[256];
 };
@@ -194,15 +195,18 @@ double orc_limited_slope(const double q[5], const int ok[5], double h) {
   return sgn(dc) * fmin(fabs(d4), dl) / h;
 }
 
-/* SI "Godunov-type upwinding scheme": normal-velocity choice and upwinding of the rest */
-double orc_godunov_normal(double L, double R) {
-  if (L > 0.0 && L + R > 0.0) return L;
-  if (R < 0.0 && L + R < 0.0) return R;
+/* SI "Godunov-type upwinding scheme": normal-velocity choice and upwinding of the rest.
+ * Reading: the sign tests use a tolerance tol (the "= 0" cases hold for |v| <= tol), so that a
+ * velocity that vanishes in exact arithmetic (a symmetry plane) does not pick its side from
+ * rounding noise; the step uses tol = 1e-12 h/dt, the pins tol = 0. */
+double orc_godunov_normal(double L, double R, double tol) {
+  if (L > tol && L + R > tol) return L;
+  if (R < -tol && L + R < -tol) return R;
   return 0.0;
 }
-double orc_upwind(double L, double R, double un) {
-  if (un > 0.0) return L;
-  if (un < 0.0) return R;
+double orc_upwind(double L, double R, double un, double tol) {
+  if (un > tol) return L;
+  if (un < -tol) return R;
   return 0.5 * (L + R);
 }
 
@@ -329,6 +333,7 @@ void orc_destroy(orc_grid* g) {
 const char* orc_error(orc_grid* g) { return g ? g->err : "null grid"; }
 double orc_dt(orc_grid* g) { return g->dt; }
 int orc_last_iters(orc_grid* g, int which) { return g->iters[which ? 1 : 0]; }
+double orc_last_true_residual(orc_grid* g, int which) { return g->true_rel[which ? 1 : 0]; }
 
 /* ------------------------------------------------------------------------------- */
 /* extrapolation of xi: layers + weighted least squares (main text "Extrapolation of  */
@@ -705,9 +710,9 @@ static void bar_states(orc_grid* g) {
             qD[a] = uval(g, a, lo[0], lo[1], lo[2]) + (0.5 * h - 0.5 * dt * uD) * slope_u(g, a, e, lo[0], lo[1], lo[2]);
             qU[a] = uval(g, a, i, j, k) - (0.5 * h + 0.5 * dt * uU) * slope_u(g, a, e, i, j, k);
           }
-          double va = orc_godunov_normal(qD[e], qU[e]);
+          double va = orc_godunov_normal(qD[e], qU[e], g->utol);
           g->vadv[e][f] = va;
-          for (int a = 0; a < 3; a++) g->ub[e][a][f] = orc_upwind(qD[a], qU[a], va);
+          for (int a = 0; a < 3; a++) g->ub[e][a][f] = orc_upwind(qD[a], qU[a], va, g->utol);
           for (int m = 0; m < g->nsol; m++) {
             solid* S = &g->sol[m];
             double xD[3], xU[3];
@@ -723,7 +728,7 @@ static void bar_states(orc_grid* g) {
               double sU = slope_x(g, S->xi, S->lay, a, e, i, j, k);
               double bD = xD[a] + (0.5 * h - 0.5 * dt * uD) * sD;
               double bU = xU[a] - (0.5 * h + 0.5 * dt * uU) * sU;
-              S->xb[e][a][f] = orc_upwind(bD, bU, va);
+              S->xb[e][a][f] = orc_upwind(bD, bU, va, g->utol);
             }
           }
         }
@@ -810,8 +815,8 @@ static void face_states(orc_grid* g) {
               Rq[a] = g->u[a][cb] - (0.5 * h + 0.5 * dt * ubv) * slope_u(g, a, d, wb[0], wb[1], wb[2]) -
                       0.5 * dt * trans_u(g, d, a, wb[0], wb[1], wb[2]) + 0.5 * dt / g->rho[cb] * F[a][cb];
             }
-            un = orc_godunov_normal(Lq[d], Rq[d]);
-            for (int a = 0; a < 3; a++) g->uf[d][a][f] = (a == d) ? un : orc_upwind(Lq[a], Rq[a], un);
+            un = orc_godunov_normal(Lq[d], Rq[d], g->utol);
+            for (int a = 0; a < 3; a++) g->uf[d][a][f] = (a == d) ? un : orc_upwind(Lq[a], Rq[a], un, g->utol);
           }
           /* xi faces: both sides -> upwind with the same normal velocity; one side -> that side
            * (Reading; this is also the wall-face rule) */
@@ -828,7 +833,7 @@ static void face_states(orc_grid* g) {
               if (okB)
                 Rx = S->xi[a][cb] - (0.5 * h + 0.5 * dt * g->u[d][cb]) * slope_x(g, S->xi, S->lay, a, d, wb[0], wb[1], wb[2]) -
                      0.5 * dt * trans_x(g, S, d, a, wb[0], wb[1], wb[2]);
-              S->xf[d][a][f] = (okA && okB) ? orc_upwind(Lx, Rx, un) : (okA ? Lx : Rx);
+              S->xf[d][a][f] = (okA && okB) ? orc_upwind(Lx, Rx, un, g->utol) : (okA ? Lx : Rx);
             }
           }
         }
@@ -874,15 +879,24 @@ static int cg(orc_grid* g, opfn A, const double* coef, const double* b_in, doubl
     if (!(pAp > 0.0)) break;
     double al = rr / pAp;
     for (long i = 0; i < n; i++) { x[i] += al * pv[i]; r[i] -= al * Ap[i]; }
+    it++;
+    if (it % 50 == 0) {
+      /* residual replacement: keep the recursive residual equal to the true one */
+      A(g, coef, x, Ap);
+      for (long i = 0; i < n; i++) r[i] = b[i] - Ap[i];
+    }
     demean(r, n);
     double rr2 = dotp(r, r, n);
     double be = rr2 / rr;
     rr = rr2;
     for (long i = 0; i < n; i++) pv[i] = r[i] + be * pv[i];
-    it++;
   }
 done:
   demean(x, n);
+  /* true relative residual of the returned solution */
+  A(g, coef, x, Ap);
+  for (long i = 0; i < n; i++) r[i] = b[i] - Ap[i];
+  g->last_true_rel = bn > 0.0 ? sqrt(dotp(r, r, n)) / bn : 0.0;
   free(r); free(pv); free(Ap); free(b);
   return (bn == 0.0 || sqrt(rr) <= tol * bn) ? it : -1;
 }
@@ -929,6 +943,7 @@ int orc_mac_project(orc_grid* g, const double* rho, double* ufx, double* ufy, do
       }
   int it = cg(g, mac_apply, rho, rhs, q_out, g->N);
   g->iters[0] = it;
+  g->true_rel[0] = g->last_true_rel;
   for (int d = 0; d < 3; d++) {
     int ext[3] = {g->n[0], g->n[1], g->n[2]};
     ext[d] += 1;
@@ -1005,6 +1020,7 @@ int orc_fe_solve(orc_grid* g, const double* rho, const double* V, double* psi_ou
   orc_fe_weak_div(g, V, f);
   int it = cg(g, fe_apply_op, beta, f, psi_out, g->NN);
   g->iters[1] = it;
+  g->true_rel[1] = g->last_true_rel;
   free(beta); free(f);
   return it < 0 ? ENOCONV_ : OK;
 }
@@ -1062,6 +1078,7 @@ static void ensure_init(orc_grid* g) {
   if (g->inited) return;
   g->inited = 1;
   g->dt = pick_dt(g);
+  g->utol = 1e-12 * g->h / g->dt;
   for (int m = 0; m < g->nsol; m++) init_solid(g, &g->sol[m]);
   mix_density(g, 0, g->rho);
 }
@@ -1078,7 +1095,6 @@ static int one_step(orc_grid* g) {
   /* 3. MAC projection of the normal face velocities */
   for (int d = 0; d < 3; d++) memcpy(g->umac[d], g->uf[d][d], sizeof(double) * g->NF[d]);
   if (orc_mac_project(g, g->rho, g->umac[0], g->umac[1], g->umac[2], dt, g->q) != OK) rc = ENOCONV_;
-  for (int d = 0; d < 3; d++) memcpy(g->uf[d][d], g->umac[d], sizeof(double) * g->NF[d]);
   /* 4. advective terms (eq. adv_terms) and 5. predictor of xi (eq. dis_xi_adv) */
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
@@ -1088,8 +1104,12 @@ static int one_step(orc_grid* g) {
         for (int d = 0; d < 3; d++) {
           long fl, fh;
           efaces(g, d, i, j, k, &fl, &fh);
-          double vavg = 0.5 * (g->uf[d][d][fl] + g->uf[d][d][fh]);
-          for (int a = 0; a < 3; a++) acc[a] += vavg * (g->uf[d][a][fh] - g->uf[d][a][fl]) / h;
+          /* the normal component is the MAC-corrected one; the others are the upwinded states */
+          double vavg = 0.5 * (g->umac[d][fl] + g->umac[d][fh]);
+          for (int a = 0; a < 3; a++) {
+            const double* Q = a == d ? g->umac[d] : g->uf[d][a];
+            acc[a] += vavg * (Q[fh] - Q[fl]) / h;
+          }
         }
         for (int a = 0; a < 3; a++) g->adv[a][c] = acc[a];
       }
@@ -1110,7 +1130,7 @@ static int one_step(orc_grid* g) {
             long fl, fh;
             efaces(g, d, i, j, k, &fl, &fh);
             if (!S->xfok[d][fl] || !S->xfok[d][fh]) { ok = 0; break; }
-            double vavg = 0.5 * (g->uf[d][d][fl] + g->uf[d][d][fh]);
+            double vavg = 0.5 * (g->umac[d][fl] + g->umac[d][fh]);
             for (int a = 0; a < 3; a++) acc[a] += vavg * (S->xf[d][a][fh] - S->xf[d][a][fl]) / h;
           }
           if (!ok) continue;

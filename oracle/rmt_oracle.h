@@ -71,14 +71,15 @@ int  orc_write(orc_grid* g, int field, int solid, const double* src, long n);
 void orc_destroy(orc_grid* g);
 double orc_dt(orc_grid* g);
 int  orc_last_iters(orc_grid* g, int which);   /* 0: MAC CG iterations, 1: FE CG iterations */
+double orc_last_true_residual(orc_grid* g, int which); /* true relative residual of that solve */
 const char* orc_error(orc_grid* g);
 
 /* Building blocks exposed for the pin tests. */
 double orc_heaviside(double phi, double eps);
 double orc_dheaviside(double phi, double eps);
 double orc_limited_slope(const double q[5], const int ok[5], double h);
-double orc_godunov_normal(double L, double R);
-double orc_upwind(double L, double R, double un);
+double orc_godunov_normal(double L, double R, double tol);
+double orc_upwind(double L, double R, double un, double tol);
 double orc_phi0(const orc_solid_desc* s, const double X[3]);
 /* Neo-Hookean deviatoric stress (3x3 row-major) from A = grad xi (row-major). */
 int  orc_neohookean(const double A[9], double G, double tau[9]);

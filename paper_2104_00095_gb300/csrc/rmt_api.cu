@@ -383,7 +383,8 @@ rmt_status step_t(rmt_grid* g) {
   launch_fe_setup<T>(G, u, (const T*)g->ustar, (const T*)g->rho_h, mg_rhs(g->fe), (T*)mg_coef0(g->fe, 0), s);
   pe(g, P_FE_SETUP);
   pb(g, P_FE_SOLVE);
-  cyc = mg_solve(g->fe, rtol, maxc, g->desc.mg_fixed_cycles, s, &ce);
+  cyc = mg_solve(g->fe, rtol, maxc, g->desc.mg_fixed_cycles_fe > 0 ? g->desc.mg_fixed_cycles_fe : g->desc.mg_fixed_cycles,
+               s, &ce);
   pe(g, P_FE_SOLVE);
   if (ce != cudaSuccess) return fail(g, RMT_ECUDA, "FE solve: %s", cudaGetErrorString(ce));
   if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "FE multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
@@ -403,6 +404,7 @@ rmt_status step_t(rmt_grid* g) {
 rmt_status ensure_init(rmt_grid* g) {
   if (g->inited) return RMT_OK;
   g->g.dt = pick_dt(g);
+  g->g.utol = 1e-12 * g->g.h / g->g.dt;
   g->bodies.clear();
   for (const auto& s : g->solids) {
     Body b;

@@ -17,6 +17,7 @@ struct Geo {
   int nn[3];       // nodes per axis (n+1 walled, n periodic)
   long N, NN;      // cells, nodes
   double h, dt, eps, rho_f, mu;
+  double utol;     // |v| <= utol counts as zero in the upwind decisions (1e-12 h/dt)
   double lo[3], len[3];
   double wall[6][3];
   double grav[3];
@@ -195,15 +196,17 @@ __device__ __forceinline__ T lim_slope(const T q[5], unsigned okmask, T inv_h) {
 
 // Godunov choice of the normal velocity and upwinding of other quantities
 // (SI "Godunov-type upwinding scheme")
+// (SI "Godunov-type upwinding scheme"); the "= 0" cases hold for |v| <= tol so that a velocity
+// that vanishes in exact arithmetic does not choose its side from rounding noise
 template <typename T>
-__device__ __forceinline__ T god_normal(T L, T R) {
-  if (L > T(0) && L + R > T(0)) return L;
-  if (R < T(0) && L + R < T(0)) return R;
+__device__ __forceinline__ T god_normal(T L, T R, T tol) {
+  if (L > tol && L + R > tol) return L;
+  if (R < -tol && L + R < -tol) return R;
   return T(0);
 }
 template <typename T>
-__device__ __forceinline__ T upwind(T L, T R, T un) {
-  return un > T(0) ? L : (un < T(0) ? R : T(0.5) * (L + R));
+__device__ __forceinline__ T upwind(T L, T R, T un, T tol) {
+  return un > tol ? L : (un < -tol ? R : T(0.5) * (L + R));
 }
 
 // Multi-body mixing (SI eq. mod_heaviside): in place, w[m] = 1 - H_m on entry, the

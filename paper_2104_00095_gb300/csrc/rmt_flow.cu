@@ -77,10 +77,10 @@ __global__ void k_bar(Geo g, int e, const T* __restrict__ u, T* __restrict__ ub0
       qD[a] = uval(g, u, a, lo[0], lo[1], lo[2]) + (T(0.5) * h - T(0.5) * dt * uD) * slope_u(g, u, a, e, lo[0], lo[1], lo[2]);
       qU[a] = uval(g, u, a, i, j, k) - (T(0.5) * h + T(0.5) * dt * uU) * slope_u(g, u, a, e, i, j, k);
     }
-    const T va = god_normal(qD[e], qU[e]);
+    const T va = god_normal(qD[e], qU[e], T(g.utol));
     vadv[f] = va;
 #pragma unroll
-    for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va);
+    for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va, T(g.utol));
   }
 }
 
@@ -148,9 +148,9 @@ __global__ void k_face(Geo g, int d, const T* __restrict__ u, const T* __restric
                       T(0.5) * dt / r * F;
       }
     }
-    const T un = god_normal(st[0][d], st[1][d]);
+    const T un = god_normal(st[0][d], st[1][d], T(g.utol));
 #pragma unroll
-    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un);
+    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un, T(g.utol));
   }
 }
 

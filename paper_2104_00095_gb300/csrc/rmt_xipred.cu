@@ -92,7 +92,8 @@ __device__ __noinline__ bool xbar(const Geo& g, const T* __restrict__ u, const T
   const T va = vadv_e[fidx(g, e, hi[0], hi[1], hi[2])];
 #pragma unroll
   for (int a = 0; a < 3; a++)
-    out[a] = upwind(xD[a] + (T(0.5) * h - T(0.5) * dt * uD) * sD[a], xU[a] - (T(0.5) * h + T(0.5) * dt * uU) * sU[a], va);
+    out[a] = upwind(xD[a] + (T(0.5) * h - T(0.5) * dt * uD) * sD[a], xU[a] - (T(0.5) * h + T(0.5) * dt * uU) * sU[a], va,
+                    T(g.utol));
   return true;
 }
 
@@ -166,7 +167,7 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
         if (okA) xi_state(g, u, x, lay, pp, d, 0, ca[0], ca[1], ca[2], L);
         if (okB) xi_state(g, u, x, lay, pp, d, 1, cb[0], cb[1], cb[2], R);
 #pragma unroll
-        for (int a = 0; a < 3; a++) xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un) : (okA ? L[a] : R[a]);
+        for (int a = 0; a < 3; a++) xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un, T(g.utol)) : (okA ? L[a] : R[a]);
       }
       long lo, hi;
       cell_faces<T>(g, d, i, j, k, lo, hi);

@@ -33,7 +33,8 @@ class rmt_grid_desc(C.Structure):
         ("wall_u", (C.c_double * 3) * 6), ("rho_f", C.c_double), ("mu", C.c_double),
         ("eps_h", C.c_double), ("band_layers", C.c_int), ("dt", C.c_double),
         ("gravity", C.c_double * 3), ("precision", C.c_int), ("mg_rtol", C.c_double),
-        ("mg_max_cycles", C.c_int), ("mg_fixed_cycles", C.c_int), ("cuda_stream", C.c_void_p),
+        ("mg_max_cycles", C.c_int), ("mg_fixed_cycles", C.c_int), ("mg_fixed_cycles_fe", C.c_int),
+        ("cuda_stream", C.c_void_p),
     ]
 
 
@@ -111,6 +112,7 @@ def make_grid_desc(scene: dict, stream: int = 0) -> rmt_grid_desc:
     d.mg_rtol = scene.get("mg_rtol", 0.0)
     d.mg_max_cycles = scene.get("mg_max_cycles", 0)
     d.mg_fixed_cycles = scene.get("mg_fixed_cycles", 0)
+    d.mg_fixed_cycles_fe = scene.get("mg_fixed_cycles_fe", 0)
     d.cuda_stream = stream or None
     return d
 

@@ -110,9 +110,27 @@ def test_godunov_normal_is_burgers_riemann_solution():
         uL, uR = rng.normal(size=2)
         if abs(uL + uR) < 1e-12:
             continue
-        assert L.orc_godunov_normal(uL, uR) == _burgers_riemann_at_zero(uL, uR)
+        assert L.orc_godunov_normal(uL, uR, 0.0) == _burgers_riemann_at_zero(uL, uR)
     for uL, uR in [(0.0, 1.0), (-1.0, 0.0), (0.0, 0.0), (-1.0, 1.0), (2.0, 3.0), (-3.0, -2.0)]:
-        assert L.orc_godunov_normal(uL, uR) == _burgers_riemann_at_zero(uL, uR)
+        assert L.orc_godunov_normal(uL, uR, 0.0) == _burgers_riemann_at_zero(uL, uR)
+
+
+def test_upwind_tolerance_only_changes_near_zero_velocities():
+    """With a tolerance t the choices differ from the exact rule only where |u_L|, |u_L + u_R|
+    or |u_n| is within t of zero; there the normal velocity is taken as 0."""
+    rng = np.random.default_rng(13)
+    t = 1e-9
+    for _ in range(5000):
+        uL, uR = rng.normal(size=2) * rng.choice([1.0, 1e-9])
+        a, b = L.orc_godunov_normal(uL, uR, 0.0), L.orc_godunov_normal(uL, uR, t)
+        if a != b:
+            assert b == 0.0 and (abs(uL) <= t or abs(uL + uR) <= t or abs(uR) <= t)
+        q1, q2 = rng.normal(size=2)
+        un = rng.normal() * rng.choice([1.0, 1e-10])
+        if abs(un) <= t:
+            assert L.orc_upwind(q1, q2, un, t) == 0.5 * (q1 + q2)
+        else:
+            assert L.orc_upwind(q1, q2, un, t) == L.orc_upwind(q1, q2, un, 0.0)
 
 
 # --------------------------------------------------------------------------- stress

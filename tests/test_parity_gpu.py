@@ -166,7 +166,7 @@ def _taxicab_layers_local(lay, per, L):
 def test_full_size_properties(cfg):
     if cfg == "swimmers256_fp32":
         sc = S.swimmers(n=256, steps=1)
-        sc.update(mg_fixed_cycles=4)
+        sc.update(mg_fixed_cycles=7, mg_fixed_cycles_fe=4)  # the launch configuration bench.py times
         xtol = 2e-6
     else:
         sc = S.settling(n=128, steps=1)
