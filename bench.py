@@ -43,14 +43,15 @@ CONFIGS = {
 CPU_SAMPLE_N = 48
 
 
-def make_scene(cfg: dict, n: int | None = None):
+def make_scene(cfg: dict, n: int | None = None, nbodies: int | None = None):
     from paper_2104_00095_gb300 import scenes as S
 
     n = n or cfg["n"]
+    kw = {} if nbodies is None else {"nbodies": nbodies}
     if cfg["kind"] == "swimmers":
-        return S.swimmers(n=n, precision=cfg["precision"])
+        return S.swimmers(n=n, precision=cfg["precision"], **kw)
     if cfg["kind"] == "settling":
-        return S.settling(n=n, precision=cfg["precision"])
+        return S.settling(n=n, precision=cfg["precision"], **kw)
     return S.cavity_sphere(n, precision=cfg["precision"])
 
 
@@ -159,6 +160,8 @@ def main():
                     help="V-cycles per MAC solve (fixed, no host sync; 7 reach ~1e-6 relative residual)")
     ap.add_argument("--mg-cycles-fe", type=int, default=4,
                     help="V-cycles per FE solve (fixed; 4 reach ~1e-6 relative residual)")
+    ap.add_argument("--nbodies", type=int, default=None,
+                    help="override the body count (profiling captures only; changes the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -185,7 +188,7 @@ def main():
             dist.barrier()
 
     stream = torch.cuda.current_stream()
-    scene = make_scene(cfg)
+    scene = make_scene(cfg, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
     g = rmt.Grid(scene, stream=stream.cuda_stream)

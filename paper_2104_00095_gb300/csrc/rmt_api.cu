@@ -20,6 +20,10 @@ void rmt_count_launches(long n) { g_launches.fetch_add(n, std::memory_order_rela
 namespace {
 
 struct BodyMem {
+  int* bb = nullptr;  // band bounding boxes of the two parities (2 x 6 ints, device)
+  int blocks = 1;     // launch width of the body's window kernels
+  int* list = nullptr;   // compacted band cells of the current step (capacity N)
+  int* count = nullptr;  // its length (device)
   void* X[2] = {nullptr, nullptr};
   void* PHI[2] = {nullptr, nullptr};
   int8_t* LAY[2] = {nullptr, nullptr};
@@ -37,7 +41,7 @@ enum {
 const char* const kProfNames[P_NUM] = {
     "stress_n", "godunov_velocity", "mac_setup", "mac_solve", "mac_correct_advect", "xi_predict", "extrapolate",
     "corrector", "stress_half", "density_ustar", "fe_setup", "fe_solve", "fe_update_density",
-    "k_smooth(mac,level0,colour)", "k_resid64(mac)", "k_smooth(fe,level0,colour)", "k_resid64(fe)"};
+    "k_rbgs(mac,level0,colour)", "k_resid64(mac)", "k_jacobi(fe,level0)", "k_resid64(fe)"};
 struct Prof {
   int on = 0;
   std::vector<cudaEvent_t> pool;
@@ -89,9 +93,15 @@ struct rmt_grid {
   std::vector<void*> allocs;
   Prof prof;
   HookCtx hctx[2];
+  // smoother schedule (negative: solver default)
+  int mac_pre = -1, mac_post = -1, fe_pre = -1, fe_post = -1;
+  double fe_omega = -1.0;
 };
 
 namespace {
+
+// launch width of the one-warp-per-band-cell fits: 4 resident blocks of 128 threads per SM
+constexpr int WLS_BLOCKS = 152 * 4;
 
 rmt_status fail(rmt_grid* g, rmt_status st, const char* fmt, ...) {
   if (g) {
@@ -150,16 +160,16 @@ void mg_hook(void* ctx, int which, int begin, cudaStream_t) {
   if (begin) pb(h->g, e);
   else pe(h->g, e);
 }
-// algorithmic bytes of one launch of the profiled multigrid kernels (w = bytes per word):
-// smoother colour (7-point): x 1, b 1/2, three face coefficients 3, x written 1/2 words per cell;
-// smoother colour (27-point): x 1 + b 1/8 + written 1/8 words per node, beta 1 word per cell;
-// FP64 residual: x and b 8 bytes each, coefficients (3 or 1 words), residual copy 1 word.
+// algorithmic bytes of one launch of the profiled multigrid kernels (w = bytes per word, N
+// cells, NN nodes): red-black colour pass (7-point): x and rho read once, b read and x written
+// for half the cells; Jacobi pass (27-point): x, b read and x written per node, rho per cell;
+// FP64 residual: x and b 8 bytes each, rho, and the residual copy in the storage type.
 double prof_bytes(const rmt_grid* g, int e) {
   const double w = (double)g->esz, N = (double)g->g.N, NN = (double)g->g.NN;
   switch (e) {
-    case P_MAC_SMOOTH: return 5.0 * N * w;
-    case P_MAC_RESID: return 16.0 * N + 4.0 * N * w;
-    case P_FE_SMOOTH: return 1.25 * NN * w + N * w;
+    case P_MAC_SMOOTH: return 3.0 * N * w;
+    case P_MAC_RESID: return 16.0 * N + 2.0 * N * w;
+    case P_FE_SMOOTH: return 3.0 * NN * w + N * w;
     case P_FE_RESID: return 16.0 * NN + N * w + NN * w;
   }
   return 0.0;
@@ -237,6 +247,27 @@ rmt_status build_views(rmt_grid* g) {
   return RMT_OK;
 }
 
+// launch width of each body's window kernels from its band box (the kernels stride over the
+// whole window, so this only sizes the launch)
+rmt_status size_windows(rmt_grid* g) {
+  const Geo& G = g->g;
+  for (auto& b : g->bm) {
+    int h[6];
+    CK(g, cudaMemcpy(h, b.bb, sizeof h, cudaMemcpyDeviceToHost));
+    long vol = 1;
+    for (int d = 0; d < 3; d++) {
+      long e = h[d] <= h[3 + d] ? (long)(h[3 + d] - h[d] + 1) + 8 : 0;
+      if (e > G.n[d]) e = G.n[d];
+      vol *= e;
+    }
+    long blocks = (vol + 127) / 128;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 152L * 64) blocks = 152L * 64;
+    b.blocks = (int)blocks;
+  }
+  return RMT_OK;
+}
+
 template <typename T>
 rmt_status init_t(rmt_grid* g) {
   const Geo& G = g->g;
@@ -274,6 +305,9 @@ rmt_status init_t(rmt_grid* g) {
     }
     AL(b.XH, 3 * N * e);
     AL(b.PHIH, N * e);
+    AL(b.bb, 12 * sizeof(int));
+    AL(b.list, N * sizeof(int));
+    AL(b.count, 16);
   }
   AL(g->bodies_d, (nb > 0 ? nb : 1) * sizeof(Body));
   AL(g->views_d, (size_t)6 * (nb > 0 ? nb : 1) * sizeof(BodyView<T>));
@@ -295,18 +329,32 @@ rmt_status init_t(rmt_grid* g) {
   g->hctx[1] = {g, 1};
   mg_set_hook(g->mac, mg_hook, &g->hctx[0]);
   mg_set_hook(g->fe, mg_hook, &g->hctx[1]);
-  for (int m = 0; m < nb; m++) launch_fill<int8_t>(g->bm[m].LAY[1], (int8_t)-1, N, g->s);
+  mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
+  mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+  // outside a body's band every per-body array reads "absent" (layer -1, NaN); the window
+  // kernels rely on it, since they only ever touch the band's neighbourhood
+  const T nanv = (T)NAN;
+  for (int m = 0; m < nb; m++) {
+    BodyMem& b = g->bm[m];
+    launch_fill<int8_t>(b.LAY[1], (int8_t)-1, N, g->s);
+    launch_fill<T>((T*)b.X[1], nanv, 3 * N, g->s);
+    launch_fill<T>((T*)b.PHI[1], nanv, N, g->s);
+    launch_fill<T>((T*)b.XH, nanv, 3 * N, g->s);
+    launch_fill<T>((T*)b.PHIH, nanv, N, g->s);
+  }
   if ((st = build_views<T>(g)) != RMT_OK) return st;
   // SI "Initialization": u^0 = 0, p = 0, xi^0 = x, extrapolation, phi, rho^0
+  const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
     launch_init_xi<T>(G, g->bodies[m], (T*)b.X[0], g->s);
-    launch_extrapolate<T>(G, g->bodies_d + m, g->bodies[m], (T*)b.X[0], (T*)b.PHI[0], b.LAY[0], g->err_d, g->s);
+    launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[0],
+                          (T*)b.PHI[0], b.LAY[0], g->err_d, g->s);
   }
   launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, (T*)g->rho, g->s);
   CK(g, cudaGetLastError());
   CK(g, cudaStreamSynchronize(g->s));
-  return RMT_OK;
+  return size_windows(g);
 }
 
 template <typename T>
@@ -338,9 +386,9 @@ rmt_status step_t(rmt_grid* g) {
   launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, ub, vadv, uf, s);
   pe(g, P_GODUNOV);
   // 3. MAC projection of the normal face velocities
-  T* mbeta[3] = {(T*)mg_coef0(g->mac, 0), (T*)mg_coef0(g->mac, 1), (T*)mg_coef0(g->mac, 2)};
   pb(g, P_MAC_SETUP);
-  launch_mac_setup<T>(G, uf, (const T*)g->rho, mg_rhs(g->mac), mbeta, s);
+  launch_mac_setup<T>(G, uf, mg_rhs(g->mac), s);
+  mg_set_density(g->mac, g->rho);
   pe(g, P_MAC_SETUP);
   cudaError_t ce = cudaSuccess;
   const double rtol = g->desc.mg_rtol > 0 ? g->desc.mg_rtol : 1e-12;
@@ -352,22 +400,24 @@ rmt_status step_t(rmt_grid* g) {
   if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "MAC multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
   g->cycles[0] = cyc;
   pb(g, P_MAC_CORR_ADV);
-  launch_mac_correct<T>(G, uf, mbeta, mg_solution(g->mac), umac, s);
+  launch_mac_correct<T>(G, uf, (const T*)g->rho, mg_solution(g->mac), umac, s);
   // 4. advective term
   launch_advect<T>(G, uf, umac, (T*)g->adv, s);
   pe(g, P_MAC_CORR_ADV);
   // 5.-7. predictor, re-extrapolation, corrector for every body
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
+    const int* bbc = b.bb + 6 * cur;
     pb(g, P_XI_PRED);
-    launch_xi_predict<T>(G, u, vadv, uf, umac, (const T*)b.X[cur], b.LAY[cur], (T*)b.X[nxt], s);
+    launch_xi_predict<T>(G, u, vadv, uf, umac, bbc, b.blocks, (const T*)b.X[cur], b.LAY[cur], (T*)b.X[nxt], s);
     pe(g, P_XI_PRED);
     pb(g, P_EXTRAP);
-    launch_extrapolate<T>(G, g->bodies_d + m, g->bodies[m], (T*)b.X[nxt], (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, s);
+    launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[nxt],
+                          (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, s);
     pe(g, P_EXTRAP);
     pb(g, P_CORR);
-    launch_corrector<T>(G, g->bodies_d + m, g->bodies[m], (const T*)b.X[cur], b.LAY[cur], (const T*)b.X[nxt],
-                        b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, s);
+    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, WLS_BLOCKS, (const T*)b.X[cur], b.LAY[cur],
+                        (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, s);
     pe(g, P_CORR);
   }
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
@@ -380,7 +430,8 @@ rmt_status step_t(rmt_grid* g) {
   pe(g, P_USTAR);
   // 11. approximate projection, u^{n+1}, p^{n+1/2}
   pb(g, P_FE_SETUP);
-  launch_fe_setup<T>(G, u, (const T*)g->ustar, (const T*)g->rho_h, mg_rhs(g->fe), (T*)mg_coef0(g->fe, 0), s);
+  launch_fe_setup<T>(G, u, (const T*)g->ustar, mg_rhs(g->fe), s);
+  mg_set_density(g->fe, g->rho_h);
   pe(g, P_FE_SETUP);
   pb(g, P_FE_SOLVE);
   cyc = mg_solve(g->fe, rtol, maxc, g->desc.mg_fixed_cycles_fe > 0 ? g->desc.mg_fixed_cycles_fe : g->desc.mg_fixed_cycles,
@@ -493,8 +544,9 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
   } else {
     BodyMem& b = g->bm[sid];
     k_cvt_back<T><<<nbk(3 * G.N), 256, 0, s>>>(g->stage, (T*)b.X[g->par], 3 * G.N); rmt_count_launches(1);
-    launch_extrapolate<T>(G, g->bodies_d + sid, g->bodies[sid], (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par],
-                          g->err_d, s);
+    const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
+    launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count, WLS_BLOCKS,
+                          (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s);
     launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), (T*)g->rho, s);
   }
   CK(g, cudaGetLastError());
@@ -625,7 +677,10 @@ rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* sr
                         src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
   st = g->fp32 ? scatter_t<float>(g, field, solid_id) : scatter_t<double>(g, field, solid_id);
   if (st != RMT_OK) return st;
-  if (field == RMT_F_XI) return check_err(g);
+  if (field == RMT_F_XI) {
+    if ((st = check_err(g)) != RMT_OK) return st;
+    return size_windows(g);
+  }
   if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
   return RMT_OK;
 }
@@ -668,6 +723,29 @@ rmt_status rmt_profile(rmt_grid* g, int enable) {
 }
 
 int rmt_profile_entries(void) { return P_NUM; }
+
+rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
+  if (!g || !name) return RMT_EINVAL;
+  int* ip = nullptr;
+  if (!strcmp(name, "mac_pre")) ip = &g->mac_pre;
+  else if (!strcmp(name, "mac_post")) ip = &g->mac_post;
+  else if (!strcmp(name, "fe_pre")) ip = &g->fe_pre;
+  else if (!strcmp(name, "fe_post")) ip = &g->fe_post;
+  if (ip) {
+    if (value < 0 || value > 16) return fail(g, RMT_EINVAL, "%s out of range", name);
+    *ip = (int)value;
+  } else if (!strcmp(name, "fe_omega")) {
+    if (!(value > 0.0 && value < 2.0)) return fail(g, RMT_EINVAL, "fe_omega out of range");
+    g->fe_omega = value;
+  } else {
+    return fail(g, RMT_EINVAL, "unknown option %s", name);
+  }
+  if (g->inited) {
+    mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
+    mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+  }
+  return RMT_OK;
+}
 
 const char* rmt_profile_name(int entry) { return (entry >= 0 && entry < P_NUM) ? kProfNames[entry] : ""; }
 

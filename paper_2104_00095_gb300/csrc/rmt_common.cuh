@@ -99,6 +99,24 @@ __device__ __forceinline__ T uval(const Geo& g, const T* __restrict__ u, int a, 
   return add + s * u[a * g.N + cidx(g, ii[0], ii[1], ii[2])];
 }
 
+// u component a at (i,j,k) along with its +-r neighbours on axis d: direct loads when the whole
+// stencil lies inside the grid (the common case), the boundary rules otherwise
+template <typename T>
+__device__ __forceinline__ bool inside(const Geo& g, int d, int i, int j, int k, int r) {
+  const int ii[3] = {i, j, k};
+  if (ii[0] < 0 || ii[0] >= g.n[0] || ii[1] < 0 || ii[1] >= g.n[1] || ii[2] < 0 || ii[2] >= g.n[2]) return false;
+  return ii[d] - r >= 0 && ii[d] + r < g.n[d];
+}
+
+// 3-D launch geometry for cell/face/node kernels: 32 x 4 threads per block in x and y, one
+// block layer per z index
+#define TILE_X 32
+#define TILE_Y 4
+#define THREAD_XYZ(i, j, k)                     \
+  const int i = blockIdx.x * TILE_X + threadIdx.x; \
+  const int j = blockIdx.y * TILE_Y + threadIdx.y; \
+  const int k = blockIdx.z
+
 // -------------------------------------------------------------------------------------
 // explicitly rounded arithmetic (no contraction), used where a sign decides an integer
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -238,6 +256,64 @@ __device__ __forceinline__ bool inv3(const T A[9], T F[9]) {
   F[8] = (A[0] * A[4] - A[1] * A[3]) / det;
   return true;
 }
+
+// Work window of one body: the bounding box of its band (unwrapped cell coordinates,
+// inclusive min in bb[0..2], max in bb[3..5]) dilated by dil cells, clamped at walls; a null
+// box means the whole grid.  The band moves less than a cell per step, so a window dilated by
+// two cells covers every cell a step can add to or remove from the band.
+struct Win {
+  int lo[3], ext[3];
+  long vol;
+};
+__device__ __forceinline__ Win make_win(const Geo& g, const int* bb, int dil) {
+  Win w;
+  w.vol = 1;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int lo = 0, hi = g.n[d];
+    if (bb) {
+      if (bb[d] > bb[3 + d]) {
+        lo = 0;
+        hi = 0;
+      } else {
+        lo = bb[d] - dil;
+        hi = bb[3 + d] + dil + 1;
+        if (!g.per[d]) {
+          if (lo < 0) lo = 0;
+          if (hi > g.n[d]) hi = g.n[d];
+        } else if (hi - lo > g.n[d]) {
+          lo = 0;
+          hi = g.n[d];
+        }
+      }
+    }
+    w.lo[d] = lo;
+    w.ext[d] = hi > lo ? hi - lo : 0;
+    w.vol *= w.ext[d];
+  }
+  return w;
+}
+// t-th cell of a window: unwrapped coordinates u[] and the wrapped cell index c
+__device__ __forceinline__ void win_cell(const Geo& g, const Win& w, long t, int u[3], int& i, int& j, int& k,
+                                         long& c) {
+  const int a = (int)(t % w.ext[0]);
+  const long r = t / w.ext[0];
+  u[0] = w.lo[0] + a;
+  u[1] = w.lo[1] + (int)(r % w.ext[1]);
+  u[2] = w.lo[2] + (int)(r / w.ext[1]);
+  int v[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    v[d] = u[d] % g.n[d];
+    if (v[d] < 0) v[d] += g.n[d];
+  }
+  i = v[0];
+  j = v[1];
+  k = v[2];
+  c = cidx(g, i, j, k);
+}
+#define WIN_LOOP(t, w) \
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (w).vol; t += (long)gridDim.x * blockDim.x)
 
 // grid-stride helper
 #define GRID_LOOP(idx, total) \

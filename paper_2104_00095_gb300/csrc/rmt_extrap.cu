@@ -41,8 +41,13 @@ __global__ void k_init_xi(Geo g, Body b, T* __restrict__ x) {
 
 // layer 0 = candidates (finite xi) with phi_0(xi) < 0; everything else unmarked
 template <typename T>
-__global__ void k_classify(Geo g, Body b, const T* __restrict__ x, int8_t* __restrict__ lay) {
-  GRID_LOOP(c, g.N) {
+__global__ void k_classify(Geo g, Body b, const int* __restrict__ bb, const T* __restrict__ x,
+                           int8_t* __restrict__ lay) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
     const T x0 = x[c], x1 = x[g.N + c], x2 = x[2 * g.N + c];
     int8_t l = -1;
     if (isfinite(x0) && isfinite(x1) && isfinite(x2) && phi0(b, x0, x1, x2) < T(0)) l = 0;
@@ -52,11 +57,13 @@ __global__ void k_classify(Geo g, Body b, const T* __restrict__ x, int8_t* __res
 
 // unmarked face neighbours of layer l-1 become layer l (walls stop, periodic axes wrap);
 // in place is race-free: only -1 -> l writes, and only l-1 is tested
-__global__ void k_bfs(Geo g, int l, int8_t* __restrict__ lay) {
-  GRID_LOOP(c, g.N) {
+__global__ void k_bfs(Geo g, const int* __restrict__ bb, int l, int8_t* __restrict__ lay) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
     if (lay[c] != -1) continue;
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
     const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
     for (int f = 0; f < 6; f++) {
       long nb;
@@ -106,53 +113,79 @@ __device__ bool solve4(double A[4][4], double B[4][3], double X[4][3]) {
   return true;
 }
 
-// One affine WLS fit centred at cell (i,j,k) of layer le with search radius rs.
+// One affine WLS fit centred at cell (i,j,k) of layer le with search radius rs, computed by a
+// whole warp: the lanes split the (2 rs + 1)^3 candidate cells and the normal-equation sums are
+// combined by a butterfly (every lane ends with the same totals, in a fixed order).
 // mode 0: kernel 2^-(|di|+|dj|+|dk|); mode 1: times max(0, cos) against the normal n_e.
 template <typename T>
-__device__ bool wls_fit(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j, int k,
-                        int le, int rs, int mode, const double nrm[3], double sol[4][3]) {
-  double A[4][4], B[4][3];
-  for (int r = 0; r < 4; r++) {
-    for (int q = 0; q < 4; q++) A[r][q] = 0.0;
-    for (int a = 0; a < 3; a++) B[r][a] = 0.0;
-  }
+__device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j,
+                             int k, int le, int rs, int mode, const double nrm[3], double sol[4][3]) {
+  const int lane = threadIdx.x & 31;
+  double a[10], bsum[12];
+#pragma unroll
+  for (int q = 0; q < 10; q++) a[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 12; q++) bsum[q] = 0.0;
   int npos = 0;
-  for (int dk = -rs; dk <= rs; dk++)
-    for (int dj = -rs; dj <= rs; dj++)
-      for (int di = -rs; di <= rs; di++) {
-        long c;
-        if (!cell_at(g, i + di, j + dj, k + dk, c)) continue;
-        const int ld = lay[c];
-        if (ld < 0 || ld >= le) continue;
-        const int s = abs(di) + abs(dj) + abs(dk);
-        double w = ldexp(1.0, -s);
-        if (mode == 1) {
-          const double len = sqrt((double)(di * di + dj * dj + dk * dk));
-          const double cs = -((double)di * nrm[0] + (double)dj * nrm[1] + (double)dk * nrm[2]) / len;
-          w = cs * w;
-          if (!(w > 0.0)) continue;
-        }
-        const double v[4] = {1.0, (double)di, (double)dj, (double)dk};
-        const double xv[3] = {(double)x[c], (double)x[g.N + c], (double)x[2 * g.N + c]};
-        for (int r = 0; r < 4; r++) {
-          for (int q = 0; q < 4; q++) A[r][q] += w * v[r] * v[q];
-          for (int a = 0; a < 3; a++) B[r][a] += w * v[r] * xv[a];
-        }
-        npos++;
-      }
+  const int w = 2 * rs + 1, nc = w * w * w;
+  for (int t = lane; t < nc; t += 32) {
+    const int di = t % w - rs, dj = (t / w) % w - rs, dk = t / (w * w) - rs;
+    long c;
+    if (!cell_at(g, i + di, j + dj, k + dk, c)) continue;
+    const int ld = lay[c];
+    if (ld < 0 || ld >= le) continue;
+    const int sr = abs(di) + abs(dj) + abs(dk);
+    double wt = ldexp(1.0, -sr);
+    if (mode == 1) {
+      const double len = sqrt((double)(di * di + dj * dj + dk * dk));
+      const double cs = -((double)di * nrm[0] + (double)dj * nrm[1] + (double)dk * nrm[2]) / len;
+      wt = cs * wt;
+      if (!(wt > 0.0)) continue;
+    }
+    const double v[4] = {1.0, (double)di, (double)dj, (double)dk};
+    const double xv[3] = {(double)x[c], (double)x[g.N + c], (double)x[2 * g.N + c]};
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int cc = r; cc < 4; cc++) a[q++] += wt * v[r] * v[cc];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+      for (int d = 0; d < 3; d++) bsum[3 * r + d] += wt * v[r] * xv[d];
+    npos++;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 10; q++) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+#pragma unroll
+    for (int q = 0; q < 12; q++) bsum[q] += __shfl_xor_sync(0xffffffffu, bsum[q], o);
+    npos += __shfl_xor_sync(0xffffffffu, npos, o);
+  }
   if (npos < 4) return false;
+  double A[4][4], B[4][3];
+  int q = 0;
+  for (int r = 0; r < 4; r++)
+    for (int cc = r; cc < 4; cc++) {
+      A[r][cc] = a[q];
+      A[cc][r] = a[q];
+      q++;
+    }
+  for (int r = 0; r < 4; r++)
+    for (int d = 0; d < 3; d++) B[r][d] = bsum[3 * r + d];
   return solve4(A, B, sol);
 }
 
-// Extrapolates one cell: kernel-only fit, then (layers 1 and 2) the fit weighted by the
-// normal n_e = normalised (grad xi)^T grad_X phi_0(xi_e) of that first fit; the search
+// Extrapolates one cell (whole warp): kernel-only fit, then (layers 1 and 2) the fit weighted
+// by the normal n_e = normalised (grad xi)^T grad_X phi_0(xi_e) of that first fit; the search
 // radius grows up to 4 while the system stays degenerate.
 template <typename T>
-__device__ bool wls_cell(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay, int i,
-                         int j, int k, int le, double out[3]) {
+__device__ bool wls_cell_warp(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                              int i, int j, int k, int le, double out[3]) {
   for (int rs = 2; rs <= 4; rs++) {
     double s1[4][3];
-    if (!wls_fit(g, x, lay, i, j, k, le, rs, 0, nullptr, s1)) continue;
+    if (!wls_fit_warp(g, x, lay, i, j, k, le, rs, 0, nullptr, s1)) continue;
     if (le <= 2) {
       const double c0[3] = {s1[0][0], s1[0][1], s1[0][2]};
       double gX[3], v[3];
@@ -162,7 +195,7 @@ __device__ bool wls_cell(const Geo& g, const Body& b, const T* __restrict__ x, c
       if (!(nv > 0.0)) continue;
       const double nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
       double s2[4][3];
-      if (!wls_fit(g, x, lay, i, j, k, le, rs, 1, nrm, s2)) continue;
+      if (!wls_fit_warp(g, x, lay, i, j, k, le, rs, 1, nrm, s2)) continue;
       out[0] = s2[0][0]; out[1] = s2[0][1]; out[2] = s2[0][2];
       return true;
     }
@@ -172,28 +205,61 @@ __device__ bool wls_cell(const Geo& g, const Body& b, const T* __restrict__ x, c
   return false;
 }
 
+// compacted list of the band cells (layers 1..L) of a body's window
+__global__ void k_band_list(Geo g, const int* __restrict__ bb, const int8_t* __restrict__ lay, int* __restrict__ list,
+                            int* __restrict__ count) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
+    const int l = lay[c];
+    if (l >= 1) list[atomicAdd(count, 1)] = (int)c;
+  }
+}
+
+// one warp per listed cell of layer l
 template <typename T>
-__global__ void k_wls(Geo g, Body b, int l, T* __restrict__ x, int8_t* __restrict__ lay, int* __restrict__ err) {
-  GRID_LOOP(c, g.N) {
+__global__ void k_wls(Geo g, Body b, int l, T* __restrict__ x, int8_t* __restrict__ lay, const int* __restrict__ list,
+                      const int* __restrict__ count, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int n = *count;
+  for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
+    const long c = list[e];
     if (lay[c] != l) continue;
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
+    const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
     double out[3];
-    if (wls_cell(g, b, x, lay, i, j, k, l, out)) {
-      x[c] = (T)out[0];
-      x[g.N + c] = (T)out[1];
-      x[2 * g.N + c] = (T)out[2];
-    } else {
-      lay[c] = -1;
-      atomicAdd(err, 1);
+    const bool ok = wls_cell_warp(g, b, x, lay, i, j, k, l, out);
+    __syncwarp();
+    if (lane == 0) {
+      if (ok) {
+        x[c] = (T)out[0];
+        x[g.N + c] = (T)out[1];
+        x[2 * g.N + c] = (T)out[2];
+      } else {
+        lay[c] = -1;
+        atomicAdd(err, 1);
+      }
     }
   }
 }
 
 template <typename T>
-__global__ void k_finalize(Geo g, Body b, T* __restrict__ x, T* __restrict__ phi, const int8_t* __restrict__ lay) {
+__global__ void k_finalize(Geo g, Body b, const int* __restrict__ bb, T* __restrict__ x, T* __restrict__ phi,
+                           const int8_t* __restrict__ lay, int* __restrict__ bb_out) {
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
-  GRID_LOOP(c, g.N) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
+    if (lay[c] >= 0) {
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        atomicMin(&bb_out[d], u[d]);
+        atomicMax(&bb_out[3 + d], u[d]);
+      }
+    }
     if (lay[c] >= 0) {
       phi[c] = phi0(b, x[c], x[g.N + c], x[2 * g.N + c]);
     } else {
@@ -205,10 +271,14 @@ __global__ void k_finalize(Geo g, Body b, T* __restrict__ x, T* __restrict__ phi
 
 // corrector xi^{n+1/2} = (xi^n + xi^{n+1})/2 where both exist
 template <typename T>
-__global__ void k_corr(Geo g, const T* __restrict__ x, const int8_t* __restrict__ lay, const T* __restrict__ xn,
-                       const int8_t* __restrict__ layn, T* __restrict__ xh) {
+__global__ void k_corr(Geo g, const int* __restrict__ bb, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                       const T* __restrict__ xn, const int8_t* __restrict__ layn, T* __restrict__ xh) {
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
-  GRID_LOOP(c, g.N) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
     if (layn[c] < 0 || lay[c] < 0) {
       xh[c] = xh[g.N + c] = xh[2 * g.N + c] = nanv;
       continue;
@@ -221,30 +291,61 @@ __global__ void k_corr(Geo g, const T* __restrict__ x, const int8_t* __restrict_
 // cells new to the band: xi^{n+1/2} by the same WLS from the corrected lower layers
 template <typename T>
 __global__ void k_wls_half(Geo g, Body b, int l, const int8_t* __restrict__ lay, const int8_t* __restrict__ layn,
-                           const T* __restrict__ xn, T* __restrict__ xh, int* __restrict__ err) {
-  GRID_LOOP(c, g.N) {
+                           const T* __restrict__ xn, T* __restrict__ xh, const int* __restrict__ list,
+                           const int* __restrict__ count, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int n = *count;
+  for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
+    const long c = list[e];
     if (layn[c] != l || lay[c] >= 0) continue;
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
+    const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
     double out[3];
-    if (wls_cell(g, b, xh, layn, i, j, k, l, out)) {
-      xh[c] = (T)out[0];
-      xh[g.N + c] = (T)out[1];
-      xh[2 * g.N + c] = (T)out[2];
-    } else {
-      xh[c] = xn[c];
-      xh[g.N + c] = xn[g.N + c];
-      xh[2 * g.N + c] = xn[2 * g.N + c];
-      atomicAdd(err, 1);
+    const bool ok = wls_cell_warp(g, b, xh, layn, i, j, k, l, out);
+    __syncwarp();
+    if (lane == 0) {
+      if (ok) {
+        xh[c] = (T)out[0];
+        xh[g.N + c] = (T)out[1];
+        xh[2 * g.N + c] = (T)out[2];
+      } else {
+        xh[c] = xn[c];
+        xh[g.N + c] = xn[g.N + c];
+        xh[2 * g.N + c] = xn[2 * g.N + c];
+        atomicAdd(err, 1);
+      }
     }
   }
 }
 
 template <typename T>
-__global__ void k_phi_half(Geo g, Body b, const T* __restrict__ xh, const int8_t* __restrict__ layn, T* __restrict__ phih) {
+__global__ void k_phi_half(Geo g, Body b, const int* __restrict__ bb, const T* __restrict__ xh,
+                           const int8_t* __restrict__ layn, T* __restrict__ phih) {
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
-  GRID_LOOP(c, g.N) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int u[3], i, j, k;
+    long c;
+    win_cell(g, w, t, u, i, j, k, c);
     phih[c] = layn[c] >= 0 ? phi0(b, xh[c], xh[g.N + c], xh[2 * g.N + c]) : nanv;
+  }
+}
+
+// empty bounding box (min above max)
+__global__ void k_bb_reset(int* bb) {
+  if (threadIdx.x == 0) {
+    bb[0] = bb[1] = bb[2] = 0x7fffffff;
+    bb[3] = bb[4] = bb[5] = -0x7fffffff;
+  }
+}
+// shift the box of a periodic axis so that its minimum lies in [0, n)
+__global__ void k_bb_normalise(Geo g, int* bb) {
+  if (threadIdx.x != 0) return;
+  for (int d = 0; d < 3; d++) {
+    if (!g.per[d] || bb[d] > bb[3 + d]) continue;
+    int q = bb[d] / g.n[d];
+    if (bb[d] < 0 && bb[d] % g.n[d]) q -= 1;
+    bb[d] -= q * g.n[d];
+    bb[3 + d] -= q * g.n[d];
   }
 }
 
@@ -256,26 +357,48 @@ void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_extrapolate(const Geo& g, const Body* /*bdev*/, const Body& b, T* x, T* phi, int8_t* lay, int* err,
-                        cudaStream_t s) {
-  k_classify<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, x, lay); rmt_count_launches(1);
-  for (int l = 1; l <= g.layers; l++) { k_bfs<<<nblocks(g.N), TPB, 0, s>>>(g, l, lay); rmt_count_launches(1); }
-  for (int l = 1; l <= g.layers; l++) { k_wls<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, l, x, lay, err); rmt_count_launches(1); }
-  k_finalize<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, x, phi, lay); rmt_count_launches(1);
+void launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list, int* count,
+                        int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s) {
+  k_classify<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, lay);
+  rmt_count_launches(1);
+  for (int l = 1; l <= g.layers; l++) {
+    k_bfs<<<blocks, TPB, 0, s>>>(g, bb_in, l, lay);
+    rmt_count_launches(1);
+  }
+  cudaMemsetAsync(count, 0, sizeof(int), s);
+  k_band_list<<<blocks, TPB, 0, s>>>(g, bb_in, lay, list, count);
+  rmt_count_launches(1);
+  for (int l = 1; l <= g.layers; l++) {
+    k_wls<T><<<wls_blocks, TPB, 0, s>>>(g, b, l, x, lay, list, count, err);
+    rmt_count_launches(1);
+  }
+  k_bb_reset<<<1, 32, 0, s>>>(bb_out);
+  rmt_count_launches(1);
+  k_finalize<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, phi, lay, bb_out);
+  rmt_count_launches(1);
+  k_bb_normalise<<<1, 32, 0, s>>>(g, bb_out);
+  rmt_count_launches(1);
 }
 
 template <typename T>
-void launch_corrector(const Geo& g, const Body* /*bdev*/, const Body& b, const T* x, const int8_t* lay, const T* xn,
-                      const int8_t* layn, T* xh, T* phih, int* err, cudaStream_t s) {
-  k_corr<T><<<nblocks(g.N), TPB, 0, s>>>(g, x, lay, xn, layn, xh); rmt_count_launches(1);
-  for (int l = 1; l <= g.layers; l++) { k_wls_half<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, l, lay, layn, xn, xh, err); rmt_count_launches(1); }
-  k_phi_half<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, xh, layn, phih); rmt_count_launches(1);
+void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, const int* count,
+                      int wls_blocks, const T* x, const int8_t* lay, const T* xn, const int8_t* layn, T* xh, T* phih,
+                      int* err, cudaStream_t s) {
+  k_corr<T><<<blocks, TPB, 0, s>>>(g, bb_in, x, lay, xn, layn, xh);
+  rmt_count_launches(1);
+  for (int l = 1; l <= g.layers; l++) {
+    k_wls_half<T><<<wls_blocks, TPB, 0, s>>>(g, b, l, lay, layn, xn, xh, list, count, err);
+    rmt_count_launches(1);
+  }
+  k_phi_half<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, xh, layn, phih);
+  rmt_count_launches(1);
 }
 
-#define INST(T)                                                                                               \
-  template void launch_init_xi<T>(const Geo&, const Body&, T*, cudaStream_t);                                  \
-  template void launch_extrapolate<T>(const Geo&, const Body*, const Body&, T*, T*, int8_t*, int*, cudaStream_t); \
-  template void launch_corrector<T>(const Geo&, const Body*, const Body&, const T*, const int8_t*, const T*,    \
-                                    const int8_t*, T*, T*, int*, cudaStream_t);
+#define INST(T)                                                                                                \
+  template void launch_init_xi<T>(const Geo&, const Body&, T*, cudaStream_t);                                   \
+  template void launch_extrapolate<T>(const Geo&, const Body&, const int*, int*, int, int*, int*, int, T*, T*,    \
+                                      int8_t*, int*, cudaStream_t);                                             \
+  template void launch_corrector<T>(const Geo&, const Body&, const int*, int, const int*, const int*, int,        \
+                                    const T*, const int8_t*, const T*, const int8_t*, T*, T*, int*, cudaStream_t);
 INST(float)
 INST(double)

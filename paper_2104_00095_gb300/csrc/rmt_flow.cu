@@ -35,11 +35,18 @@ __device__ __forceinline__ void cell_faces(const Geo& g, int e, int i, int j, in
 template <typename T>
 __device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int a, int d, int i, int j, int k) {
   T q[5];
+  if (inside<T>(g, d, i, j, k, 2)) {
+    const long c = (long)a * g.N + cidx(g, i, j, k);
+    const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
 #pragma unroll
-  for (int s = -2; s <= 2; s++) {
-    int ii[3] = {i, j, k};
-    ii[d] += s;
-    q[s + 2] = uval(g, u, a, ii[0], ii[1], ii[2]);
+    for (int s = -2; s <= 2; s++) q[s + 2] = u[c + s * st];
+  } else {
+#pragma unroll
+    for (int s = -2; s <= 2; s++) {
+      int ii[3] = {i, j, k};
+      ii[d] += s;
+      q[s + 2] = uval(g, u, a, ii[0], ii[1], ii[2]);
+    }
   }
   return lim_slope(q, 0x1Fu, T(1.0 / g.h));
 }
@@ -52,20 +59,19 @@ __device__ __forceinline__ bool is_wall_face(const Geo& g, int d, int f) {
 template <typename T>
 __global__ void k_bar(Geo g, int e, const T* __restrict__ u, T* __restrict__ ub0, T* __restrict__ ub1,
                       T* __restrict__ ub2, T* __restrict__ vadv) {
-  const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1);
-  const long nf = nfaces(g, e);
+  const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1), ez = g.n[2] + (e == 2);
   const T h = T(g.h), dt = T(g.dt);
   T* ub[3] = {ub0, ub1, ub2};
-  GRID_LOOP(f, nf) {
-    int i, j, k;
-    decode(f, ex, ey, i, j, k);
+  THREAD_XYZ(i, j, k);
+  if (i < ex && j < ey && k < ez) {
+    const long f = i + (long)ex * (j + (long)ey * k);
     const int fi = e == 0 ? i : (e == 1 ? j : k);
     if (is_wall_face(g, e, fi)) {
       const int face = fi == 0 ? 2 * e : 2 * e + 1;
 #pragma unroll
       for (int a = 0; a < 3; a++) ub[a][f] = T(g.wall[face][a]);
       vadv[f] = T(g.wall[face][e]);
-      continue;
+      return;
     }
     int lo[3] = {i, j, k};
     lo[e] -= 1;
@@ -95,19 +101,18 @@ struct BarPtrs {
 template <typename T>
 __global__ void k_face(Geo g, int d, const T* __restrict__ u, const T* __restrict__ p, const T* __restrict__ rho,
                        const T* __restrict__ divtau, BarPtrs bp) {
-  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
-  const long nf = nfaces(g, d);
+  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1), ez = g.n[2] + (d == 2);
   const T h = T(g.h), dt = T(g.dt), ih = T(1.0 / g.h);
   T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
-  GRID_LOOP(f, nf) {
-    int i, j, k;
-    decode(f, ex, ey, i, j, k);
+  THREAD_XYZ(i, j, k);
+  if (i < ex && j < ey && k < ez) {
+    const long f = i + (long)ex * (j + (long)ey * k);
     const int fi = d == 0 ? i : (d == 1 ? j : k);
     if (is_wall_face(g, d, fi)) {
       const int face = fi == 0 ? 2 * d : 2 * d + 1;
 #pragma unroll
       for (int a = 0; a < 3; a++) uf[a][f] = T(g.wall[face][a]);
-      continue;
+      return;
     }
     T st[2][3];
 #pragma unroll
@@ -181,27 +186,7 @@ __global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
 }
 
 template <typename T>
-__global__ void k_mac_beta(Geo g, int d, const T* __restrict__ rho, T* __restrict__ beta) {
-  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
-  GRID_LOOP(f, nfaces(g, d)) {
-    int i, j, k;
-    decode(f, ex, ey, i, j, k);
-    const int fi = d == 0 ? i : (d == 1 ? j : k);
-    if (is_wall_face(g, d, fi)) {
-      beta[f] = T(0);
-      continue;
-    }
-    int a[3] = {i, j, k};
-    a[d] -= 1;
-    long ca, cb;
-    cell_at(g, a[0], a[1], a[2], ca);
-    cell_at(g, i, j, k, cb);
-    beta[f] = T(2) / (rho[ca] + rho[cb]);
-  }
-}
-
-template <typename T>
-__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ beta,
+__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ rho,
                               const double* __restrict__ q, T* __restrict__ umac) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
   const T fac = T(0.5 * g.dt / g.h);
@@ -218,7 +203,9 @@ __global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* _
     long ca, cb;
     cell_at(g, a[0], a[1], a[2], ca);
     cell_at(g, i, j, k, cb);
-    umac[f] = un[f] - fac * beta[f] * (T)(q[cb] - q[ca]);
+    // face coefficient 1/rho_face, rho_face the mean of the two cells
+    const T beta = T(2) / (rho[ca] + rho[cb]);
+    umac[f] = un[f] - fac * beta * (T)(q[cb] - q[ca]);
   }
 }
 
@@ -322,11 +309,6 @@ __global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ u
 }
 
 template <typename T>
-__global__ void k_inv(long n, const T* __restrict__ rho, T* __restrict__ beta) {
-  GRID_LOOP(c, n) beta[c] = T(1) / rho[c];
-}
-
-template <typename T>
 __global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h,
                               const double* __restrict__ psi, T* __restrict__ u) {
   const double q4 = 0.25 / g.h;
@@ -368,7 +350,10 @@ __global__ void k_fill(T* a, T v, long n) {
 template <typename T>
 void launch_bar_states(const Geo& g, const T* u, T* const ubar[3][3], T* const vadv[3], cudaStream_t s) {
   for (int e = 0; e < 3; e++) {
-    k_bar<T><<<nblocks(nfaces(g, e)), TPB, 0, s>>>(g, e, u, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]); rmt_count_launches(1); }
+    const dim3 gr((g.n[0] + (e == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (e == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (e == 2));
+    k_bar<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, e, u, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]);
+    rmt_count_launches(1);
+  }
 }
 template <typename T>
 void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const ubar[3][3],
@@ -380,21 +365,25 @@ void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, cons
   }
   for (int d = 0; d < 3; d++) {
     for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
-    k_face<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, u, p, rho, divtau, bp); rmt_count_launches(1);
+    const dim3 gr((g.n[0] + (d == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (d == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (d == 2));
+    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, p, rho, divtau, bp);
+    rmt_count_launches(1);
   }
 }
 template <typename T>
-void launch_mac_setup(const Geo& g, T* const uf[3][3], const T* rho, double* b64, T* const beta[3], cudaStream_t s) {
+void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s) {
   FacePtrs3 un;
   for (int d = 0; d < 3; d++) un.p[d] = uf[d][d];
-  k_mac_rhs<T><<<nblocks(g.N), TPB, 0, s>>>(g, un, b64); rmt_count_launches(1);
-  for (int d = 0; d < 3; d++) { k_mac_beta<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, rho, beta[d]); rmt_count_launches(1); }
+  k_mac_rhs<T><<<nblocks(g.N), TPB, 0, s>>>(g, un, b64);
+  rmt_count_launches(1);
 }
 template <typename T>
-void launch_mac_correct(const Geo& g, T* const uf[3][3], T* const beta[3], const double* q, T* const umac[3],
+void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, const double* q, T* const umac[3],
                         cudaStream_t s) {
   for (int d = 0; d < 3; d++) {
-    k_mac_correct<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, uf[d][d], beta[d], q, umac[d]); rmt_count_launches(1); }
+    k_mac_correct<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, uf[d][d], rho, q, umac[d]);
+    rmt_count_launches(1);
+  }
 }
 template <typename T>
 void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s) {
@@ -415,9 +404,9 @@ void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* r
   k_ustar<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, adv, p, rho_h, divtau_h, ustar); rmt_count_launches(1);
 }
 template <typename T>
-void launch_fe_setup(const Geo& g, const T* u, const T* ustar, const T* rho_h, double* b64, T* beta, cudaStream_t s) {
-  k_fe_rhs<T><<<nblocks(g.NN), TPB, 0, s>>>(g, u, ustar, b64); rmt_count_launches(1);
-  k_inv<T><<<nblocks(g.N), TPB, 0, s>>>(g.N, rho_h, beta); rmt_count_launches(1);
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, double* b64, cudaStream_t s) {
+  k_fe_rhs<T><<<nblocks(g.NN), TPB, 0, s>>>(g, u, ustar, b64);
+  rmt_count_launches(1);
 }
 template <typename T>
 void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p, T* psi_out,
@@ -434,13 +423,13 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
   template void launch_bar_states<T>(const Geo&, const T*, T* const[3][3], T* const[3], cudaStream_t);            \
   template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[3][3],        \
                                       T* const[3], T* const[3][3], cudaStream_t);                                \
-  template void launch_mac_setup<T>(const Geo&, T* const[3][3], const T*, double*, T* const[3], cudaStream_t);    \
-  template void launch_mac_correct<T>(const Geo&, T* const[3][3], T* const[3], const double*, T* const[3],       \
+  template void launch_mac_setup<T>(const Geo&, T* const[3][3], double*, cudaStream_t);                          \
+  template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, const double*, T* const[3],          \
                                       cudaStream_t);                                                             \
   template void launch_advect<T>(const Geo&, T* const[3][3], T* const[3], T*, cudaStream_t);                      \
   template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, T*, cudaStream_t);          \
   template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, cudaStream_t); \
-  template void launch_fe_setup<T>(const Geo&, const T*, const T*, const T*, double*, T*, cudaStream_t);         \
+  template void launch_fe_setup<T>(const Geo&, const T*, const T*, double*, cudaStream_t);                      \
   template void launch_fe_update<T>(const Geo&, const T*, const T*, const double*, T*, T*, T*, cudaStream_t);    \
   template void launch_fill<T>(T*, T, long, cudaStream_t);
 

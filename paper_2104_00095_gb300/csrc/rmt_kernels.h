@@ -21,16 +21,15 @@ template <typename T>
 void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau,
                         T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
 template <typename T>
-void launch_mac_setup(const Geo& g, T* const uf[3][3], const T* rho, double* b64, T* const beta[3],
-                      cudaStream_t s);
+void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s);
 template <typename T>
-void launch_mac_correct(const Geo& g, T* const uf[3][3], T* const beta[3], const double* q, T* const umac[3],
+void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, const double* q, T* const umac[3],
                         cudaStream_t s);
 template <typename T>
 void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s);
 template <typename T>
 void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3],
-                       const T* x, const int8_t* lay, T* xn, cudaStream_t s);
+                       const int* bb, int blocks, const T* x, const int8_t* lay, T* xn, cudaStream_t s);
 template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho,
                     cudaStream_t s);
@@ -38,8 +37,7 @@ template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h,
                   T* ustar, cudaStream_t s);
 template <typename T>
-void launch_fe_setup(const Geo& g, const T* u, const T* ustar, const T* rho_h, double* b64, T* beta,
-                     cudaStream_t s);
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, double* b64, cudaStream_t s);
 template <typename T>
 void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p,
                       T* psi_out, cudaStream_t s);
@@ -49,12 +47,18 @@ void launch_fill(T* a, T v, long n, cudaStream_t s);
 // ---- extrapolation (rmt_extrap.cu) ------------------------------------------------
 template <typename T>
 void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s);
+// bb_in: band bounding box of the step (null: whole grid); bb_out receives the new band's box;
+// blocks: launch width for the body's window (kernels stride over the whole window); list and
+// count: device buffers for the compacted band (capacity: the grid), filled by
+// launch_extrapolate and read by launch_corrector of the same step; wls_blocks: launch width
+// of the one-warp-per-cell fits
 template <typename T>
-void launch_extrapolate(const Geo& g, const Body* bdev, const Body& b, T* x, T* phi, int8_t* lay,
-                        int* err, cudaStream_t s);
+void launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list, int* count,
+                        int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s);
 template <typename T>
-void launch_corrector(const Geo& g, const Body* bdev, const Body& b, const T* x, const int8_t* lay,
-                      const T* xn, const int8_t* layn, T* xh, T* phih, int* err, cudaStream_t s);
+void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, const int* count,
+                      int wls_blocks, const T* x, const int8_t* lay, const T* xn, const int8_t* layn, T* xh, T* phih,
+                      int* err, cudaStream_t s);
 
 // ---- multigrid (rmt_mg.cu) ----------------------------------------------------------
 struct MGSolver;  // opaque
@@ -63,7 +67,10 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err);
 void mg_destroy(MGSolver* m);
 double* mg_rhs(MGSolver* m);        // level-0 FP64 right-hand side (fill before solve)
 double* mg_solution(MGSolver* m);   // level-0 FP64 solution
-void* mg_coef0(MGSolver* m, int d); // level-0 coefficients: MAC d=0..2 face beta; FE d=0 cell beta
+// the cell density the operator is built from on the finest level (the caller's array, type T)
+void mg_set_density(MGSolver* m, const void* rho);
+// smoother sweeps before/after the coarse correction and the Jacobi weight (negative: keep)
+void mg_set_smoother(MGSolver* m, int pre, int post, double omega);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
 // hook(ctx, which, begin, stream) with which = 0 (smoother colour) or 1 (FP64 residual).
 typedef void (*mg_hook_fn)(void* ctx, int which, int begin, cudaStream_t s);

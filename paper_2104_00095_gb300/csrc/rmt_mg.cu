@@ -3,19 +3,22 @@
 // with its own multigrid library whose design it does not describe).
 //
 // kind 0 (MAC): cell-centred variable-coefficient 7-point operator
-//     (A q)_c = h^-2 sum_faces beta_f (q_c - q_nb),  beta_f = 1/rho_face, 0 on walls.
-// kind 1 (FE): nodal trilinear finite-element stiffness, beta = 1/rho per cell
-//     (K psi)_i = (h/12) sum_{cells c at i} beta_c (4 psi_i - sum of the 4 corners of c that
-//     differ from i in two or three coordinates).
-// Both operators are symmetric positive semi-definite with the constants as null space
-// (walls are Neumann, periodic axes wrap); right-hand sides and solutions are kept mean-free.
+//     (A q)_c = h^-2 sum_faces beta_f (q_c - q_nb),  beta_f = 2/(rho_a + rho_b), 0 on walls.
+// kind 1 (FE): nodal trilinear finite-element stiffness with beta_c = 1/rho_c per cell
+//     (K psi)_i = (h/12) sum_{cells c at i} beta_c (4 psi_i - the 4 corners of c that differ
+//     from i in two or three coordinates).
+// Both are symmetric positive semi-definite with the constants as null space (walls are
+// Neumann, periodic axes wrap); right-hand sides and solutions are kept mean-free.  The MAC
+// operator reads the cell density rho (the caller's array on the finest level); the FE operator
+// reads beta = 1/rho per cell, formed once per solve.  Coefficients are evaluated in the
+// storage type; the FP64 residual only accumulates in FP64, so it needs no FP64 division.
 //
-// Solve = iterative refinement: the residual of the FP64 iterate is formed in FP64 and a
-// V(2,2)-cycle in the storage type T (double or float) approximately solves for the
-// correction.  Smoothers: red-black Gauss-Seidel (7-point), 8-colour Gauss-Seidel
-// (27-point).  Transfers: averaging / trilinear (cell-centred), full weighting / trilinear
-// (nodal).  Coarse operators are re-discretised with averaged coefficients.  The coarsest
-// level is solved by one thread block with many smoothing sweeps.  All norms use fixed-order
+// Solve = iterative refinement: the residual of an FP64 iterate is formed in FP64 and a
+// V-cycle in the storage type T (double or float) computes the correction.  Smoothers:
+// red-black Gauss-Seidel (7-point; one thread per same-colour cell pair along x) and weighted
+// Jacobi (27-point; one fused pass per sweep).  Transfers: 8-cell average / trilinear
+// (cell-centred), full weighting / trilinear (nodal).  Coarse densities are 8-cell means.
+// The coarsest level is solved by one block with many sweeps.  Norms use fixed-order
 // two-stage reductions, so results are deterministic.
 #include <cstdio>
 #include <cstdlib>
@@ -28,6 +31,8 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int RED_BLOCKS = 1024;
+constexpr int BX = 32, BY = 4;
+
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
   if (b > 152L * 32) b = 152L * 32;
@@ -40,87 +45,100 @@ struct Lv {
   double h;
 };
 
-__device__ __forceinline__ void dec3(long c, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(c % nx);
-  long r = c / nx;
-  j = (int)(r % ny);
-  k = (int)(r / ny);
-}
+inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
+
 __device__ __forceinline__ long cix(const Lv& L, int i, int j, int k) { return i + (long)L.n[0] * (j + (long)L.n[1] * k); }
 __device__ __forceinline__ long nix(const Lv& L, int i, int j, int k) { return i + (long)L.nn[0] * (j + (long)L.nn[1] * k); }
-__device__ __forceinline__ long fix(const Lv& L, int d, int i, int j, int k) {
-  long e0 = L.n[0] + (d == 0), e1 = L.n[1] + (d == 1);
-  return i + e0 * (j + e1 * (long)k);
-}
-// neighbour cell along d (s = +-1): wrap on periodic axes, clamp at walls (face beta is 0 there)
-__device__ __forceinline__ int nbc(const Lv& L, int d, int i, int s) {
-  int v = i + s;
-  if (v < 0) return L.per[d] ? L.n[d] - 1 : 0;
-  if (v >= L.n[d]) return L.per[d] ? 0 : L.n[d] - 1;
+// neighbour cell index along d: wrap on periodic axes; -1 outside a wall
+__device__ __forceinline__ int cnb(const Lv& L, int d, int v) {
+  if (v < 0) return L.per[d] ? L.n[d] - 1 : -1;
+  if (v >= L.n[d]) return L.per[d] ? 0 : -1;
   return v;
 }
-// cell coordinate for the FE cell loop; false outside a wall
-__device__ __forceinline__ bool cellc(const Lv& L, int d, int& i) {
-  if (i >= 0 && i < L.n[d]) return true;
-  if (!L.per[d]) return false;
-  i = (i + L.n[d]) % L.n[d];
-  return true;
-}
-__device__ __forceinline__ int nodec(const Lv& L, int d, int i) {
-  if (L.per[d]) {
-    if (i >= L.nn[d]) i -= L.nn[d];
-    if (i < 0) i += L.nn[d];
-  }
-  return i;
+// neighbour node index along d: wrap on periodic axes; clamped on walls (its weight is 0 there)
+__device__ __forceinline__ int nnb(const Lv& L, int d, int v) {
+  if (v < 0) return L.per[d] ? L.nn[d] - 1 : 0;
+  if (v >= L.nn[d]) return L.per[d] ? 0 : L.nn[d] - 1;
+  return v;
 }
 
 // ----------------------------------------------------------------------------- operators
-// MAC: returns (A x)_c and the diagonal; XT: type of x, CT: type of coefficients
-template <typename XT, typename CT>
-__device__ __forceinline__ double mac_apply(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ bx,
-                                            const CT* __restrict__ by, const CT* __restrict__ bz, int i, int j, int k,
-                                            double& diag) {
-  const long c = cix(L, i, j, k);
-  const double b0 = bx[fix(L, 0, i, j, k)], b1 = bx[fix(L, 0, i + 1, j, k)];
-  const double b2 = by[fix(L, 1, i, j, k)], b3 = by[fix(L, 1, i, j + 1, k)];
-  const double b4 = bz[fix(L, 2, i, j, k)], b5 = bz[fix(L, 2, i, j, k + 1)];
-  const double off = b0 * (double)x[cix(L, nbc(L, 0, i, -1), j, k)] + b1 * (double)x[cix(L, nbc(L, 0, i, 1), j, k)] +
-                     b2 * (double)x[cix(L, i, nbc(L, 1, j, -1), k)] + b3 * (double)x[cix(L, i, nbc(L, 1, j, 1), k)] +
-                     b4 * (double)x[cix(L, i, j, nbc(L, 2, k, -1))] + b5 * (double)x[cix(L, i, j, nbc(L, 2, k, 1))];
-  diag = b0 + b1 + b2 + b3 + b4 + b5;
-  const double ih2 = 1.0 / (L.h * L.h);
-  diag *= ih2;
-  return diag * (double)x[c] - off * ih2;
+// MAC face coefficient 2/(rho_a + rho_b) in the coefficient type; FAST: approximate reciprocal
+// (smoothers only)
+template <bool FAST, typename CT>
+__device__ __forceinline__ CT face_beta(CT ra, CT rb) {
+  if constexpr (FAST && sizeof(CT) == 4) return __fdividef(2.0f, ra + rb);
+  return CT(2) / (ra + rb);
 }
 
-// FE: returns (K x)_i and the diagonal
-template <typename XT, typename CT>
-__device__ __forceinline__ double fe_apply(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ beta, int i,
-                                           int j, int k, double& diag) {
-  const double xi = (double)x[nix(L, i, j, k)];
-  double acc = 0.0, bs = 0.0;
+// MAC at cell (i,j,k): returns (A x)_c (in AT) and its diagonal
+template <typename AT, bool FAST = false, typename XT, typename CT>
+__device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ rho, int i, int j,
+                                     int k, AT& diag) {
+  const long c = cix(L, i, j, k);
+  const CT rc = rho[c];
+  AT off = AT(0), dg = AT(0);
+  const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
 #pragma unroll
-  for (int s = 0; s < 8; s++) {
-    const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-    int ci = i - 1 + sx, cj = j - 1 + sy, ck = k - 1 + sz;
-    if (!cellc(L, 0, ci) || !cellc(L, 1, cj) || !cellc(L, 2, ck)) continue;
-    const double b = (double)beta[cix(L, ci, cj, ck)];
-    // node i sits at local corner (1-sx, 1-sy, 1-sz) of this cell; the corners differing in
-    // two or three coordinates are the ones with at least two flipped bits
-    const int qi = (1 - sx) | ((1 - sy) << 1) | ((1 - sz) << 2);
-    double so = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      if (__popc(q ^ qi) < 2) continue;
-      const int ni = nodec(L, 0, ci + (q & 1)), nj = nodec(L, 1, cj + ((q >> 1) & 1)), nk = nodec(L, 2, ck + ((q >> 2) & 1));
-      so += (double)x[nix(L, ni, nj, nk)];
-    }
-    acc += b * (4.0 * xi - so);
-    bs += b;
+  for (int f = 0; f < 6; f++) {
+    const int d = f >> 1;
+    const int v = cnb(L, d, nb[f][d]);
+    if (v < 0) continue;
+    int q[3] = {i, j, k};
+    q[d] = v;
+    const long cn = cix(L, q[0], q[1], q[2]);
+    const AT beta = (AT)face_beta<FAST>(rc, rho[cn]);
+    off += beta * (AT)x[cn];
+    dg += beta;
   }
-  const double s12 = L.h / 12.0;
-  diag = 4.0 * bs * s12;
-  return acc * s12;
+  const AT ih2 = AT(1.0 / (L.h * L.h));
+  diag = dg * ih2;
+  return (dg * (AT)x[c] - off) * ih2;
+}
+
+// FE at node (i,j,k): returns (K x)_i and its diagonal
+template <typename AT, typename XT, typename CT>
+__device__ __forceinline__ AT fe_op(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ beta, int i, int j,
+                                    int k, AT& diag) {
+  AT b[2][2][2];
+  AT bs = AT(0);
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+      for (int sx = 0; sx < 2; sx++) {
+        const int ci = cnb(L, 0, i - 1 + sx), cj = cnb(L, 1, j - 1 + sy), ck = cnb(L, 2, k - 1 + sz);
+        AT v = AT(0);
+        if (ci >= 0 && cj >= 0 && ck >= 0) v = (AT)beta[cix(L, ci, cj, ck)];
+        b[sx][sy][sz] = v;
+        bs += v;
+      }
+  const int X[2] = {nnb(L, 0, i - 1), nnb(L, 0, i + 1)};
+  const int Y[2] = {nnb(L, 1, j - 1), nnb(L, 1, j + 1)};
+  const int Z[2] = {nnb(L, 2, k - 1), nnb(L, 2, k + 1)};
+  AT s = AT(0);
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+      for (int sx = 0; sx < 2; sx++) s += b[sx][sy][sz] * (AT)x[nix(L, X[sx], Y[sy], Z[sz])];  // body diagonals
+#pragma unroll
+  for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+    for (int sx = 0; sx < 2; sx++) s += (b[sx][sy][0] + b[sx][sy][1]) * (AT)x[nix(L, X[sx], Y[sy], k)];  // xy
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sx = 0; sx < 2; sx++) s += (b[sx][0][sz] + b[sx][1][sz]) * (AT)x[nix(L, X[sx], j, Z[sz])];  // xz
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++) s += (b[0][sy][sz] + b[1][sy][sz]) * (AT)x[nix(L, i, Y[sy], Z[sz])];  // yz
+  const AT s12 = AT(L.h / 12.0);
+  diag = AT(4) * bs * s12;
+  return (AT(4) * bs * (AT)x[nix(L, i, j, k)] - s) * s12;
 }
 
 // ----------------------------------------------------------------------------- kernels
@@ -129,39 +147,201 @@ __global__ void k_zero(T* a, long n) {
   GRID_LOOP(i, n) a[i] = T(0);
 }
 
-// FP64 residual r = b - A x of the FP64 iterate; writes the T copy for the V-cycle and
-// per-block partial sums of r^2
-template <typename CT>
-__global__ void k_resid64(Lv L, int kind, const double* __restrict__ x, const double* __restrict__ b,
-                          const CT* __restrict__ c0, const CT* __restrict__ c1, const CT* __restrict__ c2,
-                          CT* __restrict__ rT, double* __restrict__ part) {
-  __shared__ double sh[TPB / 32];
-  double loc = 0.0;
-  GRID_LOOP(u, L.nunk) {
-    int i, j, k;
-    double dg, ax;
-    if (kind == 0) {
-      dec3(u, L.n[0], L.n[1], i, j, k);
-      ax = mac_apply(L, x, c0, c1, c2, i, j, k, dg);
-    } else {
-      dec3(u, L.nn[0], L.nn[1], i, j, k);
-      ax = fe_apply(L, x, c0, i, j, k, dg);
-    }
-    const double r = b[u] - ax;
-    rT[u] = (CT)r;
-    loc += r * r;
-  }
+__device__ __forceinline__ bool thread_cell(const int ext[3], int& i, int& j, int& k) {
+  i = blockIdx.x * BX + threadIdx.x;
+  j = blockIdx.y * BY + threadIdx.y;
+  k = blockIdx.z;
+  return i < ext[0] && j < ext[1];
+}
+
+__device__ __forceinline__ void block_partial(double loc, double* part) {
+  __shared__ double sh[BX * BY / 32];
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = loc;
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) sh[t >> 5] = loc;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     double s = 0.0;
-    for (int w = 0; w < TPB / 32; w++) s += sh[w];
-    part[blockIdx.x] = s;
+    for (int w = 0; w < BX * BY / 32; w++) s += sh[w];
+    part[((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
   }
 }
 
-// sum (mode 0) or sum of squares (mode 1) of a vector: per-block partials
+// FP64 residual r = b - A x of the FP64 iterate (FP64 arithmetic); writes the T copy for the
+// V-cycle and per-block partial sums of r^2
+template <typename CT>
+__global__ void __launch_bounds__(BX* BY) k_resid64(Lv L, int kind, const double* __restrict__ x,
+                                                     const double* __restrict__ b, const CT* __restrict__ rho,
+                                                     CT* __restrict__ rT, double* __restrict__ part) {
+  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
+  int i, j, k;
+  double loc = 0.0;
+  if (thread_cell(ext, i, j, k)) {
+    double dg;
+    const double ax = kind == 0 ? mac_op<double>(L, x, rho, i, j, k, dg) : fe_op<double>(L, x, rho, i, j, k, dg);
+    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const double r = b[u] - ax;
+    rT[u] = (CT)r;
+    loc = r * r;
+  }
+  block_partial(loc, part);
+}
+
+// red-black Gauss-Seidel colour pass (7-point): each thread updates the cell of this colour
+// among x = 2p and 2p+1 of its row
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_rbgs(Lv L, int colour, T* __restrict__ x, const T* __restrict__ b,
+                                                  const T* __restrict__ rho) {
+  const int p = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (j >= L.n[1]) return;
+  const int i = 2 * p + ((j + k + colour) & 1);
+  if (i >= L.n[0]) return;
+  T dg;
+  const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
+  const long c = cix(L, i, j, k);
+  if (dg > T(0)) x[c] = x[c] + (b[c] - ax) / dg;
+}
+
+// weighted Jacobi pass (27-point): xo = xi + w (b - K xi)/diag
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_jacobi(Lv L, T w, const T* __restrict__ xi, T* __restrict__ xo,
+                                                    const T* __restrict__ b, const T* __restrict__ rho) {
+  int i, j, k;
+  if (!thread_cell(L.nn, i, j, k)) return;
+  T dg;
+  const T ax = fe_op<T>(L, xi, rho, i, j, k, dg);
+  const long u = nix(L, i, j, k);
+  xo[u] = dg > T(0) ? xi[u] + w * (b[u] - ax) / dg : xi[u];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b,
+                                                   const T* __restrict__ rho, T* __restrict__ r) {
+  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
+  int i, j, k;
+  if (!thread_cell(ext, i, j, k)) return;
+  T dg;
+  const T ax = kind == 0 ? mac_op<T>(L, x, rho, i, j, k, dg) : fe_op<T>(L, x, rho, i, j, k, dg);
+  const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+  r[u] = b[u] - ax;
+}
+
+// restriction of the residual to the coarse right-hand side (coarse x zeroed)
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
+                                                      T* __restrict__ bc, T* __restrict__ xc) {
+  const int ext[3] = {kind == 0 ? C.n[0] : C.nn[0], kind == 0 ? C.n[1] : C.nn[1], kind == 0 ? C.n[2] : C.nn[2]};
+  int I, J, K;
+  if (!thread_cell(ext, I, J, K)) return;
+  T s = T(0);
+  if (kind == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) s += rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
+    s *= T(0.125);
+  } else {
+    for (int oz = -1; oz <= 1; oz++)
+      for (int oy = -1; oy <= 1; oy++)
+        for (int ox = -1; ox <= 1; ox++) {
+          int ff[3] = {2 * I + ox, 2 * J + oy, 2 * K + oz};
+          bool in = true;
+#pragma unroll
+          for (int d = 0; d < 3; d++) {
+            if (ff[d] < 0 || ff[d] >= F.nn[d]) {
+              if (F.per[d]) ff[d] = ff[d] < 0 ? ff[d] + F.nn[d] : ff[d] - F.nn[d];
+              else in = false;
+            }
+          }
+          if (!in) continue;
+          const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+          s += w * rf[nix(F, ff[0], ff[1], ff[2])];
+        }
+  }
+  const long u = I + (long)ext[0] * (J + (long)ext[1] * K);
+  bc[u] = s;
+  xc[u] = T(0);
+}
+
+// trilinear prolongation of the coarse correction, added to the fine iterate
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong(Lv F, Lv C, int kind, const T* __restrict__ xc,
+                                                     T* __restrict__ xf) {
+  const int ext[3] = {kind == 0 ? F.n[0] : F.nn[0], kind == 0 ? F.n[1] : F.nn[1], kind == 0 ? F.n[2] : F.nn[2]};
+  int i, j, k;
+  if (!thread_cell(ext, i, j, k)) return;
+  const int ff[3] = {i, j, k};
+  T v = T(0);
+  if (kind == 0) {
+    int own[3], oth[3];
+    T wo[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      own[d] = ff[d] >> 1;
+      int o = own[d] + ((ff[d] & 1) ? 1 : -1);
+      wo[d] = T(0.75);
+      if (o < 0 || o >= C.n[d]) {
+        if (C.per[d]) {
+          o = o < 0 ? o + C.n[d] : o - C.n[d];
+        } else {
+          o = own[d];
+          wo[d] = T(1);  // Neumann: the mirror value equals the boundary cell
+        }
+      }
+      oth[d] = o;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
+      const T w = (sx ? T(1) - wo[0] : wo[0]) * (sy ? T(1) - wo[1] : wo[1]) * (sz ? T(1) - wo[2] : wo[2]);
+      if (w == T(0)) continue;
+      v += w * xc[cix(C, sx ? oth[0] : own[0], sy ? oth[1] : own[1], sz ? oth[2] : own[2])];
+    }
+  } else {
+    int lo[3], hi[3];
+    T wl[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      lo[d] = ff[d] >> 1;
+      if (ff[d] & 1) {
+        hi[d] = lo[d] + 1;
+        if (C.per[d] && hi[d] >= C.nn[d]) hi[d] -= C.nn[d];
+        wl[d] = T(0.5);
+      } else {
+        hi[d] = lo[d];
+        wl[d] = T(1);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
+      const T w = (sx ? T(1) - wl[0] : wl[0]) * (sy ? T(1) - wl[1] : wl[1]) * (sz ? T(1) - wl[2] : wl[2]);
+      if (w == T(0)) continue;
+      v += w * xc[nix(C, sx ? hi[0] : lo[0], sy ? hi[1] : lo[1], sz ? hi[2] : lo[2])];
+    }
+  }
+  const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+  xf[u] += v;
+}
+
+// FE coefficient beta = 1/rho per cell (finest level)
+template <typename T>
+__global__ void k_inv(long n, const T* __restrict__ rho, T* __restrict__ beta) {
+  GRID_LOOP(i, n) beta[i] = T(1) / rho[i];
+}
+
+// coarse coefficient (MAC: density, FE: beta) = mean of the 8 fine cells
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_coarsen(Lv F, Lv C, const T* __restrict__ rf, T* __restrict__ rc) {
+  int I, J, K;
+  if (!thread_cell(C.n, I, J, K)) return;
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < 8; q++) s += rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
+  rc[cix(C, I, J, K)] = T(0.125) * s;
+}
+
+// sum (mode 0) or sum of squares (mode 1): per-block partials
 template <typename XT>
 __global__ void k_partial(const XT* __restrict__ a, long n, int mode, double* __restrict__ part) {
   __shared__ double sh[TPB / 32];
@@ -181,7 +361,8 @@ __global__ void k_partial(const XT* __restrict__ a, long n, int mode, double* __
 }
 
 // final fixed-order sum of the partials (one block); out = scale * sum
-__global__ void k_final(const double* __restrict__ part, int np, double scale, double* __restrict__ out) {
+__global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part, int np, double scale,
+                                                double* __restrict__ out) {
   __shared__ double sh[1024];
   double loc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) loc += part[i];
@@ -201,193 +382,18 @@ __global__ void k_sub_scalar(XT* __restrict__ a, long n, const double* __restric
 }
 
 template <typename T>
-__global__ void k_copy_to64(const T* __restrict__ a, double* __restrict__ b, long n, int add) {
-  GRID_LOOP(i, n) b[i] = add ? b[i] + (double)a[i] : (double)a[i];
-}
-
-// one colour of the smoother: MAC red-black (colour = (i+j+k)&1); FE 8 colours
-template <typename T>
-__global__ void k_smooth(Lv L, int kind, int colour, T* __restrict__ x, const T* __restrict__ b,
-                         const T* __restrict__ c0, const T* __restrict__ c1, const T* __restrict__ c2) {
-  if (kind == 0) {
-    GRID_LOOP(u, L.ncell) {
-      int i, j, k;
-      dec3(u, L.n[0], L.n[1], i, j, k);
-      if (((i + j + k) & 1) != colour) continue;
-      double dg;
-      const double ax = mac_apply(L, x, c0, c1, c2, i, j, k, dg);
-      if (dg > 0.0) x[u] = (T)((double)x[u] + ((double)b[u] - ax) / dg);
-    }
-  } else {
-    const int cx = colour & 1, cy = (colour >> 1) & 1, cz = (colour >> 2) & 1;
-    const int mx = (L.nn[0] - cx + 1) / 2, my = (L.nn[1] - cy + 1) / 2, mz = (L.nn[2] - cz + 1) / 2;
-    GRID_LOOP(t, (long)mx * my * mz) {
-      int a, bb, cc;
-      dec3(t, mx, my, a, bb, cc);
-      const int i = 2 * a + cx, j = 2 * bb + cy, k = 2 * cc + cz;
-      double dg;
-      const double ax = fe_apply(L, x, c0, i, j, k, dg);
-      const long u = nix(L, i, j, k);
-      if (dg > 0.0) x[u] = (T)((double)x[u] + ((double)b[u] - ax) / dg);
-    }
-  }
-}
-
-template <typename T>
-__global__ void k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ c0,
-                        const T* __restrict__ c1, const T* __restrict__ c2, T* __restrict__ r) {
-  GRID_LOOP(u, L.nunk) {
-    int i, j, k;
-    double dg, ax;
-    if (kind == 0) {
-      dec3(u, L.n[0], L.n[1], i, j, k);
-      ax = mac_apply(L, x, c0, c1, c2, i, j, k, dg);
-    } else {
-      dec3(u, L.nn[0], L.nn[1], i, j, k);
-      ax = fe_apply(L, x, c0, i, j, k, dg);
-    }
-    r[u] = (T)((double)b[u] - ax);
-  }
-}
-
-// restriction of the residual to the coarse right-hand side (coarse x zeroed)
-template <typename T>
-__global__ void k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf, T* __restrict__ bc, T* __restrict__ xc) {
-  GRID_LOOP(u, C.nunk) {
-    int I, J, K;
-    double s = 0.0;
-    if (kind == 0) {
-      dec3(u, C.n[0], C.n[1], I, J, K);
-#pragma unroll
-      for (int q = 0; q < 8; q++) s += (double)rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
-      s *= 0.125;
-    } else {
-      dec3(u, C.nn[0], C.nn[1], I, J, K);
-      for (int oz = -1; oz <= 1; oz++)
-        for (int oy = -1; oy <= 1; oy++)
-          for (int ox = -1; ox <= 1; ox++) {
-            int fi = 2 * I + ox, fj = 2 * J + oy, fk = 2 * K + oz;
-            bool in = true;
-            int ff[3] = {fi, fj, fk};
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-              if (F.per[d]) ff[d] = (ff[d] + F.nn[d]) % F.nn[d];
-              else if (ff[d] < 0 || ff[d] >= F.nn[d]) in = false;
-            }
-            if (!in) continue;
-            const double w = (ox ? 0.5 : 1.0) * (oy ? 0.5 : 1.0) * (oz ? 0.5 : 1.0);
-            s += w * (double)rf[nix(F, ff[0], ff[1], ff[2])];
-          }
-    }
-    bc[u] = (T)s;
-    xc[u] = T(0);
-  }
-}
-
-// trilinear prolongation of the coarse correction, added to the fine iterate
-template <typename T>
-__global__ void k_prolong(Lv F, Lv C, int kind, const T* __restrict__ xc, T* __restrict__ xf) {
-  GRID_LOOP(u, F.nunk) {
-    int i, j, k;
-    double v = 0.0;
-    if (kind == 0) {
-      dec3(u, F.n[0], F.n[1], i, j, k);
-      const int ff[3] = {i, j, k};
-      int own[3], oth[3];
-      double wo[3];
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        own[d] = ff[d] >> 1;
-        int o = own[d] + ((ff[d] & 1) ? 1 : -1);
-        if (o < 0 || o >= C.n[d]) {
-          if (C.per[d]) {
-            o = (o + C.n[d]) % C.n[d];
-            wo[d] = 0.75;
-          } else {
-            o = own[d];
-            wo[d] = 1.0;  // Neumann: the mirror value equals the boundary cell
-          }
-        } else {
-          wo[d] = 0.75;
-        }
-        oth[d] = o;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
-        const double w = (sx ? 1.0 - wo[0] : wo[0]) * (sy ? 1.0 - wo[1] : wo[1]) * (sz ? 1.0 - wo[2] : wo[2]);
-        if (w == 0.0) continue;
-        v += w * (double)xc[cix(C, sx ? oth[0] : own[0], sy ? oth[1] : own[1], sz ? oth[2] : own[2])];
-      }
-    } else {
-      dec3(u, F.nn[0], F.nn[1], i, j, k);
-      const int ff[3] = {i, j, k};
-      int lo[3], hi[3];
-      double wl[3];
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        lo[d] = ff[d] >> 1;
-        if (ff[d] & 1) {
-          hi[d] = lo[d] + 1;
-          if (C.per[d] && hi[d] >= C.nn[d]) hi[d] -= C.nn[d];
-          wl[d] = 0.5;
-        } else {
-          hi[d] = lo[d];
-          wl[d] = 1.0;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
-        const double w = (sx ? 1.0 - wl[0] : wl[0]) * (sy ? 1.0 - wl[1] : wl[1]) * (sz ? 1.0 - wl[2] : wl[2]);
-        if (w == 0.0) continue;
-        v += w * (double)xc[nix(C, sx ? hi[0] : lo[0], sy ? hi[1] : lo[1], sz ? hi[2] : lo[2])];
-      }
-    }
-    xf[u] = (T)((double)xf[u] + v);
-  }
-}
-
-// coarse coefficients: MAC face beta = mean of the 4 fine faces; FE cell beta = mean of 8
-template <typename T>
-__global__ void k_coarsen_mac(Lv F, Lv C, int d, const T* __restrict__ bf, T* __restrict__ bc) {
-  const int ex = C.n[0] + (d == 0), ey = C.n[1] + (d == 1);
-  const long nf = C.ncell / C.n[d] * (C.n[d] + 1);
-  GRID_LOOP(f, nf) {
-    int I, J, K;
-    dec3(f, ex, ey, I, J, K);
-    int base[3] = {2 * I, 2 * J, 2 * K};
-    double s = 0.0;
-    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int c3[3] = {base[0], base[1], base[2]};
-      c3[e1] += q & 1;
-      c3[e2] += (q >> 1) & 1;
-      s += (double)bf[fix(F, d, c3[0], c3[1], c3[2])];
-    }
-    bc[f] = (T)(0.25 * s);
-  }
-}
-template <typename T>
-__global__ void k_coarsen_fe(Lv F, Lv C, const T* __restrict__ bf, T* __restrict__ bc) {
-  GRID_LOOP(u, C.ncell) {
-    int I, J, K;
-    dec3(u, C.n[0], C.n[1], I, J, K);
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; q++) s += (double)bf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
-    bc[u] = (T)(0.125 * s);
-  }
+__global__ void k_add_to64(const T* __restrict__ a, double* __restrict__ b, long n) {
+  GRID_LOOP(i, n) b[i] += (double)a[i];
 }
 
 // coarsest level: one block, mean-free right-hand side, many smoothing sweeps, mean-free result
+constexpr int COARSE_TPB = 512;
 template <typename T>
-__global__ void k_coarse_solve(Lv L, int kind, int sweeps, T* __restrict__ x, T* __restrict__ b, const T* __restrict__ c0,
-                               const T* __restrict__ c1, const T* __restrict__ c2) {
+__global__ void __launch_bounds__(COARSE_TPB) k_coarse_solve(Lv L, int kind, int sweeps, T w, T* __restrict__ x,
+                                                             T* __restrict__ xt,
+                               T* __restrict__ b, const T* __restrict__ rho) {
   __shared__ double sh[1024];
   __shared__ double mean;
-  // mean of b
   double loc = 0.0;
   for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) loc += (double)b[u];
   sh[threadIdx.x] = loc;
@@ -403,23 +409,28 @@ __global__ void k_coarse_solve(Lv L, int kind, int sweeps, T* __restrict__ x, T*
     x[u] = T(0);
   }
   __syncthreads();
-  const int ncol = kind == 0 ? 2 : 8;
+  const int ex = kind == 0 ? L.n[0] : L.nn[0], ey = kind == 0 ? L.n[1] : L.nn[1];
   for (int it = 0; it < sweeps; it++) {
-    for (int col = 0; col < ncol; col++) {
-      for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
-        int i, j, k;
-        double dg, ax;
-        if (kind == 0) {
-          dec3(u, L.n[0], L.n[1], i, j, k);
+    if (kind == 0) {
+      for (int col = 0; col < 2; col++) {
+        for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
+          const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
           if (((i + j + k) & 1) != col) continue;
-          ax = mac_apply(L, x, c0, c1, c2, i, j, k, dg);
-        } else {
-          dec3(u, L.nn[0], L.nn[1], i, j, k);
-          if (((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) != col) continue;
-          ax = fe_apply(L, x, c0, i, j, k, dg);
+          T dg;
+          const T ax = mac_op<T>(L, x, rho, i, j, k, dg);
+          if (dg > T(0)) x[u] = x[u] + (b[u] - ax) / dg;
         }
-        if (dg > 0.0) x[u] = (T)((double)x[u] + ((double)b[u] - ax) / dg);
+        __syncthreads();
       }
+    } else {
+      for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
+        const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
+        T dg;
+        const T ax = fe_op<T>(L, x, rho, i, j, k, dg);
+        xt[u] = dg > T(0) ? x[u] + w * (b[u] - ax) / dg : x[u];
+      }
+      __syncthreads();
+      for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) x[u] = xt[u];
       __syncthreads();
     }
   }
@@ -443,12 +454,16 @@ struct MGSolver {
   int kind = 0, fp32 = 0, nlev = 0;
   Lv lv[16];
   void* x[16] = {};
+  void* xt[16] = {};
   void* b[16] = {};
   void* r[16] = {};
-  void* c[16][3] = {};
+  void* rho[16] = {};  // per-level coefficient: MAC density (level 0: the caller's array), FE beta
+  const void* rho_in = nullptr;
   double *x64 = nullptr, *b64 = nullptr, *part = nullptr, *scal = nullptr;
   double* hpin = nullptr;
   size_t esz = 8;
+  int pre = 2, post = 2;
+  double omega = 0.8;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
 };
@@ -457,12 +472,11 @@ void mg_set_hook(MGSolver* m, mg_hook_fn fn, void* ctx) {
   m->hook = fn;
   m->hook_ctx = ctx;
 }
-
-namespace {
-inline void hk(MGSolver* m, int l, int which, int begin, cudaStream_t s) {
-  if (m->hook && l == 0) m->hook(m->hook_ctx, which, begin, s);
+void mg_set_smoother(MGSolver* m, int pre, int post, double omega) {
+  if (pre >= 0) m->pre = pre;
+  if (post >= 0) m->post = post;
+  if (omega > 0) m->omega = omega;
 }
-}  // namespace
 
 static cudaError_t dmalloc(void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
@@ -475,6 +489,7 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
   m->kind = kind;
   m->fp32 = prec_fp32;
   m->esz = prec_fp32 ? 4 : 8;
+  m->omega = kind == 0 ? 1.0 : 0.8;
   Lv L;
   for (int d = 0; d < 3; d++) {
     L.n[d] = g.n[d];
@@ -491,14 +506,10 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     m->nlev = l + 1;
     const size_t vb = (size_t)L.nunk * m->esz;
     if (e == cudaSuccess) e = dmalloc(&m->x[l], vb);
+    if (e == cudaSuccess) e = dmalloc(&m->xt[l], vb);
     if (e == cudaSuccess) e = dmalloc(&m->b[l], vb);
     if (e == cudaSuccess) e = dmalloc(&m->r[l], vb);
-    if (kind == 0) {
-      for (int d = 0; d < 3 && e == cudaSuccess; d++)
-        e = dmalloc(&m->c[l][d], (size_t)(L.ncell / L.n[d] * (L.n[d] + 1)) * m->esz);
-    } else if (e == cudaSuccess) {
-      e = dmalloc(&m->c[l][0], (size_t)L.ncell * m->esz);
-    }
+    if (e == cudaSuccess && (l > 0 || kind == 1)) e = dmalloc(&m->rho[l], (size_t)L.ncell * m->esz);
     // coarsen while every axis halves to an even-enough size
     bool can = true;
     for (int d = 0; d < 3; d++) {
@@ -510,9 +521,10 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     L.h *= 2.0;
   }
   const Lv& L0 = m->lv[0];
+  const long nbr = (long)((L0.nn[0] + BX - 1) / BX) * ((L0.nn[1] + BY - 1) / BY) * L0.nn[2];
   if (e == cudaSuccess) e = dmalloc((void**)&m->x64, L0.nunk * sizeof(double));
   if (e == cudaSuccess) e = dmalloc((void**)&m->b64, L0.nunk * sizeof(double));
-  if (e == cudaSuccess) e = dmalloc((void**)&m->part, RED_BLOCKS * sizeof(double));
+  if (e == cudaSuccess) e = dmalloc((void**)&m->part, (size_t)(nbr > RED_BLOCKS ? nbr : RED_BLOCKS) * sizeof(double));
   if (e == cudaSuccess) e = dmalloc((void**)&m->scal, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->hpin, 8 * sizeof(double));
   if (err) *err = e;
@@ -523,9 +535,10 @@ void mg_destroy(MGSolver* m) {
   if (!m) return;
   for (int l = 0; l < m->nlev; l++) {
     cudaFree(m->x[l]);
+    cudaFree(m->xt[l]);
     cudaFree(m->b[l]);
     cudaFree(m->r[l]);
-    for (int d = 0; d < 3; d++) cudaFree(m->c[l][d]);
+    if (l > 0 || m->kind == 1) cudaFree(m->rho[l]);
   }
   cudaFree(m->x64);
   cudaFree(m->b64);
@@ -537,77 +550,105 @@ void mg_destroy(MGSolver* m) {
 
 double* mg_rhs(MGSolver* m) { return m->b64; }
 double* mg_solution(MGSolver* m) { return m->x64; }
-void* mg_coef0(MGSolver* m, int d) { return m->c[0][d]; }
+void mg_set_density(MGSolver* m, const void* rho) {
+  m->rho_in = rho;
+  if (m->kind == 0) m->rho[0] = (void*)rho;
+}
 
 namespace {
+
+inline void hk(MGSolver* m, int l, int which, int begin, cudaStream_t s) {
+  if (m->hook && l == 0) m->hook(m->hook_ctx, which, begin, s);
+}
 
 template <typename T>
 void sum_into(MGSolver* m, const T* a, long n, int mode, double scale, double* out, cudaStream_t s) {
   int nb = nblocks(n);
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
-  k_partial<T><<<nb, TPB, 0, s>>>(a, n, mode, m->part); rmt_count_launches(1);
-  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out); rmt_count_launches(1);
+  k_partial<T><<<nb, TPB, 0, s>>>(a, n, mode, m->part);
+  rmt_count_launches(1);
+  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out);
+  rmt_count_launches(1);
+}
+
+template <typename T>
+void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
+  const Lv& L = m->lv[l];
+  const T* b = (const T*)m->b[l];
+  const T* rho = (const T*)m->rho[l];
+  for (int it = 0; it < sweeps; it++) {
+    if (m->kind == 0) {
+      const dim3 gr((L.n[0] / 2 + 1 + BX - 1) / BX, (L.n[1] + BY - 1) / BY, L.n[2]);
+      for (int q = 0; q < 2; q++) {
+        const int col = forward ? q : 1 - q;
+        hk(m, l, 0, 1, s);
+        k_rbgs<T><<<gr, dim3(BX, BY), 0, s>>>(L, col, (T*)m->x[l], b, rho);
+        rmt_count_launches(1);
+        hk(m, l, 0, 0, s);
+      }
+    } else {
+      hk(m, l, 0, 1, s);
+      k_jacobi<T><<<grid3(L.nn[0], L.nn[1], L.nn[2]), dim3(BX, BY), 0, s>>>(L, T(m->omega), (const T*)m->x[l],
+                                                                              (T*)m->xt[l], b, rho);
+      rmt_count_launches(1);
+      hk(m, l, 0, 0, s);
+      void* t = m->x[l];
+      m->x[l] = m->xt[l];
+      m->xt[l] = t;
+    }
+  }
 }
 
 template <typename T>
 void vcycle(MGSolver* m, int l, cudaStream_t s) {
   const Lv& L = m->lv[l];
-  T* x = (T*)m->x[l];
-  T* b = (T*)m->b[l];
-  const T* c0 = (const T*)m->c[l][0];
-  const T* c1 = (const T*)m->c[l][1];
-  const T* c2 = (const T*)m->c[l][2];
-  const int ncol = m->kind == 0 ? 2 : 8;
   if (l == m->nlev - 1) {
     int nmax = L.n[0];
     if (L.n[1] > nmax) nmax = L.n[1];
     if (L.n[2] > nmax) nmax = L.n[2];
-    const int sweeps = 2 * nmax * nmax + 20;
-    k_coarse_solve<T><<<1, 1024, 0, s>>>(L, m->kind, sweeps, x, b, c0, c1, c2); rmt_count_launches(1);
+    const int sweeps = (m->kind == 0 ? 2 : 4) * nmax * nmax + 20;
+    k_coarse_solve<T><<<1, COARSE_TPB, 0, s>>>(L, m->kind, sweeps, T(m->omega), (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
+                                         (const T*)m->rho[l]);
+    rmt_count_launches(1);
     return;
   }
-  const int nb = nblocks(L.nunk);
-  for (int it = 0; it < 2; it++)
-    for (int col = 0; col < ncol; col++) {
-      hk(m, l, 0, 1, s);
-      k_smooth<T><<<nb, TPB, 0, s>>>(L, m->kind, col, x, b, c0, c1, c2);
-      rmt_count_launches(1);
-      hk(m, l, 0, 0, s);
-    }
-  k_resid<T><<<nb, TPB, 0, s>>>(L, m->kind, x, b, c0, c1, c2, (T*)m->r[l]); rmt_count_launches(1);
+  const int ex = m->kind == 0 ? L.n[0] : L.nn[0], ey = m->kind == 0 ? L.n[1] : L.nn[1],
+            ez = m->kind == 0 ? L.n[2] : L.nn[2];
+  smooth<T>(m, l, m->pre, true, s);
+  k_resid<T><<<grid3(ex, ey, ez), dim3(BX, BY), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
+                                                        (const T*)m->rho[l], (T*)m->r[l]);
+  rmt_count_launches(1);
   const Lv& C = m->lv[l + 1];
-  k_restrict<T><<<nblocks(C.nunk), TPB, 0, s>>>(L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1], (T*)m->x[l + 1]); rmt_count_launches(1);
+  const int cx = m->kind == 0 ? C.n[0] : C.nn[0], cy = m->kind == 0 ? C.n[1] : C.nn[1],
+            cz = m->kind == 0 ? C.n[2] : C.nn[2];
+  k_restrict<T><<<grid3(cx, cy, cz), dim3(BX, BY), 0, s>>>(L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1],
+                                                           (T*)m->x[l + 1]);
+  rmt_count_launches(1);
   vcycle<T>(m, l + 1, s);
-  k_prolong<T><<<nb, TPB, 0, s>>>(L, C, m->kind, (const T*)m->x[l + 1], x); rmt_count_launches(1);
-  for (int it = 0; it < 2; it++)
-    for (int col = ncol - 1; col >= 0; col--) {
-      hk(m, l, 0, 1, s);
-      k_smooth<T><<<nb, TPB, 0, s>>>(L, m->kind, col, x, b, c0, c1, c2);
-      rmt_count_launches(1);
-      hk(m, l, 0, 0, s);
-    }
+  k_prolong<T><<<grid3(ex, ey, ez), dim3(BX, BY), 0, s>>>(L, C, m->kind, (const T*)m->x[l + 1], (T*)m->x[l]);
+  rmt_count_launches(1);
+  smooth<T>(m, l, m->post, false, s);
 }
 
 template <typename T>
 int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStream_t s, cudaError_t* err) {
   const Lv& L0 = m->lv[0];
   const long n = L0.nunk;
-  // coarse-level coefficients from level 0
+  // coefficients of every level
+  if (m->kind == 1) {
+    k_inv<T><<<nblocks(L0.ncell), TPB, 0, s>>>(L0.ncell, (const T*)m->rho_in, (T*)m->rho[0]);
+    rmt_count_launches(1);
+  }
   for (int l = 1; l < m->nlev; l++) {
     const Lv& F = m->lv[l - 1];
     const Lv& C = m->lv[l];
-    if (m->kind == 0) {
-      for (int d = 0; d < 3; d++) {
-        const long nf = C.ncell / C.n[d] * (C.n[d] + 1);
-        k_coarsen_mac<T><<<nblocks(nf), TPB, 0, s>>>(F, C, d, (const T*)m->c[l - 1][d], (T*)m->c[l][d]); rmt_count_launches(1);
-      }
-    } else {
-      k_coarsen_fe<T><<<nblocks(C.ncell), TPB, 0, s>>>(F, C, (const T*)m->c[l - 1][0], (T*)m->c[l][0]); rmt_count_launches(1);
-    }
+    k_coarsen<T><<<grid3(C.n[0], C.n[1], C.n[2]), dim3(BX, BY), 0, s>>>(F, C, (const T*)m->rho[l - 1], (T*)m->rho[l]);
+    rmt_count_launches(1);
   }
   // mean-free right-hand side, zero start
   sum_into<double>(m, m->b64, n, 0, 1.0 / (double)n, m->scal, s);
-  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal); rmt_count_launches(1);
+  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal);
+  rmt_count_launches(1);
   double bn2 = 0.0;
   if (fixed_cycles <= 0) {
     sum_into<double>(m, m->b64, n, 1, 1.0, m->scal + 1, s);
@@ -615,12 +656,12 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
     if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
     bn2 = m->hpin[0];
   }
-  k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n); rmt_count_launches(1);
-  const T* c0 = (const T*)m->c[0][0];
-  const T* c1 = (const T*)m->c[0][1];
-  const T* c2 = (const T*)m->c[0][2];
-  int nbr = nblocks(n);
-  if (nbr > RED_BLOCKS) nbr = RED_BLOCKS;
+  k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n);
+  rmt_count_launches(1);
+  const int ex = m->kind == 0 ? L0.n[0] : L0.nn[0], ey = m->kind == 0 ? L0.n[1] : L0.nn[1],
+            ez = m->kind == 0 ? L0.n[2] : L0.nn[2];
+  const dim3 g0 = grid3(ex, ey, ez);
+  const int nbr = (int)((long)g0.x * g0.y * g0.z);
   int cycles = 0;
   int ok = 1;
   if (fixed_cycles <= 0 && bn2 == 0.0) {
@@ -630,29 +671,36 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
   const int cap = fixed_cycles > 0 ? fixed_cycles : max_cycles;
   for (;;) {
     hk(m, 0, 1, 1, s);
-    k_resid64<T><<<nbr, TPB, 0, s>>>(L0, m->kind, m->x64, m->b64, c0, c1, c2, (T*)m->b[0], m->part);
+    k_resid64<T><<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->x64, m->b64, (const T*)m->rho[0], (T*)m->b[0], m->part);
     rmt_count_launches(1);
     hk(m, 0, 1, 0, s);
     if (fixed_cycles <= 0) {
-      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2); rmt_count_launches(1);
+      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
+      rmt_count_launches(1);
       cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
       if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
       const double rn2 = m->hpin[1];
-      if (!(rn2 == rn2)) { ok = 0; break; }  // NaN
+      if (!(rn2 == rn2)) {
+        ok = 0;
+        break;
+      }
       if (rn2 <= rtol * rtol * bn2) break;
     }
     if (cycles >= cap) {
       if (fixed_cycles <= 0) ok = 0;
       break;
     }
-    k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n); rmt_count_launches(1);
+    k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
+    rmt_count_launches(1);
     vcycle<T>(m, 0, s);
-    k_copy_to64<T><<<nblocks(n), TPB, 0, s>>>((const T*)m->x[0], m->x64, n, 1); rmt_count_launches(1);
+    k_add_to64<T><<<nblocks(n), TPB, 0, s>>>((const T*)m->x[0], m->x64, n);
+    rmt_count_launches(1);
     cycles++;
     if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
   }
   sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);
-  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3); rmt_count_launches(1);
+  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3);
+  rmt_count_launches(1);
   *err = cudaGetLastError();
   return ok ? cycles : -1;
 }

@@ -122,17 +122,45 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
 }
 
 template <typename T>
-__global__ void k_stress_div(Geo g, const T* __restrict__ u, const Body* __restrict__ bodies,
-                             const BodyView<T>* __restrict__ views, int nb, T tt, T* __restrict__ out) {
-  GRID_LOOP(c, g.N) {
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
-    // bodies that have xi at this cell: only they can contribute at its six faces
-    uint64_t bm = 0;
-    for (int m = 0; m < nb; m++)
-      if (views[m].lay[c] >= 0) bm |= (1ull << m);
-    T acc[3] = {T(0), T(0), T(0)};
-    const T ih = T(1.0 / g.h);
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* __restrict__ u,
+                                                                const Body* __restrict__ bodies,
+                                                                const BodyView<T>* __restrict__ views, int nb, T tt,
+                                                                T* __restrict__ out) {
+  THREAD_XYZ(i, j, k);
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const long c = cidx(g, i, j, k);
+  // bodies that have xi at this cell: only they can contribute at its six faces
+  uint64_t bm = 0;
+  for (int m = 0; m < nb; m++)
+    if (views[m].lay[c] >= 0) bm |= (1ull << m);
+  T acc[3] = {T(0), T(0), T(0)};
+  const T ih = T(1.0 / g.h);
+  if (bm == 0) {
+    // pure fluid around this cell: every face row is mu (u_b - u_a)/h
+    const T mu = T(g.mu);
+    const bool in = i > 0 && i + 1 < g.n[0] && j > 0 && j + 1 < g.n[1] && k > 0 && k + 1 < g.n[2];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const T* ua = u + (long)a * g.N;
+      const T uc = ua[c];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        T up, um;
+        if (in) {
+          const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
+          up = ua[c + st];
+          um = ua[c - st];
+        } else {
+          int p[3] = {i, j, k}, q[3] = {i, j, k};
+          p[d] += 1;
+          q[d] -= 1;
+          up = uval(g, u, a, p[0], p[1], p[2]);
+          um = uval(g, u, a, q[0], q[1], q[2]);
+        }
+        acc[a] += (mu * ((up - uc) * ih) - mu * ((uc - um) * ih)) * ih;
+      }
+    }
+  } else {
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       int ip[3] = {i, j, k};
@@ -143,9 +171,9 @@ __global__ void k_stress_div(Geo g, const T* __restrict__ u, const Body* __restr
 #pragma unroll
       for (int a = 0; a < 3; a++) acc[a] += (rp[a] - rm[a]) * ih;
     }
-#pragma unroll
-    for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
   }
+#pragma unroll
+  for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
 }
 
 }  // namespace
@@ -153,7 +181,9 @@ __global__ void k_stress_div(Geo g, const T* __restrict__ u, const Body* __restr
 template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb, double t,
                        T* out, cudaStream_t s) {
-  k_stress_div<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, bodies, views, nb, T(t), out); rmt_count_launches(1);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  k_stress_div<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, bodies, views, nb, T(t), out);
+  rmt_count_launches(1);
 }
 
 template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, double,

@@ -134,18 +134,20 @@ __device__ __noinline__ void xi_state(const Geo& g, const T* __restrict__ u, con
 }
 
 template <typename T>
-__global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, const T* __restrict__ x,
-                             const int8_t* __restrict__ lay, T* __restrict__ xn) {
+__global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, const int* __restrict__ bb,
+                             const T* __restrict__ x, const int8_t* __restrict__ lay, T* __restrict__ xn) {
   const T ih = T(1.0 / g.h), dt = T(g.dt);
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
-  GRID_LOOP(c, g.N) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int uu[3], i, j, k;
+    long c;
+    win_cell(g, w, t, uu, i, j, k, c);
     const int l = lay[c];
     if (l < 0 || l > 1) {
       xn[c] = nanv; xn[g.N + c] = nanv; xn[2 * g.N + c] = nanv;
       continue;
     }
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -184,18 +186,20 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
 }  // namespace
 
 template <typename T>
-void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3], const T* x,
-                       const int8_t* lay, T* xn, cudaStream_t s) {
+void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3], const int* bb,
+                       int blocks, const T* x, const int8_t* lay, T* xn, cudaStream_t s) {
   XiPredPtrs pp;
   for (int d = 0; d < 3; d++) {
     pp.vadv[d] = vadv[d];
     pp.unpre[d] = uf[d][d];
     pp.umac[d] = umac[d];
   }
-  k_xi_predict<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, pp, x, lay, xn); rmt_count_launches(1);
+  k_xi_predict<T><<<blocks, TPB, 0, s>>>(g, u, pp, bb, x, lay, xn);
+  rmt_count_launches(1);
 }
 
 template void launch_xi_predict<float>(const Geo&, const float*, float* const[3], float* const[3][3], float* const[3],
-                                       const float*, const int8_t*, float*, cudaStream_t);
+                                       const int*, int, const float*, const int8_t*, float*, cudaStream_t);
 template void launch_xi_predict<double>(const Geo&, const double*, double* const[3], double* const[3][3],
-                                        double* const[3], const double*, const int8_t*, double*, cudaStream_t);
+                                        double* const[3], const int*, int, const double*, const int8_t*, double*,
+                                        cudaStream_t);

@@ -23,7 +23,7 @@ RMT_F_MAC_Q, RMT_F_ADV_U, RMT_F_USTAR, RMT_F_PSI, RMT_F_RHO_HALF, RMT_F_XI_HALF 
 RMT_F_UMAC_X, RMT_F_UMAC_Y, RMT_F_UMAC_Z = 31, 32, 33
 
 EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt_read_fields",
-           "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_kernel_launches", "rmt_profile",
+           "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_set_option", "rmt_kernel_launches", "rmt_profile",
            "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_destroy_grid", "rmt_last_error")
 
 
@@ -70,6 +70,8 @@ def load(build: bool = True):
     L.rmt_last_cycles.argtypes = [vp, C.c_int]
     L.rmt_dt.argtypes = [vp]
     L.rmt_dt.restype = C.c_double
+    L.rmt_set_option.argtypes = [vp, C.c_char_p, C.c_double]
+    L.rmt_set_option.restype = C.c_int
     L.rmt_kernel_launches.argtypes = []
     L.rmt_kernel_launches.restype = C.c_long
     L.rmt_profile.argtypes = [vp, C.c_int]
@@ -147,6 +149,8 @@ class Grid:
         self._check("rmt_create_grid", self._L.rmt_create_grid(C.byref(make_grid_desc(scene, stream)),
                                                               C.byref(self._g)))
         self.nsolids = 0
+        for k, v in scene.get("options", {}).items():
+            self.set_option(k, v)
         for s in scene.get("solids", []):
             sid = C.c_int()
             self._check("rmt_add_solid", self._L.rmt_add_solid(self._g, C.byref(make_solid_desc(s)),
@@ -194,6 +198,9 @@ class Grid:
     def dt(self) -> float:
         self.read(RMT_F_RHO)
         return self._L.rmt_dt(self._g)
+
+    def set_option(self, name: str, value: float):
+        self._check("rmt_set_option", self._L.rmt_set_option(self._g, name.encode(), float(value)))
 
     def profile(self, enable: bool):
         self._check("rmt_profile", self._L.rmt_profile(self._g, 1 if enable else 0))
