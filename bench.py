@@ -156,10 +156,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
-    ap.add_argument("--mg-cycles-mac", type=int, default=7,
-                    help="V-cycles per MAC solve (fixed, no host sync; 7 reach ~1e-6 relative residual)")
+    ap.add_argument("--mg-cycles-mac", type=int, default=5,
+                    help="V-cycles per MAC solve (fixed, no host sync; 5 reach 1e-6 relative residual)")
     ap.add_argument("--mg-cycles-fe", type=int, default=4,
-                    help="V-cycles per FE solve (fixed; 4 reach ~1e-6 relative residual)")
+                    help="V-cycles per FE solve (fixed; 4 reach 1e-6 relative residual)")
+    ap.add_argument("--fe-inner", type=int, default=2,
+                    help="FE V-cycles per FP64 residual (mixed-precision refinement)")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -191,6 +193,7 @@ def main():
     scene = make_scene(cfg, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
+    scene["options"] = {"fe_inner": args.fe_inner}
     g = rmt.Grid(scene, stream=stream.cuda_stream)
     N = int(np.prod(scene["n"]))
     for _ in range(args.warmup):
@@ -287,7 +290,8 @@ def main():
                 "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": args.config, "description": cfg["desc"], "grid": list(scene["n"]),
                            "bodies": len(scene["solids"]),
-                           "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe},
+                           "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
+                                                   "fe_inner": args.fe_inner},
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,

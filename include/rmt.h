@@ -119,8 +119,10 @@ int rmt_last_cycles(rmt_grid* g, int which);
 double rmt_dt(rmt_grid* g);
 
 /* Solver schedule options (any time): "mac_pre", "mac_post" (red-black Gauss-Seidel sweeps
- * before / after the coarse correction, 0..16, default 2), "fe_pre", "fe_post" (weighted Jacobi
- * sweeps, default 2), "fe_omega" (Jacobi weight in (0,2), default 0.8).  Errors: RMT_EINVAL. */
+ * before / after the coarse correction, 0..16, default 3), "fe_pre", "fe_post" (weighted Jacobi
+ * sweeps, default 2), "fe_omega" (Jacobi weight in (0,2), default 0.9), "mac_inner", "fe_inner"
+ * (V-cycles on the storage-precision correction equation per FP64 residual, 1..16, default 1).  Cycle
+ * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL. */
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
 
 /* Total number of CUDA kernels this library has launched in this process (all grids). */

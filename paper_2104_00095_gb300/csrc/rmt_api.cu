@@ -78,6 +78,7 @@ struct rmt_grid {
   void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
   void *adv = nullptr, *ustar = nullptr, *psi = nullptr;
   void* ub[3][3] = {};
+  void* slopes[9] = {};
   void* vadv[3] = {};
   void* uf[3][3] = {};
   void* umac[3] = {};
@@ -94,7 +95,7 @@ struct rmt_grid {
   Prof prof;
   HookCtx hctx[2];
   // smoother schedule (negative: solver default)
-  int mac_pre = -1, mac_post = -1, fe_pre = -1, fe_post = -1;
+  int mac_pre = -1, mac_post = -1, fe_pre = -1, fe_post = -1, mac_inner = 1, fe_inner = 1;
   double fe_omega = -1.0;
 };
 
@@ -285,6 +286,7 @@ rmt_status init_t(rmt_grid* g) {
   AL(g->adv, 3 * N * e);
   AL(g->ustar, 3 * N * e);
   AL(g->psi, G.NN * e);
+  for (int q = 0; q < 9; q++) AL(g->slopes[q], N * e);
   for (int d = 0; d < 3; d++) {
     const long nf = nfaces(G, d);
     for (int a = 0; a < 3; a++) {
@@ -331,6 +333,8 @@ rmt_status init_t(rmt_grid* g) {
   mg_set_hook(g->fe, mg_hook, &g->hctx[1]);
   mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
   mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+  mg_set_inner(g->mac, g->mac_inner);
+  mg_set_inner(g->fe, g->fe_inner);
   // outside a body's band every per-body array reads "absent" (layer -1, NaN); the window
   // kernels rely on it, since they only ever touch the band's neighbourhood
   const T nanv = (T)NAN;
@@ -364,6 +368,7 @@ rmt_status step_t(rmt_grid* g) {
   const int nb = (int)g->bodies.size();
   const int cur = g->par, nxt = 1 - g->par;
   T* ub[3][3];
+  T* slopes[9];
   T* vadv[3];
   T* uf[3][3];
   T* umac[3];
@@ -375,6 +380,7 @@ rmt_status step_t(rmt_grid* g) {
     vadv[d] = (T*)g->vadv[d];
     umac[d] = (T*)g->umac[d];
   }
+  for (int q = 0; q < 9; q++) slopes[q] = (T*)g->slopes[q];
   T* u = (T*)g->u;
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
@@ -382,8 +388,8 @@ rmt_status step_t(rmt_grid* g) {
   pe(g, P_STRESS_N);
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
-  launch_bar_states<T>(G, u, ub, vadv, s);
-  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, ub, vadv, uf, s);
+  launch_bar_states<T>(G, u, slopes, ub, vadv, s);
+  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, slopes, ub, vadv, uf, s);
   pe(g, P_GODUNOV);
   // 3. MAC projection of the normal face velocities
   pb(g, P_MAC_SETUP);
@@ -731,6 +737,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   else if (!strcmp(name, "mac_post")) ip = &g->mac_post;
   else if (!strcmp(name, "fe_pre")) ip = &g->fe_pre;
   else if (!strcmp(name, "fe_post")) ip = &g->fe_post;
+  else if (!strcmp(name, "mac_inner")) ip = &g->mac_inner;
+  else if (!strcmp(name, "fe_inner")) ip = &g->fe_inner;
   if (ip) {
     if (value < 0 || value > 16) return fail(g, RMT_EINVAL, "%s out of range", name);
     *ip = (int)value;
@@ -743,6 +751,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   if (g->inited) {
     mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
     mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+    mg_set_inner(g->mac, g->mac_inner);
+    mg_set_inner(g->fe, g->fe_inner);
   }
   return RMT_OK;
 }

@@ -76,36 +76,37 @@ __global__ void k_bfs(Geo g, const int* __restrict__ bb, int l, int8_t* __restri
   }
 }
 
-// LDL^T solve of the 4x4 normal equations, three right-hand sides; degenerate when a
-// pivot is not above 1e-12 trace(A)/4
-__device__ bool solve4(double A[4][4], double B[4][3], double X[4][3]) {
-  double L[4][4], D[4];
+// LDL^T solve of the 4x4 normal equations, three right-hand sides, in AT; fails (degenerate)
+// when a pivot is not above tolfac * trace(A)/4 (tolfac = 1e-12 in FP64)
+template <typename AT>
+__device__ bool solve4(AT A[4][4], AT B[4][3], AT X[4][3], AT tolfac) {
+  AT L[4][4], D[4];
   for (int r = 0; r < 4; r++)
-    for (int q = 0; q < 4; q++) L[r][q] = 0.0;
-  const double tr = A[0][0] + A[1][1] + A[2][2] + A[3][3];
-  const double tol = 1e-12 * tr / 4.0;
+    for (int q = 0; q < 4; q++) L[r][q] = AT(0);
+  const AT tr = A[0][0] + A[1][1] + A[2][2] + A[3][3];
+  const AT tol = tolfac * tr / AT(4);
   for (int k = 0; k < 4; k++) {
-    double s = A[k][k];
+    AT s = A[k][k];
     for (int j = 0; j < k; j++) s -= L[k][j] * L[k][j] * D[j];
     D[k] = s;
     if (!(s > tol)) return false;
-    L[k][k] = 1.0;
+    L[k][k] = AT(1);
     for (int i = k + 1; i < 4; i++) {
-      double t = A[i][k];
+      AT t = A[i][k];
       for (int j = 0; j < k; j++) t -= L[i][j] * L[k][j] * D[j];
       L[i][k] = t / D[k];
     }
   }
   for (int c = 0; c < 3; c++) {
-    double y[4];
+    AT y[4];
     for (int i = 0; i < 4; i++) {
-      double t = B[i][c];
+      AT t = B[i][c];
       for (int j = 0; j < i; j++) t -= L[i][j] * y[j];
       y[i] = t;
     }
     for (int i = 0; i < 4; i++) y[i] /= D[i];
     for (int i = 3; i >= 0; i--) {
-      double t = y[i];
+      AT t = y[i];
       for (int j = i + 1; j < 4; j++) t -= L[j][i] * X[j][c];
       X[i][c] = t;
     }
@@ -117,15 +118,15 @@ __device__ bool solve4(double A[4][4], double B[4][3], double X[4][3]) {
 // whole warp: the lanes split the (2 rs + 1)^3 candidate cells and the normal-equation sums are
 // combined by a butterfly (every lane ends with the same totals, in a fixed order).
 // mode 0: kernel 2^-(|di|+|dj|+|dk|); mode 1: times max(0, cos) against the normal n_e.
-template <typename T>
+template <typename AT, typename T>
 __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j,
-                             int k, int le, int rs, int mode, const double nrm[3], double sol[4][3]) {
+                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, AT sol[4][3]) {
   const int lane = threadIdx.x & 31;
-  double a[10], bsum[12];
+  AT a[10], bsum[12];
 #pragma unroll
-  for (int q = 0; q < 10; q++) a[q] = 0.0;
+  for (int q = 0; q < 10; q++) a[q] = AT(0);
 #pragma unroll
-  for (int q = 0; q < 12; q++) bsum[q] = 0.0;
+  for (int q = 0; q < 12; q++) bsum[q] = AT(0);
   int npos = 0;
   const int w = 2 * rs + 1, nc = w * w * w;
   for (int t = lane; t < nc; t += 32) {
@@ -135,15 +136,15 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
     const int ld = lay[c];
     if (ld < 0 || ld >= le) continue;
     const int sr = abs(di) + abs(dj) + abs(dk);
-    double wt = ldexp(1.0, -sr);
+    AT wt = sizeof(AT) == 4 ? (AT)ldexpf(1.0f, -sr) : (AT)ldexp(1.0, -sr);
     if (mode == 1) {
-      const double len = sqrt((double)(di * di + dj * dj + dk * dk));
-      const double cs = -((double)di * nrm[0] + (double)dj * nrm[1] + (double)dk * nrm[2]) / len;
+      const AT len = sqrt((AT)(di * di + dj * dj + dk * dk));
+      const AT cs = -((AT)di * nrm[0] + (AT)dj * nrm[1] + (AT)dk * nrm[2]) / len;
       wt = cs * wt;
-      if (!(wt > 0.0)) continue;
+      if (!(wt > AT(0))) continue;
     }
-    const double v[4] = {1.0, (double)di, (double)dj, (double)dk};
-    const double xv[3] = {(double)x[c], (double)x[g.N + c], (double)x[2 * g.N + c]};
+    const AT v[4] = {AT(1), (AT)di, (AT)dj, (AT)dk};
+    const AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
     int q = 0;
 #pragma unroll
     for (int r = 0; r < 4; r++)
@@ -164,7 +165,7 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
     npos += __shfl_xor_sync(0xffffffffu, npos, o);
   }
   if (npos < 4) return false;
-  double A[4][4], B[4][3];
+  AT A[4][4], B[4][3];
   int q = 0;
   for (int r = 0; r < 4; r++)
     for (int cc = r; cc < 4; cc++) {
@@ -174,35 +175,58 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
     }
   for (int r = 0; r < 4; r++)
     for (int d = 0; d < 3; d++) B[r][d] = bsum[3 * r + d];
-  return solve4(A, B, sol);
+  return solve4<AT>(A, B, sol, tolfac);
 }
 
-// Extrapolates one cell (whole warp): kernel-only fit, then (layers 1 and 2) the fit weighted
-// by the normal n_e = normalised (grad xi)^T grad_X phi_0(xi_e) of that first fit; the search
-// radius grows up to 4 while the system stays degenerate.
+// Extrapolates one cell (whole warp) with fits accumulated in AT: kernel-only fit, then (layers
+// 1 and 2) the fit weighted by the normal n_e = normalised (grad xi)^T grad_X phi_0(xi_e) of that
+// first fit; the search radius grows up to 4 while the system stays degenerate.  Returns 1 on
+// success, 0 when degenerate, -1 when an FP32 attempt was too ill-conditioned to trust.
+template <typename AT, typename T>
+__device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                            int i, int j, int k, int le, double out[3]) {
+  // FP64: the degeneracy threshold; FP32: also the point below which the fit is redone in FP64
+  const AT tolfac = sizeof(AT) == 8 ? AT(1e-12) : AT(1e-4);
+  for (int rs = 2; rs <= 4; rs++) {
+    AT s1[4][3];
+    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, s1)) {
+      if (sizeof(AT) == 4) return -1;
+      continue;
+    }
+    if (le <= 2) {
+      const AT c0[3] = {s1[0][0], s1[0][1], s1[0][2]};
+      AT gX[3], v[3];
+      phi0_dir<AT>(b, c0, gX);
+      for (int q = 0; q < 3; q++) v[q] = s1[1 + q][0] * gX[0] + s1[1 + q][1] * gX[1] + s1[1 + q][2] * gX[2];
+      const AT nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      if (!(nv > AT(0))) {
+        if (sizeof(AT) == 4) return -1;
+        continue;
+      }
+      const AT nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
+      AT s2[4][3];
+      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, s2)) {
+        if (sizeof(AT) == 4) return -1;
+        continue;
+      }
+      out[0] = s2[0][0]; out[1] = s2[0][1]; out[2] = s2[0][2];
+      return 1;
+    }
+    out[0] = s1[0][0]; out[1] = s1[0][1]; out[2] = s1[0][2];
+    return 1;
+  }
+  return 0;
+}
+
+// FP64 storage: FP64 fits.  FP32 storage: FP32 fits, redone in FP64 when ill-conditioned.
 template <typename T>
 __device__ bool wls_cell_warp(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
                               int i, int j, int k, int le, double out[3]) {
-  for (int rs = 2; rs <= 4; rs++) {
-    double s1[4][3];
-    if (!wls_fit_warp(g, x, lay, i, j, k, le, rs, 0, nullptr, s1)) continue;
-    if (le <= 2) {
-      const double c0[3] = {s1[0][0], s1[0][1], s1[0][2]};
-      double gX[3], v[3];
-      phi0_dir<double>(b, c0, gX);
-      for (int q = 0; q < 3; q++) v[q] = s1[1 + q][0] * gX[0] + s1[1 + q][1] * gX[1] + s1[1 + q][2] * gX[2];
-      const double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      if (!(nv > 0.0)) continue;
-      const double nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
-      double s2[4][3];
-      if (!wls_fit_warp(g, x, lay, i, j, k, le, rs, 1, nrm, s2)) continue;
-      out[0] = s2[0][0]; out[1] = s2[0][1]; out[2] = s2[0][2];
-      return true;
-    }
-    out[0] = s1[0][0]; out[1] = s1[0][1]; out[2] = s1[0][2];
-    return true;
+  if (sizeof(T) == 4) {
+    const int r = wls_cell_try<float>(g, b, x, lay, i, j, k, le, out);
+    if (r >= 0) return r == 1;
   }
-  return false;
+  return wls_cell_try<double>(g, b, x, lay, i, j, k, le, out) == 1;
 }
 
 // compacted list of the band cells (layers 1..L) of a body's window

@@ -51,45 +51,64 @@ __device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int 
   return lim_slope(q, 0x1Fu, T(1.0 / g.h));
 }
 
+// limited slopes of the three velocity components along the three axes at every cell
+// (SI "Normal derivatives"); S[3 * d + a] = d u_a / d x_d
+struct Slopes9 {
+  void* s[9];
+};
+template <typename T>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_slopes(Geo g, const T* __restrict__ u, Slopes9 S) {
+  THREAD_XYZ(i, j, k);
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const long c = cidx(g, i, j, k);
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) ((T*)S.s[3 * d + a])[c] = slope_u(g, u, a, d, i, j, k);
+}
+
 __device__ __forceinline__ bool is_wall_face(const Geo& g, int d, int f) {
   return !g.per[d] && (f == 0 || f == g.n[d]);
 }
 
 // transverse bar states at every e-face (SI "Tangential derivatives")
 template <typename T>
-__global__ void k_bar(Geo g, int e, const T* __restrict__ u, T* __restrict__ ub0, T* __restrict__ ub1,
-                      T* __restrict__ ub2, T* __restrict__ vadv) {
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, int e, const T* __restrict__ u, Slopes9 S,
+                                                         T* __restrict__ ub0, T* __restrict__ ub1, T* __restrict__ ub2,
+                                                         T* __restrict__ vadv) {
   const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1), ez = g.n[2] + (e == 2);
   const T h = T(g.h), dt = T(g.dt);
   T* ub[3] = {ub0, ub1, ub2};
   THREAD_XYZ(i, j, k);
-  if (i < ex && j < ey && k < ez) {
-    const long f = i + (long)ex * (j + (long)ey * k);
-    const int fi = e == 0 ? i : (e == 1 ? j : k);
-    if (is_wall_face(g, e, fi)) {
-      const int face = fi == 0 ? 2 * e : 2 * e + 1;
+  if (i >= ex || j >= ey || k >= ez) return;
+  const long f = i + (long)ex * (j + (long)ey * k);
+  const int fi = e == 0 ? i : (e == 1 ? j : k);
+  if (is_wall_face(g, e, fi)) {
+    const int face = fi == 0 ? 2 * e : 2 * e + 1;
 #pragma unroll
-      for (int a = 0; a < 3; a++) ub[a][f] = T(g.wall[face][a]);
-      vadv[f] = T(g.wall[face][e]);
-      return;
-    }
-    int lo[3] = {i, j, k};
-    lo[e] -= 1;
-    const T uD = uval(g, u, e, lo[0], lo[1], lo[2]);
-    const T uU = uval(g, u, e, i, j, k);
-    T qD[3], qU[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      qD[a] = uval(g, u, a, lo[0], lo[1], lo[2]) + (T(0.5) * h - T(0.5) * dt * uD) * slope_u(g, u, a, e, lo[0], lo[1], lo[2]);
-      qU[a] = uval(g, u, a, i, j, k) - (T(0.5) * h + T(0.5) * dt * uU) * slope_u(g, u, a, e, i, j, k);
-    }
-    const T va = god_normal(qD[e], qU[e], T(g.utol));
-    vadv[f] = va;
-#pragma unroll
-    for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va, T(g.utol));
+    for (int a = 0; a < 3; a++) ub[a][f] = T(g.wall[face][a]);
+    vadv[f] = T(g.wall[face][e]);
+    return;
   }
+  // the two cells of an interior (or periodic) face: D below, U above
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  lo[e] -= 1;
+  if (lo[e] < 0) lo[e] += g.n[e];
+  if (hi[e] >= g.n[e]) hi[e] -= g.n[e];
+  const long cD = cidx(g, lo[0], lo[1], lo[2]), cU = cidx(g, hi[0], hi[1], hi[2]);
+  const T uD = u[e * g.N + cD], uU = u[e * g.N + cU];
+  T qD[3], qU[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const T* Sa = (const T*)S.s[3 * e + a];
+    qD[a] = u[a * g.N + cD] + (T(0.5) * h - T(0.5) * dt * uD) * Sa[cD];
+    qU[a] = u[a * g.N + cU] - (T(0.5) * h + T(0.5) * dt * uU) * Sa[cU];
+  }
+  const T va = god_normal(qD[e], qU[e], T(g.utol));
+  vadv[f] = va;
+#pragma unroll
+  for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va, T(g.utol));
 }
-
 
 struct BarPtrs {
   const void* ub[3][3];
@@ -99,8 +118,9 @@ struct BarPtrs {
 
 // normal-face states of the velocity (eqs. left_final, right_final) + Godunov choice
 template <typename T>
-__global__ void k_face(Geo g, int d, const T* __restrict__ u, const T* __restrict__ p, const T* __restrict__ rho,
-                       const T* __restrict__ divtau, BarPtrs bp) {
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* __restrict__ u, const T* __restrict__ p,
+                                                          const T* __restrict__ rho, const T* __restrict__ divtau,
+                                                          Slopes9 S, BarPtrs bp) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1), ez = g.n[2] + (d == 2);
   const T h = T(g.h), dt = T(g.dt), ih = T(1.0 / g.h);
   T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
@@ -149,7 +169,7 @@ __global__ void k_face(Geo g, int d, const T* __restrict__ u, const T* __restric
           const T* ube = (const T*)bp.ub[e][a];
           tr += T(0.5) * (vad[lo] + vad[hi]) * (ube[hi] - ube[lo]) * ih;
         }
-        st[side][a] = u[a * g.N + c] + coef * slope_u(g, u, a, d, cc[0], cc[1], cc[2]) - T(0.5) * dt * tr +
+        st[side][a] = u[a * g.N + c] + coef * ((const T*)S.s[3 * d + a])[c] - T(0.5) * dt * tr +
                       T(0.5) * dt / r * F;
       }
     }
@@ -348,17 +368,25 @@ __global__ void k_fill(T* a, T v, long n) {
 }  // namespace
 
 template <typename T>
-void launch_bar_states(const Geo& g, const T* u, T* const ubar[3][3], T* const vadv[3], cudaStream_t s) {
+void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ubar[3][3], T* const vadv[3],
+                       cudaStream_t s) {
+  Slopes9 S;
+  for (int q = 0; q < 9; q++) S.s[q] = slopes[q];
+  const dim3 gc((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  k_slopes<T><<<gc, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, S);
+  rmt_count_launches(1);
   for (int e = 0; e < 3; e++) {
     const dim3 gr((g.n[0] + (e == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (e == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (e == 2));
-    k_bar<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, e, u, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]);
+    k_bar<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, e, u, S, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]);
     rmt_count_launches(1);
   }
 }
 template <typename T>
-void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const ubar[3][3],
-                        T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
+                        T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
   BarPtrs bp;
+  Slopes9 S;
+  for (int q = 0; q < 9; q++) S.s[q] = slopes[q];
   for (int e = 0; e < 3; e++) {
     for (int a = 0; a < 3; a++) bp.ub[e][a] = ubar[e][a];
     bp.vadv[e] = vadv[e];
@@ -366,7 +394,7 @@ void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, cons
   for (int d = 0; d < 3; d++) {
     for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
     const dim3 gr((g.n[0] + (d == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (d == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (d == 2));
-    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, p, rho, divtau, bp);
+    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, p, rho, divtau, S, bp);
     rmt_count_launches(1);
   }
 }
@@ -420,9 +448,9 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                                   \
-  template void launch_bar_states<T>(const Geo&, const T*, T* const[3][3], T* const[3], cudaStream_t);            \
-  template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[3][3],        \
-                                      T* const[3], T* const[3][3], cudaStream_t);                                \
+  template void launch_bar_states<T>(const Geo&, const T*, T* const[9], T* const[3][3], T* const[3], cudaStream_t); \
+  template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[9],           \
+                                      T* const[3][3], T* const[3], T* const[3][3], cudaStream_t);                \
   template void launch_mac_setup<T>(const Geo&, T* const[3][3], double*, cudaStream_t);                          \
   template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, const double*, T* const[3],          \
                                       cudaStream_t);                                                             \

@@ -15,10 +15,13 @@ struct Faces3 {
 template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
                        double t, T* out, cudaStream_t s);
+// slopes: nine cell arrays, written by launch_bar_states (limited slope of u_a along d at 3d+a)
+// and read by launch_face_states
 template <typename T>
-void launch_bar_states(const Geo& g, const T* u, T* const ubar[3][3], T* const vadv[3], cudaStream_t s);
+void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ubar[3][3], T* const vadv[3],
+                       cudaStream_t s);
 template <typename T>
-void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau,
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
                         T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
 template <typename T>
 void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s);
@@ -71,6 +74,8 @@ double* mg_solution(MGSolver* m);   // level-0 FP64 solution
 void mg_set_density(MGSolver* m, const void* rho);
 // smoother sweeps before/after the coarse correction and the Jacobi weight (negative: keep)
 void mg_set_smoother(MGSolver* m, int pre, int post, double omega);
+// V-cycles on the correction equation between FP64 residual evaluations (>= 1)
+void mg_set_inner(MGSolver* m, int inner);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
 // hook(ctx, which, begin, stream) with which = 0 (smoother colour) or 1 (FP64 residual).
 typedef void (*mg_hook_fn)(void* ctx, int which, int begin, cudaStream_t s);

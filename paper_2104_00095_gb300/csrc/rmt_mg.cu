@@ -463,7 +463,8 @@ struct MGSolver {
   double* hpin = nullptr;
   size_t esz = 8;
   int pre = 2, post = 2;
-  double omega = 0.8;
+  int inner = 1;  // V-cycles on the FP32 correction equation per FP64 residual
+  double omega = 0.9;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
 };
@@ -477,6 +478,9 @@ void mg_set_smoother(MGSolver* m, int pre, int post, double omega) {
   if (post >= 0) m->post = post;
   if (omega > 0) m->omega = omega;
 }
+void mg_set_inner(MGSolver* m, int inner) {
+  if (inner >= 1) m->inner = inner;
+}
 
 static cudaError_t dmalloc(void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
@@ -489,7 +493,8 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
   m->kind = kind;
   m->fp32 = prec_fp32;
   m->esz = prec_fp32 ? 4 : 8;
-  m->omega = kind == 0 ? 1.0 : 0.8;
+  m->omega = kind == 0 ? 1.0 : 0.9;
+  m->pre = m->post = kind == 0 ? 3 : 2;
   Lv L;
   for (int d = 0; d < 3; d++) {
     L.n[d] = g.n[d];
@@ -692,10 +697,13 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
     }
     k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
     rmt_count_launches(1);
-    vcycle<T>(m, 0, s);
+    // inner V-cycles on A e = r in the storage type (the FP64 residual is re-formed after them)
+    for (int q = 0; q < m->inner && cycles < cap; q++) {
+      vcycle<T>(m, 0, s);
+      cycles++;
+    }
     k_add_to64<T><<<nblocks(n), TPB, 0, s>>>((const T*)m->x[0], m->x64, n);
     rmt_count_launches(1);
-    cycles++;
     if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
   }
   sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);

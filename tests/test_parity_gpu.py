@@ -113,7 +113,7 @@ def test_degenerate_extrapolation_is_reported_on_both_paths():
     assert ei.value.status == rmt.RMT_EDEGENERATE
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_uniform_translation_is_exact(prec, tol):
     """Periodic box, uniform velocity, unstressed sphere: xi = x - U t and u = U stay exact."""
     n = 32
@@ -166,8 +166,9 @@ def _taxicab_layers_local(lay, per, L):
 def test_full_size_properties(cfg):
     if cfg == "swimmers256_fp32":
         sc = S.swimmers(n=256, steps=1)
-        sc.update(mg_fixed_cycles=7, mg_fixed_cycles_fe=4)  # the launch configuration bench.py times
-        xtol = 2e-6
+        # the launch configuration bench.py times
+        sc.update(mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options={"fe_inner": 2})
+        xtol = 1e-6  # FP32 fits of an affine map: a few units in the last place of x ~ O(1)
     else:
         sc = S.settling(n=128, steps=1)
         sc.update(mg_rtol=1e-12)
