@@ -125,6 +125,28 @@ double rmt_dt(rmt_grid* g);
  * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL. */
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
 
+/* Extrapolates one body's reference map on caller-owned device buffers without allocating
+ * anything (the paper has no counterpart: this serves callers that cannot allocate device
+ * memory while they run, e.g. because their own pool owns the memory budget, or because
+ * cudaMalloc may synchronise the device in the middle of their pipeline).  It runs the same
+ * classification, layer marking and least-squares extrapolation as initialisation and
+ * rmt_write_fields(RMT_F_XI), in FP64, on the grid and body that desc and s describe
+ * (desc: n, lo, hi, bc, eps_h, band_layers are read).
+ *   xi_in     device, 3 N doubles ([3][nz][ny][nx]); finite entries are candidate primary
+ *             values, NaN marks "no value" (as rmt_write_fields).  Not modified.
+ *   xi_out    device, 3 N doubles: the extrapolated map, NaN outside the band.
+ *   phi_out   device, N doubles: phi_0(xi) in the band, NaN outside.
+ *   layer_out device, N signed chars: layer labels, -1 outside the band.
+ *   stream    cudaStream_t the work is ordered on; the call synchronises it before returning.
+ * Scratch (band list, bounding box, counters) lives in one static device array sized for grids
+ * of at most 2^21 cells (e.g. 128^3); larger grids return RMT_EINVAL before any work.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on each device outside any stream capture.  All calls in the process share the
+ * array: calls that overlap on the GPU (other streams, other threads) race; serialise them.
+ * Returns RMT_EDEGENERATE when a fit stayed degenerate, RMT_ECUDA on a CUDA error. */
+rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* desc, const rmt_solid_desc* s, const double* xi_in,
+                                   double* xi_out, double* phi_out, signed char* layer_out, void* stream);
+
 /* Total number of CUDA kernels this library has launched in this process (all grids). */
 long rmt_kernel_launches(void);
 

@@ -24,7 +24,8 @@ RMT_F_UMAC_X, RMT_F_UMAC_Y, RMT_F_UMAC_Z = 31, 32, 33
 
 EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt_read_fields",
            "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_set_option", "rmt_kernel_launches", "rmt_profile",
-           "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_destroy_grid", "rmt_last_error")
+           "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_extrapolate_noalloc", "rmt_destroy_grid",
+           "rmt_last_error")
 
 
 class rmt_grid_desc(C.Structure):
@@ -82,6 +83,8 @@ def load(build: bool = True):
     L.rmt_profile_name.restype = C.c_char_p
     L.rmt_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long), dp]
     L.rmt_profile_read.restype = C.c_int
+    L.rmt_extrapolate_noalloc.argtypes = [C.POINTER(rmt_grid_desc), C.POINTER(rmt_solid_desc), vp, vp, vp, vp, vp]
+    L.rmt_extrapolate_noalloc.restype = C.c_int
     L.rmt_destroy_grid.argtypes = [vp]
     L.rmt_last_error.argtypes = [vp]
     L.rmt_last_error.restype = C.c_char_p
