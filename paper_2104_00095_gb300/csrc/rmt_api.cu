@@ -462,6 +462,7 @@ rmt_status ensure_init(rmt_grid* g) {
   if (g->inited) return RMT_OK;
   g->g.dt = pick_dt(g);
   g->g.utol = 1e-12 * g->g.h / g->g.dt;
+  geo_finish(g->g);
   g->bodies.clear();
   for (const auto& s : g->solids) {
     Body b;
@@ -478,6 +479,7 @@ rmt_status ensure_init(rmt_grid* g) {
     b.actA = s.active_A;
     b.actW = s.active_omega;
     b.actL = s.active_len;
+    body_finish(b);
     g->bodies.push_back(b);
   }
   g->inited = 1;

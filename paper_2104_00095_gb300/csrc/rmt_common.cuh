@@ -22,14 +22,73 @@ struct Geo {
   double wall[6][3];
   double grav[3];
   int layers;      // extrapolation layers
+  // derived constants (host-computed by geo_finish) and float mirrors of everything a kernel
+  // reads, so that FP32 kernels never convert or divide in FP64
+  double ih, q4, hdt_h, two_dt, fe_rhs;  // 1/h, 0.25/h, dt/(2h), 2/dt, h^2/(4 dt)
+  struct {
+    float h, ih, q4, hdt_h, dt, eps, rho_f, mu, utol, wall[6][3], grav[3];
+  } f;
 };
 
-// One body's constants (Table pars + shape + active stress).
+// One body's constants (Table pars + shape + active stress), with float mirrors.
 struct Body {
   int shape;
   double c[3], a[3], R[9];
   double rho_s, G, mu_a, gamma_t, actA, actW, actL;
+  double a2[3], mina;  // squared semi-axes, smallest semi-axis (body_finish)
+  struct {
+    float c[3], a[3], R[9], a2[3], mina, rho_s, G, mu_a, gamma_t, actA, actW, actL;
+  } f;
 };
+
+// the value of a constant in the compute type: its float mirror for float, itself for double
+template <typename T>
+__host__ __device__ __forceinline__ T cv(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
+
+// fills the derived constants and float mirrors of a grid (host)
+inline void geo_finish(Geo& g) {
+  g.ih = 1.0 / g.h;
+  g.q4 = 0.25 / g.h;
+  g.hdt_h = 0.5 * g.dt / g.h;
+  g.two_dt = g.dt > 0 ? 2.0 / g.dt : 0.0;
+  g.fe_rhs = g.dt > 0 ? g.h * g.h / 4.0 / g.dt : 0.0;
+  g.f.h = (float)g.h;
+  g.f.ih = (float)g.ih;
+  g.f.q4 = (float)g.q4;
+  g.f.hdt_h = (float)g.hdt_h;
+  g.f.dt = (float)g.dt;
+  g.f.eps = (float)g.eps;
+  g.f.rho_f = (float)g.rho_f;
+  g.f.mu = (float)g.mu;
+  g.f.utol = (float)g.utol;
+  for (int q = 0; q < 6; q++)
+    for (int a = 0; a < 3; a++) g.f.wall[q][a] = (float)g.wall[q][a];
+  for (int a = 0; a < 3; a++) g.f.grav[a] = (float)g.grav[a];
+}
+// fills the derived constants and float mirrors of a body (host)
+inline void body_finish(Body& b) {
+  b.mina = b.a[0];
+  if (b.a[1] < b.mina) b.mina = b.a[1];
+  if (b.a[2] < b.mina) b.mina = b.a[2];
+  for (int a = 0; a < 3; a++) {
+    b.a2[a] = b.a[a] * b.a[a];
+    b.f.c[a] = (float)b.c[a];
+    b.f.a[a] = (float)b.a[a];
+    b.f.a2[a] = (float)b.a2[a];
+  }
+  for (int q = 0; q < 9; q++) b.f.R[q] = (float)b.R[q];
+  b.f.mina = (float)b.mina;
+  b.f.rho_s = (float)b.rho_s;
+  b.f.G = (float)b.G;
+  b.f.mu_a = (float)b.mu_a;
+  b.f.gamma_t = (float)b.gamma_t;
+  b.f.actA = (float)b.actA;
+  b.f.actW = (float)b.actW;
+  b.f.actL = (float)b.actL;
+}
 
 // The reference-map fields of one body at one time level.
 template <typename T>
@@ -90,7 +149,7 @@ __device__ __forceinline__ T uval(const Geo& g, const T* __restrict__ u, int a, 
         if (ii[d] < 0) ii[d] += n;
       } else {
         const int f = ii[d] < 0 ? 2 * d : 2 * d + 1;
-        add += s * T(2.0 * g.wall[f][a]);
+        add += s * (T(2) * cv<T>(g.wall[f][a], g.f.wall[f][a]));
         s = -s;
         ii[d] = ii[d] < 0 ? -1 - ii[d] : 2 * n - 1 - ii[d];
       }
@@ -134,21 +193,17 @@ __device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
 // Sphere: exact signed distance.  Ellipsoid: (g-1)/|grad g| with g = |D^-1 R^T (X-c)|.
 template <typename T>
 __device__ T phi0(const Body& b, T X0, T X1, T X2) {
-  const T r0 = sub_rn(X0, T(b.c[0])), r1 = sub_rn(X1, T(b.c[1])), r2 = sub_rn(X2, T(b.c[2]));
+#define BC(x) cv<T>(b.x, b.f.x)
+  const T r0 = sub_rn(X0, BC(c[0])), r1 = sub_rn(X1, BC(c[1])), r2 = sub_rn(X2, BC(c[2]));
   if (b.shape == 0)
-    return sub_rn(sqrt_rn(add_rn(add_rn(mul_rn(r0, r0), mul_rn(r1, r1)), mul_rn(r2, r2))), T(b.a[0]));
-  const T z0 = add_rn(add_rn(mul_rn(T(b.R[0]), r0), mul_rn(T(b.R[3]), r1)), mul_rn(T(b.R[6]), r2));
-  const T z1 = add_rn(add_rn(mul_rn(T(b.R[1]), r0), mul_rn(T(b.R[4]), r1)), mul_rn(T(b.R[7]), r2));
-  const T z2 = add_rn(add_rn(mul_rn(T(b.R[2]), r0), mul_rn(T(b.R[5]), r1)), mul_rn(T(b.R[8]), r2));
-  const T y0 = div_rn(z0, T(b.a[0])), y1 = div_rn(z1, T(b.a[1])), y2 = div_rn(z2, T(b.a[2]));
+    return sub_rn(sqrt_rn(add_rn(add_rn(mul_rn(r0, r0), mul_rn(r1, r1)), mul_rn(r2, r2))), BC(a[0]));
+  const T z0 = add_rn(add_rn(mul_rn(BC(R[0]), r0), mul_rn(BC(R[3]), r1)), mul_rn(BC(R[6]), r2));
+  const T z1 = add_rn(add_rn(mul_rn(BC(R[1]), r0), mul_rn(BC(R[4]), r1)), mul_rn(BC(R[7]), r2));
+  const T z2 = add_rn(add_rn(mul_rn(BC(R[2]), r0), mul_rn(BC(R[5]), r1)), mul_rn(BC(R[8]), r2));
+  const T y0 = div_rn(z0, BC(a[0])), y1 = div_rn(z1, BC(a[1])), y2 = div_rn(z2, BC(a[2]));
   const T gg = sqrt_rn(add_rn(add_rn(mul_rn(y0, y0), mul_rn(y1, y1)), mul_rn(y2, y2)));
-  if (gg < T(1e-12)) {
-    double m = b.a[0];
-    if (b.a[1] < m) m = b.a[1];
-    if (b.a[2] < m) m = b.a[2];
-    return T(-m);
-  }
-  const T w0 = div_rn(y0, T(b.a[0])), w1 = div_rn(y1, T(b.a[1])), w2 = div_rn(y2, T(b.a[2]));
+  if (gg < T(1e-12)) return -BC(mina);
+  const T w0 = div_rn(y0, BC(a[0])), w1 = div_rn(y1, BC(a[1])), w2 = div_rn(y2, BC(a[2]));
   const T wn = sqrt_rn(add_rn(add_rn(mul_rn(w0, w0), mul_rn(w1, w1)), mul_rn(w2, w2)));
   return div_rn(mul_rn(sub_rn(gg, T(1)), gg), wn);
 }
@@ -156,7 +211,7 @@ __device__ T phi0(const Body& b, T X0, T X1, T X2) {
 // direction of grad_X phi_0 (the WLS weights use its direction only)
 template <typename T>
 __device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
-  const T r[3] = {X[0] - T(b.c[0]), X[1] - T(b.c[1]), X[2] - T(b.c[2])};
+  const T r[3] = {X[0] - BC(c[0]), X[1] - BC(c[1]), X[2] - BC(c[2])};
   if (b.shape == 0) {
     gd[0] = r[0]; gd[1] = r[1]; gd[2] = r[2];
     return;
@@ -164,12 +219,13 @@ __device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
   T w[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const T z = T(b.R[a]) * r[0] + T(b.R[3 + a]) * r[1] + T(b.R[6 + a]) * r[2];
-    w[a] = z / T(b.a[a] * b.a[a]);
+    const T z = BC(R[a]) * r[0] + BC(R[3 + a]) * r[1] + BC(R[6 + a]) * r[2];
+    w[a] = z / BC(a2[a]);
   }
 #pragma unroll
-  for (int a = 0; a < 3; a++) gd[a] = T(b.R[3 * a]) * w[0] + T(b.R[3 * a + 1]) * w[1] + T(b.R[3 * a + 2]) * w[2];
+  for (int a = 0; a < 3; a++) gd[a] = BC(R[3 * a]) * w[0] + BC(R[3 * a + 1]) * w[1] + BC(R[3 * a + 2]) * w[2];
 }
+#undef BC
 
 // smoothed Heaviside (eq. sm_heavi) and its derivative
 template <typename T>

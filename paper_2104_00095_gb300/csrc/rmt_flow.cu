@@ -48,7 +48,7 @@ __device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int 
       q[s + 2] = uval(g, u, a, ii[0], ii[1], ii[2]);
     }
   }
-  return lim_slope(q, 0x1Fu, T(1.0 / g.h));
+  return lim_slope(q, 0x1Fu, cv<T>(g.ih, g.f.ih));
 }
 
 // limited slopes of the three velocity components along the three axes at every cell
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, int e, const T* _
                                                          T* __restrict__ ub0, T* __restrict__ ub1, T* __restrict__ ub2,
                                                          T* __restrict__ vadv) {
   const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1), ez = g.n[2] + (e == 2);
-  const T h = T(g.h), dt = T(g.dt);
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
   T* ub[3] = {ub0, ub1, ub2};
   THREAD_XYZ(i, j, k);
   if (i >= ex || j >= ey || k >= ez) return;
@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, int e, const T* _
   if (is_wall_face(g, e, fi)) {
     const int face = fi == 0 ? 2 * e : 2 * e + 1;
 #pragma unroll
-    for (int a = 0; a < 3; a++) ub[a][f] = T(g.wall[face][a]);
-    vadv[f] = T(g.wall[face][e]);
+    for (int a = 0; a < 3; a++) ub[a][f] = cv<T>(g.wall[face][a], g.f.wall[face][a]);
+    vadv[f] = cv<T>(g.wall[face][e], g.f.wall[face][e]);
     return;
   }
   // the two cells of an interior (or periodic) face: D below, U above
@@ -104,10 +104,10 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, int e, const T* _
     qD[a] = u[a * g.N + cD] + (T(0.5) * h - T(0.5) * dt * uD) * Sa[cD];
     qU[a] = u[a * g.N + cU] - (T(0.5) * h + T(0.5) * dt * uU) * Sa[cU];
   }
-  const T va = god_normal(qD[e], qU[e], T(g.utol));
+  const T va = god_normal(qD[e], qU[e], cv<T>(g.utol, g.f.utol));
   vadv[f] = va;
 #pragma unroll
-  for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va, T(g.utol));
+  for (int a = 0; a < 3; a++) ub[a][f] = upwind(qD[a], qU[a], va, cv<T>(g.utol, g.f.utol));
 }
 
 struct BarPtrs {
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* 
                                                           const T* __restrict__ rho, const T* __restrict__ divtau,
                                                           Slopes9 S, BarPtrs bp) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1), ez = g.n[2] + (d == 2);
-  const T h = T(g.h), dt = T(g.dt), ih = T(1.0 / g.h);
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
   T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
   THREAD_XYZ(i, j, k);
   if (i < ex && j < ey && k < ez) {
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* 
     if (is_wall_face(g, d, fi)) {
       const int face = fi == 0 ? 2 * d : 2 * d + 1;
 #pragma unroll
-      for (int a = 0; a < 3; a++) uf[a][f] = T(g.wall[face][a]);
+      for (int a = 0; a < 3; a++) uf[a][f] = cv<T>(g.wall[face][a], g.f.wall[face][a]);
       return;
     }
     T st[2][3];
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* 
       const T coef = side == 0 ? (T(0.5) * h - T(0.5) * dt * ud) : -(T(0.5) * h + T(0.5) * dt * ud);
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] + (r - T(g.rho_f)) * T(g.grav[a]);
+        const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
         T tr = T(0);
 #pragma unroll
         for (int e = 0; e < 3; e++) {
@@ -173,9 +173,9 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* 
                       T(0.5) * dt / r * F;
       }
     }
-    const T un = god_normal(st[0][d], st[1][d], T(g.utol));
+    const T un = god_normal(st[0][d], st[1][d], cv<T>(g.utol, g.f.utol));
 #pragma unroll
-    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un, T(g.utol));
+    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un, cv<T>(g.utol, g.f.utol));
   }
 }
 
@@ -188,7 +188,7 @@ struct FacePtrs3 {
 
 template <typename T>
 __global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
-  const T ih = T(1.0 / g.h);
+  const T ih = cv<T>(g.ih, g.f.ih);
   GRID_LOOP(c, g.N) {
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);
@@ -201,7 +201,7 @@ __global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
       dv += (U[hi] - U[lo]) * ih;
     }
     // positive operator A = -div(beta grad): A q = -div(u)/(dt/2)
-    b[c] = -(double)dv / (0.5 * g.dt);
+    b[c] = -(double)dv * g.two_dt;
   }
 }
 
@@ -209,7 +209,7 @@ template <typename T>
 __global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ rho,
                               const double* __restrict__ q, T* __restrict__ umac) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
-  const T fac = T(0.5 * g.dt / g.h);
+  const T fac = cv<T>(g.hdt_h, g.f.hdt_h);
   GRID_LOOP(f, nfaces(g, d)) {
     int i, j, k;
     decode(f, ex, ey, i, j, k);
@@ -237,7 +237,7 @@ struct AdvPtrs {
 
 template <typename T>
 __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
-  const T ih = T(1.0 / g.h);
+  const T ih = cv<T>(g.ih, g.f.ih);
   GRID_LOOP(c, g.N) {
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);
@@ -265,25 +265,25 @@ __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
 template <typename T>
 __global__ void k_density(Geo g, const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb,
                           T* __restrict__ rho) {
-  const T eps = T(g.eps);
+  const T eps = cv<T>(g.eps, g.f.eps);
   GRID_LOOP(c, g.N) {
     T wsum = T(0), acc = T(0);
     for (int m = 0; m < nb; m++) {
       if (views[m].lay[c] < 0) continue;
       const T w = T(1) - heavi(views[m].phi[c], eps);
-      acc += w * T(bodies[m].rho_s);
+      acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
       wsum += w;
     }
     const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
     const T sc = wsum > T(1) ? T(1) / wsum : T(1);
-    rho[c] = Hf * T(g.rho_f) + acc * sc;
+    rho[c] = Hf * cv<T>(g.rho_f, g.f.rho_f) + acc * sc;
   }
 }
 
 template <typename T>
 __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ adv, const T* __restrict__ p,
                         const T* __restrict__ rho_h, const T* __restrict__ divtau_h, T* __restrict__ ustar) {
-  const T dt = T(g.dt), q4 = T(0.25 / g.h);
+  const T dt = cv<T>(g.dt, g.f.dt), q4 = cv<T>(g.q4, g.f.q4);
   GRID_LOOP(c, g.N) {
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);
@@ -300,7 +300,7 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
 #pragma unroll
     for (int a = 0; a < 3; a++)
       ustar[a * g.N + c] = u[a * g.N + c] - dt * adv[a * g.N + c] +
-                           dt / r * (divtau_h[a * g.N + c] - gp[a] * q4 + (r - T(g.rho_f)) * T(g.grav[a]));
+                           dt / r * (divtau_h[a * g.N + c] - gp[a] * q4 + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]));
   }
 }
 
@@ -311,7 +311,7 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
 // (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d
 template <typename T>
 __global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ ustar, double* __restrict__ b) {
-  const double s = g.h * g.h / 4.0 / g.dt;
+  const double s = g.fe_rhs;
   GRID_LOOP(nd, g.NN) {
     int i, j, k;
     decode(nd, g.nn[0], g.nn[1], i, j, k);
@@ -331,8 +331,8 @@ __global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ u
 template <typename T>
 __global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h,
                               const double* __restrict__ psi, T* __restrict__ u) {
-  const double q4 = 0.25 / g.h;
-  const T dt = T(g.dt);
+  const double q4 = g.q4;
+  const T dt = cv<T>(g.dt, g.f.dt);
   GRID_LOOP(c, g.N) {
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);

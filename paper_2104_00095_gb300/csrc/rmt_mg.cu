@@ -42,7 +42,8 @@ inline int nblocks(long n) {
 struct Lv {
   int n[3], nn[3], per[3];
   long ncell, nnode, nunk;
-  double h;
+  double h, ih2, s12;  // spacing, 1/h^2 (MAC), h/12 (FE)
+  float f_ih2, f_s12;
 };
 
 inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
@@ -91,7 +92,7 @@ __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, cons
     off += beta * (AT)x[cn];
     dg += beta;
   }
-  const AT ih2 = AT(1.0 / (L.h * L.h));
+  const AT ih2 = cv<AT>(L.ih2, L.f_ih2);
   diag = dg * ih2;
   return (dg * (AT)x[c] - off) * ih2;
 }
@@ -136,7 +137,7 @@ __device__ __forceinline__ AT fe_op(const Lv& L, const XT* __restrict__ x, const
   for (int sz = 0; sz < 2; sz++)
 #pragma unroll
     for (int sy = 0; sy < 2; sy++) s += (b[0][sy][sz] + b[1][sy][sz]) * (AT)x[nix(L, i, Y[sy], Z[sz])];  // yz
-  const AT s12 = AT(L.h / 12.0);
+  const AT s12 = cv<AT>(L.s12, L.f_s12);
   diag = AT(4) * bs * s12;
   return (AT(4) * bs * (AT)x[nix(L, i, j, k)] - s) * s12;
 }
@@ -507,6 +508,10 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     L.ncell = (long)L.n[0] * L.n[1] * L.n[2];
     L.nnode = (long)L.nn[0] * L.nn[1] * L.nn[2];
     L.nunk = kind == 0 ? L.ncell : L.nnode;
+    L.ih2 = 1.0 / (L.h * L.h);
+    L.s12 = L.h / 12.0;
+    L.f_ih2 = (float)L.ih2;
+    L.f_s12 = (float)L.s12;
     m->lv[l] = L;
     m->nlev = l + 1;
     const size_t vb = (size_t)L.nunk * m->esz;

@@ -92,6 +92,8 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   b.actA = s->active_A;
   b.actW = s->active_omega;
   b.actL = s->active_len;
+  body_finish(b);
+  geo_finish(G);
 
   cudaStream_t st = (cudaStream_t)stream;
   int* scr = nullptr;

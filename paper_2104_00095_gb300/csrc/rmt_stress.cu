@@ -41,7 +41,7 @@ template <typename T>
 __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, const Body* __restrict__ bodies,
                          const BodyView<T>* __restrict__ views, uint64_t bmask, int d, int i, int j, int k,
                          T tt, T row[3]) {
-  const T ih = T(1.0 / g.h);
+  const T ih = cv<T>(g.ih, g.f.ih);
   int ia[3] = {i, j, k};
   ia[d] -= 1;
   T du[3];
@@ -49,7 +49,7 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
   for (int a = 0; a < 3; a++) du[a] = (uval(g, u, a, i, j, k) - uval(g, u, a, ia[0], ia[1], ia[2])) * ih;
   T acc[3] = {T(0), T(0), T(0)};
   T wsum = T(0);
-  const T eps = T(g.eps);
+  const T eps = cv<T>(g.eps, g.f.eps);
   while (bmask) {
     const int m = __ffsll((long long)bmask) - 1;
     bmask &= bmask - 1;
@@ -89,17 +89,17 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
     for (int a = 0; a < 3; a++) Bd[a] = F[3 * a] * F[3 * d] + F[3 * a + 1] * F[3 * d + 1] + F[3 * a + 2] * F[3 * d + 2];
     const T tr3 = (F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + F[4] * F[4] + F[5] * F[5] +
                    F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) / T(3);
-    const T G = T(B.G);
+    const T G = cv<T>(B.G, B.f.G);
     T tau[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) tau[a] = G * (Bd[a] - (a == d ? tr3 : T(0)));
     if (B.actA != 0.0) {
       // active stress (3 Z s0 / 2)(e e^T - I/3), e = F E_X / |F E_X|, s0 = A sin(2 pi X/l - w t)
-      const T r[3] = {xf[0] - T(B.c[0]), xf[1] - T(B.c[1]), xf[2] - T(B.c[2])};
-      const T Xb = T(B.R[0]) * r[0] + T(B.R[3]) * r[1] + T(B.R[6]) * r[2];
-      const T Zb = T(B.R[2]) * r[0] + T(B.R[5]) * r[1] + T(B.R[8]) * r[2];
-      const T s0 = T(B.actA) * sin(T(2.0 * RMT_PI) * Xb / T(B.actL) - T(B.actW) * tt);
-      const T EX[3] = {T(B.R[0]), T(B.R[3]), T(B.R[6])};
+      const T r[3] = {xf[0] - cv<T>(B.c[0], B.f.c[0]), xf[1] - cv<T>(B.c[1], B.f.c[1]), xf[2] - cv<T>(B.c[2], B.f.c[2])};
+      const T Xb = cv<T>(B.R[0], B.f.R[0]) * r[0] + cv<T>(B.R[3], B.f.R[3]) * r[1] + cv<T>(B.R[6], B.f.R[6]) * r[2];
+      const T Zb = cv<T>(B.R[2], B.f.R[2]) * r[0] + cv<T>(B.R[5], B.f.R[5]) * r[1] + cv<T>(B.R[8], B.f.R[8]) * r[2];
+      const T s0 = cv<T>(B.actA, B.f.actA) * sin(T(2.0 * RMT_PI) * Xb / cv<T>(B.actL, B.f.actL) - cv<T>(B.actW, B.f.actW) * tt);
+      const T EX[3] = {cv<T>(B.R[0], B.f.R[0]), cv<T>(B.R[3], B.f.R[3]), cv<T>(B.R[6], B.f.R[6])};
       T f[3];
 #pragma unroll
       for (int a = 0; a < 3; a++) f[a] = F[3 * a] * EX[0] + F[3 * a + 1] * EX[1] + F[3 * a + 2] * EX[2];
@@ -109,14 +109,14 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
 #pragma unroll
       for (int a = 0; a < 3; a++) tau[a] += amp * ((f[a] / fn) * ed - (a == d ? T(1.0 / 3.0) : T(0)));
     }
-    const T visc = T(B.mu_a) * (T(1) + T(B.gamma_t) * eps * dheavi(ph, eps));
+    const T visc = cv<T>(B.mu_a, B.f.mu_a) * (T(1) + cv<T>(B.gamma_t, B.f.gamma_t) * eps * dheavi(ph, eps));
 #pragma unroll
     for (int a = 0; a < 3; a++) acc[a] += w * (tau[a] + visc * du[a]);
     wsum += w;
   }
   const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
   const T sc = wsum > T(1) ? T(1) / wsum : T(1);
-  const T mu = T(g.mu);
+  const T mu = cv<T>(g.mu, g.f.mu);
 #pragma unroll
   for (int a = 0; a < 3; a++) row[a] = Hf * mu * du[a] + acc[a] * sc;
 }
@@ -134,10 +134,10 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* _
   for (int m = 0; m < nb; m++)
     if (views[m].lay[c] >= 0) bm |= (1ull << m);
   T acc[3] = {T(0), T(0), T(0)};
-  const T ih = T(1.0 / g.h);
+  const T ih = cv<T>(g.ih, g.f.ih);
   if (bm == 0) {
     // pure fluid around this cell: every face row is mu (u_b - u_a)/h
-    const T mu = T(g.mu);
+    const T mu = cv<T>(g.mu, g.f.mu);
     const bool in = i > 0 && i + 1 < g.n[0] && j > 0 && j + 1 < g.n[1] && k > 0 && k + 1 < g.n[2];
 #pragma unroll
     for (int a = 0; a < 3; a++) {

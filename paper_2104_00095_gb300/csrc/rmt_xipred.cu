@@ -65,7 +65,7 @@ __device__ __noinline__ void slope_xi(const Geo& g, const T* __restrict__ x, con
       q[0][t + 2] = q[1][t + 2] = q[2][t + 2] = T(0);
     }
   }
-  const T ih = T(1.0 / g.h);
+  const T ih = cv<T>(g.ih, g.f.ih);
 #pragma unroll
   for (int a = 0; a < 3; a++) s[a] = lim_slope(q[a], ok, ih);
 }
@@ -83,7 +83,7 @@ __device__ __noinline__ bool xbar(const Geo& g, const T* __restrict__ u, const T
   T sD[3], sU[3];
   slope_xi(g, x, lay, e, lo[0], lo[1], lo[2], sD);
   slope_xi(g, x, lay, e, i, j, k, sU);
-  const T h = T(g.h), dt = T(g.dt);
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
   const T uD = uval(g, u, e, lo[0], lo[1], lo[2]), uU = uval(g, u, e, i, j, k);
   int hi[3] = {i, j, k};
   wrap_axis(g, 0, hi[0]);
@@ -93,7 +93,7 @@ __device__ __noinline__ bool xbar(const Geo& g, const T* __restrict__ u, const T
 #pragma unroll
   for (int a = 0; a < 3; a++)
     out[a] = upwind(xD[a] + (T(0.5) * h - T(0.5) * dt * uD) * sD[a], xU[a] - (T(0.5) * h + T(0.5) * dt * uU) * sU[a], va,
-                    T(g.utol));
+                    cv<T>(g.utol, g.f.utol));
   return true;
 }
 
@@ -103,7 +103,7 @@ template <typename T>
 __device__ __noinline__ void xi_state(const Geo& g, const T* __restrict__ u, const T* __restrict__ x,
                          const int8_t* __restrict__ lay, const XiPredPtrs& pp, int d, int side, int i, int j, int k,
                          T out[3]) {
-  const T h = T(g.h), dt = T(g.dt), ih = T(1.0 / g.h);
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
   T xc[3], s[3];
   xi3(g, x, lay, i, j, k, xc);
   slope_xi(g, x, lay, d, i, j, k, s);
@@ -136,7 +136,7 @@ __device__ __noinline__ void xi_state(const Geo& g, const T* __restrict__ u, con
 template <typename T>
 __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, const int* __restrict__ bb,
                              const T* __restrict__ x, const int8_t* __restrict__ lay, T* __restrict__ xn) {
-  const T ih = T(1.0 / g.h), dt = T(g.dt);
+  const T ih = cv<T>(g.ih, g.f.ih), dt = cv<T>(g.dt, g.f.dt);
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
   const Win w = make_win(g, bb, 2);
   WIN_LOOP(t, w) {
@@ -169,7 +169,7 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
         if (okA) xi_state(g, u, x, lay, pp, d, 0, ca[0], ca[1], ca[2], L);
         if (okB) xi_state(g, u, x, lay, pp, d, 1, cb[0], cb[1], cb[2], R);
 #pragma unroll
-        for (int a = 0; a < 3; a++) xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un, T(g.utol)) : (okA ? L[a] : R[a]);
+        for (int a = 0; a < 3; a++) xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un, cv<T>(g.utol, g.f.utol)) : (okA ? L[a] : R[a]);
       }
       long lo, hi;
       cell_faces<T>(g, d, i, j, k, lo, hi);
