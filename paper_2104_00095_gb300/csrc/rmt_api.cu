@@ -79,6 +79,10 @@ struct rmt_grid {
   void *adv = nullptr, *ustar = nullptr, *psi = nullptr;
   void* ub[3][3] = {};
   void* slopes[9] = {};
+  void* wcell[9] = {};
+  void* xscr_s[9] = {};
+  void* xscr_b[9] = {};
+  int8_t* xscr_ok[3] = {};
   void* vadv[3] = {};
   void* uf[3][3] = {};
   void* umac[3] = {};
@@ -287,6 +291,14 @@ rmt_status init_t(rmt_grid* g) {
   AL(g->ustar, 3 * N * e);
   AL(g->psi, G.NN * e);
   for (int q = 0; q < 9; q++) AL(g->slopes[q], N * e);
+  for (int q = 0; q < 9; q++) AL(g->wcell[q], N * e);
+  if (!g->bodies.empty()) {
+    for (int q = 0; q < 9; q++) {
+      AL(g->xscr_s[q], N * e);
+      AL(g->xscr_b[q], N * e);
+    }
+    for (int q = 0; q < 3; q++) AL(g->xscr_ok[q], N);
+  }
   for (int d = 0; d < 3; d++) {
     const long nf = nfaces(G, d);
     for (int a = 0; a < 3; a++) {
@@ -369,6 +381,7 @@ rmt_status step_t(rmt_grid* g) {
   const int cur = g->par, nxt = 1 - g->par;
   T* ub[3][3];
   T* slopes[9];
+  T* wcell[9];
   T* vadv[3];
   T* uf[3][3];
   T* umac[3];
@@ -380,7 +393,10 @@ rmt_status step_t(rmt_grid* g) {
     vadv[d] = (T*)g->vadv[d];
     umac[d] = (T*)g->umac[d];
   }
-  for (int q = 0; q < 9; q++) slopes[q] = (T*)g->slopes[q];
+  for (int q = 0; q < 9; q++) {
+    slopes[q] = (T*)g->slopes[q];
+    wcell[q] = (T*)g->wcell[q];
+  }
   T* u = (T*)g->u;
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
@@ -389,7 +405,7 @@ rmt_status step_t(rmt_grid* g) {
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
   launch_bar_states<T>(G, u, slopes, ub, vadv, s);
-  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, slopes, ub, vadv, uf, s);
+  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, slopes, wcell, ub, vadv, uf, s);
   pe(g, P_GODUNOV);
   // 3. MAC projection of the normal face velocities
   pb(g, P_MAC_SETUP);
@@ -415,7 +431,8 @@ rmt_status step_t(rmt_grid* g) {
     BodyMem& b = g->bm[m];
     const int* bbc = b.bb + 6 * cur;
     pb(g, P_XI_PRED);
-    launch_xi_predict<T>(G, u, vadv, uf, umac, bbc, b.blocks, (const T*)b.X[cur], b.LAY[cur], (T*)b.X[nxt], s);
+    launch_xi_predict<T>(G, u, vadv, uf, umac, bbc, b.blocks, (const T*)b.X[cur], b.LAY[cur], (T* const*)g->xscr_s,
+                         (T* const*)g->xscr_b, g->xscr_ok, (T*)b.X[nxt], s);
     pe(g, P_XI_PRED);
     pb(g, P_EXTRAP);
     launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[nxt],

@@ -116,67 +116,87 @@ struct BarPtrs {
   void* uf[3];
 };
 
-// normal-face states of the velocity (eqs. left_final, right_final) + Godunov choice
+// Side-independent part of the face states of every cell (eqs. left_final, right_final):
+// W[3d+a] = u_a - (dt/2) T_d(u_a) + dt/(2 rho) F_a, with T_d the tangential terms along the two
+// axes other than d (SI "Tangential derivatives") and F = -grad p^{n-1/2} + div tau^n + b^n,
+// b = (rho - rho_f) g.  A face state is then W + (+-h/2 - dt/2 u_d) * slope.
 template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* __restrict__ u, const T* __restrict__ p,
-                                                          const T* __restrict__ rho, const T* __restrict__ divtau,
-                                                          Slopes9 S, BarPtrs bp) {
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_cellw(Geo g, const T* __restrict__ u, const T* __restrict__ p,
+                                                           const T* __restrict__ rho, const T* __restrict__ divtau,
+                                                           BarPtrs bp, Slopes9 W) {
+  THREAD_XYZ(i, j, k);
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const T dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
+  const long c = cidx(g, i, j, k);
+  T gp[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
+    const T pv = p[node_at(g, i + sa, j + sb, k + sc)];
+    gp[0] += sa ? pv : -pv;
+    gp[1] += sb ? pv : -pv;
+    gp[2] += sc ? pv : -pv;
+  }
+  const T r = rho[c];
+  T vavg[3];
+  long lo[3], hi[3];
+#pragma unroll
+  for (int e = 0; e < 3; e++) {
+    cell_faces<T>(g, e, i, j, k, lo[e], hi[e]);
+    const T* vad = (const T*)bp.vadv[e];
+    vavg[e] = T(0.5) * (vad[lo[e]] + vad[hi[e]]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] +
+                (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
+    T term[3];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      const T* ube = (const T*)bp.ub[e][a];
+      term[e] = vavg[e] * (ube[hi[e]] - ube[lo[e]]) * ih;
+    }
+    const T base = u[a * g.N + c] + T(0.5) * dt / r * F;
+    ((T*)W.s[a])[c] = base - T(0.5) * dt * (term[1] + term[2]);
+    ((T*)W.s[3 + a])[c] = base - T(0.5) * dt * (term[0] + term[2]);
+    ((T*)W.s[6 + a])[c] = base - T(0.5) * dt * (term[0] + term[1]);
+  }
+}
+
+// normal-face states of the velocity and the Godunov choice (SI "Godunov-type upwinding")
+template <typename T>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* __restrict__ u, Slopes9 S, Slopes9 W,
+                                                          BarPtrs bp) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1), ez = g.n[2] + (d == 2);
-  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
   T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
   THREAD_XYZ(i, j, k);
-  if (i < ex && j < ey && k < ez) {
-    const long f = i + (long)ex * (j + (long)ey * k);
-    const int fi = d == 0 ? i : (d == 1 ? j : k);
-    if (is_wall_face(g, d, fi)) {
-      const int face = fi == 0 ? 2 * d : 2 * d + 1;
+  if (i >= ex || j >= ey || k >= ez) return;
+  const long f = i + (long)ex * (j + (long)ey * k);
+  const int fi = d == 0 ? i : (d == 1 ? j : k);
+  if (is_wall_face(g, d, fi)) {
+    const int face = fi == 0 ? 2 * d : 2 * d + 1;
 #pragma unroll
-      for (int a = 0; a < 3; a++) uf[a][f] = cv<T>(g.wall[face][a], g.f.wall[face][a]);
-      return;
-    }
-    T st[2][3];
-#pragma unroll
-    for (int side = 0; side < 2; side++) {
-      int cc[3] = {i, j, k};
-      if (side == 0) cc[d] -= 1;
-      wrap_axis(g, 0, cc[0]);
-      wrap_axis(g, 1, cc[1]);
-      wrap_axis(g, 2, cc[2]);
-      const long c = cidx(g, cc[0], cc[1], cc[2]);
-      // forcing -grad p^{n-1/2} + div tau^n + b^n, b = (rho - rho_f) g
-      T gp[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
-        const T pv = p[node_at(g, cc[0] + sa, cc[1] + sb, cc[2] + sc)];
-        gp[0] += sa ? pv : -pv;
-        gp[1] += sb ? pv : -pv;
-        gp[2] += sc ? pv : -pv;
-      }
-      const T r = rho[c];
-      const T ud = u[d * g.N + c];
-      const T coef = side == 0 ? (T(0.5) * h - T(0.5) * dt * ud) : -(T(0.5) * h + T(0.5) * dt * ud);
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
-        T tr = T(0);
-#pragma unroll
-        for (int e = 0; e < 3; e++) {
-          if (e == d) continue;
-          long lo, hi;
-          cell_faces<T>(g, e, cc[0], cc[1], cc[2], lo, hi);
-          const T* vad = (const T*)bp.vadv[e];
-          const T* ube = (const T*)bp.ub[e][a];
-          tr += T(0.5) * (vad[lo] + vad[hi]) * (ube[hi] - ube[lo]) * ih;
-        }
-        st[side][a] = u[a * g.N + c] + coef * ((const T*)S.s[3 * d + a])[c] - T(0.5) * dt * tr +
-                      T(0.5) * dt / r * F;
-      }
-    }
-    const T un = god_normal(st[0][d], st[1][d], cv<T>(g.utol, g.f.utol));
-#pragma unroll
-    for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un, cv<T>(g.utol, g.f.utol));
+    for (int a = 0; a < 3; a++) uf[a][f] = cv<T>(g.wall[face][a], g.f.wall[face][a]);
+    return;
   }
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  lo[d] -= 1;
+  if (lo[d] < 0) lo[d] += g.n[d];
+  if (hi[d] >= g.n[d]) hi[d] -= g.n[d];
+  const long cc[2] = {cidx(g, lo[0], lo[1], lo[2]), cidx(g, hi[0], hi[1], hi[2])};
+  T st[2][3];
+#pragma unroll
+  for (int side = 0; side < 2; side++) {
+    const long c = cc[side];
+    const T ud = u[d * g.N + c];
+    const T coef = side == 0 ? (T(0.5) * h - T(0.5) * dt * ud) : -(T(0.5) * h + T(0.5) * dt * ud);
+#pragma unroll
+    for (int a = 0; a < 3; a++) st[side][a] = ((const T*)W.s[3 * d + a])[c] + coef * ((const T*)S.s[3 * d + a])[c];
+  }
+  const T un = god_normal(st[0][d], st[1][d], cv<T>(g.utol, g.f.utol));
+#pragma unroll
+  for (int a = 0; a < 3; a++) uf[a][f] = (a == d) ? un : upwind(st[0][a], st[1][a], un, cv<T>(g.utol, g.f.utol));
 }
 
 // ---------------------------------------------------------------------------------
@@ -383,18 +403,24 @@ void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ub
 }
 template <typename T>
 void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
-                        T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
+                        T* const wcell[9], T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
   BarPtrs bp;
-  Slopes9 S;
-  for (int q = 0; q < 9; q++) S.s[q] = slopes[q];
+  Slopes9 S, W;
+  for (int q = 0; q < 9; q++) {
+    S.s[q] = slopes[q];
+    W.s[q] = wcell[q];
+  }
   for (int e = 0; e < 3; e++) {
     for (int a = 0; a < 3; a++) bp.ub[e][a] = ubar[e][a];
     bp.vadv[e] = vadv[e];
   }
+  const dim3 gc((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  k_cellw<T><<<gc, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, p, rho, divtau, bp, W);
+  rmt_count_launches(1);
   for (int d = 0; d < 3; d++) {
     for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
     const dim3 gr((g.n[0] + (d == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (d == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (d == 2));
-    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, p, rho, divtau, S, bp);
+    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, S, W, bp);
     rmt_count_launches(1);
   }
 }
@@ -450,7 +476,7 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
 #define INST(T)                                                                                                   \
   template void launch_bar_states<T>(const Geo&, const T*, T* const[9], T* const[3][3], T* const[3], cudaStream_t); \
   template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[9],           \
-                                      T* const[3][3], T* const[3], T* const[3][3], cudaStream_t);                \
+                                      T* const[9], T* const[3][3], T* const[3], T* const[3][3], cudaStream_t);   \
   template void launch_mac_setup<T>(const Geo&, T* const[3][3], double*, cudaStream_t);                          \
   template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, const double*, T* const[3],          \
                                       cudaStream_t);                                                             \

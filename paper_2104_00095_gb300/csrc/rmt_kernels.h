@@ -20,9 +20,10 @@ void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyV
 template <typename T>
 void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ubar[3][3], T* const vadv[3],
                        cudaStream_t s);
+// wcell: nine cell arrays of scratch for the side-independent part of the face states
 template <typename T>
 void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
-                        T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
+                        T* const wcell[9], T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
 template <typename T>
 void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s);
 template <typename T>
@@ -30,9 +31,12 @@ void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, const dou
                         cudaStream_t s);
 template <typename T>
 void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s);
+// scratch_s, scratch_xb, scratch_ok: N-sized scratch (9 + 9 arrays of T, 3 of int8) reused by
+// every body in turn
 template <typename T>
 void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3],
-                       const int* bb, int blocks, const T* x, const int8_t* lay, T* xn, cudaStream_t s);
+                       const int* bb, int blocks, const T* x, const int8_t* lay, T* const scratch_s[9],
+                       T* const scratch_xb[9], int8_t* const scratch_ok[3], T* xn, cudaStream_t s);
 template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho,
                     cudaStream_t s);

@@ -1,6 +1,7 @@
 // Predictor of the reference map (arXiv 2104.00095, eq. dis_xi_adv with the Godunov face
 // states of eq. xi_taylor_final and the tangential terms of SI "Tangential derivatives").
-// One thread per cell of layers 0 and 1 rebuilds the xi states at its six faces.
+// Three passes over a body's window: limited slopes of xi, transverse bar states on faces,
+// then the predictor at the cells of layers 0 and 1.
 #include "rmt_kernels.h"
 
 namespace {
@@ -49,8 +50,8 @@ __device__ __forceinline__ bool xi3(const Geo& g, const T* __restrict__ x, const
 }
 
 template <typename T>
-__device__ __noinline__ void slope_xi(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int d, int i, int j,
-                         int k, T s[3]) {
+__device__ __forceinline__ void slope_xi(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int d,
+                                         int i, int j, int k, T s[3]) {
   T q[3][5];
   unsigned ok = 0;
 #pragma unroll
@@ -70,72 +71,115 @@ __device__ __noinline__ void slope_xi(const Geo& g, const T* __restrict__ x, con
   for (int a = 0; a < 3; a++) s[a] = lim_slope(q[a], ok, ih);
 }
 
-// xi bar state at the e-face below cell (i,j,k); false when unavailable
+// Per-body scratch shared by the three passes (N-sized arrays, reused body after body):
+// s[3d+a] limited slope of xi_a along d at a cell; xb[3e+a] the upwinded bar state of xi_a
+// on the e-face below a cell, ok[e] its availability.
+struct XiScratch {
+  void* s[9];
+  void* xb[9];
+  int8_t* ok[3];
+};
+
+// pass 1: limited slopes of xi at every band cell of the window
 template <typename T>
-__device__ __noinline__ bool xbar(const Geo& g, const T* __restrict__ u, const T* __restrict__ x, const int8_t* __restrict__ lay,
-                     const T* __restrict__ vadv_e, int e, int i, int j, int k, T out[3]) {
-  int fc = e == 0 ? i : (e == 1 ? j : k);
-  if (!g.per[e] && (fc <= 0 || fc >= g.n[e])) return false;  // wall face
-  int lo[3] = {i, j, k};
-  lo[e] -= 1;
-  T xD[3], xU[3];
-  if (!xi3(g, x, lay, lo[0], lo[1], lo[2], xD) || !xi3(g, x, lay, i, j, k, xU)) return false;
-  T sD[3], sU[3];
-  slope_xi(g, x, lay, e, lo[0], lo[1], lo[2], sD);
-  slope_xi(g, x, lay, e, i, j, k, sU);
-  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
-  const T uD = uval(g, u, e, lo[0], lo[1], lo[2]), uU = uval(g, u, e, i, j, k);
-  int hi[3] = {i, j, k};
-  wrap_axis(g, 0, hi[0]);
-  wrap_axis(g, 1, hi[1]);
-  wrap_axis(g, 2, hi[2]);
-  const T va = vadv_e[fidx(g, e, hi[0], hi[1], hi[2])];
+__global__ void k_xi_slopes(Geo g, const int* __restrict__ bb, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                            XiScratch sc) {
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int uu[3], i, j, k;
+    long c;
+    win_cell(g, w, t, uu, i, j, k, c);
+    if (lay[c] < 0) continue;
 #pragma unroll
-  for (int a = 0; a < 3; a++)
-    out[a] = upwind(xD[a] + (T(0.5) * h - T(0.5) * dt * uD) * sD[a], xU[a] - (T(0.5) * h + T(0.5) * dt * uU) * sU[a], va,
-                    cv<T>(g.utol, g.f.utol));
-  return true;
+    for (int d = 0; d < 3; d++) {
+      T s3[3];
+      slope_xi(g, x, lay, d, i, j, k, s3);
+#pragma unroll
+      for (int a = 0; a < 3; a++) ((T*)sc.s[3 * d + a])[c] = s3[a];
+    }
+  }
 }
 
-// Taylor state of xi from cell c toward its d-face; side 0: the face above c (L state),
-// side 1: the face below c (R state)
+// pass 2: transverse bar states of xi on the e-face below every window cell (SI "Tangential
+// derivatives"), upwinded with the velocity's advecting bar velocity; unavailable on walls
+// and where either cell lacks xi
 template <typename T>
-__device__ __noinline__ void xi_state(const Geo& g, const T* __restrict__ u, const T* __restrict__ x,
-                         const int8_t* __restrict__ lay, const XiPredPtrs& pp, int d, int side, int i, int j, int k,
-                         T out[3]) {
+__global__ void k_xi_bar(Geo g, const int* __restrict__ bb, const T* __restrict__ u, XiPredPtrs pp,
+                         const T* __restrict__ x, const int8_t* __restrict__ lay, XiScratch sc) {
+  const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
+  const Win w = make_win(g, bb, 2);
+  WIN_LOOP(t, w) {
+    int uu[3], i, j, k;
+    long c;
+    win_cell(g, w, t, uu, i, j, k, c);
+    const int cc[3] = {i, j, k};
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      int8_t ok = 0;
+      if ((g.per[e] || cc[e] > 0) && lay[c] >= 0) {
+        int lo[3] = {i, j, k};
+        lo[e] = cc[e] > 0 ? cc[e] - 1 : g.n[e] - 1;
+        const long cD = cidx(g, lo[0], lo[1], lo[2]);
+        if (lay[cD] >= 0) {
+          ok = 1;
+          const T uD = u[e * g.N + cD], uU = u[e * g.N + c];
+          const T va = ((const T*)pp.vadv[e])[fidx(g, e, i, j, k)];
+#pragma unroll
+          for (int a = 0; a < 3; a++) {
+            const T sD = ((const T*)sc.s[3 * e + a])[cD], sU = ((const T*)sc.s[3 * e + a])[c];
+            ((T*)sc.xb[3 * e + a])[c] = upwind(x[a * g.N + cD] + (T(0.5) * h - T(0.5) * dt * uD) * sD,
+                                               x[a * g.N + c] - (T(0.5) * h + T(0.5) * dt * uU) * sU, va,
+                                               cv<T>(g.utol, g.f.utol));
+          }
+        }
+      }
+      sc.ok[e][c] = ok;
+    }
+  }
+}
+
+// Taylor state of xi from cell (i,j,k) (inside the grid) toward its d-face (eq. xi_taylor_final):
+// side 0 the face above the cell (L state), side 1 the face below (R state)
+template <typename T>
+__device__ __forceinline__ void xi_state(const Geo& g, const T* __restrict__ u, const T* __restrict__ x,
+                                         const XiPredPtrs& pp, const XiScratch& sc, int d, int side, int i, int j,
+                                         int k, T out[3]) {
   const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
-  T xc[3], s[3];
-  xi3(g, x, lay, i, j, k, xc);
-  slope_xi(g, x, lay, d, i, j, k, s);
-  const T ud = uval(g, u, d, i, j, k);
+  const long c = cidx(g, i, j, k);
+  const T ud = u[d * g.N + c];
   const T coef = side == 0 ? (T(0.5) * h - T(0.5) * dt * ud) : -(T(0.5) * h + T(0.5) * dt * ud);
   T tr[3] = {T(0), T(0), T(0)};
+  const int cc[3] = {i, j, k};
 #pragma unroll
   for (int e = 0; e < 3; e++) {
     if (e == d) continue;
+    // bar states on the e-faces below and above the cell; the one above is owned by the next
+    // cell along e (none past a wall)
+    if (!sc.ok[e][c]) continue;
+    if (!g.per[e] && cc[e] == g.n[e] - 1) continue;
     int up[3] = {i, j, k};
-    up[e] += 1;
-    T bl[3], bh[3];
-    if (!xbar(g, u, x, lay, (const T*)pp.vadv[e], e, i, j, k, bl)) continue;
-    if (!xbar(g, u, x, lay, (const T*)pp.vadv[e], e, up[0], up[1], up[2], bh)) continue;
-    int cw[3] = {i, j, k};
-    wrap_axis(g, 0, cw[0]);
-    wrap_axis(g, 1, cw[1]);
-    wrap_axis(g, 2, cw[2]);
+    up[e] = cc[e] + 1 < g.n[e] ? cc[e] + 1 : 0;
+    const long cu = cidx(g, up[0], up[1], up[2]);
+    if (!sc.ok[e][cu]) continue;
     long lo, hi;
-    cell_faces<T>(g, e, cw[0], cw[1], cw[2], lo, hi);
+    cell_faces<T>(g, e, i, j, k, lo, hi);
     const T* va = (const T*)pp.vadv[e];
     const T vav = T(0.5) * (va[lo] + va[hi]);
 #pragma unroll
-    for (int a = 0; a < 3; a++) tr[a] += vav * (bh[a] - bl[a]) * ih;
+    for (int a = 0; a < 3; a++)
+      tr[a] += vav * (((const T*)sc.xb[3 * e + a])[cu] - ((const T*)sc.xb[3 * e + a])[c]) * ih;
   }
 #pragma unroll
-  for (int a = 0; a < 3; a++) out[a] = xc[a] + coef * s[a] - T(0.5) * dt * tr[a];
+  for (int a = 0; a < 3; a++)
+    out[a] = x[a * g.N + c] + coef * ((const T*)sc.s[3 * d + a])[c] - T(0.5) * dt * tr[a];
 }
 
+// pass 3: xi^{n+1} = xi^n - dt [(u.grad) xi]^{n+1/2} at the cells of layers 0 and 1 whose six faces
+// carry xi^{n+1/2}; NaN at every other window cell
 template <typename T>
 __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, const int* __restrict__ bb,
-                             const T* __restrict__ x, const int8_t* __restrict__ lay, T* __restrict__ xn) {
+                             const T* __restrict__ x, const int8_t* __restrict__ lay, XiScratch sc,
+                             T* __restrict__ xn) {
   const T ih = cv<T>(g.ih, g.f.ih), dt = cv<T>(g.dt, g.f.dt);
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
   const Win w = make_win(g, bb, 2);
@@ -157,19 +201,19 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
         // fs = 0: face below c (a = c - e_d, b = c); fs = 1: face above (a = c, b = c + e_d)
         int ca[3] = {i, j, k}, cb[3] = {i, j, k};
         if (fs == 0) ca[d] -= 1; else cb[d] += 1;
-        T t0[3];
-        const bool okA = xi3(g, x, lay, ca[0], ca[1], ca[2], t0);
-        const bool okB = xi3(g, x, lay, cb[0], cb[1], cb[2], t0);
-        int fw[3] = {cb[0], cb[1], cb[2]};
-        // face index: the d-index of cell b before wrapping (n_d allowed)
-        if (fw[d] > g.n[d]) fw[d] -= g.n[d];
-        const long f = fidx(g, d, fw[0], fw[1], fw[2]);
+        const long f = fidx(g, d, cb[0], cb[1], cb[2]);  // face index: d-index of b, up to n_d
+        long la, lb;
+        const bool okA = cell_at(g, ca[0], ca[1], ca[2], la) && lay[la] >= 0;
+        const bool okB = cell_at(g, cb[0], cb[1], cb[2], lb) && lay[lb] >= 0;
+        wrap_axis(g, d, ca[d]);
+        wrap_axis(g, d, cb[d]);
         const T un = ((const T*)pp.unpre[d])[f];
         T L[3], R[3];
-        if (okA) xi_state(g, u, x, lay, pp, d, 0, ca[0], ca[1], ca[2], L);
-        if (okB) xi_state(g, u, x, lay, pp, d, 1, cb[0], cb[1], cb[2], R);
+        if (okA) xi_state(g, u, x, pp, sc, d, 0, ca[0], ca[1], ca[2], L);
+        if (okB) xi_state(g, u, x, pp, sc, d, 1, cb[0], cb[1], cb[2], R);
 #pragma unroll
-        for (int a = 0; a < 3; a++) xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un, cv<T>(g.utol, g.f.utol)) : (okA ? L[a] : R[a]);
+        for (int a = 0; a < 3; a++)
+          xf[fs][a] = (okA && okB) ? upwind(L[a], R[a], un, cv<T>(g.utol, g.f.utol)) : (okA ? L[a] : R[a]);
       }
       long lo, hi;
       cell_faces<T>(g, d, i, j, k, lo, hi);
@@ -187,19 +231,31 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
 
 template <typename T>
 void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3][3], T* const umac[3], const int* bb,
-                       int blocks, const T* x, const int8_t* lay, T* xn, cudaStream_t s) {
+                       int blocks, const T* x, const int8_t* lay, T* const scratch_s[9], T* const scratch_xb[9],
+                       int8_t* const scratch_ok[3], T* xn, cudaStream_t s) {
   XiPredPtrs pp;
+  XiScratch sc;
   for (int d = 0; d < 3; d++) {
     pp.vadv[d] = vadv[d];
     pp.unpre[d] = uf[d][d];
     pp.umac[d] = umac[d];
+    sc.ok[d] = scratch_ok[d];
   }
-  k_xi_predict<T><<<blocks, TPB, 0, s>>>(g, u, pp, bb, x, lay, xn);
+  for (int q = 0; q < 9; q++) {
+    sc.s[q] = scratch_s[q];
+    sc.xb[q] = scratch_xb[q];
+  }
+  k_xi_slopes<T><<<blocks, TPB, 0, s>>>(g, bb, x, lay, sc);
+  rmt_count_launches(1);
+  k_xi_bar<T><<<blocks, TPB, 0, s>>>(g, bb, u, pp, x, lay, sc);
+  rmt_count_launches(1);
+  k_xi_predict<T><<<blocks, TPB, 0, s>>>(g, u, pp, bb, x, lay, sc, xn);
   rmt_count_launches(1);
 }
 
 template void launch_xi_predict<float>(const Geo&, const float*, float* const[3], float* const[3][3], float* const[3],
-                                       const int*, int, const float*, const int8_t*, float*, cudaStream_t);
+                                       const int*, int, const float*, const int8_t*, float* const[9], float* const[9],
+                                       int8_t* const[3], float*, cudaStream_t);
 template void launch_xi_predict<double>(const Geo&, const double*, double* const[3], double* const[3][3],
-                                        double* const[3], const int*, int, const double*, const int8_t*, double*,
-                                        cudaStream_t);
+                                        double* const[3], const int*, int, const double*, const int8_t*,
+                                        double* const[9], double* const[9], int8_t* const[3], double*, cudaStream_t);
