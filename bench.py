@@ -55,6 +55,23 @@ def make_scene(cfg: dict, n: int | None = None, nbodies: int | None = None):
     return S.cavity_sphere(n, precision=cfg["precision"])
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x of all ranks (x itself when world == 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job cell-updates/s: every replica advances its own grid of `cells` cells."""
+    return world * cells * steps / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,6 +181,8 @@ def main():
                     help="FE V-cycles per FP64 residual (mixed-precision refinement)")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="override the grid edge (profiling captures of a smaller case only; changes the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -190,7 +209,7 @@ def main():
             dist.barrier()
 
     stream = torch.cuda.current_stream()
-    scene = make_scene(cfg, nbodies=args.nbodies)
+    scene = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
     scene["options"] = {"fe_inner": args.fe_inner}
@@ -219,11 +238,8 @@ def main():
     clocks = clk.stop()
     launches = rmt.kernel_launches() - l0
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = job_rate(world, N, args.steps, ms / 1e3)
 
     # the same steps again with the library's CUDA-event profiler on: per-stage times and the
     # per-launch duration of the finest-level multigrid kernels
@@ -268,11 +284,8 @@ def main():
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         et = t1 - t0
-        if world > 1:
-            t = torch.tensor([et], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": world * N * args.steps / et, "unit": "cell-updates/s",
+        et = max_over_ranks(et, world)
+        e2e = {"value": job_rate(world, N, args.steps, et), "unit": "cell-updates/s",
                "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
                "ms_per_step": 1e3 * et / args.steps}
 
@@ -288,13 +301,14 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if cfg["precision"] == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": args.config, "description": cfg["desc"], "grid": list(scene["n"]),
+                "config": {"workload": args.config if args.n is None else f"{args.config} resized to {args.n}^3",
+                           "description": cfg["desc"], "grid": list(scene["n"]),
                            "bodies": len(scene["solids"]),
                            "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
                                                    "fe_inner": args.fe_inner},
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
-                "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,
+                "gpu_launches": launches, "gpu_launches_before_timed": l0, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,
                 "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     g.close()

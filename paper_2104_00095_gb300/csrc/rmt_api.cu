@@ -73,6 +73,7 @@ struct rmt_grid {
   std::vector<Body> bodies;
   std::vector<BodyMem> bm;
   Body* bodies_d = nullptr;
+  int* bb_all = nullptr;  // band boxes: body m, parity p at 12 m + 6 p
   void* views_d = nullptr;  // BodyView<T>[2 parities][3 levels][nb]
   int par = 0;
   void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
@@ -319,10 +320,12 @@ rmt_status init_t(rmt_grid* g) {
     }
     AL(b.XH, 3 * N * e);
     AL(b.PHIH, N * e);
-    AL(b.bb, 12 * sizeof(int));
+    b.bb = nullptr;  // set below: all bodies' boxes are contiguous
     AL(b.list, N * sizeof(int));
     AL(b.count, 16);
   }
+  AL(g->bb_all, (nb > 0 ? nb : 1) * 12 * sizeof(int));
+  for (int m = 0; m < nb; m++) g->bm[m].bb = g->bb_all + 12 * m;
   AL(g->bodies_d, (nb > 0 ? nb : 1) * sizeof(Body));
   AL(g->views_d, (size_t)6 * (nb > 0 ? nb : 1) * sizeof(BodyView<T>));
   AL(g->err_d, 16);
@@ -367,7 +370,7 @@ rmt_status init_t(rmt_grid* g) {
     launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[0],
                           (T*)b.PHI[0], b.LAY[0], g->err_d, g->s);
   }
-  launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, (T*)g->rho, g->s);
+  launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, g->bb_all, 12, (T*)g->rho, g->s);
   CK(g, cudaGetLastError());
   CK(g, cudaStreamSynchronize(g->s));
   return size_windows(g);
@@ -400,7 +403,7 @@ rmt_status step_t(rmt_grid* g) {
   T* u = (T*)g->u;
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->t, (T*)g->divn, s);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t, (T*)g->divn, s);
   pe(g, P_STRESS_N);
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
@@ -445,10 +448,11 @@ rmt_status step_t(rmt_grid* g) {
   }
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
   pb(g, P_STRESS_H);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->t + 0.5 * G.dt, (T*)g->divh, s);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t + 0.5 * G.dt,
+                       (T*)g->divh, s);
   pe(g, P_STRESS_H);
   pb(g, P_USTAR);
-  launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, (T*)g->rho_h, s);
+  launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho_h, s);
   launch_ustar<T>(G, u, (const T*)g->adv, (const T*)g->p, (const T*)g->rho_h, (const T*)g->divh, (T*)g->ustar, s);
   pe(g, P_USTAR);
   // 11. approximate projection, u^{n+1}, p^{n+1/2}
@@ -467,7 +471,7 @@ rmt_status step_t(rmt_grid* g) {
   launch_fe_update<T>(G, (const T*)g->ustar, (const T*)g->rho_h, mg_solution(g->fe), u, (T*)g->p, (T*)g->psi, s);
   // 12. xi <- xi^{n+1} (parity flip); 13. rho^{n+1}
   g->par = nxt;
-  launch_density<T>(G, g->bodies_d, views<T>(g, nxt, 0), nb, (T*)g->rho, s);
+  launch_density<T>(G, g->bodies_d, views<T>(g, nxt, 0), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho, s);
   pe(g, P_FE_UPDATE);
   CK(g, cudaGetLastError());
   g->t += G.dt;
@@ -572,7 +576,8 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
     const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
     launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count, WLS_BLOCKS,
                           (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s);
-    launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), (T*)g->rho, s);
+    launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), g->bb_all + 6 * g->par, 12,
+                      (T*)g->rho, s);
   }
   CK(g, cudaGetLastError());
   return RMT_OK;

@@ -371,6 +371,26 @@ __device__ __forceinline__ void win_cell(const Geo& g, const Win& w, long t, int
 #define WIN_LOOP(t, w) \
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < (w).vol; t += (long)gridDim.x * blockDim.x)
 
+// Band boxes of all bodies staged in shared memory (6 ints per body: inclusive min, max; min
+// above max for an empty band), so that a cell reads a body's layer byte only inside its box.
+__device__ __forceinline__ void stage_boxes(const int* __restrict__ bbs, int stride, int nb, int* sbb) {
+  for (int q = threadIdx.x + blockDim.x * threadIdx.y; q < 6 * nb; q += blockDim.x * blockDim.y)
+    sbb[q] = bbs[(q / 6) * stride + q % 6];
+  __syncthreads();
+}
+__device__ __forceinline__ bool in_box(const Geo& g, const int* bb, int i, int j, int k) {
+  const int c[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const int lo = bb[d], hi = bb[3 + d];
+    if (lo > hi) return false;
+    int t = c[d] - lo;
+    if (g.per[d] && t < 0) t += g.n[d];
+    if (t < 0 || t > hi - lo) return false;
+  }
+  return true;
+}
+
 // grid-stride helper
 #define GRID_LOOP(idx, total) \
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (total); idx += (long)gridDim.x * blockDim.x)

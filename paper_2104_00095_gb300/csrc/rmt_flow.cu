@@ -284,12 +284,16 @@ __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
 
 template <typename T>
 __global__ void k_density(Geo g, const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb,
-                          T* __restrict__ rho) {
+                          const int* __restrict__ bbs, int bstride, T* __restrict__ rho) {
+  __shared__ int sbb[6 * RMT_MAX_BODIES];
+  stage_boxes(bbs, bstride, nb, sbb);
   const T eps = cv<T>(g.eps, g.f.eps);
   GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
     T wsum = T(0), acc = T(0);
     for (int m = 0; m < nb; m++) {
-      if (views[m].lay[c] < 0) continue;
+      if (!in_box(g, sbb + 6 * m, i, j, k) || views[m].lay[c] < 0) continue;
       const T w = T(1) - heavi(views[m].phi[c], eps);
       acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
       wsum += w;
@@ -449,8 +453,9 @@ void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cu
   k_adv<T><<<nblocks(g.N), TPB, 0, s>>>(g, ap, adv); rmt_count_launches(1);
 }
 template <typename T>
-void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho, cudaStream_t s) {
-  k_density<T><<<nblocks(g.N), TPB, 0, s>>>(g, bodies, views, nb, rho); rmt_count_launches(1);
+void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
+                    T* rho, cudaStream_t s) {
+  k_density<T><<<nblocks(g.N), TPB, 0, s>>>(g, bodies, views, nb, bbs, bstride, rho); rmt_count_launches(1);
 }
 template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h, T* ustar,
@@ -481,7 +486,8 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
   template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, const double*, T* const[3],          \
                                       cudaStream_t);                                                             \
   template void launch_advect<T>(const Geo&, T* const[3][3], T* const[3], T*, cudaStream_t);                      \
-  template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, T*, cudaStream_t);          \
+  template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, const int*, int, T*,        \
+                                  cudaStream_t);                                                                \
   template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, cudaStream_t); \
   template void launch_fe_setup<T>(const Geo&, const T*, const T*, double*, cudaStream_t);                      \
   template void launch_fe_update<T>(const Geo&, const T*, const T*, const double*, T*, T*, T*, cudaStream_t);    \

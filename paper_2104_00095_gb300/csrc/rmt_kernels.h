@@ -12,9 +12,10 @@ struct Faces3 {
 };
 
 // ---- flow (rmt_flow.cu) -------------------------------------------------------------
+// bbs: band boxes of the bodies (6 ints each, stride ints apart) of the time level of views
 template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
-                       double t, T* out, cudaStream_t s);
+                       const int* bbs, int bstride, double t, T* out, cudaStream_t s);
 // slopes: nine cell arrays, written by launch_bar_states (limited slope of u_a along d at 3d+a)
 // and read by launch_face_states
 template <typename T>
@@ -38,8 +39,8 @@ void launch_xi_predict(const Geo& g, const T* u, T* const vadv[3], T* const uf[3
                        const int* bb, int blocks, const T* x, const int8_t* lay, T* const scratch_s[9],
                        T* const scratch_xb[9], int8_t* const scratch_ok[3], T* xn, cudaStream_t s);
 template <typename T>
-void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, T* rho,
-                    cudaStream_t s);
+void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
+                    T* rho, cudaStream_t s);
 template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h,
                   T* ustar, cudaStream_t s);

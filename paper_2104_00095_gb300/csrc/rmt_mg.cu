@@ -13,8 +13,12 @@
 // reads beta = 1/rho per cell, formed once per solve.  Coefficients are evaluated in the
 // storage type; the FP64 residual only accumulates in FP64, so it needs no FP64 division.
 //
-// Solve = iterative refinement: the residual of an FP64 iterate is formed in FP64 and a
-// V-cycle in the storage type T (double or float) computes the correction.  Smoothers:
+// Solve = iterative refinement: the residual of a high-precision iterate is formed in high
+// precision and V-cycles in the storage type T (double or float) compute the correction.  With
+// T = double the iterate and its residual are FP64.  With T = float they are two-float numbers
+// (hi + lo, about 48 significant bits; Knuth's two-sum and the FMA two-product), so the
+// residual runs on the FP32 pipe: GB300 issues FP64 at 1/64 of the FP32 rate, and an FP64
+// residual of the 27-point operator costs several times a V-cycle.  Smoothers:
 // red-black Gauss-Seidel (7-point; one thread per same-colour cell pair along x) and weighted
 // Jacobi (27-point; one fused pass per sweep).  Transfers: 8-cell average / trilinear
 // (cell-centred), full weighting / trilinear (nodal).  Coarse densities are 8-cell means.
@@ -44,6 +48,7 @@ struct Lv {
   long ncell, nnode, nunk;
   double h, ih2, s12;  // spacing, 1/h^2 (MAC), h/12 (FE)
   float f_ih2, f_s12;
+  float f_ih2_lo, f_s12_lo;  // ih2 - f_ih2, s12 - f_s12: the two-float constants
 };
 
 inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
@@ -79,6 +84,20 @@ __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, cons
   const long c = cix(L, i, j, k);
   const CT rc = rho[c];
   AT off = AT(0), dg = AT(0);
+  if (i > 0 && i + 1 < L.n[0] && j > 0 && j + 1 < L.n[1] && k > 0 && k + 1 < L.n[2]) {
+    // interior: six neighbours at fixed offsets, no boundary rules
+    const long st[3] = {1, (long)L.n[0], (long)L.n[0] * L.n[1]};
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      const long cn = c + ((f & 1) ? st[f >> 1] : -st[f >> 1]);
+      const AT beta = (AT)face_beta<FAST>(rc, rho[cn]);
+      off += beta * (AT)x[cn];
+      dg += beta;
+    }
+    const AT ih2 = cv<AT>(L.ih2, L.f_ih2);
+    diag = dg * ih2;
+    return (dg * (AT)x[c] - off) * ih2;
+  }
   const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
 #pragma unroll
   for (int f = 0; f < 6; f++) {
@@ -99,8 +118,55 @@ __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, cons
 
 // FE at node (i,j,k): returns (K x)_i and its diagonal
 template <typename AT, typename XT, typename CT>
+__device__ __forceinline__ AT fe_op_interior(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ beta, int i,
+                                             int j, int k, AT& diag) {
+  // node away from every boundary: its 8 cells and 26 neighbours at fixed offsets
+  const long sx = 1, sy = L.nn[0], sz = (long)L.nn[0] * L.nn[1];
+  const long cy = L.n[0], cz = (long)L.n[0] * L.n[1];
+  const long c0 = cix(L, i - 1, j - 1, k - 1);
+  AT b[2][2][2];
+  AT bs = AT(0);
+#pragma unroll
+  for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+    for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++) {
+        b[qx][qy][qz] = (AT)beta[c0 + qx + qy * cy + qz * cz];
+        bs += b[qx][qy][qz];
+      }
+  const long n0 = nix(L, i, j, k);
+  AT s = AT(0);
+#pragma unroll
+  for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+    for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++)
+        s += b[qx][qy][qz] * (AT)x[n0 + (2 * qx - 1) * sx + (2 * qy - 1) * sy + (2 * qz - 1) * sz];
+#pragma unroll
+  for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+    for (int qx = 0; qx < 2; qx++) s += (b[qx][qy][0] + b[qx][qy][1]) * (AT)x[n0 + (2 * qx - 1) * sx + (2 * qy - 1) * sy];
+#pragma unroll
+  for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+    for (int qx = 0; qx < 2; qx++) s += (b[qx][0][qz] + b[qx][1][qz]) * (AT)x[n0 + (2 * qx - 1) * sx + (2 * qz - 1) * sz];
+#pragma unroll
+  for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+    for (int qy = 0; qy < 2; qy++) s += (b[0][qy][qz] + b[1][qy][qz]) * (AT)x[n0 + (2 * qy - 1) * sy + (2 * qz - 1) * sz];
+  const AT s12 = cv<AT>(L.s12, L.f_s12);
+  diag = AT(4) * bs * s12;
+  return (AT(4) * bs * (AT)x[n0] - s) * s12;
+}
+
+template <typename AT, typename XT, typename CT>
 __device__ __forceinline__ AT fe_op(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ beta, int i, int j,
                                     int k, AT& diag) {
+  if (i > 0 && i + 1 < L.nn[0] && j > 0 && j + 1 < L.nn[1] && k > 0 && k + 1 < L.nn[2] && i <= L.n[0] &&
+      j <= L.n[1] && k <= L.n[2])
+    return fe_op_interior<AT>(L, x, beta, i, j, k, diag);
   AT b[2][2][2];
   AT bs = AT(0);
 #pragma unroll
@@ -142,6 +208,86 @@ __device__ __forceinline__ AT fe_op(const Lv& L, const XT* __restrict__ x, const
   return (AT(4) * bs * (AT)x[nix(L, i, j, k)] - s) * s12;
 }
 
+// ----------------------------------------------------------------------------- two-float residual
+// A two-float number is an unevaluated sum hi + lo of floats.  Every rounding step is spelled
+// with an _rn intrinsic so that no multiply-add contraction can change it.
+struct F2 {
+  float h, l;
+};
+// Knuth's two-sum: s + e == a + b exactly
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+// product of two two-float numbers (the FMA gives the rounding error of the leading product)
+__device__ __forceinline__ F2 ff_mul(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  return two_sum(p, e);
+}
+// (sh, sl) += w (a - b) with a = ah + al, b = bh + bl and a float weight w: the difference of
+// the leading parts is exact (two-sum), the product's leading rounding error is kept (FMA)
+__device__ __forceinline__ void acc_wdiff(float w, float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const F2 d = two_sum(ah, -bh);
+  const float dlo = __fadd_rn(d.l, __fsub_rn(al, bl));
+  const float ph = __fmul_rn(w, d.h);
+  const float pl = __fmaf_rn(w, dlo, __fmaf_rn(w, d.h, -ph));
+  const F2 t = two_sum(sh, ph);
+  sh = t.h;
+  sl = __fadd_rn(sl, __fadd_rn(t.l, pl));
+}
+
+// MAC operator on a two-float iterate: h^-2 sum_faces beta_f (x_c - x_nb), beta_f the same
+// float coefficient the smoothers and the velocity correction use
+__device__ __forceinline__ F2 mac_op_ff(const Lv& L, const float* __restrict__ xh, const float* __restrict__ xl,
+                                        const float* __restrict__ rho, int i, int j, int k) {
+  const long c = cix(L, i, j, k);
+  const float rc = rho[c], ch = xh[c], cl = xl[c];
+  float sh = 0.0f, sl = 0.0f;
+  const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    const int d = f >> 1;
+    const int v = cnb(L, d, nb[f][d]);
+    if (v < 0) continue;
+    int q[3] = {i, j, k};
+    q[d] = v;
+    const long cn = cix(L, q[0], q[1], q[2]);
+    acc_wdiff(face_beta<false>(rc, rho[cn]), ch, cl, xh[cn], xl[cn], sh, sl);
+  }
+  return ff_mul(sh, sl, L.f_ih2, L.f_ih2_lo);
+}
+
+// FE operator on a two-float iterate: (h/12) sum_{cells c at the node} beta_c sum_{the 4 corners
+// of c that differ from the node in two or three coordinates} (x_node - x_corner)
+__device__ __forceinline__ F2 fe_op_ff(const Lv& L, const float* __restrict__ xh, const float* __restrict__ xl,
+                                       const float* __restrict__ beta, int i, int j, int k) {
+  const int X[2] = {nnb(L, 0, i - 1), nnb(L, 0, i + 1)};
+  const int Y[2] = {nnb(L, 1, j - 1), nnb(L, 1, j + 1)};
+  const int Z[2] = {nnb(L, 2, k - 1), nnb(L, 2, k + 1)};
+  const long n0 = nix(L, i, j, k);
+  const float ch = xh[n0], cl = xl[n0];
+  float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+      for (int sx = 0; sx < 2; sx++) {
+        const int ci = cnb(L, 0, i - 1 + sx), cj = cnb(L, 1, j - 1 + sy), ck = cnb(L, 2, k - 1 + sz);
+        if (ci < 0 || cj < 0 || ck < 0) continue;
+        const float bc = beta[cix(L, ci, cj, ck)];
+        const long q[4] = {nix(L, X[sx], Y[sy], Z[sz]), nix(L, X[sx], Y[sy], k), nix(L, X[sx], j, Z[sz]),
+                           nix(L, i, Y[sy], Z[sz])};
+#pragma unroll
+        for (int t = 0; t < 4; t++) acc_wdiff(bc, ch, cl, xh[q[t]], xl[q[t]], sh, sl);
+      }
+  return ff_mul(sh, sl, L.f_s12, L.f_s12_lo);
+}
+
 // ----------------------------------------------------------------------------- kernels
 template <typename T>
 __global__ void k_zero(T* a, long n) {
@@ -168,12 +314,11 @@ __device__ __forceinline__ void block_partial(double loc, double* part) {
   }
 }
 
-// FP64 residual r = b - A x of the FP64 iterate (FP64 arithmetic); writes the T copy for the
-// V-cycle and per-block partial sums of r^2
-template <typename CT>
+// FP64 residual r = b - A x of the FP64 iterate (T = double); writes r for the V-cycle and
+// per-block partial sums of r^2
 __global__ void __launch_bounds__(BX* BY) k_resid64(Lv L, int kind, const double* __restrict__ x,
-                                                     const double* __restrict__ b, const CT* __restrict__ rho,
-                                                     CT* __restrict__ rT, double* __restrict__ part) {
+                                                     const double* __restrict__ b, const double* __restrict__ rho,
+                                                     double* __restrict__ rT, double* __restrict__ part) {
   const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
   int i, j, k;
   double loc = 0.0;
@@ -182,10 +327,94 @@ __global__ void __launch_bounds__(BX* BY) k_resid64(Lv L, int kind, const double
     const double ax = kind == 0 ? mac_op<double>(L, x, rho, i, j, k, dg) : fe_op<double>(L, x, rho, i, j, k, dg);
     const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
     const double r = b[u] - ax;
-    rT[u] = (CT)r;
+    rT[u] = r;
     loc = r * r;
   }
   block_partial(loc, part);
+}
+
+// per-block partial sum of a float per thread: warp sums in float, block sum in FP64
+__device__ __forceinline__ void block_partial_f(float loc, double* part) {
+  __shared__ double sh[BX * BY / 32];
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) sh[t >> 5] = (double)loc;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int w = 0; w < BX * BY / 32; w++) s += sh[w];
+    part[((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// first residual of the zero iterate, r = b: removes the mean (*mean) from b, writes the T copy
+// of r and per-block partial sums of r^2; with T = float it also splits b into two floats
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_first_resid(Lv L, int kind, double* __restrict__ b,
+                                                         const double* __restrict__ mean, T* __restrict__ rT,
+                                                         float* __restrict__ bh, float* __restrict__ bl,
+                                                         double* __restrict__ part) {
+  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
+  int i, j, k;
+  double loc = 0.0;
+  if (thread_cell(ext, i, j, k)) {
+    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const double v = b[u] - *mean;
+    b[u] = v;
+    rT[u] = (T)v;
+    if constexpr (sizeof(T) == 4) {
+      const float hi = (float)v;
+      bh[u] = hi;
+      bl[u] = (float)(v - (double)hi);
+      loc = (double)((float)v * (float)v);
+    } else {
+      loc = v * v;
+    }
+  }
+  block_partial(loc, part);
+}
+
+// residual r = b - A x of the two-float iterate (xh + xl) against the two-float right-hand
+// side (bh + bl); writes the float r for the V-cycle and per-block partial sums of r^2
+__global__ void __launch_bounds__(BX* BY) k_resid_ff(Lv L, int kind, const float* __restrict__ xh,
+                                                      const float* __restrict__ xl, const float* __restrict__ bh,
+                                                      const float* __restrict__ bl, const float* __restrict__ rho,
+                                                      float* __restrict__ rT, double* __restrict__ part) {
+  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
+  int i, j, k;
+  float loc = 0.0f;
+  if (thread_cell(ext, i, j, k)) {
+    const F2 ax = kind == 0 ? mac_op_ff(L, xh, xl, rho, i, j, k) : fe_op_ff(L, xh, xl, rho, i, j, k);
+    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const F2 t = two_sum(bh[u], -ax.h);
+    const float r = __fadd_rn(t.h, __fadd_rn(t.l, __fsub_rn(bl[u], ax.l)));
+    rT[u] = r;
+    loc = r * r;
+  }
+  block_partial_f(loc, part);
+}
+
+// two-float iterate update (xh + xl) += e; set: (xh, xl) = (e, 0)
+__global__ void k_add_ff(const float* __restrict__ e, float* __restrict__ xh, float* __restrict__ xl, long n,
+                         int set) {
+  GRID_LOOP(i, n) {
+    if (set) {
+      xh[i] = e[i];
+      xl[i] = 0.0f;
+    } else {
+      const F2 s = two_sum(xh[i], e[i]);
+      const F2 r = two_sum(s.h, __fadd_rn(s.l, xl[i]));
+      xh[i] = r.h;
+      xl[i] = r.l;
+    }
+  }
+}
+
+// FP64 solution from the two-float iterate, minus its mean (*m0 + *m1: the means of xh and xl)
+__global__ void k_ff_to64(const float* __restrict__ xh, const float* __restrict__ xl, const double* __restrict__ m0,
+                          const double* __restrict__ m1, double* __restrict__ x, long n) {
+  const double mean = *m0 + *m1;
+  GRID_LOOP(i, n) x[i] = ((double)xh[i] + (double)xl[i]) - mean;
 }
 
 // red-black Gauss-Seidel colour pass (7-point): each thread updates the cell of this colour
@@ -382,19 +611,29 @@ __global__ void k_sub_scalar(XT* __restrict__ a, long n, const double* __restric
   GRID_LOOP(i, n) a[i] = (XT)((double)a[i] - v);
 }
 
+// b += a (set: b = a)
 template <typename T>
-__global__ void k_add_to64(const T* __restrict__ a, double* __restrict__ b, long n) {
-  GRID_LOOP(i, n) b[i] += (double)a[i];
+__global__ void k_add_to64(const T* __restrict__ a, double* __restrict__ b, long n, int set) {
+  GRID_LOOP(i, n) b[i] = set ? (double)a[i] : b[i] + (double)a[i];
 }
 
 // coarsest level: one block, mean-free right-hand side, many smoothing sweeps, mean-free result
 constexpr int COARSE_TPB = 512;
 template <typename T>
-__global__ void __launch_bounds__(COARSE_TPB) k_coarse_solve(Lv L, int kind, int sweeps, T w, T* __restrict__ x,
-                                                             T* __restrict__ xt,
-                               T* __restrict__ b, const T* __restrict__ rho) {
+__global__ void __launch_bounds__(COARSE_TPB) k_coarse_solve(Lv L, int kind, int sweeps, T w, T* __restrict__ gx,
+                                                             T* __restrict__ gxt, T* __restrict__ gb,
+                                                             const T* __restrict__ grho) {
   __shared__ double sh[1024];
   __shared__ double mean;
+  // the whole level lives in shared memory for the sweeps
+  extern __shared__ unsigned char smem[];
+  T* x = (T*)smem;
+  T* xt = x + L.nunk;
+  T* b = xt + L.nunk;
+  T* rho = b + L.nunk;
+  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) b[u] = gb[u];
+  for (long u = threadIdx.x; u < L.ncell; u += blockDim.x) rho[u] = grho[u];
+  __syncthreads();
   double loc = 0.0;
   for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) loc += (double)b[u];
   sh[threadIdx.x] = loc;
@@ -445,7 +684,7 @@ __global__ void __launch_bounds__(COARSE_TPB) k_coarse_solve(Lv L, int kind, int
   }
   if (threadIdx.x == 0) mean = sh[0] / (double)L.nunk;
   __syncthreads();
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) x[u] = (T)((double)x[u] - mean);
+  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) gx[u] = (T)((double)x[u] - mean);
 }
 
 }  // namespace
@@ -461,6 +700,7 @@ struct MGSolver {
   void* rho[16] = {};  // per-level coefficient: MAC density (level 0: the caller's array), FE beta
   const void* rho_in = nullptr;
   double *x64 = nullptr, *b64 = nullptr, *part = nullptr, *scal = nullptr;
+  float *xh = nullptr, *xl = nullptr, *bh = nullptr, *bl = nullptr;  // two-float iterate and rhs (T = float)
   double* hpin = nullptr;
   size_t esz = 8;
   int pre = 2, post = 2;
@@ -512,6 +752,8 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     L.s12 = L.h / 12.0;
     L.f_ih2 = (float)L.ih2;
     L.f_s12 = (float)L.s12;
+    L.f_ih2_lo = (float)(L.ih2 - (double)L.f_ih2);
+    L.f_s12_lo = (float)(L.s12 - (double)L.f_s12);
     m->lv[l] = L;
     m->nlev = l + 1;
     const size_t vb = (size_t)L.nunk * m->esz;
@@ -534,6 +776,12 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
   const long nbr = (long)((L0.nn[0] + BX - 1) / BX) * ((L0.nn[1] + BY - 1) / BY) * L0.nn[2];
   if (e == cudaSuccess) e = dmalloc((void**)&m->x64, L0.nunk * sizeof(double));
   if (e == cudaSuccess) e = dmalloc((void**)&m->b64, L0.nunk * sizeof(double));
+  if (prec_fp32) {
+    if (e == cudaSuccess) e = dmalloc((void**)&m->xh, L0.nunk * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&m->xl, L0.nunk * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&m->bh, L0.nunk * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&m->bl, L0.nunk * sizeof(float));
+  }
   if (e == cudaSuccess) e = dmalloc((void**)&m->part, (size_t)(nbr > RED_BLOCKS ? nbr : RED_BLOCKS) * sizeof(double));
   if (e == cudaSuccess) e = dmalloc((void**)&m->scal, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&m->hpin, 8 * sizeof(double));
@@ -552,6 +800,10 @@ void mg_destroy(MGSolver* m) {
   }
   cudaFree(m->x64);
   cudaFree(m->b64);
+  cudaFree(m->xh);
+  cudaFree(m->xl);
+  cudaFree(m->bh);
+  cudaFree(m->bl);
   cudaFree(m->part);
   cudaFree(m->scal);
   cudaFreeHost(m->hpin);
@@ -617,8 +869,10 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     if (L.n[1] > nmax) nmax = L.n[1];
     if (L.n[2] > nmax) nmax = L.n[2];
     const int sweeps = (m->kind == 0 ? 2 : 4) * nmax * nmax + 20;
-    k_coarse_solve<T><<<1, COARSE_TPB, 0, s>>>(L, m->kind, sweeps, T(m->omega), (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
-                                         (const T*)m->rho[l]);
+    const size_t smem = (3 * (size_t)L.nunk + (size_t)L.ncell) * sizeof(T);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_coarse_solve<T><<<1, COARSE_TPB, smem, s>>>(L, m->kind, sweeps, T(m->omega), (T*)m->x[l], (T*)m->xt[l],
+                                                  (T*)m->b[l], (const T*)m->rho[l]);
     rmt_count_launches(1);
     return;
   }
@@ -657,63 +911,89 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
   }
   // mean-free right-hand side, zero start
   sum_into<double>(m, m->b64, n, 0, 1.0 / (double)n, m->scal, s);
-  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal);
-  rmt_count_launches(1);
   double bn2 = 0.0;
   if (fixed_cycles <= 0) {
+    // |b|^2 of the mean-free b: sum b^2 - n mean^2 would cancel, so subtract first
+    k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal);
+    rmt_count_launches(1);
+    k_zero<double><<<1, 32, 0, s>>>(m->scal, 1);
+    rmt_count_launches(1);
     sum_into<double>(m, m->b64, n, 1, 1.0, m->scal + 1, s);
     cudaMemcpyAsync(m->hpin, m->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
     if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
     bn2 = m->hpin[0];
   }
-  k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n);
-  rmt_count_launches(1);
+  constexpr bool ff = sizeof(T) == 4;  // two-float iterate
   const int ex = m->kind == 0 ? L0.n[0] : L0.nn[0], ey = m->kind == 0 ? L0.n[1] : L0.nn[1],
             ez = m->kind == 0 ? L0.n[2] : L0.nn[2];
   const dim3 g0 = grid3(ex, ey, ez);
   const int nbr = (int)((long)g0.x * g0.y * g0.z);
   int cycles = 0;
   int ok = 1;
-  if (fixed_cycles <= 0 && bn2 == 0.0) {
-    *err = cudaGetLastError();
-    return 0;
-  }
-  const int cap = fixed_cycles > 0 ? fixed_cycles : max_cycles;
-  for (;;) {
-    hk(m, 0, 1, 1, s);
-    k_resid64<T><<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->x64, m->b64, (const T*)m->rho[0], (T*)m->b[0], m->part);
-    rmt_count_launches(1);
-    hk(m, 0, 1, 0, s);
-    if (fixed_cycles <= 0) {
-      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
-      rmt_count_launches(1);
-      cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
-      if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
-      const double rn2 = m->hpin[1];
-      if (!(rn2 == rn2)) {
-        ok = 0;
+  bool have_x = false;  // false: the iterate is still zero
+  if (fixed_cycles > 0 || bn2 != 0.0) {
+    const int cap = fixed_cycles > 0 ? fixed_cycles : max_cycles;
+    for (;;) {
+      if (!have_x) {
+        // r = b (also removes the mean of b, which scal[0] holds, or zero when already removed)
+        k_first_resid<T><<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->b64, m->scal, (T*)m->b[0], m->bh, m->bl, m->part);
+        rmt_count_launches(1);
+      } else {
+        hk(m, 0, 1, 1, s);
+        if constexpr (sizeof(T) == 4)
+          k_resid_ff<<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->xh, m->xl, m->bh, m->bl, (const float*)m->rho[0],
+                                                 (float*)m->b[0], m->part);
+        else
+          k_resid64<<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->x64, m->b64, (const double*)m->rho[0],
+                                                (double*)m->b[0], m->part);
+        rmt_count_launches(1);
+        hk(m, 0, 1, 0, s);
+      }
+      if (fixed_cycles <= 0) {
+        k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
+        rmt_count_launches(1);
+        cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
+        const double rn2 = m->hpin[1];
+        if (!(rn2 == rn2)) {
+          ok = 0;
+          break;
+        }
+        if (rn2 <= rtol * rtol * bn2) break;
+      }
+      if (cycles >= cap) {
+        if (fixed_cycles <= 0) ok = 0;
         break;
       }
-      if (rn2 <= rtol * rtol * bn2) break;
+      k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
+      rmt_count_launches(1);
+      // inner V-cycles on A e = r in the storage type (the high-precision residual is re-formed after them)
+      for (int q = 0; q < m->inner && cycles < cap; q++) {
+        vcycle<T>(m, 0, s);
+        cycles++;
+      }
+      if constexpr (sizeof(T) == 4)
+        k_add_ff<<<nblocks(n), TPB, 0, s>>>((const float*)m->x[0], m->xh, m->xl, n, have_x ? 0 : 1);
+      else
+        k_add_to64<<<nblocks(n), TPB, 0, s>>>((const double*)m->x[0], m->x64, n, have_x ? 0 : 1);
+      rmt_count_launches(1);
+      have_x = true;
+      if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
     }
-    if (cycles >= cap) {
-      if (fixed_cycles <= 0) ok = 0;
-      break;
-    }
-    k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
-    rmt_count_launches(1);
-    // inner V-cycles on A e = r in the storage type (the FP64 residual is re-formed after them)
-    for (int q = 0; q < m->inner && cycles < cap; q++) {
-      vcycle<T>(m, 0, s);
-      cycles++;
-    }
-    k_add_to64<T><<<nblocks(n), TPB, 0, s>>>((const T*)m->x[0], m->x64, n);
-    rmt_count_launches(1);
-    if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
   }
-  sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);
-  k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3);
-  rmt_count_launches(1);
+  if (!have_x) {
+    k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n);
+    rmt_count_launches(1);
+  } else if (ff) {
+    sum_into<float>(m, m->xh, n, 0, 1.0 / (double)n, m->scal + 3, s);
+    sum_into<float>(m, m->xl, n, 0, 1.0 / (double)n, m->scal + 4, s);
+    k_ff_to64<<<nblocks(n), TPB, 0, s>>>(m->xh, m->xl, m->scal + 3, m->scal + 4, m->x64, n);
+    rmt_count_launches(1);
+  } else {
+    sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);
+    k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3);
+    rmt_count_launches(1);
+  }
   *err = cudaGetLastError();
   return ok ? cycles : -1;
 }

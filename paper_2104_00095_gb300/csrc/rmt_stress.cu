@@ -124,15 +124,18 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* __restrict__ u,
                                                                 const Body* __restrict__ bodies,
-                                                                const BodyView<T>* __restrict__ views, int nb, T tt,
+                                                                const BodyView<T>* __restrict__ views, int nb,
+                                                                const int* __restrict__ bbs, int bstride, T tt,
                                                                 T* __restrict__ out) {
+  __shared__ int sbb[6 * RMT_MAX_BODIES];
+  stage_boxes(bbs, bstride, nb, sbb);
   THREAD_XYZ(i, j, k);
   if (i >= g.n[0] || j >= g.n[1]) return;
   const long c = cidx(g, i, j, k);
   // bodies that have xi at this cell: only they can contribute at its six faces
   uint64_t bm = 0;
   for (int m = 0; m < nb; m++)
-    if (views[m].lay[c] >= 0) bm |= (1ull << m);
+    if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
   T acc[3] = {T(0), T(0), T(0)};
   const T ih = cv<T>(g.ih, g.f.ih);
   if (bm == 0) {
@@ -179,14 +182,14 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* _
 }  // namespace
 
 template <typename T>
-void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb, double t,
-                       T* out, cudaStream_t s) {
+void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
+                       const int* bbs, int bstride, double t, T* out, cudaStream_t s) {
   const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
-  k_stress_div<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, bodies, views, nb, T(t), out);
+  k_stress_div<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, bodies, views, nb, bbs, bstride, T(t), out);
   rmt_count_launches(1);
 }
 
-template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, double,
-                                       float*, cudaStream_t);
-template void launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int, double,
-                                        double*, cudaStream_t);
+template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, const int*,
+                                       int, double, float*, cudaStream_t);
+template void launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int,
+                                        const int*, int, double, double*, cudaStream_t);

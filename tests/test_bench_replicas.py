@@ -1,0 +1,56 @@
+"""The multi-GPU bench path (one independent replica per rank) on CPU with gloo, world size 2:
+max-over-ranks timing, the whole-job rate, and the reference arm running on rank 0 only."""
+import io
+import os
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = [12.5, 30.25][rank]
+        ms = bench.max_over_ranks(local_ms, world, device="cpu")
+        rate = bench.job_rate(world, 256**3, 10, ms / 1e3)
+        # the reference arm: only rank 0 runs and prints; the others return without work
+        buf = io.StringIO()
+        args = type("A", (), dict(steps=1, warmup=0, gpus=world, config="cavity32"))()
+        called = []
+        orig = bench.cpu_oracle_rate
+        bench.cpu_oracle_rate = lambda cfg, steps, warmup: (called.append(1) or (1.0e4, 0.5))
+        with redirect_stdout(buf):
+            bench.run_reference(args, bench.CONFIGS["cavity32"])
+        bench.cpu_oracle_rate = orig
+        q.put((rank, ms, rate, len(called), buf.getvalue()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_max_over_ranks_and_job_rate():
+    port = 29500 + (os.getpid() % 2000)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res = {r: (ms, rate, called, text) for r, ms, rate, called, text in out}
+    for r in (0, 1):
+        assert res[r][0] == 30.25  # the slowest rank's time
+        assert res[r][1] == pytest.approx(2 * 256**3 * 10 / 30.25e-3)
+    assert res[0][2] == 1 and '"impl": "reference"' in res[0][3]
+    assert res[1][2] == 0 and res[1][3] == ""
