@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -166,6 +168,161 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(g, steps: int, stream) -> float:
+    """ms per step of g over `steps` steps (CUDA events on the stream)."""
+    import torch
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def plain_fp64_leg(cfg: dict, args, stream) -> dict:
+    """The same workload on the plain FP64 path (no mixed precision), same cycle counts."""
+    from paper_2104_00095_gb300 import rmt
+
+    sc = make_scene(cfg, n=args.n, nbodies=args.nbodies)
+    sc.update(precision="fp64", mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe,
+              options={"fe_inner": args.fe_inner, "mac_warm": args.mac_warm, "graph": args.graph})
+    g = rmt.Grid(sc, stream=stream.cuda_stream)
+    g.step(3)
+    k = max(3, args.steps // 2)
+    ms = timed_steps(g, k, stream)
+    n = int(np.prod(sc["n"]))
+    g.close()
+    return {"value": n / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": k, "dtype": "f64"}
+
+
+def batched_leg(args, stream) -> dict:
+    """64 independent lid-driven cavities of {32..128}^3 with 1-6 spheres, FP32, advanced as one
+    batch (one CUDA-graph launch per step).  The multigrid schedule of each grid size is picked by
+    the autotuner (relative residual 1e-6) on one grid of that size.  Beside it: the same grids
+    stepped one after another."""
+    import torch
+
+    from paper_2104_00095_gb300 import rmt, scenes as S
+
+    scenes = S.batched(nsims=args.batch_sims)
+    cells = sum(int(np.prod(sc["n"])) for sc in scenes)
+    grids = [rmt.Grid(sc, stream=stream.cuda_stream) for sc in scenes]
+    tuned = {}
+    t0 = time.perf_counter()
+    for g, sc in zip(grids, scenes):
+        n = sc["n"][0]
+        if n not in tuned:
+            g.step(1)
+            tuned[n] = g.autotune(1e-6)
+    tune_s = time.perf_counter() - t0
+    keys = ("mac_pre", "mac_post", "mac_inner", "mac_block", "mac_cycles", "fe_pre", "fe_post", "fe_inner",
+            "fe_block", "fe_omega", "fe_cycles")
+    for g, sc in zip(grids, scenes):
+        for k in keys:
+            g.set_option(k, tuned[sc["n"][0]][k])
+    # one after another, each grid launching its own kernels
+    for g in grids:
+        g.step(1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for g in grids:
+        g.step(2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b) / 2
+    bt = rmt.Batch(stream=stream.cuda_stream)
+    for g in grids:
+        bt.add(g)
+    bt.step(3)  # captures both step graphs
+    bt.sync()
+    l0 = rmt.kernel_launches()
+    k = args.batch_steps
+    a.record(stream)
+    bt.step(k)
+    b.record(stream)
+    torch.cuda.synchronize()
+    bt.sync()
+    ms = a.elapsed_time(b) / k
+    launches = (rmt.kernel_launches() - l0) // k
+    bt.close()
+    for g in grids:
+        g.close()
+    return {"workload": f"{len(scenes)} lid-driven cavities, grids from {{32,48,64,96,128}}^3, 1-6 spheres, FP32",
+            "value": cells / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": k,
+            "cells_per_step": cells, "kernels_per_step": launches, "graph_launches_per_step": 1,
+            "autotune": {"seconds": tune_s, "per_size": {str(n): {k: tuned[n][k] for k in keys} for n in tuned}},
+            "sequential": {"value": cells / (seq_ms / 1e3), "ms_per_step": seq_ms,
+                           "note": "the same grids, same settings, stepped one after another, kernel by kernel"}}
+
+
+def serving_leg(args, stream) -> dict:
+    """Poisson arrivals (4 jobs/s) of settling / swimmer jobs of {48..192}^3 with 1-10 bodies under
+    an 80 GB budget, served by continuous batching; beside it the same jobs run one after another
+    on the plain FP64 path (per-step times measured on short runs, FIFO schedule)."""
+    import torch
+
+    from paper_2104_00095_gb300 import rmt, scenes as S
+
+    lo, hi = args.serve_steps
+    jobs = S.serving_stream(njobs=args.serve_jobs, steps=(lo, hi))
+    for _, sc in jobs:
+        sc.update(mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe)
+    srv = rmt.Server(80 * 10**9, stream=stream.cuda_stream,
+                     options={"fe_inner": args.fe_inner, "mac_warm": args.mac_warm})
+    t_start = time.perf_counter()
+    pending = list(jobs)
+    ids = []
+    while True:
+        now = time.perf_counter() - t_start
+        while pending and pending[0][0] <= now:
+            _, sc = pending.pop(0)
+            ids.append(srv.submit(sc, sc["steps"]))
+        r, q = srv.poll()
+        if r == 0 and q == 0 and not pending:
+            break
+        if r == 0 and q == 0:
+            time.sleep(max(0.0, pending[0][0] - (time.perf_counter() - t_start)))
+    torch.cuda.synchronize()
+    infos = [srv.job(i) for i in ids]
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    failed = sum(1 for i in infos if i["state"] != rmt.RMT_JOB_DONE)
+    first = min(i["t_submit"] for i in infos)
+    span = max(i["t_done"] for i in infos) - first
+    cell_steps = srv.cell_steps()
+    stats = srv.stats()
+    srv.close()
+    # the same jobs one after another on the plain FP64 path: init + per-step time from short runs
+    arr = np.array([t for t, _ in jobs])
+    dur = []
+    for _, sc in jobs:
+        s64 = dict(sc, precision="fp64")
+        t0 = time.perf_counter()
+        g = rmt.Grid(s64, stream=stream.cuda_stream)
+        g.step(1)
+        torch.cuda.synchronize()
+        init = time.perf_counter() - t0
+        ms = timed_steps(g, 2, stream)
+        g.close()
+        dur.append(init + sc["steps"] * ms / 1e3)
+    fin, t = [], 0.0
+    for a_, d_ in zip(arr, dur):
+        t = max(t, a_) + d_
+        fin.append(t)
+    slat = np.array(fin) - arr
+    return {"workload": f"{len(jobs)} jobs, Poisson 4/s, grids {{48..192}}^3, 1-10 bodies, steps U[{lo},{hi}], "
+                        f"FP32, 80 GB budget",
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "value": cell_steps / span, "unit": "cell-updates/s", "makespan_s": span, "failed_jobs": failed,
+            "runtime": stats,
+            "serial_fp64": {"p50_latency_s": float(np.percentile(slat, 50)),
+                            "p99_latency_s": float(np.percentile(slat, 99)),
+                            "value": float(sum(np.prod(sc["n"]) * sc["steps"] for _, sc in jobs) / (fin[-1] - arr[0])),
+                            "method": "FIFO, one job at a time, FP64; duration = measured init + steps x measured "
+                                      "per-step time (2-step sample)"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,17 +330,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
-    ap.add_argument("--mg-cycles-mac", type=int, default=5,
-                    help="V-cycles per MAC solve (fixed, no host sync; 5 reach 1e-6 relative residual)")
+    ap.add_argument("--mg-cycles-mac", type=int, default=4,
+                    help="V-cycles per MAC solve (fixed, no host sync; warm-started, 4 hold the 1e-6 relative "
+                         "residual that the adaptive solve needs in steady state)")
     ap.add_argument("--mg-cycles-fe", type=int, default=4,
                     help="V-cycles per FE solve (fixed; 4 reach 1e-6 relative residual)")
     ap.add_argument("--fe-inner", type=int, default=2,
-                    help="FE V-cycles per FP64 residual (mixed-precision refinement)")
+                    help="FE V-cycles per high-precision residual (mixed-precision refinement)")
+    ap.add_argument("--mac-warm", type=int, default=1, help="warm-start the MAC solve from the last step")
+    ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
     ap.add_argument("--n", type=int, default=None,
                     help="override the grid edge (profiling captures of a smaller case only; changes the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the plain-FP64, batched and serving legs (profiling captures)")
+    ap.add_argument("--batch-sims", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-steps", type=int, nargs=2, default=(10, 200),
+                    help="step-count range of the serving sample (the full mix draws from 100..2000)")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
@@ -193,7 +360,6 @@ def main():
         run_reference(args, cfg)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -212,7 +378,7 @@ def main():
     scene = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
-    scene["options"] = {"fe_inner": args.fe_inner}
+    scene["options"] = {"fe_inner": args.fe_inner, "mac_warm": args.mac_warm, "graph": args.graph}
     g = rmt.Grid(scene, stream=stream.cuda_stream)
     N = int(np.prod(scene["n"]))
     for _ in range(args.warmup):
@@ -243,7 +409,7 @@ def main():
 
     # the same steps again with the library's CUDA-event profiler on: per-stage times and the
     # per-launch duration of the finest-level multigrid kernels
-    g.profile(True)
+    g.profile(True)  # stage timing runs the same kernels launched one by one (no graph replay)
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
@@ -296,6 +462,15 @@ def main():
                "sample": f"2 steps of the same scene on a {CPU_SAMPLE_N}^3 grid, FP64 oracle, one host thread "
                          f"({dt:.1f} s)"}
 
+    extra = {}
+    if world == 1 and not args.no_extra:
+        for key, leg in (("plain_fp64", lambda: plain_fp64_leg(cfg, args, stream)),
+                         ("batched", lambda: batched_leg(args, stream)), ("serving", lambda: serving_leg(args, stream))):
+            try:
+                extra[key] = leg()
+            except Exception as ex:  # a failed side leg is reported, the headline line still prints
+                extra[key] = {"error": f"{type(ex).__name__}: {ex}"}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -305,11 +480,13 @@ def main():
                            "description": cfg["desc"], "grid": list(scene["n"]),
                            "bodies": len(scene["solids"]),
                            "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
-                                                   "fe_inner": args.fe_inner},
+                                                   "fe_inner": args.fe_inner, "mac_warm_start": bool(args.mac_warm)},
+                           "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
                 "gpu_launches": launches, "gpu_launches_before_timed": l0, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,
                 "e2e": e2e, "cpu_baseline": cpu}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     g.close()
     if world > 1:

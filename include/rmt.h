@@ -121,9 +121,37 @@ double rmt_dt(rmt_grid* g);
 /* Solver schedule options (any time): "mac_pre", "mac_post" (red-black Gauss-Seidel sweeps
  * before / after the coarse correction, 0..16, default 3), "fe_pre", "fe_post" (weighted Jacobi
  * sweeps, default 2), "fe_omega" (Jacobi weight in (0,2), default 0.9), "mac_inner", "fe_inner"
- * (V-cycles on the storage-precision correction equation per FP64 residual, 1..16, default 1).  Cycle
- * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL. */
+ * (V-cycles on the storage-precision correction equation per high-precision residual, 1..16,
+ * default 1), "mac_block", "fe_block" (rows of 32 threads per block of the multigrid level
+ * kernels: 1, 2, 4 or 8, default 4), "mac_cycles", "fe_cycles" (replace the descriptor's
+ * mg_fixed_cycles / mg_fixed_cycles_fe), "mac_warm", "fe_warm" (nonzero: each solve starts from the
+ * previous step's solution instead of zero; default 0), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
+ * of the step instead of launching its kernels one by one; the results are the same).  Cycle
+ * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL, RMT_ESTATE for
+ * a batch member. */
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
+
+/* Autotuner of the two multigrid solves (no paper counterpart: the paper's multigrid library
+ * is not described).  On the right-hand sides of the grid's last step (RMT_ESTATE before the
+ * first step) it tries, per solver, smoother sweeps before/after the coarse correction (1..4
+ * for the 7-point solve, 1..3 for the nodal one), the Jacobi weight of the nodal smoother (0.8,
+ * 0.9, 1.0) and 1 or 2 V-cycles per high-precision residual: for each, it counts the V-cycles
+ * needed to reach the relative residual rtol and times that many with CUDA events.  It then
+ * times the block height of the level kernels (1, 2, 4, 8 rows of 32 threads) for the fastest
+ * schedule.  The winners are applied with rmt_set_option, including the cycle counts
+ * ("mac_cycles", "fe_cycles"), so that later steps run fixed-cycle without host
+ * synchronisation.  The solvers' solution buffers are overwritten (fields MAC_Q and PSI read
+ * afterwards show a tuning solve); the simulation state is not changed.  Synchronous.
+ * Errors: RMT_EINVAL (rtol outside (0,1)), RMT_ESTATE, RMT_ENOCONVERGE (no schedule reached rtol
+ * within 40 cycles), RMT_ECUDA. */
+typedef struct {
+  int mac_pre, mac_post, mac_inner, mac_block, mac_cycles;
+  int fe_pre, fe_post, fe_inner, fe_block, fe_cycles;
+  double fe_omega;
+  double mac_ms, fe_ms; /* time of one solve with the chosen settings */
+  int trials;           /* schedules and shapes tried */
+} rmt_tune_result;
+rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* out);
 
 /* Extrapolates one body's reference map on caller-owned device buffers without allocating
  * anything (the paper has no counterpart: this serves callers that cannot allocate device
@@ -147,7 +175,90 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
 rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* desc, const rmt_solid_desc* s, const double* xi_in,
                                    double* xi_out, double* phi_out, signed char* layer_out, void* stream);
 
-/* Total number of CUDA kernels this library has launched in this process (all grids). */
+/* Device bytes that a grid described by desc with nsolids bodies requests from cudaMalloc over
+ * its lifetime: every field, scratch array and both multigrid hierarchies, each allocation
+ * counted in 256-byte units.  0 for an invalid description.  The serving runtime admits jobs by
+ * this number.  (The paper has no counterpart: its runs own whole MPI ranks.) */
+size_t rmt_grid_footprint(const rmt_grid_desc* desc, int nsolids);
+/* Device bytes the grid has requested so far; equals rmt_grid_footprint after initialisation. */
+size_t rmt_grid_device_bytes(const rmt_grid* g);
+
+/* ---- batched stepping (no paper counterpart: the paper runs one simulation per MPI job) ----
+ * A batch advances several independent grids together, each step of all members being one
+ * launch of an instantiated CUDA graph.  Every member's step is captured on its own branch of
+ * the graph, so the kernels of different members run concurrently on the GPU; the graph is
+ * captured once per membership (two graphs: the reference-map buffers alternate between two
+ * parities) and replayed.  Members need fixed multigrid cycle counts (mg_fixed_cycles > 0 and
+ * mg_fixed_cycles_fe > 0, so that a step never waits for the host) and profiling off.  While a
+ * grid is a member, rmt_step, rmt_write_fields, rmt_set_option and rmt_destroy_grid on it return
+ * RMT_ESTATE, and rmt_read_fields first waits for the batch's stream.  Members share no data, so
+ * every member's result is the same as when it is stepped alone.
+ *   rmt_batch_create: stream = cudaStream_t the step graphs are launched on (may be null).
+ *   rmt_batch_add:    initialises the grid if needed; synchronous.  RMT_EINVAL for a grid
+ *                     without fixed cycle counts or already a member.
+ *   rmt_batch_remove: waits for the batch's work; the grid keeps its state and can step alone.
+ *   rmt_batch_step:   asynchronous; nsteps launches of the step graph.
+ *   rmt_batch_sync:   waits, then reads every member's error flag; the first error is returned
+ *                     (the member's rmt_last_error has the message).
+ *   rmt_batch_destroy: removes all members (they are not destroyed). */
+typedef struct rmt_batch rmt_batch;
+rmt_status rmt_batch_create(void* cuda_stream, rmt_batch** out);
+rmt_status rmt_batch_add(rmt_batch* b, rmt_grid* g);
+rmt_status rmt_batch_remove(rmt_batch* b, rmt_grid* g);
+rmt_status rmt_batch_step(rmt_batch* b, int nsteps);
+rmt_status rmt_batch_sync(rmt_batch* b);
+int rmt_batch_size(const rmt_batch* b);
+rmt_status rmt_batch_destroy(rmt_batch* b);
+const char* rmt_batch_last_error(const rmt_batch* b);
+
+/* ---- serving: continuous batching of simulation jobs (no paper counterpart) ----------------
+ * rmt_server_submit queues a job (grid description with fixed cycle counts, bodies, number of
+ * steps); its footprint (rmt_grid_footprint) must fit the budget.  Each rmt_server_poll
+ *   1. retires the running jobs whose last step has been launched: completion time = when the
+ *      GPU finished that step (CUDA event), then the job's error flag is read;
+ *   2. admits queued jobs in arrival order while their footprint fits next to the resident
+ *      jobs (a job that does not fit waits; later, smaller jobs may pass it); an admitted job's
+ *      grid is created, initialised and added to the server's batch;
+ *   3. launches one batched step of all running jobs, with at most two steps in flight.
+ * A job that fails (bad description, allocation, degenerate extrapolation) is marked failed
+ * and the others carry on.  Finished jobs keep their fields on the device, readable through
+ * rmt_server_job_grid, until rmt_server_release, and count against the budget until then.
+ * Times are seconds since rmt_server_create (rmt_server_clock).  rmt_server_set_option applies
+ * rmt_set_option(name, value) to every job grid at admission. */
+typedef struct rmt_server rmt_server;
+enum { RMT_JOB_QUEUED = 0, RMT_JOB_RUNNING = 1, RMT_JOB_DONE = 2, RMT_JOB_FAILED = 3 };
+typedef struct {
+  int state;           /* RMT_JOB_* */
+  rmt_status status;   /* RMT_OK, or why the job failed */
+  long steps_done, steps_total;
+  double t_submit, t_admit, t_done;  /* seconds; -1 while not reached */
+  size_t device_bytes; /* footprint charged against the budget */
+} rmt_job_info;
+rmt_status rmt_server_create(size_t budget_bytes, void* cuda_stream, rmt_server** out);
+rmt_status rmt_server_set_option(rmt_server* s, const char* name, double value);
+rmt_status rmt_server_submit(rmt_server* s, const rmt_grid_desc* desc, const rmt_solid_desc* solids, int nsolids,
+                             long nsteps, int* job_id);
+rmt_status rmt_server_poll(rmt_server* s, int* n_running, int* n_queued);
+rmt_status rmt_server_job(rmt_server* s, int job_id, rmt_job_info* info);
+rmt_grid* rmt_server_job_grid(rmt_server* s, int job_id);
+rmt_status rmt_server_release(rmt_server* s, int job_id);
+size_t rmt_server_resident_bytes(const rmt_server* s);
+const char* rmt_server_last_error(const rmt_server* s);
+typedef struct {
+  long batched_steps;   /* batched steps launched */
+  long graph_captures;  /* step graphs captured and instantiated (two per membership) */
+  double capture_s;     /* host seconds spent capturing and instantiating them */
+  double admit_s;       /* host seconds spent admitting jobs (grid creation and initialisation) */
+  double retire_s;      /* host seconds spent retiring jobs (waiting for their last step, error check) */
+  double cell_steps;    /* cells x steps launched for all jobs */
+} rmt_server_stats_t;
+rmt_status rmt_server_stats(const rmt_server* s, rmt_server_stats_t* out);
+double rmt_server_clock(const rmt_server* s);
+double rmt_server_cell_steps(const rmt_server* s); /* cells x steps launched for all jobs */
+rmt_status rmt_server_destroy(rmt_server* s);
+
+/* Total number of CUDA kernels this library has launched in this process (all grids).  A
+ * replayed step graph counts its kernel nodes. */
 long rmt_kernel_launches(void);
 
 /* Timing of the step's stages and of the finest-level multigrid kernels with CUDA events on

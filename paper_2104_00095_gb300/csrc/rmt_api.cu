@@ -12,6 +12,7 @@
 #include <atomic>
 
 #include "rmt.h"
+#include "rmt_internal.h"
 #include "rmt_kernels.h"
 
 static std::atomic<long> g_launches{0};
@@ -74,6 +75,8 @@ struct rmt_grid {
   std::vector<BodyMem> bm;
   Body* bodies_d = nullptr;
   int* bb_all = nullptr;  // band boxes: body m, parity p at 12 m + 6 p
+  int *slist = nullptr, *scount = nullptr;  // cells some band reaches (stress pass 2)
+  double* t_d = nullptr;                      // simulated time (device copy of t)
   void* views_d = nullptr;  // BodyView<T>[2 parities][3 levels][nb]
   int par = 0;
   void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
@@ -101,7 +104,19 @@ struct rmt_grid {
   HookCtx hctx[2];
   // smoother schedule (negative: solver default)
   int mac_pre = -1, mac_post = -1, fe_pre = -1, fe_post = -1, mac_inner = 1, fe_inner = 1;
+  int mac_block = 4, fe_block = 4;  // block height of the multigrid level kernels
+  int mac_warm = 0, fe_warm = 0;    // warm-started solves
   double fe_omega = -1.0;
+  size_t bytes = 0;  // device bytes requested by dalloc
+  int dry = 0;       // dalloc only counts (footprint model)
+  // captured step graphs (fixed-cycle mode): one per parity of the reference-map buffers
+  int use_graph = 0;
+  cudaStream_t cap_s = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  long gnodes[2] = {0, 0};
+  // set while the grid is a member of a batch: its work runs on that batch's stream
+  cudaStream_t batch_s = nullptr;
+  int in_batch = 0;
 };
 
 namespace {
@@ -118,6 +133,12 @@ rmt_status fail(rmt_grid* g, rmt_status st, const char* fmt, ...) {
     if (st != RMT_EINVAL) g->sticky = st;
   }
   return st;
+}
+
+// a call refused in the grid's present state: message only, the grid stays usable
+rmt_status refuse(rmt_grid* g, const char* why) {
+  snprintf(g->msg, sizeof g->msg, "%s", why);
+  return RMT_ESTATE;
 }
 
 #define CK(g, call)                                                                           \
@@ -182,6 +203,11 @@ double prof_bytes(const rmt_grid* g, int e) {
 }
 
 rmt_status dalloc(rmt_grid* g, void** p, size_t bytes) {
+  g->bytes += dev_bytes(bytes);
+  if (g->dry) {
+    *p = nullptr;
+    return RMT_OK;
+  }
   cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) return fail(g, RMT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   g->allocs.push_back(*p);
@@ -274,8 +300,9 @@ rmt_status size_windows(rmt_grid* g) {
   return RMT_OK;
 }
 
+// every device allocation of the grid (with g->dry set: only their sizes, into g->bytes)
 template <typename T>
-rmt_status init_t(rmt_grid* g) {
+rmt_status alloc_t(rmt_grid* g) {
   const Geo& G = g->g;
   const long N = G.N;
   rmt_status st;
@@ -325,11 +352,13 @@ rmt_status init_t(rmt_grid* g) {
     AL(b.count, 16);
   }
   AL(g->bb_all, (nb > 0 ? nb : 1) * 12 * sizeof(int));
+  AL(g->slist, (nb > 0 ? N : 1) * sizeof(int));
+  AL(g->scount, 16);
+  AL(g->t_d, 16);
   for (int m = 0; m < nb; m++) g->bm[m].bb = g->bb_all + 12 * m;
   AL(g->bodies_d, (nb > 0 ? nb : 1) * sizeof(Body));
   AL(g->views_d, (size_t)6 * (nb > 0 ? nb : 1) * sizeof(BodyView<T>));
   AL(g->err_d, 16);
-  CK(g, cudaMallocHost((void**)&g->err_h, 16));
   long sl = 3 * N;
   for (int d = 0; d < 3; d++)
     if (3 * nfaces(G, d) > sl) sl = 3 * nfaces(G, d);
@@ -337,6 +366,11 @@ rmt_status init_t(rmt_grid* g) {
   AL(g->stage, sl * sizeof(double));
   g->stage_len = sl;
 #undef AL
+  if (g->dry) {
+    g->bytes += mg_footprint(G, 0, g->fp32) + mg_footprint(G, 1, g->fp32);
+    return RMT_OK;
+  }
+  CK(g, cudaMallocHost((void**)&g->err_h, 16));
   cudaError_t ce = cudaSuccess;
   g->mac = mg_create(G, 0, g->fp32, &ce);
   if (ce != cudaSuccess) return fail(g, RMT_ENOMEM, "multigrid (MAC) allocation: %s", cudaGetErrorString(ce));
@@ -350,6 +384,21 @@ rmt_status init_t(rmt_grid* g) {
   mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
   mg_set_inner(g->mac, g->mac_inner);
   mg_set_inner(g->fe, g->fe_inner);
+  mg_set_block(g->mac, g->mac_block);
+  mg_set_block(g->fe, g->fe_block);
+  mg_set_warm(g->mac, g->mac_warm);
+  mg_set_warm(g->fe, g->fe_warm);
+  g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
+  return RMT_OK;
+}
+
+template <typename T>
+rmt_status init_t(rmt_grid* g) {
+  const Geo& G = g->g;
+  const long N = G.N;
+  const int nb = (int)g->bodies.size();
+  rmt_status st = alloc_t<T>(g);
+  if (st != RMT_OK) return st;
   // outside a body's band every per-body array reads "absent" (layer -1, NaN); the window
   // kernels rely on it, since they only ever touch the band's neighbourhood
   const T nanv = (T)NAN;
@@ -403,7 +452,8 @@ rmt_status step_t(rmt_grid* g) {
   T* u = (T*)g->u;
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t, (T*)g->divn, s);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t_d, 0.0,
+                       (T*)g->divn, g->slist, g->scount, s);
   pe(g, P_STRESS_N);
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
@@ -448,8 +498,8 @@ rmt_status step_t(rmt_grid* g) {
   }
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
   pb(g, P_STRESS_H);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t + 0.5 * G.dt,
-                       (T*)g->divh, s);
+  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t_d, 0.5 * G.dt,
+                       (T*)g->divh, g->slist, g->scount, s);
   pe(g, P_STRESS_H);
   pb(g, P_USTAR);
   launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho_h, s);
@@ -472,6 +522,7 @@ rmt_status step_t(rmt_grid* g) {
   // 12. xi <- xi^{n+1} (parity flip); 13. rho^{n+1}
   g->par = nxt;
   launch_density<T>(G, g->bodies_d, views<T>(g, nxt, 0), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho, s);
+  launch_tick(g->t_d, G.dt, s);
   pe(g, P_FE_UPDATE);
   CK(g, cudaGetLastError());
   g->t += G.dt;
@@ -517,6 +568,66 @@ rmt_status check_err(rmt_grid* g) {
   return RMT_OK;
 }
 
+// ----------------------------------------------------------------------------- step graphs
+bool fixed_cycles(const rmt_grid* g) { return g->desc.mg_fixed_cycles > 0 && g->desc.mg_fixed_cycles_fe > 0; }
+
+void drop_graphs(rmt_grid* g) {
+  for (int p = 0; p < 2; p++) {
+    if (g->gexec[p]) cudaGraphExecDestroy(g->gexec[p]);
+    g->gexec[p] = nullptr;
+    g->gnodes[p] = 0;
+  }
+}
+
+// host-side effect of one step, for a step that ran from a captured graph
+void advance_host(rmt_grid* g) {
+  g->par = 1 - g->par;
+  g->t += g->g.dt;
+  g->step++;
+  g->cycles[0] = g->desc.mg_fixed_cycles;
+  g->cycles[1] = g->desc.mg_fixed_cycles_fe;
+}
+
+// Records one step of g on stream cs, which is capturing; the host state (parity, time, step
+// count) is left as it was, since nothing has run yet.
+rmt_status capture_step(rmt_grid* g, cudaStream_t cs) {
+  const int par = g->par, prof = g->prof.on;
+  const double t = g->t;
+  const long step = g->step;
+  cudaStream_t s0 = g->s;
+  g->s = cs;
+  g->prof.on = 0;
+  rmt_status st = g->fp32 ? step_t<float>(g) : step_t<double>(g);
+  g->s = s0;
+  g->prof.on = prof;
+  g->par = par;
+  g->t = t;
+  g->step = step;
+  return st;
+}
+
+// captures and instantiates the step graph of the grid's current parity
+rmt_status build_graph(rmt_grid* g) {
+  if (!g->cap_s) CK(g, cudaStreamCreateWithFlags(&g->cap_s, cudaStreamNonBlocking));
+  const long c0 = rmt_kernel_launches();
+  CK(g, cudaStreamBeginCapture(g->cap_s, cudaStreamCaptureModeRelaxed));
+  rmt_status st = capture_step(g, g->cap_s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->cap_s, &graph);
+  const long nodes = rmt_kernel_launches() - c0;
+  rmt_count_launches(-nodes);  // counted when the graph is launched
+  if (st != RMT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(g, RMT_ECUDA, "step capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g->gexec[g->par], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(g, RMT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  g->gnodes[g->par] = nodes;
+  return RMT_OK;
+}
+
 }  // namespace
 
 namespace {
@@ -540,10 +651,10 @@ rmt_status gather_t(rmt_grid* g, int field, int sid, double* out) {
     case RMT_F_USTAR: cvt(g->ustar, 3 * N, 0); break;
     case RMT_F_RHO_HALF: cvt(g->rho_h, N, 0); break;
     case RMT_F_MAC_Q:
-      CK(g, cudaMemcpyAsync(out, mg_solution(g->mac), N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(g, cudaMemcpyAsync(out, mg_solution64(g->mac, s), N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       break;
     case RMT_F_PSI:
-      CK(g, cudaMemcpyAsync(out, mg_solution(g->fe), G.NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(g, cudaMemcpyAsync(out, mg_solution64(g->fe, s), G.NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
       break;
     case RMT_F_UFACE_X: case RMT_F_UFACE_Y: case RMT_F_UFACE_Z: {
       const int d = field - RMT_F_UFACE_X;
@@ -649,8 +760,18 @@ rmt_status rmt_add_solid(rmt_grid* g, const rmt_solid_desc* s, int* solid_id) {
 rmt_status rmt_step(rmt_grid* g, int nsteps) {
   if (!g || nsteps < 0) return RMT_EINVAL;
   if (g->sticky != RMT_OK) return RMT_ESTATE;
+  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
   rmt_status st = ensure_init(g);
   if (st != RMT_OK) return st;
+  if (g->use_graph && fixed_cycles(g) && !g->prof.on) {
+    for (int k = 0; k < nsteps; k++) {
+      if (!g->gexec[g->par] && (st = build_graph(g)) != RMT_OK) return st;
+      CK(g, cudaGraphLaunch(g->gexec[g->par], g->s));
+      rmt_count_launches(g->gnodes[g->par]);
+      advance_host(g);
+    }
+    return RMT_OK;
+  }
   for (int k = 0; k < nsteps; k++) {
     st = g->fp32 ? step_t<float>(g) : step_t<double>(g);
     if (st != RMT_OK) return st;
@@ -684,6 +805,7 @@ rmt_status rmt_read_fields(rmt_grid* g, int field, int solid_id, void* dst, size
   if ((field == RMT_F_XI || field == RMT_F_PHI || field == RMT_F_LAYER || field == RMT_F_XI_HALF) &&
       (solid_id < 0 || solid_id >= (int)g->bodies.size()))
     return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  if (g->in_batch && g->batch_s != g->s) CK(g, cudaStreamSynchronize(g->batch_s));  // the batch's steps first
   double* out = dst_is_device ? (double*)dst : g->stage;
   st = g->fp32 ? gather_t<float>(g, field, solid_id, out) : gather_t<double>(g, field, solid_id, out);
   if (st != RMT_OK) return st;
@@ -698,6 +820,7 @@ rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* sr
   if (g->sticky != RMT_OK) return RMT_ESTATE;
   rmt_status st = ensure_init(g);
   if (st != RMT_OK) return st;
+  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
   if (field != RMT_F_U && field != RMT_F_P && field != RMT_F_XI) return fail(g, RMT_EINVAL, "field %d is not writable", field);
   if (field == RMT_F_XI && (solid_id < 0 || solid_id >= (int)g->bodies.size()))
     return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
@@ -705,6 +828,7 @@ rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* sr
   if (src_bytes < (size_t)n * sizeof(double)) return fail(g, RMT_EINVAL, "source too small");
   CK(g, cudaMemcpyAsync(g->stage, src, (size_t)n * sizeof(double),
                         src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
+  if (field == RMT_F_XI) drop_graphs(g);  // re-extrapolation resizes the body's launch windows
   st = g->fp32 ? scatter_t<float>(g, field, solid_id) : scatter_t<double>(g, field, solid_id);
   if (st != RMT_OK) return st;
   if (field == RMT_F_XI) {
@@ -720,8 +844,11 @@ double rmt_dt(rmt_grid* g) { return g ? g->g.dt : 0.0; }
 
 rmt_status rmt_destroy_grid(rmt_grid* g) {
   if (!g) return RMT_EINVAL;
+  if (g->in_batch) return refuse(g, "remove the grid from its batch first");
   if (g->s) cudaStreamSynchronize(g->s);
   else cudaDeviceSynchronize();
+  drop_graphs(g);
+  if (g->cap_s) cudaStreamDestroy(g->cap_s);
   for (void* p : g->allocs) cudaFree(p);
   if (g->err_h) cudaFreeHost(g->err_h);
   mg_destroy(g->mac);
@@ -756,6 +883,7 @@ int rmt_profile_entries(void) { return P_NUM; }
 
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   if (!g || !name) return RMT_EINVAL;
+  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
   int* ip = nullptr;
   if (!strcmp(name, "mac_pre")) ip = &g->mac_pre;
   else if (!strcmp(name, "mac_post")) ip = &g->mac_post;
@@ -763,23 +891,53 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   else if (!strcmp(name, "fe_post")) ip = &g->fe_post;
   else if (!strcmp(name, "mac_inner")) ip = &g->mac_inner;
   else if (!strcmp(name, "fe_inner")) ip = &g->fe_inner;
+  else if (!strcmp(name, "mac_warm")) ip = &g->mac_warm;
+  else if (!strcmp(name, "fe_warm")) ip = &g->fe_warm;
   if (ip) {
     if (value < 0 || value > 16) return fail(g, RMT_EINVAL, "%s out of range", name);
     *ip = (int)value;
+  } else if (!strcmp(name, "mac_block") || !strcmp(name, "fe_block")) {
+    const int v = (int)value;
+    if (v != 1 && v != 2 && v != 4 && v != 8) return fail(g, RMT_EINVAL, "%s must be 1, 2, 4 or 8", name);
+    (name[0] == 'm' ? g->mac_block : g->fe_block) = v;
+  } else if (!strcmp(name, "mac_cycles") || !strcmp(name, "fe_cycles")) {
+    if (value < 0 || value > 1000) return fail(g, RMT_EINVAL, "%s out of range", name);
+    (name[0] == 'm' ? g->desc.mg_fixed_cycles : g->desc.mg_fixed_cycles_fe) = (int)value;
   } else if (!strcmp(name, "fe_omega")) {
     if (!(value > 0.0 && value < 2.0)) return fail(g, RMT_EINVAL, "fe_omega out of range");
     g->fe_omega = value;
+  } else if (!strcmp(name, "graph")) {
+    g->use_graph = value != 0.0;
   } else {
     return fail(g, RMT_EINVAL, "unknown option %s", name);
   }
+  drop_graphs(g);
   if (g->inited) {
     mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
     mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
     mg_set_inner(g->mac, g->mac_inner);
     mg_set_inner(g->fe, g->fe_inner);
+    mg_set_block(g->mac, g->mac_block);
+    mg_set_block(g->fe, g->fe_block);
+    mg_set_warm(g->mac, g->mac_warm);
+    mg_set_warm(g->fe, g->fe_warm);
   }
   return RMT_OK;
 }
+
+size_t rmt_grid_footprint(const rmt_grid_desc* d, int nsolids) {
+  if (nsolids < 0 || nsolids > RMT_MAX_BODIES) return 0;
+  rmt_grid* g = nullptr;
+  if (rmt_create_grid(d, &g) != RMT_OK) return 0;
+  g->bodies.resize(nsolids);  // only the count matters to the allocation sizes
+  g->dry = 1;
+  const rmt_status st = g->fp32 ? alloc_t<float>(g) : alloc_t<double>(g);
+  const size_t b = st == RMT_OK ? g->bytes : 0;
+  delete g;  // nothing was allocated
+  return b;
+}
+
+size_t rmt_grid_device_bytes(const rmt_grid* g) { return g ? g->bytes : 0; }
 
 const char* rmt_profile_name(int entry) { return (entry >= 0 && entry < P_NUM) ? kProfNames[entry] : ""; }
 
@@ -793,3 +951,40 @@ rmt_status rmt_profile_read(rmt_grid* g, int entry, double* total_ms, long* laun
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- batch hooks
+rmt_status grid_join_batch(rmt_grid* g, cudaStream_t batch_stream) {
+  if (!g) return RMT_EINVAL;
+  if (g->in_batch) return refuse(g, "the grid already belongs to a batch");
+  if (g->sticky != RMT_OK) return RMT_ESTATE;
+  if (!fixed_cycles(g)) return fail(g, RMT_EINVAL, "batched grids need mg_fixed_cycles and mg_fixed_cycles_fe > 0");
+  if (g->prof.on) return refuse(g, "profiling is on");
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  if ((st = check_err(g)) != RMT_OK) return st;  // also waits for the grid's own work
+  g->in_batch = 1;
+  g->batch_s = batch_stream;
+  return RMT_OK;
+}
+void grid_leave_batch(rmt_grid* g) {
+  g->in_batch = 0;
+  g->batch_s = nullptr;
+}
+rmt_status grid_capture_step(rmt_grid* g, cudaStream_t s) { return capture_step(g, s); }
+void grid_advance_host(rmt_grid* g) { advance_host(g); }
+int grid_parity(const rmt_grid* g) { return g->par; }
+rmt_status grid_check(rmt_grid* g) {
+  if (g->sticky != RMT_OK) return g->sticky;
+  return check_err(g);
+}
+rmt_status grid_fail(rmt_grid* g, rmt_status st, const char* msg) { return fail(g, st, "%s", msg); }
+
+// ----------------------------------------------------------------------------- autotuner hooks
+rmt_status grid_solvers(rmt_grid* g, MGSolver** mac, MGSolver** fe, cudaStream_t* s, double* rtol) {
+  if (!g->inited || g->step == 0) return refuse(g, "the autotuner needs a grid that has taken a step");
+  *mac = g->mac;
+  *fe = g->fe;
+  *s = g->s;
+  *rtol = g->desc.mg_rtol > 0 ? g->desc.mg_rtol : 1e-12;
+  return RMT_OK;
+}

@@ -27,6 +27,7 @@ struct Geo {
   double ih, q4, hdt_h, two_dt, fe_rhs;  // 1/h, 0.25/h, dt/(2h), 2/dt, h^2/(4 dt)
   struct {
     float h, ih, q4, hdt_h, dt, eps, rho_f, mu, utol, wall[6][3], grav[3];
+    float two_dt, two_dt_lo, fe_rhs, fe_rhs_lo;  // two-float pairs (value = hi + lo)
   } f;
 };
 
@@ -67,6 +68,10 @@ inline void geo_finish(Geo& g) {
   for (int q = 0; q < 6; q++)
     for (int a = 0; a < 3; a++) g.f.wall[q][a] = (float)g.wall[q][a];
   for (int a = 0; a < 3; a++) g.f.grav[a] = (float)g.grav[a];
+  g.f.two_dt = (float)g.two_dt;
+  g.f.two_dt_lo = (float)(g.two_dt - (double)g.f.two_dt);
+  g.f.fe_rhs = (float)g.fe_rhs;
+  g.f.fe_rhs_lo = (float)(g.fe_rhs - (double)g.f.fe_rhs);
 }
 // fills the derived constants and float mirrors of a body (host)
 inline void body_finish(Body& b) {

@@ -206,8 +206,32 @@ struct FacePtrs3 {
   void* p[3];
 };
 
+// Two-float helpers (FP32 mode hands the multigrid right-hand side and solution over as
+// value = hi + lo pairs): Knuth's two-sum and the FMA product, with explicit rounding so that
+// no contraction changes them.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// a - b for two-float a = (ah, al), b = (bh, bl), rounded to float (the leading difference is exact)
+__device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl) {
+  float s, e;
+  two_sum_f(ah, -bh, s, e);
+  return __fadd_rn(s, __fadd_rn(e, __fsub_rn(al, bl)));
+}
+// writes the exact product x * (ch + cl) (x float, c a two-float constant) as a two-float pair
+__device__ __forceinline__ void store_prod(MGVec b, long i, float x, float ch, float cl) {
+  const float p = __fmul_rn(x, ch);
+  const float e = __fmaf_rn(x, cl, __fmaf_rn(x, ch, -p));
+  float s, t;
+  two_sum_f(p, e, s, t);
+  b.h[i] = s;
+  b.l[i] = t;
+}
+
 template <typename T>
-__global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
+__global__ void k_mac_rhs(Geo g, FacePtrs3 un, MGVec b) {
   const T ih = cv<T>(g.ih, g.f.ih);
   GRID_LOOP(c, g.N) {
     int i, j, k;
@@ -221,13 +245,16 @@ __global__ void k_mac_rhs(Geo g, FacePtrs3 un, double* __restrict__ b) {
       dv += (U[hi] - U[lo]) * ih;
     }
     // positive operator A = -div(beta grad): A q = -div(u)/(dt/2)
-    b[c] = -(double)dv * g.two_dt;
+    if constexpr (sizeof(T) == 8)
+      b.d[c] = -(double)dv * g.two_dt;
+    else
+      store_prod(b, c, -dv, g.f.two_dt, g.f.two_dt_lo);
   }
 }
 
 template <typename T>
-__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ rho,
-                              const double* __restrict__ q, T* __restrict__ umac) {
+__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ rho, MGVec q,
+                              T* __restrict__ umac) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
   const T fac = cv<T>(g.hdt_h, g.f.hdt_h);
   GRID_LOOP(f, nfaces(g, d)) {
@@ -245,7 +272,12 @@ __global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* _
     cell_at(g, i, j, k, cb);
     // face coefficient 1/rho_face, rho_face the mean of the two cells
     const T beta = T(2) / (rho[ca] + rho[cb]);
-    umac[f] = un[f] - fac * beta * (T)(q[cb] - q[ca]);
+    T dq;
+    if constexpr (sizeof(T) == 8)
+      dq = q.d[cb] - q.d[ca];
+    else
+      dq = ff_diff(q.h[cb], q.l[cb], q.h[ca], q.l[ca]);
+    umac[f] = un[f] - fac * beta * dq;
   }
 }
 
@@ -334,8 +366,7 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
 // weak divergence of V = (u* - u^n)/dt at every node: sum over adjacent cells of
 // (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d
 template <typename T>
-__global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ ustar, double* __restrict__ b) {
-  const double s = g.fe_rhs;
+__global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ ustar, MGVec b) {
   GRID_LOOP(nd, g.NN) {
     int i, j, k;
     decode(nd, g.nn[0], g.nn[1], i, j, k);
@@ -348,37 +379,66 @@ __global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ u
       const T v0 = ustar[c] - u[c], v1 = ustar[g.N + c] - u[g.N + c], v2 = ustar[2 * g.N + c] - u[2 * g.N + c];
       acc += (sx ? -v0 : v0) + (sy ? -v1 : v1) + (sz ? -v2 : v2);
     }
-    b[nd] = (double)acc * s;
+    if constexpr (sizeof(T) == 8)
+      b.d[nd] = (double)acc * g.fe_rhs;
+    else
+      store_prod(b, nd, acc, g.f.fe_rhs, g.f.fe_rhs_lo);
   }
 }
 
 template <typename T>
-__global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h,
-                              const double* __restrict__ psi, T* __restrict__ u) {
-  const double q4 = g.q4;
+__global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h, MGVec psi,
+                              T* __restrict__ u) {
   const T dt = cv<T>(g.dt, g.f.dt);
   GRID_LOOP(c, g.N) {
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);
-    double gp[3] = {0, 0, 0};
+    long nd[8];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int sa = q & 1, sb = (q >> 1) & 1, sc = (q >> 2) & 1;
-      const double pv = psi[node_at(g, i + sa, j + sb, k + sc)];
-      gp[0] += sa ? pv : -pv;
-      gp[1] += sb ? pv : -pv;
-      gp[2] += sc ? pv : -pv;
+    for (int q = 0; q < 8; q++) nd[q] = node_at(g, i + (q & 1), j + ((q >> 1) & 1), k + ((q >> 2) & 1));
+    T gp[3];
+    if constexpr (sizeof(T) == 8) {
+      double s[3] = {0, 0, 0};
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const double pv = psi.d[nd[q]];
+        s[0] += (q & 1) ? pv : -pv;
+        s[1] += ((q >> 1) & 1) ? pv : -pv;
+        s[2] += ((q >> 2) & 1) ? pv : -pv;
+      }
+      for (int a = 0; a < 3; a++) gp[a] = s[a] * g.q4;
+    } else {
+      // each component: four differences across the cell, each exact to float rounding
+      float v[8][2];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        v[q][0] = psi.h[nd[q]];
+        v[q][1] = psi.l[nd[q]];
+      }
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const int bit = 1 << a;
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          if (q & bit) s += ff_diff(v[q][0], v[q][1], v[q ^ bit][0], v[q ^ bit][1]);
+        gp[a] = s * g.f.q4;
+      }
     }
     const T r = rho_h[c];
 #pragma unroll
-    for (int a = 0; a < 3; a++) u[a * g.N + c] = ustar[a * g.N + c] - dt / r * (T)(gp[a] * q4);
+    for (int a = 0; a < 3; a++) u[a * g.N + c] = ustar[a * g.N + c] - dt / r * gp[a];
   }
 }
 
 template <typename T>
-__global__ void k_fe_update_p(long nn, const double* __restrict__ psi, T* __restrict__ p, T* __restrict__ psi_out) {
+__global__ void k_fe_update_p(long nn, MGVec psi, T* __restrict__ p, T* __restrict__ psi_out) {
   GRID_LOOP(i, nn) {
-    const T v = (T)psi[i];
+    T v;
+    if constexpr (sizeof(T) == 8)
+      v = psi.d[i];
+    else
+      v = __fadd_rn(psi.h[i], psi.l[i]);
     p[i] += v;
     psi_out[i] = v;
   }
@@ -429,14 +489,14 @@ void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, cons
   }
 }
 template <typename T>
-void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s) {
+void launch_mac_setup(const Geo& g, T* const uf[3][3], MGVec b64, cudaStream_t s) {
   FacePtrs3 un;
   for (int d = 0; d < 3; d++) un.p[d] = uf[d][d];
   k_mac_rhs<T><<<nblocks(g.N), TPB, 0, s>>>(g, un, b64);
   rmt_count_launches(1);
 }
 template <typename T>
-void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, const double* q, T* const umac[3],
+void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, MGVec q, T* const umac[3],
                         cudaStream_t s) {
   for (int d = 0; d < 3; d++) {
     k_mac_correct<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, uf[d][d], rho, q, umac[d]);
@@ -463,12 +523,12 @@ void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* r
   k_ustar<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, adv, p, rho_h, divtau_h, ustar); rmt_count_launches(1);
 }
 template <typename T>
-void launch_fe_setup(const Geo& g, const T* u, const T* ustar, double* b64, cudaStream_t s) {
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b64, cudaStream_t s) {
   k_fe_rhs<T><<<nblocks(g.NN), TPB, 0, s>>>(g, u, ustar, b64);
   rmt_count_launches(1);
 }
 template <typename T>
-void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p, T* psi_out,
+void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, MGVec psi, T* u, T* p, T* psi_out,
                       cudaStream_t s) {
   k_fe_update_u<T><<<nblocks(g.N), TPB, 0, s>>>(g, ustar, rho_h, psi, u); rmt_count_launches(1);
   k_fe_update_p<T><<<nblocks(g.NN), TPB, 0, s>>>(g.NN, psi, p, psi_out); rmt_count_launches(1);
@@ -482,15 +542,15 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
   template void launch_bar_states<T>(const Geo&, const T*, T* const[9], T* const[3][3], T* const[3], cudaStream_t); \
   template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[9],           \
                                       T* const[9], T* const[3][3], T* const[3], T* const[3][3], cudaStream_t);   \
-  template void launch_mac_setup<T>(const Geo&, T* const[3][3], double*, cudaStream_t);                          \
-  template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, const double*, T* const[3],          \
+  template void launch_mac_setup<T>(const Geo&, T* const[3][3], MGVec, cudaStream_t);                            \
+  template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, MGVec, T* const[3],                 \
                                       cudaStream_t);                                                             \
   template void launch_advect<T>(const Geo&, T* const[3][3], T* const[3], T*, cudaStream_t);                      \
   template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, const int*, int, T*,        \
                                   cudaStream_t);                                                                \
   template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, cudaStream_t); \
-  template void launch_fe_setup<T>(const Geo&, const T*, const T*, double*, cudaStream_t);                      \
-  template void launch_fe_update<T>(const Geo&, const T*, const T*, const double*, T*, T*, T*, cudaStream_t);    \
+  template void launch_fe_setup<T>(const Geo&, const T*, const T*, MGVec, cudaStream_t);                        \
+  template void launch_fe_update<T>(const Geo&, const T*, const T*, MGVec, T*, T*, T*, cudaStream_t);          \
   template void launch_fill<T>(T*, T, long, cudaStream_t);
 
 INST(float)

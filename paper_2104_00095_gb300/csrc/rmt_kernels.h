@@ -5,6 +5,15 @@
 
 #include "rmt_common.cuh"
 
+// A multigrid right-hand side or solution as the step kernels see it.  FP64 mode: the FP64
+// array d.  FP32 mode: two-float pairs, value = h + l (d is null), so that no FP64 arithmetic
+// runs in the FP32 step.
+struct MGVec {
+  double* d;
+  float* h;
+  float* l;
+};
+
 // face-array bundle: vector value at every d-face (3 comps) for d = 0..2
 template <typename T>
 struct Faces3 {
@@ -12,10 +21,14 @@ struct Faces3 {
 };
 
 // ---- flow (rmt_flow.cu) -------------------------------------------------------------
-// bbs: band boxes of the bodies (6 ints each, stride ints apart) of the time level of views
+// bbs: band boxes of the bodies (6 ints each, stride ints apart) of the time level of views;
+// list (N ints) and count: scratch for the cells a band reaches
+// t: device pointer to the simulated time; the stress is evaluated at *t + toff
 template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
-                       const int* bbs, int bstride, double t, T* out, cudaStream_t s);
+                       const int* bbs, int bstride, const double* t, double toff, T* out, int* list, int* count,
+                       cudaStream_t s);
+void launch_tick(double* t, double dt, cudaStream_t s);
 // slopes: nine cell arrays, written by launch_bar_states (limited slope of u_a along d at 3d+a)
 // and read by launch_face_states
 template <typename T>
@@ -26,9 +39,9 @@ template <typename T>
 void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
                         T* const wcell[9], T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
 template <typename T>
-void launch_mac_setup(const Geo& g, T* const uf[3][3], double* b64, cudaStream_t s);
+void launch_mac_setup(const Geo& g, T* const uf[3][3], MGVec b, cudaStream_t s);
 template <typename T>
-void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, const double* q, T* const umac[3],
+void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, MGVec q, T* const umac[3],
                         cudaStream_t s);
 template <typename T>
 void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s);
@@ -45,9 +58,9 @@ template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h,
                   T* ustar, cudaStream_t s);
 template <typename T>
-void launch_fe_setup(const Geo& g, const T* u, const T* ustar, double* b64, cudaStream_t s);
+void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b, cudaStream_t s);
 template <typename T>
-void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, const double* psi, T* u, T* p,
+void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, MGVec psi, T* u, T* p,
                       T* psi_out, cudaStream_t s);
 template <typename T>
 void launch_fill(T* a, T v, long n, cudaStream_t s);
@@ -72,15 +85,26 @@ void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks,
 struct MGSolver;  // opaque
 // kind 0: cell-centred 7-point (MAC), kind 1: nodal trilinear FE (27-point)
 MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err);
+size_t mg_footprint(const Geo& g, int kind, int prec_fp32);  // device bytes mg_create would request
+size_t mg_device_bytes(const MGSolver* m);                   // device bytes it did request
+// device bytes charged for one allocation of `bytes` (allocations are 256-byte granular, at least 16 bytes asked)
+inline size_t dev_bytes(size_t bytes) { return ((bytes < 16 ? 16 : bytes) + 255) / 256 * 256; }
 void mg_destroy(MGSolver* m);
-double* mg_rhs(MGSolver* m);        // level-0 FP64 right-hand side (fill before solve)
-double* mg_solution(MGSolver* m);   // level-0 FP64 solution
+// Level-0 right-hand side (filled before a solve) and solution, as MGVec.
+MGVec mg_rhs(MGSolver* m);
+MGVec mg_solution(MGSolver* m);
+// FP64 copy of the solution for read-back (FP32 mode: converted on s first)
+const double* mg_solution64(MGSolver* m, cudaStream_t s);
 // the cell density the operator is built from on the finest level (the caller's array, type T)
 void mg_set_density(MGSolver* m, const void* rho);
 // smoother sweeps before/after the coarse correction and the Jacobi weight (negative: keep)
 void mg_set_smoother(MGSolver* m, int pre, int post, double omega);
 // V-cycles on the correction equation between FP64 residual evaluations (>= 1)
 void mg_set_inner(MGSolver* m, int inner);
+// block height (1, 2, 4 or 8 rows of 32 threads) of the level kernels
+void mg_set_block(MGSolver* m, int by);
+// start each solve from the previous solution (zero before the first) instead of from zero
+void mg_set_warm(MGSolver* m, int warm);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
 // hook(ctx, which, begin, stream) with which = 0 (smoother colour) or 1 (FP64 residual).
 typedef void (*mg_hook_fn)(void* ctx, int which, int begin, cudaStream_t s);

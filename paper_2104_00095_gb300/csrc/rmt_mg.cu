@@ -22,11 +22,12 @@
 // red-black Gauss-Seidel (7-point; one thread per same-colour cell pair along x) and weighted
 // Jacobi (27-point; one fused pass per sweep).  Transfers: 8-cell average / trilinear
 // (cell-centred), full weighting / trilinear (nodal).  Coarse densities are 8-cell means.
-// The coarsest level is solved by one block with many sweeps.  Norms use fixed-order
+// The coarsest level is solved by one block with conjugate gradients.  Norms use fixed-order
 // two-stage reductions, so results are deterministic.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "rmt_kernels.h"
@@ -35,7 +36,9 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int RED_BLOCKS = 1024;
-constexpr int BX = 32, BY = 4;
+// Level kernels run on blocks of BX x by threads: BX = one warp along x, by (1, 2, 4 or 8) a
+// per-solver setting that the autotuner picks.
+constexpr int BX = 32, BYMAX = 8;
 
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
@@ -51,7 +54,7 @@ struct Lv {
   float f_ih2_lo, f_s12_lo;  // ih2 - f_ih2, s12 - f_s12: the two-float constants
 };
 
-inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
+inline dim3 grid3(int nx, int ny, int nz, int by) { return dim3((nx + BX - 1) / BX, (ny + by - 1) / by, nz); }
 
 __device__ __forceinline__ long cix(const Lv& L, int i, int j, int k) { return i + (long)L.n[0] * (j + (long)L.n[1] * k); }
 __device__ __forceinline__ long nix(const Lv& L, int i, int j, int k) { return i + (long)L.nn[0] * (j + (long)L.nn[1] * k); }
@@ -240,6 +243,14 @@ __device__ __forceinline__ void acc_wdiff(float w, float ah, float al, float bh,
   sl = __fadd_rn(sl, __fadd_rn(t.l, pl));
 }
 
+// (h, l) -= m, m a two-float pair (m[0] + m[1])
+__device__ __forceinline__ void ff_sub_pair(float& h, float& l, const float* m) {
+  const F2 t = two_sum(h, -m[0]);
+  const F2 r = two_sum(t.h, __fadd_rn(t.l, __fsub_rn(l, m[1])));
+  h = r.h;
+  l = r.l;
+}
+
 // MAC operator on a two-float iterate: h^-2 sum_faces beta_f (x_c - x_nb), beta_f the same
 // float coefficient the smoothers and the velocity correction use
 __device__ __forceinline__ F2 mac_op_ff(const Lv& L, const float* __restrict__ xh, const float* __restrict__ xl,
@@ -296,27 +307,27 @@ __global__ void k_zero(T* a, long n) {
 
 __device__ __forceinline__ bool thread_cell(const int ext[3], int& i, int& j, int& k) {
   i = blockIdx.x * BX + threadIdx.x;
-  j = blockIdx.y * BY + threadIdx.y;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
   k = blockIdx.z;
   return i < ext[0] && j < ext[1];
 }
 
 __device__ __forceinline__ void block_partial(double loc, double* part) {
-  __shared__ double sh[BX * BY / 32];
+  __shared__ double sh[BX * BYMAX / 32];
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
   const int t = threadIdx.y * BX + threadIdx.x;
   if ((t & 31) == 0) sh[t >> 5] = loc;
   __syncthreads();
   if (t == 0) {
     double s = 0.0;
-    for (int w = 0; w < BX * BY / 32; w++) s += sh[w];
+    for (int w = 0; w < (int)blockDim.y; w++) s += sh[w];
     part[((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
   }
 }
 
 // FP64 residual r = b - A x of the FP64 iterate (T = double); writes r for the V-cycle and
 // per-block partial sums of r^2
-__global__ void __launch_bounds__(BX* BY) k_resid64(Lv L, int kind, const double* __restrict__ x,
+__global__ void __launch_bounds__(BX* BYMAX) k_resid64(Lv L, int kind, const double* __restrict__ x,
                                                      const double* __restrict__ b, const double* __restrict__ rho,
                                                      double* __restrict__ rT, double* __restrict__ part) {
   const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
@@ -335,25 +346,23 @@ __global__ void __launch_bounds__(BX* BY) k_resid64(Lv L, int kind, const double
 
 // per-block partial sum of a float per thread: warp sums in float, block sum in FP64
 __device__ __forceinline__ void block_partial_f(float loc, double* part) {
-  __shared__ double sh[BX * BY / 32];
+  __shared__ double sh[BX * BYMAX / 32];
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
   const int t = threadIdx.y * BX + threadIdx.x;
   if ((t & 31) == 0) sh[t >> 5] = (double)loc;
   __syncthreads();
   if (t == 0) {
     double s = 0.0;
-    for (int w = 0; w < BX * BY / 32; w++) s += sh[w];
+    for (int w = 0; w < (int)blockDim.y; w++) s += sh[w];
     part[((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
   }
 }
 
-// first residual of the zero iterate, r = b: removes the mean (*mean) from b, writes the T copy
-// of r and per-block partial sums of r^2; with T = float it also splits b into two floats
-template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_first_resid(Lv L, int kind, double* __restrict__ b,
-                                                         const double* __restrict__ mean, T* __restrict__ rT,
-                                                         float* __restrict__ bh, float* __restrict__ bl,
-                                                         double* __restrict__ part) {
+// first residual of the zero iterate, r = b (FP64 mode): removes the mean (*mean) from b, writes
+// r and per-block partial sums of r^2
+__global__ void __launch_bounds__(BX* BYMAX) k_first_resid64(Lv L, int kind, double* __restrict__ b,
+                                                           const double* __restrict__ mean, double* __restrict__ rT,
+                                                           double* __restrict__ part) {
   const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
   int i, j, k;
   double loc = 0.0;
@@ -361,22 +370,35 @@ __global__ void __launch_bounds__(BX* BY) k_first_resid(Lv L, int kind, double* 
     const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
     const double v = b[u] - *mean;
     b[u] = v;
-    rT[u] = (T)v;
-    if constexpr (sizeof(T) == 4) {
-      const float hi = (float)v;
-      bh[u] = hi;
-      bl[u] = (float)(v - (double)hi);
-      loc = (double)((float)v * (float)v);
-    } else {
-      loc = v * v;
-    }
+    rT[u] = v;
+    loc = v * v;
   }
   block_partial(loc, part);
 }
 
+// the same for the two-float right-hand side (FP32 mode; mean given as a two-float pair)
+__global__ void __launch_bounds__(BX* BYMAX) k_first_resid_ff(Lv L, int kind, float* __restrict__ bh,
+                                                            float* __restrict__ bl, const float* __restrict__ mean,
+                                                            float* __restrict__ rT, double* __restrict__ part) {
+  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
+  int i, j, k;
+  float loc = 0.0f;
+  if (thread_cell(ext, i, j, k)) {
+    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    float h = bh[u], l = bl[u];
+    ff_sub_pair(h, l, mean);
+    bh[u] = h;
+    bl[u] = l;
+    const float r = __fadd_rn(h, l);
+    rT[u] = r;
+    loc = r * r;
+  }
+  block_partial_f(loc, part);
+}
+
 // residual r = b - A x of the two-float iterate (xh + xl) against the two-float right-hand
 // side (bh + bl); writes the float r for the V-cycle and per-block partial sums of r^2
-__global__ void __launch_bounds__(BX* BY) k_resid_ff(Lv L, int kind, const float* __restrict__ xh,
+__global__ void __launch_bounds__(BX* BYMAX) k_resid_ff(Lv L, int kind, const float* __restrict__ xh,
                                                       const float* __restrict__ xl, const float* __restrict__ bh,
                                                       const float* __restrict__ bl, const float* __restrict__ rho,
                                                       float* __restrict__ rT, double* __restrict__ part) {
@@ -410,20 +432,18 @@ __global__ void k_add_ff(const float* __restrict__ e, float* __restrict__ xh, fl
   }
 }
 
-// FP64 solution from the two-float iterate, minus its mean (*m0 + *m1: the means of xh and xl)
-__global__ void k_ff_to64(const float* __restrict__ xh, const float* __restrict__ xl, const double* __restrict__ m0,
-                          const double* __restrict__ m1, double* __restrict__ x, long n) {
-  const double mean = *m0 + *m1;
-  GRID_LOOP(i, n) x[i] = ((double)xh[i] + (double)xl[i]) - mean;
+// FP64 value of a two-float array (read-back only)
+__global__ void k_ff_to64(const float* __restrict__ xh, const float* __restrict__ xl, double* __restrict__ x, long n) {
+  GRID_LOOP(i, n) x[i] = (double)xh[i] + (double)xl[i];
 }
 
 // red-black Gauss-Seidel colour pass (7-point): each thread updates the cell of this colour
 // among x = 2p and 2p+1 of its row
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_rbgs(Lv L, int colour, T* __restrict__ x, const T* __restrict__ b,
+__global__ void __launch_bounds__(BX* BYMAX) k_rbgs(Lv L, int colour, T* __restrict__ x, const T* __restrict__ b,
                                                   const T* __restrict__ rho) {
   const int p = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (j >= L.n[1]) return;
   const int i = 2 * p + ((j + k + colour) & 1);
@@ -436,7 +456,7 @@ __global__ void __launch_bounds__(BX* BY) k_rbgs(Lv L, int colour, T* __restrict
 
 // weighted Jacobi pass (27-point): xo = xi + w (b - K xi)/diag
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_jacobi(Lv L, T w, const T* __restrict__ xi, T* __restrict__ xo,
+__global__ void __launch_bounds__(BX* BYMAX) k_jacobi(Lv L, T w, const T* __restrict__ xi, T* __restrict__ xo,
                                                     const T* __restrict__ b, const T* __restrict__ rho) {
   int i, j, k;
   if (!thread_cell(L.nn, i, j, k)) return;
@@ -447,7 +467,7 @@ __global__ void __launch_bounds__(BX* BY) k_jacobi(Lv L, T w, const T* __restric
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b,
+__global__ void __launch_bounds__(BX* BYMAX) k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b,
                                                    const T* __restrict__ rho, T* __restrict__ r) {
   const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
   int i, j, k;
@@ -460,7 +480,7 @@ __global__ void __launch_bounds__(BX* BY) k_resid(Lv L, int kind, const T* __res
 
 // restriction of the residual to the coarse right-hand side (coarse x zeroed)
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
+__global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
                                                       T* __restrict__ bc, T* __restrict__ xc) {
   const int ext[3] = {kind == 0 ? C.n[0] : C.nn[0], kind == 0 ? C.n[1] : C.nn[1], kind == 0 ? C.n[2] : C.nn[2]};
   int I, J, K;
@@ -495,7 +515,7 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Lv F, Lv C, int kind, const
 
 // trilinear prolongation of the coarse correction, added to the fine iterate
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong(Lv F, Lv C, int kind, const T* __restrict__ xc,
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong(Lv F, Lv C, int kind, const T* __restrict__ xc,
                                                      T* __restrict__ xf) {
   const int ext[3] = {kind == 0 ? F.n[0] : F.nn[0], kind == 0 ? F.n[1] : F.nn[1], kind == 0 ? F.n[2] : F.nn[2]};
   int i, j, k;
@@ -562,7 +582,7 @@ __global__ void k_inv(long n, const T* __restrict__ rho, T* __restrict__ beta) {
 
 // coarse coefficient (MAC: density, FE: beta) = mean of the 8 fine cells
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_coarsen(Lv F, Lv C, const T* __restrict__ rf, T* __restrict__ rc) {
+__global__ void __launch_bounds__(BX* BYMAX) k_coarsen(Lv F, Lv C, const T* __restrict__ rf, T* __restrict__ rc) {
   int I, J, K;
   if (!thread_cell(C.n, I, J, K)) return;
   T s = T(0);
@@ -592,7 +612,7 @@ __global__ void k_partial(const XT* __restrict__ a, long n, int mode, double* __
 
 // final fixed-order sum of the partials (one block); out = scale * sum
 __global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part, int np, double scale,
-                                                double* __restrict__ out) {
+                                                double* __restrict__ out, float* __restrict__ out_ff = nullptr) {
   __shared__ double sh[1024];
   double loc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) loc += part[i];
@@ -602,7 +622,45 @@ __global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part,
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = sh[0] * scale;
+  if (threadIdx.x == 0) {
+    const double v = sh[0] * scale;
+    *out = v;
+    if (out_ff) {  // the same value as a two-float pair
+      out_ff[0] = (float)v;
+      out_ff[1] = (float)(v - (double)out_ff[0]);
+    }
+  }
+}
+
+// per-block partial sums of the two-float array h + l: two-float accumulation per thread, FP64
+// across threads
+__global__ void k_partial_ff(const float* __restrict__ h, const float* __restrict__ l, long n,
+                             double* __restrict__ part) {
+  __shared__ double sh[TPB / 32];
+  float ah = 0.0f, al = 0.0f;
+  GRID_LOOP(i, n) {
+    const F2 t = two_sum(ah, h[i]);
+    ah = t.h;
+    al = __fadd_rn(al, __fadd_rn(t.l, l[i]));
+  }
+  double loc = (double)ah + (double)al;
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = loc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < TPB / 32; w++) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_ff_sub_mean(float* __restrict__ h, float* __restrict__ l, long n, const float* __restrict__ m) {
+  GRID_LOOP(i, n) {
+    float a = h[i], b = l[i];
+    ff_sub_pair(a, b, m);
+    h[i] = a;
+    l[i] = b;
+  }
 }
 
 template <typename XT>
@@ -617,74 +675,98 @@ __global__ void k_add_to64(const T* __restrict__ a, double* __restrict__ b, long
   GRID_LOOP(i, n) b[i] = set ? (double)a[i] : b[i] + (double)a[i];
 }
 
-// coarsest level: one block, mean-free right-hand side, many smoothing sweeps, mean-free result
+// coarsest level: one block solves it by conjugate gradients (the operator is symmetric
+// positive semi-definite with the constants as null space; the right-hand side is made
+// mean-free and so is the result)
 constexpr int COARSE_TPB = 512;
+// dynamic shared memory of the coarse solve: x, r, p, q = A p and the coefficient of the level,
+// or 0 when they do not fit next to the kernel's static shared memory (it then works on global
+// memory)
+inline size_t coarse_smem(const Lv& L, size_t esz) {
+  const size_t need = (4 * (size_t)L.nunk + (size_t)L.ncell) * esz;
+  constexpr size_t avail = 227 * 1024 - (COARSE_TPB / 32 + 2) * sizeof(double);
+  return need <= avail ? need : 0;
+}
+
+// sum over the block (every thread gets it): float or double per thread, FP64 across threads
+template <typename A>
+__device__ __forceinline__ double block_sum(A v, double* red) {
+  double d = (double)v;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  __syncthreads();  // red may still be read by the previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < COARSE_TPB / 32; w++) t += red[w];
+  return t;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(COARSE_TPB) k_coarse_solve(Lv L, int kind, int sweeps, T w, T* __restrict__ gx,
-                                                             T* __restrict__ gxt, T* __restrict__ gb,
-                                                             const T* __restrict__ grho) {
-  __shared__ double sh[1024];
-  __shared__ double mean;
-  // the whole level lives in shared memory for the sweeps
+__global__ void __launch_bounds__(COARSE_TPB) k_coarse_cg(Lv L, int kind, int max_it, double rtol, T* __restrict__ gx,
+                                                         T* __restrict__ gp, T* __restrict__ gb,
+                                                         T* __restrict__ gq, const T* __restrict__ grho,
+                                                         int in_smem) {
+  __shared__ double red[COARSE_TPB / 32];
   extern __shared__ unsigned char smem[];
-  T* x = (T*)smem;
-  T* xt = x + L.nunk;
-  T* b = xt + L.nunk;
-  T* rho = b + L.nunk;
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) b[u] = gb[u];
-  for (long u = threadIdx.x; u < L.ncell; u += blockDim.x) rho[u] = grho[u];
-  __syncthreads();
-  double loc = 0.0;
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) loc += (double)b[u];
-  sh[threadIdx.x] = loc;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+  const long n = L.nunk;
+  T *x = gx, *r = gb, *p = gp, *q = gq;
+  const T* rho = grho;
+  if (in_smem) {
+    x = (T*)smem;
+    r = x + n;
+    p = r + n;
+    q = p + n;
+    T* c = q + n;
+    for (long u = threadIdx.x; u < n; u += blockDim.x) r[u] = gb[u];
+    for (long u = threadIdx.x; u < L.ncell; u += blockDim.x) c[u] = grho[u];
+    rho = c;
     __syncthreads();
   }
-  if (threadIdx.x == 0) mean = sh[0] / (double)L.nunk;
-  __syncthreads();
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
-    b[u] = (T)((double)b[u] - mean);
+  using A = T;  // per-thread accumulation type
+  A loc = A(0);
+  for (long u = threadIdx.x; u < n; u += blockDim.x) loc += r[u];
+  const double mean = block_sum(loc, red) / (double)n;
+  loc = A(0);
+  for (long u = threadIdx.x; u < n; u += blockDim.x) {
+    const T v = (T)((double)r[u] - mean);
+    r[u] = v;
+    p[u] = v;
     x[u] = T(0);
+    loc += v * v;
   }
-  __syncthreads();
+  double rr = block_sum(loc, red);
+  const double stop = rtol * rtol * rr;
   const int ex = kind == 0 ? L.n[0] : L.nn[0], ey = kind == 0 ? L.n[1] : L.nn[1];
-  for (int it = 0; it < sweeps; it++) {
-    if (kind == 0) {
-      for (int col = 0; col < 2; col++) {
-        for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
-          const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
-          if (((i + j + k) & 1) != col) continue;
-          T dg;
-          const T ax = mac_op<T>(L, x, rho, i, j, k, dg);
-          if (dg > T(0)) x[u] = x[u] + (b[u] - ax) / dg;
-        }
-        __syncthreads();
-      }
-    } else {
-      for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) {
-        const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
-        T dg;
-        const T ax = fe_op<T>(L, x, rho, i, j, k, dg);
-        xt[u] = dg > T(0) ? x[u] + w * (b[u] - ax) / dg : x[u];
-      }
-      __syncthreads();
-      for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) x[u] = xt[u];
-      __syncthreads();
+  for (int it = 0; it < max_it && rr > stop; it++) {
+    __syncthreads();  // p complete
+    loc = A(0);
+    for (long u = threadIdx.x; u < n; u += blockDim.x) {
+      const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
+      T dg;
+      const T ap = kind == 0 ? mac_op<T>(L, p, rho, i, j, k, dg) : fe_op<T>(L, p, rho, i, j, k, dg);
+      q[u] = ap;
+      loc += p[u] * ap;
     }
+    const double pq = block_sum(loc, red);
+    if (!(pq > 0.0)) break;
+    const T a = (T)(rr / pq);
+    loc = A(0);
+    for (long u = threadIdx.x; u < n; u += blockDim.x) {
+      x[u] += a * p[u];
+      const T v = r[u] - a * q[u];
+      r[u] = v;
+      loc += v * v;
+    }
+    const double rr2 = block_sum(loc, red);
+    const T beta = (T)(rr2 / rr);
+    rr = rr2;
+    for (long u = threadIdx.x; u < n; u += blockDim.x) p[u] = r[u] + beta * p[u];
   }
-  loc = 0.0;
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) loc += (double)x[u];
-  sh[threadIdx.x] = loc;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) mean = sh[0] / (double)L.nunk;
-  __syncthreads();
-  for (long u = threadIdx.x; u < L.nunk; u += blockDim.x) gx[u] = (T)((double)x[u] - mean);
+  loc = A(0);
+  for (long u = threadIdx.x; u < n; u += blockDim.x) loc += x[u];
+  const double xm = block_sum(loc, red) / (double)n;
+  for (long u = threadIdx.x; u < n; u += blockDim.x) gx[u] = (T)((double)x[u] - xm);
 }
 
 }  // namespace
@@ -704,10 +786,13 @@ struct MGSolver {
   double* hpin = nullptr;
   size_t esz = 8;
   int pre = 2, post = 2;
-  int inner = 1;  // V-cycles on the FP32 correction equation per FP64 residual
+  int inner = 1;  // V-cycles on the storage-precision correction equation per high-precision residual
+  int by = 4;     // block height of the level kernels
+  int warm = 0;   // start from the last solution instead of zero
   double omega = 0.9;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
+  size_t bytes = 0;  // device bytes requested
 };
 
 void mg_set_hook(MGSolver* m, mg_hook_fn fn, void* ctx) {
@@ -722,6 +807,10 @@ void mg_set_smoother(MGSolver* m, int pre, int post, double omega) {
 void mg_set_inner(MGSolver* m, int inner) {
   if (inner >= 1) m->inner = inner;
 }
+void mg_set_warm(MGSolver* m, int warm) { m->warm = warm != 0; }
+void mg_set_block(MGSolver* m, int by) {
+  if (by == 1 || by == 2 || by == 4 || by == 8) m->by = by;
+}
 
 static cudaError_t dmalloc(void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
@@ -729,20 +818,27 @@ static cudaError_t dmalloc(void** p, size_t bytes) {
   return e;
 }
 
-MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
+namespace {
+// Builds the level hierarchy; with dry set it only adds up the device bytes it would allocate.
+MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t* err) {
   MGSolver* m = new MGSolver();
   m->kind = kind;
   m->fp32 = prec_fp32;
   m->esz = prec_fp32 ? 4 : 8;
   m->omega = kind == 0 ? 1.0 : 0.9;
   m->pre = m->post = kind == 0 ? 3 : 2;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes) {
+    m->bytes += dev_bytes(bytes);
+    if (dry || e != cudaSuccess) return;
+    e = dmalloc(p, bytes);
+  };
   Lv L;
   for (int d = 0; d < 3; d++) {
     L.n[d] = g.n[d];
     L.per[d] = g.per[d];
   }
   L.h = g.h;
-  cudaError_t e = cudaSuccess;
   for (int l = 0; l < 16; l++) {
     for (int d = 0; d < 3; d++) L.nn[d] = L.per[d] ? L.n[d] : L.n[d] + 1;
     L.ncell = (long)L.n[0] * L.n[1] * L.n[2];
@@ -757,11 +853,11 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     m->lv[l] = L;
     m->nlev = l + 1;
     const size_t vb = (size_t)L.nunk * m->esz;
-    if (e == cudaSuccess) e = dmalloc(&m->x[l], vb);
-    if (e == cudaSuccess) e = dmalloc(&m->xt[l], vb);
-    if (e == cudaSuccess) e = dmalloc(&m->b[l], vb);
-    if (e == cudaSuccess) e = dmalloc(&m->r[l], vb);
-    if (e == cudaSuccess && (l > 0 || kind == 1)) e = dmalloc(&m->rho[l], (size_t)L.ncell * m->esz);
+    alloc(&m->x[l], vb);
+    alloc(&m->xt[l], vb);
+    alloc(&m->b[l], vb);
+    alloc(&m->r[l], vb);
+    if (l > 0 || kind == 1) alloc(&m->rho[l], (size_t)L.ncell * m->esz);
     // coarsen while every axis halves to an even-enough size
     bool can = true;
     for (int d = 0; d < 3; d++) {
@@ -773,21 +869,50 @@ MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
     L.h *= 2.0;
   }
   const Lv& L0 = m->lv[0];
-  const long nbr = (long)((L0.nn[0] + BX - 1) / BX) * ((L0.nn[1] + BY - 1) / BY) * L0.nn[2];
-  if (e == cudaSuccess) e = dmalloc((void**)&m->x64, L0.nunk * sizeof(double));
-  if (e == cudaSuccess) e = dmalloc((void**)&m->b64, L0.nunk * sizeof(double));
+  const long nbr = (long)((L0.nn[0] + BX - 1) / BX) * L0.nn[1] * L0.nn[2];  // partials at by = 1
+  alloc((void**)&m->x64, L0.nunk * sizeof(double));
+  if (!prec_fp32) alloc((void**)&m->b64, L0.nunk * sizeof(double));
   if (prec_fp32) {
-    if (e == cudaSuccess) e = dmalloc((void**)&m->xh, L0.nunk * sizeof(float));
-    if (e == cudaSuccess) e = dmalloc((void**)&m->xl, L0.nunk * sizeof(float));
-    if (e == cudaSuccess) e = dmalloc((void**)&m->bh, L0.nunk * sizeof(float));
-    if (e == cudaSuccess) e = dmalloc((void**)&m->bl, L0.nunk * sizeof(float));
+    alloc((void**)&m->xh, L0.nunk * sizeof(float));
+    alloc((void**)&m->xl, L0.nunk * sizeof(float));
+    alloc((void**)&m->bh, L0.nunk * sizeof(float));
+    alloc((void**)&m->bl, L0.nunk * sizeof(float));
   }
-  if (e == cudaSuccess) e = dmalloc((void**)&m->part, (size_t)(nbr > RED_BLOCKS ? nbr : RED_BLOCKS) * sizeof(double));
-  if (e == cudaSuccess) e = dmalloc((void**)&m->scal, 8 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&m->hpin, 8 * sizeof(double));
+  alloc((void**)&m->part, (size_t)(nbr > RED_BLOCKS ? nbr : RED_BLOCKS) * sizeof(double));
+  alloc((void**)&m->scal, 8 * sizeof(double));
+  if (!dry) {
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&m->hpin, 8 * sizeof(double));
+    // the coarsest level lives in shared memory during its solve (when it fits): opt in to its
+    // size once, outside any stream capture
+    const size_t smem = coarse_smem(m->lv[m->nlev - 1], m->esz);
+    // the attribute belongs to the kernel, shared by every solver: it only ever grows
+    static std::mutex mu;
+    static size_t opted[2] = {0, 0};
+    std::lock_guard<std::mutex> lock(mu);
+    if (e == cudaSuccess && smem > opted[prec_fp32 ? 1 : 0]) {
+      if (prec_fp32)
+        e = cudaFuncSetAttribute(k_coarse_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      else
+        e = cudaFuncSetAttribute(k_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) opted[prec_fp32 ? 1 : 0] = smem;
+    }
+  }
   if (err) *err = e;
   return m;
 }
+}  // namespace
+
+MGSolver* mg_create(const Geo& g, int kind, int prec_fp32, cudaError_t* err) {
+  return mg_build(g, kind, prec_fp32, false, err);
+}
+
+size_t mg_footprint(const Geo& g, int kind, int prec_fp32) {
+  MGSolver* m = mg_build(g, kind, prec_fp32, true, nullptr);
+  const size_t b = m->bytes;
+  delete m;
+  return b;
+}
+size_t mg_device_bytes(const MGSolver* m) { return m ? m->bytes : 0; }
 
 void mg_destroy(MGSolver* m) {
   if (!m) return;
@@ -810,8 +935,16 @@ void mg_destroy(MGSolver* m) {
   delete m;
 }
 
-double* mg_rhs(MGSolver* m) { return m->b64; }
-double* mg_solution(MGSolver* m) { return m->x64; }
+MGVec mg_rhs(MGSolver* m) { return m->fp32 ? MGVec{nullptr, m->bh, m->bl} : MGVec{m->b64, nullptr, nullptr}; }
+MGVec mg_solution(MGSolver* m) { return m->fp32 ? MGVec{nullptr, m->xh, m->xl} : MGVec{m->x64, nullptr, nullptr}; }
+const double* mg_solution64(MGSolver* m, cudaStream_t s) {
+  if (m->fp32) {
+    const long n = m->lv[0].nunk;
+    k_ff_to64<<<nblocks(n), TPB, 0, s>>>(m->xh, m->xl, m->x64, n);
+    rmt_count_launches(1);
+  }
+  return m->x64;
+}
 void mg_set_density(MGSolver* m, const void* rho) {
   m->rho_in = rho;
   if (m->kind == 0) m->rho[0] = (void*)rho;
@@ -833,6 +966,17 @@ void sum_into(MGSolver* m, const T* a, long n, int mode, double scale, double* o
   rmt_count_launches(1);
 }
 
+// out = scale * sum(h + l); out_ff receives the same value as a two-float pair
+void sum_ff(MGSolver* m, const float* h, const float* l, long n, double scale, double* out, float* out_ff,
+            cudaStream_t s) {
+  int nb = nblocks(n);
+  if (nb > RED_BLOCKS) nb = RED_BLOCKS;
+  k_partial_ff<<<nb, TPB, 0, s>>>(h, l, n, m->part);
+  rmt_count_launches(1);
+  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out, out_ff);
+  rmt_count_launches(1);
+}
+
 template <typename T>
 void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   const Lv& L = m->lv[l];
@@ -840,17 +984,17 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   const T* rho = (const T*)m->rho[l];
   for (int it = 0; it < sweeps; it++) {
     if (m->kind == 0) {
-      const dim3 gr((L.n[0] / 2 + 1 + BX - 1) / BX, (L.n[1] + BY - 1) / BY, L.n[2]);
+      const dim3 gr((L.n[0] / 2 + 1 + BX - 1) / BX, (L.n[1] + m->by - 1) / m->by, L.n[2]);
       for (int q = 0; q < 2; q++) {
         const int col = forward ? q : 1 - q;
         hk(m, l, 0, 1, s);
-        k_rbgs<T><<<gr, dim3(BX, BY), 0, s>>>(L, col, (T*)m->x[l], b, rho);
+        k_rbgs<T><<<gr, dim3(BX, m->by), 0, s>>>(L, col, (T*)m->x[l], b, rho);
         rmt_count_launches(1);
         hk(m, l, 0, 0, s);
       }
     } else {
       hk(m, l, 0, 1, s);
-      k_jacobi<T><<<grid3(L.nn[0], L.nn[1], L.nn[2]), dim3(BX, BY), 0, s>>>(L, T(m->omega), (const T*)m->x[l],
+      k_jacobi<T><<<grid3(L.nn[0], L.nn[1], L.nn[2], m->by), dim3(BX, m->by), 0, s>>>(L, T(m->omega), (const T*)m->x[l],
                                                                               (T*)m->xt[l], b, rho);
       rmt_count_launches(1);
       hk(m, l, 0, 0, s);
@@ -868,28 +1012,30 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     int nmax = L.n[0];
     if (L.n[1] > nmax) nmax = L.n[1];
     if (L.n[2] > nmax) nmax = L.n[2];
-    const int sweeps = (m->kind == 0 ? 2 : 4) * nmax * nmax + 20;
-    const size_t smem = (3 * (size_t)L.nunk + (size_t)L.ncell) * sizeof(T);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_coarse_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_coarse_solve<T><<<1, COARSE_TPB, smem, s>>>(L, m->kind, sweeps, T(m->omega), (T*)m->x[l], (T*)m->xt[l],
-                                                  (T*)m->b[l], (const T*)m->rho[l]);
+    // conjugate gradients converge in O(nmax) iterations on this level; the cap only bounds
+    // the launch, the tolerance ends it
+    const int max_it = 8 * nmax + 64;
+    const double tol = sizeof(T) == 4 ? 1e-5 : 1e-10;
+    const size_t smem = coarse_smem(L, sizeof(T));  // opted in at creation
+    k_coarse_cg<T><<<1, COARSE_TPB, smem, s>>>(L, m->kind, max_it, tol, (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
+                                               (T*)m->r[l], (const T*)m->rho[l], smem > 0);
     rmt_count_launches(1);
     return;
   }
   const int ex = m->kind == 0 ? L.n[0] : L.nn[0], ey = m->kind == 0 ? L.n[1] : L.nn[1],
             ez = m->kind == 0 ? L.n[2] : L.nn[2];
   smooth<T>(m, l, m->pre, true, s);
-  k_resid<T><<<grid3(ex, ey, ez), dim3(BX, BY), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
+  k_resid<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
                                                         (const T*)m->rho[l], (T*)m->r[l]);
   rmt_count_launches(1);
   const Lv& C = m->lv[l + 1];
   const int cx = m->kind == 0 ? C.n[0] : C.nn[0], cy = m->kind == 0 ? C.n[1] : C.nn[1],
             cz = m->kind == 0 ? C.n[2] : C.nn[2];
-  k_restrict<T><<<grid3(cx, cy, cz), dim3(BX, BY), 0, s>>>(L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1],
+  k_restrict<T><<<grid3(cx, cy, cz, m->by), dim3(BX, m->by), 0, s>>>(L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1],
                                                            (T*)m->x[l + 1]);
   rmt_count_launches(1);
   vcycle<T>(m, l + 1, s);
-  k_prolong<T><<<grid3(ex, ey, ez), dim3(BX, BY), 0, s>>>(L, C, m->kind, (const T*)m->x[l + 1], (T*)m->x[l]);
+  k_prolong<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, C, m->kind, (const T*)m->x[l + 1], (T*)m->x[l]);
   rmt_count_launches(1);
   smooth<T>(m, l, m->post, false, s);
 }
@@ -906,93 +1052,117 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
   for (int l = 1; l < m->nlev; l++) {
     const Lv& F = m->lv[l - 1];
     const Lv& C = m->lv[l];
-    k_coarsen<T><<<grid3(C.n[0], C.n[1], C.n[2]), dim3(BX, BY), 0, s>>>(F, C, (const T*)m->rho[l - 1], (T*)m->rho[l]);
+    k_coarsen<T><<<grid3(C.n[0], C.n[1], C.n[2], m->by), dim3(BX, m->by), 0, s>>>(F, C, (const T*)m->rho[l - 1], (T*)m->rho[l]);
     rmt_count_launches(1);
   }
-  // mean-free right-hand side, zero start
-  sum_into<double>(m, m->b64, n, 0, 1.0 / (double)n, m->scal, s);
-  double bn2 = 0.0;
-  if (fixed_cycles <= 0) {
-    // |b|^2 of the mean-free b: sum b^2 - n mean^2 would cancel, so subtract first
-    k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal);
-    rmt_count_launches(1);
-    k_zero<double><<<1, 32, 0, s>>>(m->scal, 1);
-    rmt_count_launches(1);
-    sum_into<double>(m, m->b64, n, 1, 1.0, m->scal + 1, s);
-    cudaMemcpyAsync(m->hpin, m->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
-    bn2 = m->hpin[0];
-  }
-  constexpr bool ff = sizeof(T) == 4;  // two-float iterate
+  // scal: [0] mean of b, [2] |r|^2, [3] mean of x (FP64); fm: the two means as two-float pairs
+  float* fm = (float*)(m->scal + 6);
+  constexpr bool ff = sizeof(T) == 4;  // two-float right-hand side and iterate
+  if constexpr (ff)
+    sum_ff(m, m->bh, m->bl, n, 1.0 / (double)n, m->scal, fm, s);
+  else
+    sum_into<double>(m, m->b64, n, 0, 1.0 / (double)n, m->scal, s);
   const int ex = m->kind == 0 ? L0.n[0] : L0.nn[0], ey = m->kind == 0 ? L0.n[1] : L0.nn[1],
             ez = m->kind == 0 ? L0.n[2] : L0.nn[2];
-  const dim3 g0 = grid3(ex, ey, ez);
+  const dim3 g0 = grid3(ex, ey, ez, m->by);
   const int nbr = (int)((long)g0.x * g0.y * g0.z);
+  const int cap = fixed_cycles > 0 ? fixed_cycles : max_cycles;
   int cycles = 0;
   int ok = 1;
   bool have_x = false;  // false: the iterate is still zero
-  if (fixed_cycles > 0 || bn2 != 0.0) {
-    const int cap = fixed_cycles > 0 ? fixed_cycles : max_cycles;
-    for (;;) {
-      if (!have_x) {
-        // r = b (also removes the mean of b, which scal[0] holds, or zero when already removed)
-        k_first_resid<T><<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->b64, m->scal, (T*)m->b[0], m->bh, m->bl, m->part);
-        rmt_count_launches(1);
-      } else {
-        hk(m, 0, 1, 1, s);
-        if constexpr (sizeof(T) == 4)
-          k_resid_ff<<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->xh, m->xl, m->bh, m->bl, (const float*)m->rho[0],
-                                                 (float*)m->b[0], m->part);
-        else
-          k_resid64<<<g0, dim3(BX, BY), 0, s>>>(L0, m->kind, m->x64, m->b64, (const double*)m->rho[0],
-                                                (double*)m->b[0], m->part);
-        rmt_count_launches(1);
-        hk(m, 0, 1, 0, s);
-      }
-      if (fixed_cycles <= 0) {
-        k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
-        rmt_count_launches(1);
-        cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
-        if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
-        const double rn2 = m->hpin[1];
-        if (!(rn2 == rn2)) {
-          ok = 0;
-          break;
-        }
-        if (rn2 <= rtol * rtol * bn2) break;
-      }
-      if (cycles >= cap) {
-        if (fixed_cycles <= 0) ok = 0;
-        break;
-      }
-      k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
-      rmt_count_launches(1);
-      // inner V-cycles on A e = r in the storage type (the high-precision residual is re-formed after them)
-      for (int q = 0; q < m->inner && cycles < cap; q++) {
-        vcycle<T>(m, 0, s);
-        cycles++;
-      }
-      if constexpr (sizeof(T) == 4)
-        k_add_ff<<<nblocks(n), TPB, 0, s>>>((const float*)m->x[0], m->xh, m->xl, n, have_x ? 0 : 1);
+  double bn2 = -1.0;
+  if (m->warm) {
+    // warm start from the last solution (mean-free; zero before the first solve): remove the
+    // mean of b here, since the first residual is a full one
+    have_x = true;
+    if constexpr (ff) {
+      k_ff_sub_mean<<<nblocks(n), TPB, 0, s>>>(m->bh, m->bl, n, fm);
+    } else {
+      k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->b64, n, m->scal);
+    }
+    rmt_count_launches(1);
+    if (fixed_cycles <= 0) {
+      if constexpr (ff)
+        sum_into<float>(m, m->bh, n, 1, 1.0, m->scal + 1, s);
       else
-        k_add_to64<<<nblocks(n), TPB, 0, s>>>((const double*)m->x[0], m->x64, n, have_x ? 0 : 1);
-      rmt_count_launches(1);
-      have_x = true;
-      if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
+        sum_into<double>(m, m->b64, n, 1, 1.0, m->scal + 1, s);
+      cudaMemcpyAsync(m->hpin, m->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
+      bn2 = m->hpin[0];
     }
   }
-  if (!have_x) {
-    k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n);
+  for (;;) {
+    if (!have_x) {
+      // the residual of the zero iterate is b itself: remove its mean, no operator
+      if constexpr (ff)
+        k_first_resid_ff<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->bh, m->bl, fm, (float*)m->b[0], m->part);
+      else
+        k_first_resid64<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->b64, m->scal, (double*)m->b[0], m->part);
+      rmt_count_launches(1);
+    } else {
+      hk(m, 0, 1, 1, s);
+      if constexpr (ff)
+        k_resid_ff<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->xh, m->xl, m->bh, m->bl, (const float*)m->rho[0],
+                                               (float*)m->b[0], m->part);
+      else
+        k_resid64<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->x64, m->b64, (const double*)m->rho[0],
+                                              (double*)m->b[0], m->part);
+      rmt_count_launches(1);
+      hk(m, 0, 1, 0, s);
+    }
+    if (fixed_cycles <= 0) {
+      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
+      rmt_count_launches(1);
+      cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;
+      const double rn2 = m->hpin[1];
+      if (!(rn2 == rn2)) {
+        ok = 0;
+        break;
+      }
+      if (bn2 < 0.0) bn2 = rn2;  // |b|^2 of the mean-free right-hand side (zero start)
+      if (bn2 == 0.0) break;
+      if (rn2 <= rtol * rtol * bn2) break;
+    }
+    if (cycles >= cap) {
+      if (fixed_cycles <= 0) ok = 0;
+      break;
+    }
+    k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
     rmt_count_launches(1);
-  } else if (ff) {
-    sum_into<float>(m, m->xh, n, 0, 1.0 / (double)n, m->scal + 3, s);
-    sum_into<float>(m, m->xl, n, 0, 1.0 / (double)n, m->scal + 4, s);
-    k_ff_to64<<<nblocks(n), TPB, 0, s>>>(m->xh, m->xl, m->scal + 3, m->scal + 4, m->x64, n);
+    // inner V-cycles on A e = r in the storage type (the high-precision residual is re-formed after them)
+    for (int q = 0; q < m->inner && cycles < cap; q++) {
+      vcycle<T>(m, 0, s);
+      cycles++;
+    }
+    if constexpr (ff)
+      k_add_ff<<<nblocks(n), TPB, 0, s>>>((const float*)m->x[0], m->xh, m->xl, n, have_x ? 0 : 1);
+    else
+      k_add_to64<<<nblocks(n), TPB, 0, s>>>((const double*)m->x[0], m->x64, n, have_x ? 0 : 1);
     rmt_count_launches(1);
+    have_x = true;
+    if (fixed_cycles > 0 && cycles >= fixed_cycles) break;
+  }
+  // mean-free solution
+  if constexpr (ff) {
+    if (!have_x) {
+      k_zero<float><<<nblocks(n), TPB, 0, s>>>(m->xh, n);
+      k_zero<float><<<nblocks(n), TPB, 0, s>>>(m->xl, n);
+      rmt_count_launches(2);
+    } else {
+      sum_ff(m, m->xh, m->xl, n, 1.0 / (double)n, m->scal + 3, fm + 2, s);
+      k_ff_sub_mean<<<nblocks(n), TPB, 0, s>>>(m->xh, m->xl, n, fm + 2);
+      rmt_count_launches(1);
+    }
   } else {
-    sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);
-    k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3);
-    rmt_count_launches(1);
+    if (!have_x) {
+      k_zero<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n);
+      rmt_count_launches(1);
+    } else {
+      sum_into<double>(m, m->x64, n, 0, 1.0 / (double)n, m->scal + 3, s);
+      k_sub_scalar<double><<<nblocks(n), TPB, 0, s>>>(m->x64, n, m->scal + 3);
+      rmt_count_launches(1);
+    }
   }
   *err = cudaGetLastError();
   return ok ? cycles : -1;

@@ -1,7 +1,8 @@
 // Stress kernel of the RMT per-step update (arXiv 2104.00095, SI "Stress calculations",
 // eq. mixed_stresses and the multi-body rule; main text "Swimming" for the active stress).
-// One thread per cell computes the face-normal rows of the blended stress at its six faces
-// and their divergence; templated on T.
+// Two passes: every cell that no body's band reaches takes the pure-fluid divergence at once
+// and the rest are listed; then one thread per listed cell computes the face-normal rows of the
+// blended stress at its six faces and their divergence.  Templated on T.
 #include "rmt_kernels.h"
 
 namespace {
@@ -121,49 +122,90 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
   for (int a = 0; a < 3; a++) row[a] = Hf * mu * du[a] + acc[a] * sc;
 }
 
+// bodies whose band holds cell (i,j,k): only they can contribute at its six faces
 template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* __restrict__ u,
-                                                                const Body* __restrict__ bodies,
-                                                                const BodyView<T>* __restrict__ views, int nb,
-                                                                const int* __restrict__ bbs, int bstride, T tt,
-                                                                T* __restrict__ out) {
+__device__ __forceinline__ uint64_t cell_bodies(const Geo& g, const BodyView<T>* __restrict__ views, int nb,
+                                                const int* sbb, int i, int j, int k, long c) {
+  uint64_t bm = 0;
+  for (int m = 0; m < nb; m++)
+    if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
+  return bm;
+}
+
+// Pass 1, every cell: cells no body reaches take the pure-fluid divergence mu lap(u) here; the
+// others are appended to a list (one atomic per warp) for pass 2.
+template <typename T>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T* __restrict__ u,
+                                                                  const BodyView<T>* __restrict__ views, int nb,
+                                                                  const int* __restrict__ bbs, int bstride,
+                                                                  T* __restrict__ out, int* __restrict__ list,
+                                                                  int* __restrict__ count) {
   __shared__ int sbb[6 * RMT_MAX_BODIES];
   stage_boxes(bbs, bstride, nb, sbb);
   THREAD_XYZ(i, j, k);
   if (i >= g.n[0] || j >= g.n[1]) return;
   const long c = cidx(g, i, j, k);
-  // bodies that have xi at this cell: only they can contribute at its six faces
-  uint64_t bm = 0;
-  for (int m = 0; m < nb; m++)
-    if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
-  T acc[3] = {T(0), T(0), T(0)};
+  const uint64_t bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+  const unsigned act = __activemask();
+  const unsigned want = __ballot_sync(act, bm != 0);
+  if (bm != 0) {
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int leader = __ffs(want) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(want));
+    base = __shfl_sync(want, base, leader);
+    list[base + __popc(want & ((1u << lane) - 1u))] = (int)c;
+    return;
+  }
+  // pure fluid around this cell: every face row is mu (u_b - u_a)/h
   const T ih = cv<T>(g.ih, g.f.ih);
-  if (bm == 0) {
-    // pure fluid around this cell: every face row is mu (u_b - u_a)/h
-    const T mu = cv<T>(g.mu, g.f.mu);
-    const bool in = i > 0 && i + 1 < g.n[0] && j > 0 && j + 1 < g.n[1] && k > 0 && k + 1 < g.n[2];
+  const T mu = cv<T>(g.mu, g.f.mu);
+  const bool in = i > 0 && i + 1 < g.n[0] && j > 0 && j + 1 < g.n[1] && k > 0 && k + 1 < g.n[2];
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const T* ua = u + (long)a * g.N;
-      const T uc = ua[c];
+  for (int a = 0; a < 3; a++) {
+    const T* ua = u + (long)a * g.N;
+    const T uc = ua[c];
+    T acc = T(0);
 #pragma unroll
-      for (int d = 0; d < 3; d++) {
-        T up, um;
-        if (in) {
-          const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
-          up = ua[c + st];
-          um = ua[c - st];
-        } else {
-          int p[3] = {i, j, k}, q[3] = {i, j, k};
-          p[d] += 1;
-          q[d] -= 1;
-          up = uval(g, u, a, p[0], p[1], p[2]);
-          um = uval(g, u, a, q[0], q[1], q[2]);
-        }
-        acc[a] += (mu * ((up - uc) * ih) - mu * ((uc - um) * ih)) * ih;
+    for (int d = 0; d < 3; d++) {
+      T up, um;
+      if (in) {
+        const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
+        up = ua[c + st];
+        um = ua[c - st];
+      } else {
+        int p[3] = {i, j, k}, q[3] = {i, j, k};
+        p[d] += 1;
+        q[d] -= 1;
+        up = uval(g, u, a, p[0], p[1], p[2]);
+        um = uval(g, u, a, q[0], q[1], q[2]);
       }
+      acc += (mu * ((up - uc) * ih) - mu * ((uc - um) * ih)) * ih;
     }
-  } else {
+    out[a * g.N + c] = acc;
+  }
+}
+
+// Pass 2, the listed cells (a body's band reaches them): blended face rows at the six faces,
+// one thread per cell, so every lane of a warp takes the same long path.
+template <typename T>
+__global__ void __launch_bounds__(128) k_stress_band(Geo g, const T* __restrict__ u, const Body* __restrict__ bodies,
+                                                      const BodyView<T>* __restrict__ views, int nb,
+                                                      const int* __restrict__ bbs, int bstride,
+                                                      const double* __restrict__ t, double toff,
+                                                      const int* __restrict__ list, const int* __restrict__ count,
+                                                      T* __restrict__ out) {
+  __shared__ int sbb[6 * RMT_MAX_BODIES];
+  stage_boxes(bbs, bstride, nb, sbb);
+  const int n = *count;
+  const T tt = (T)(*t + toff);
+  const T ih = cv<T>(g.ih, g.f.ih);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const long c = list[e];
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    const uint64_t bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+    T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       int ip[3] = {i, j, k};
@@ -174,22 +216,37 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_div(Geo g, const T* _
 #pragma unroll
       for (int a = 0; a < 3; a++) acc[a] += (rp[a] - rm[a]) * ih;
     }
-  }
 #pragma unroll
-  for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
+    for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
+  }
 }
 
 }  // namespace
 
 template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
-                       const int* bbs, int bstride, double t, T* out, cudaStream_t s) {
+                       const int* bbs, int bstride, const double* t, double toff, T* out, int* list, int* count,
+                       cudaStream_t s) {
   const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
-  k_stress_div<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, bodies, views, nb, bbs, bstride, T(t), out);
+  cudaMemsetAsync(count, 0, sizeof(int), s);
+  k_stress_fluid<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, views, nb, bbs, bstride, out, list, count);
+  rmt_count_launches(1);
+  if (nb == 0) return;
+  k_stress_band<T><<<152 * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, out);
   rmt_count_launches(1);
 }
 
 template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, const int*,
-                                       int, double, float*, cudaStream_t);
+                                       int, const double*, double, float*, int*, int*, cudaStream_t);
 template void launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int,
-                                        const int*, int, double, double*, cudaStream_t);
+                                        const int*, int, const double*, double, double*, int*, int*, cudaStream_t);
+
+// simulated time on the device: t += dt after each step (read by the stress kernels, so that a
+// captured step graph needs no per-step parameter)
+__global__ void k_tick(double* t, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) t[0] = t[0] + dt;
+}
+void launch_tick(double* t, double dt, cudaStream_t s) {
+  k_tick<<<1, 32, 0, s>>>(t, dt);
+  rmt_count_launches(1);
+}

@@ -22,10 +22,17 @@ RMT_F_DIVTAU_N, RMT_F_DIVTAU_H, RMT_F_UFACE_X, RMT_F_UFACE_Y, RMT_F_UFACE_Z = 20
 RMT_F_MAC_Q, RMT_F_ADV_U, RMT_F_USTAR, RMT_F_PSI, RMT_F_RHO_HALF, RMT_F_XI_HALF = 25, 26, 27, 28, 29, 30
 RMT_F_UMAC_X, RMT_F_UMAC_Y, RMT_F_UMAC_Z = 31, 32, 33
 
+RMT_JOB_QUEUED, RMT_JOB_RUNNING, RMT_JOB_DONE, RMT_JOB_FAILED = 0, 1, 2, 3
+
 EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt_read_fields",
            "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_set_option", "rmt_kernel_launches", "rmt_profile",
            "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_extrapolate_noalloc", "rmt_destroy_grid",
-           "rmt_last_error")
+           "rmt_last_error", "rmt_grid_footprint", "rmt_grid_device_bytes", "rmt_batch_create", "rmt_batch_add",
+           "rmt_batch_remove", "rmt_batch_step", "rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy",
+           "rmt_batch_last_error", "rmt_server_create", "rmt_server_set_option", "rmt_server_submit",
+           "rmt_server_poll", "rmt_server_job", "rmt_server_job_grid", "rmt_server_release",
+           "rmt_server_resident_bytes", "rmt_server_clock", "rmt_server_cell_steps", "rmt_server_destroy",
+           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats")
 
 
 class rmt_grid_desc(C.Structure):
@@ -36,6 +43,29 @@ class rmt_grid_desc(C.Structure):
         ("gravity", C.c_double * 3), ("precision", C.c_int), ("mg_rtol", C.c_double),
         ("mg_max_cycles", C.c_int), ("mg_fixed_cycles", C.c_int), ("mg_fixed_cycles_fe", C.c_int),
         ("cuda_stream", C.c_void_p),
+    ]
+
+
+class rmt_job_info(C.Structure):
+    _fields_ = [
+        ("state", C.c_int), ("status", C.c_int), ("steps_done", C.c_long), ("steps_total", C.c_long),
+        ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double), ("device_bytes", C.c_size_t),
+    ]
+
+
+class rmt_server_stats_t(C.Structure):
+    _fields_ = [
+        ("batched_steps", C.c_long), ("graph_captures", C.c_long), ("capture_s", C.c_double),
+        ("admit_s", C.c_double), ("retire_s", C.c_double), ("cell_steps", C.c_double),
+    ]
+
+
+class rmt_tune_result(C.Structure):
+    _fields_ = [
+        ("mac_pre", C.c_int), ("mac_post", C.c_int), ("mac_inner", C.c_int), ("mac_block", C.c_int),
+        ("mac_cycles", C.c_int), ("fe_pre", C.c_int), ("fe_post", C.c_int), ("fe_inner", C.c_int),
+        ("fe_block", C.c_int), ("fe_cycles", C.c_int), ("fe_omega", C.c_double), ("mac_ms", C.c_double),
+        ("fe_ms", C.c_double), ("trials", C.c_int),
     ]
 
 
@@ -88,8 +118,43 @@ def load(build: bool = True):
     L.rmt_destroy_grid.argtypes = [vp]
     L.rmt_last_error.argtypes = [vp]
     L.rmt_last_error.restype = C.c_char_p
+    L.rmt_grid_footprint.argtypes = [C.POINTER(rmt_grid_desc), C.c_int]
+    L.rmt_grid_footprint.restype = C.c_size_t
+    L.rmt_grid_device_bytes.argtypes = [vp]
+    L.rmt_grid_device_bytes.restype = C.c_size_t
+    L.rmt_batch_create.argtypes = [vp, C.POINTER(C.c_void_p)]
+    for f in ("rmt_batch_add", "rmt_batch_remove"):
+        getattr(L, f).argtypes = [vp, vp]
+    L.rmt_batch_step.argtypes = [vp, C.c_int]
+    for f in ("rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy"):
+        getattr(L, f).argtypes = [vp]
+    L.rmt_batch_last_error.argtypes = [vp]
+    L.rmt_batch_last_error.restype = C.c_char_p
+    L.rmt_server_create.argtypes = [C.c_size_t, vp, C.POINTER(C.c_void_p)]
+    L.rmt_server_set_option.argtypes = [vp, C.c_char_p, C.c_double]
+    L.rmt_server_submit.argtypes = [vp, C.POINTER(rmt_grid_desc), C.POINTER(rmt_solid_desc), C.c_int, C.c_long,
+                                    C.POINTER(C.c_int)]
+    L.rmt_server_poll.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rmt_server_job.argtypes = [vp, C.c_int, C.POINTER(rmt_job_info)]
+    L.rmt_server_job_grid.argtypes = [vp, C.c_int]
+    L.rmt_server_job_grid.restype = C.c_void_p
+    L.rmt_server_release.argtypes = [vp, C.c_int]
+    L.rmt_server_resident_bytes.argtypes = [vp]
+    L.rmt_server_resident_bytes.restype = C.c_size_t
+    for f in ("rmt_server_clock", "rmt_server_cell_steps"):
+        getattr(L, f).argtypes = [vp]
+        getattr(L, f).restype = C.c_double
+    L.rmt_server_destroy.argtypes = [vp]
+    L.rmt_server_last_error.argtypes = [vp]
+    L.rmt_server_last_error.restype = C.c_char_p
+    L.rmt_server_stats.argtypes = [vp, C.POINTER(rmt_server_stats_t)]
+    L.rmt_server_stats.restype = C.c_int
+    L.rmt_autotune.argtypes = [vp, C.c_double, C.POINTER(rmt_tune_result)]
     for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
-              "rmt_destroy_grid"):
+              "rmt_destroy_grid", "rmt_batch_create", "rmt_batch_add", "rmt_batch_remove", "rmt_batch_step",
+              "rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy", "rmt_server_create", "rmt_server_set_option",
+              "rmt_server_submit", "rmt_server_poll", "rmt_server_job", "rmt_server_release", "rmt_server_destroy",
+              "rmt_autotune"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -135,6 +200,11 @@ def make_solid_desc(s: dict) -> rmt_solid_desc:
     return o
 
 
+def footprint(scene: dict) -> int:
+    """Device bytes a grid of this scene requests (rmt_grid_footprint); 0 if invalid."""
+    return load().rmt_grid_footprint(C.byref(make_grid_desc(scene)), len(scene.get("solids", [])))
+
+
 class RMTError(RuntimeError):
     def __init__(self, call: str, status: int, msg: str):
         super().__init__(f"{call} failed with status {status}: {msg}")
@@ -166,9 +236,9 @@ class Grid:
             raise RMTError(call, rc, msg)
 
     def close(self):
-        if getattr(self, "_g", None) and self._g.value:
+        if getattr(self, "_g", None) and self._g.value and getattr(self, "_owned", True):
             self._L.rmt_destroy_grid(self._g)
-            self._g = C.c_void_p()
+        self._g = C.c_void_p()
 
     def __del__(self):
         self.close()
@@ -219,3 +289,135 @@ class Grid:
 
     def cycles(self):
         return self._L.rmt_last_cycles(self._g, 0), self._L.rmt_last_cycles(self._g, 1)
+
+    def autotune(self, rtol: float = 1e-6) -> dict:
+        """Picks and applies the multigrid schedule, cycle counts and block shapes (rmt_autotune)."""
+        r = rmt_tune_result()
+        self._check("rmt_autotune", self._L.rmt_autotune(self._g, float(rtol), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in rmt_tune_result._fields_}
+
+    def device_bytes(self) -> int:
+        return self._L.rmt_grid_device_bytes(self._g)
+
+    @classmethod
+    def _wrap(cls, handle: int, scene: dict | None = None):
+        """A non-owning Grid view of a handle owned elsewhere (a server job)."""
+        g = cls.__new__(cls)
+        g._L = load()
+        g.scene = scene or {}
+        g._g = C.c_void_p(handle)
+        g._owned = False
+        g.nsolids = len(g.scene.get("solids", []))
+        return g
+
+
+class Batch:
+    """Grids advanced together, one CUDA-graph launch per step (rmt_batch_*)."""
+
+    def __init__(self, stream: int = 0):
+        self._L = load()
+        self._b = C.c_void_p()
+        self._check("rmt_batch_create", self._L.rmt_batch_create(stream or None, C.byref(self._b)))
+        self.members = []
+
+    def _check(self, call: str, rc: int):
+        if rc != RMT_OK:
+            msg = self._L.rmt_batch_last_error(self._b).decode() if self._b else ""
+            raise RMTError(call, rc, msg)
+
+    def add(self, g: Grid):
+        self._check("rmt_batch_add", self._L.rmt_batch_add(self._b, g._g))
+        self.members.append(g)
+
+    def remove(self, g: Grid):
+        self._check("rmt_batch_remove", self._L.rmt_batch_remove(self._b, g._g))
+        self.members.remove(g)
+
+    def step(self, nsteps: int = 1):
+        self._check("rmt_batch_step", self._L.rmt_batch_step(self._b, nsteps))
+
+    def sync(self):
+        self._check("rmt_batch_sync", self._L.rmt_batch_sync(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            self._L.rmt_batch_destroy(self._b)
+            self._b = C.c_void_p()
+            self.members = []
+
+    def __del__(self):
+        self.close()
+
+
+class Server:
+    """Continuous-batching simulation server under a device-memory budget (rmt_server_*)."""
+
+    def __init__(self, budget_bytes: int, stream: int = 0, options: dict | None = None):
+        self._L = load()
+        self._s = C.c_void_p()
+        rc = self._L.rmt_server_create(int(budget_bytes), stream or None, C.byref(self._s))
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_create", rc, "")
+        for k, v in (options or {}).items():
+            self._L.rmt_server_set_option(self._s, k.encode(), float(v))
+        self.scenes = {}
+
+    def submit(self, scene: dict, nsteps: int) -> int:
+        sol = scene.get("solids", [])
+        arr = (rmt_solid_desc * max(len(sol), 1))(*[make_solid_desc(s) for s in sol])
+        jid = C.c_int()
+        rc = self._L.rmt_server_submit(self._s, C.byref(make_grid_desc(scene)), arr, len(sol), int(nsteps),
+                                       C.byref(jid))
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_submit", rc, "job rejected")
+        self.scenes[jid.value] = scene
+        return jid.value
+
+    def poll(self):
+        """One scheduling round; returns (running, queued)."""
+        r, q = C.c_int(), C.c_int()
+        rc = self._L.rmt_server_poll(self._s, C.byref(r), C.byref(q))
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_poll", rc, self._L.rmt_server_last_error(self._s).decode())
+        return r.value, q.value
+
+    def job(self, jid: int) -> dict:
+        info = rmt_job_info()
+        rc = self._L.rmt_server_job(self._s, jid, C.byref(info))
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_job", rc, "unknown job")
+        return {k: getattr(info, k) for k, _ in rmt_job_info._fields_}
+
+    def grid(self, jid: int) -> Grid:
+        h = self._L.rmt_server_job_grid(self._s, jid)
+        if not h:
+            raise RMTError("rmt_server_job_grid", RMT_EINVAL, "no grid for this job")
+        return Grid._wrap(h, self.scenes.get(jid))
+
+    def release(self, jid: int):
+        rc = self._L.rmt_server_release(self._s, jid)
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_release", rc, "")
+        self.scenes.pop(jid, None)
+
+    def resident_bytes(self) -> int:
+        return self._L.rmt_server_resident_bytes(self._s)
+
+    def clock(self) -> float:
+        return self._L.rmt_server_clock(self._s)
+
+    def cell_steps(self) -> float:
+        return self._L.rmt_server_cell_steps(self._s)
+
+    def stats(self) -> dict:
+        st = rmt_server_stats_t()
+        self._L.rmt_server_stats(self._s, C.byref(st))
+        return {k: getattr(st, k) for k, _ in rmt_server_stats_t._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            self._L.rmt_server_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __del__(self):
+        self.close()

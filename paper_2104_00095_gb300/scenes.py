@@ -141,8 +141,17 @@ def batched(nsims: int = 64, steps: int = 100, seed: int = 1004, sizes=(32, 48, 
         s = _box(n, periodic=False, lid=1.0)
         s.update(mu=0.01, steps=steps, precision=precision)
         nb = int(rng.integers(1, 7))
-        radii = rng.uniform(0.08, 0.2, size=nb)
-        centers = _place(rng, [r + 1.5 / n for r in radii], n, False, 0, s["band_layers"])
+        # rejection: non-overlapping spheres (blur width apart) one cell inside the walls; a
+        # draw of radii that cannot be placed is drawn again
+        for _attempt in range(100):
+            radii = rng.uniform(0.08, 0.2, size=nb)
+            try:
+                centers = _place(rng, [r + 1.5 / n for r in radii], n, False, 0, 0, tries=2000)
+                break
+            except RuntimeError:
+                continue
+        else:
+            raise RuntimeError("batched scene: no placement found")
         for b in range(nb):
             s["solids"].append(solid(SPHERE, centers[b], (radii[b],) * 3, rho_s=rng.uniform(0.5, 1.5),
                                      G=rng.uniform(0.05, 1.0), mu_a=0.01))

@@ -167,7 +167,7 @@ def test_full_size_properties(cfg):
     if cfg == "swimmers256_fp32":
         sc = S.swimmers(n=256, steps=1)
         # the launch configuration bench.py times
-        sc.update(mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options={"fe_inner": 2})
+        sc.update(mg_fixed_cycles=4, mg_fixed_cycles_fe=4, options={"fe_inner": 2, "mac_warm": 1, "graph": 1})
         xtol = 1e-6  # FP32 fits of an affine map: a few units in the last place of x ~ O(1)
     else:
         sc = S.settling(n=128, steps=1)
@@ -202,3 +202,23 @@ def test_full_size_properties(cfg):
     assert np.max(np.abs(div)) <= (1e-4 if sc["precision"] == "fp32" else 1e-9) * max(scale, 1e-30)
     for f in (rmt.RMT_F_U, rmt.RMT_F_P, rmt.RMT_F_RHO):
         assert np.all(np.isfinite(g.read(f)))
+
+
+@pytest.mark.parametrize("n,prec", [(44, "fp64"), (112, "fp32")])
+def test_uneven_multigrid_hierarchies(n, prec):
+    """Periodic sizes whose coarsening stops early: 44 -> 22 (the coarsest level of the FP64
+    path does not fit in shared memory) and 112 -> 14 (a large shared-memory coarse level)."""
+    sc = S.swimmers(n=n, nbodies=1, seed=21, precision=prec)
+    g = rmt.Grid(sc)
+    if prec == "fp64":
+        o = O.Oracle(sc)
+        g.step(1)
+        assert o.step(1) == 0
+        compare_state(g, o, 1, TOL64, tag=f"n={n}")
+    else:
+        g.step(2)
+        um = [g.read(f) for f in (rmt.RMT_F_UMAC_X, rmt.RMT_F_UMAC_Y, rmt.RMT_F_UMAC_Z)]
+        div = (np.diff(um[0].reshape(n, n, n + 1), axis=2) + np.diff(um[1].reshape(n, n + 1, n), axis=1) +
+               np.diff(um[2].reshape(n + 1, n, n), axis=0)) * n
+        assert np.max(np.abs(div)) <= 1e-4 * max(np.abs(u).max() for u in um) * n
+        assert np.all(np.isfinite(g.read(rmt.RMT_F_U)))
