@@ -133,6 +133,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def dram_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/dram_traffic.txt),
+    or None when there is no record or the kernel's source file changed since it was taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    for name, nbytes, src, sha in lines:
+        if name != kernel:
+            continue
+        try:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest()[:len(sha)] != sha:
+                    return None
+        except OSError:
+            return None
+        return float(nbytes)
+    return None
+
+
 def cpu_oracle_rate(cfg: dict, steps: int, warmup: int):
     """cell-updates/s of the FP64 oracle on the CPU_SAMPLE_N^3 copy of the scene (single thread)."""
     import oracle as O
@@ -428,7 +451,8 @@ def main():
         per = tot / nl
         ach = byt / (per / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                    "frac": ach / peak, "peak_source": peak_kind,
+                    "traffic": dram_traffic(name) if args.n is None and args.nbodies is None else None,
                     "bytes_per_launch": byt, "launches": nl, "avg_launch_ms": per,
                     "share_of_step": tot / prof_ms, "profiled_ms_per_step": prof_ms / args.steps}
     stages = {p[0]: round(p[1] / args.steps, 4) for p in prof if p[1] > 0}
