@@ -466,6 +466,198 @@ __global__ void __launch_bounds__(BX* BYMAX) k_jacobi(Lv L, T w, const T* __rest
   xo[u] = dg > T(0) ? xi[u] + w * (b[u] - ax) / dg : xi[u];
 }
 
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes; size 0 fills zeros), so that
+// several planes of a stencil tile are in flight while one is computed.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// 27-point FE sweeps on a plane-marching tile: a block owns FX x FY nodes of every plane of a
+// z-chunk and keeps a ring of RING planes of x and of beta (with a one-point halo) in shared
+// memory, and each thread a register window of its column (below); the next planes arrive by
+// cp.async while one is computed.
+// Each value is read from global memory about once instead of up to 27 times.  Cells outside a
+// wall carry beta = 0, which makes the stencil uniform (the clamped x of an outside node always
+// meets a zero weight).  MODE 0: weighted Jacobi, out = x + w (b - K x) / diag (x where
+// diag = 0); MODE 1: residual, out = b - K x.
+constexpr int FX = 32, FY = 8, FZ = 32, RING = 5;
+constexpr int XH = (FX + 2) * (FY + 2) - FX * FY;  // halo nodes of an x plane (84)
+constexpr int BH = (FX + 1) * (FY + 1) - FX * FY;  // halo cells of a beta plane (41)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restrict__ x, T* __restrict__ out,
+                                                    const T* __restrict__ b, const T* __restrict__ beta) {
+  __shared__ __align__(16) T xs[RING][FY + 2][FX + 2];
+  __shared__ __align__(16) T bs[RING][FY + 1][FX + 1];
+  __shared__ __align__(16) T rs[RING][FY][FX];  // right-hand side b of the tile's nodes
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * FX + tx;
+  const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY;
+  const int k0 = blockIdx.z * FZ, k1 = min(k0 + FZ, L.nn[2]);
+  const long sy = L.nn[0], sz = (long)L.nn[0] * L.nn[1];
+  const long cy = L.n[0], cz = (long)L.n[0] * L.n[1];
+  // this thread's elements of a plane: its own node (tx+1, ty+1) and, for the first XH threads,
+  // one halo node; likewise its own cell (i0+tx, j0+ty) and one halo cell for the first BH
+  int hxa = 0, hxc = 0, hba = 0, hbc = 0;
+  if (t < XH) {
+    // halo ring of the (FX+2) x (FY+2) plane: row 0, row FY+1, then columns 0 and FX+1
+    if (t < FX + 2) {
+      hxa = t;
+      hxc = 0;
+    } else if (t < 2 * (FX + 2)) {
+      hxa = t - (FX + 2);
+      hxc = FY + 1;
+    } else {
+      const int r = t - 2 * (FX + 2);
+      hxa = (r & 1) ? FX + 1 : 0;
+      hxc = 1 + (r >> 1);
+    }
+  }
+  if (t < BH) {
+    // row 0 of the (FX+1) x (FY+1) cell plane, then column 0
+    if (t < FX + 1) {
+      hba = t;
+      hbc = 0;
+    } else {
+      hba = 0;
+      hbc = t - FX;
+    }
+  }
+  const long xo_own = nnb(L, 0, i0 + tx) + nnb(L, 1, j0 + ty) * sy;
+  const long xo_halo = nnb(L, 0, i0 - 1 + hxa) + nnb(L, 1, j0 - 1 + hxc) * sy;
+  const int ci_own = cnb(L, 0, i0 + tx), cj_own = cnb(L, 1, j0 + ty);
+  const int ci_halo = cnb(L, 0, i0 - 1 + hba), cj_halo = cnb(L, 1, j0 - 1 + hbc);
+  const bool b_own_ok = ci_own >= 0 && cj_own >= 0, b_halo_ok = ci_halo >= 0 && cj_halo >= 0;
+  const long bo_own = b_own_ok ? ci_own + cj_own * cy : 0, bo_halo = b_halo_ok ? ci_halo + cj_halo * cy : 0;
+  // x plane p lives in ring slot (p - k0 + 1) % RING, beta cell plane c in (c - k0 + 1) % RING
+  auto issue_x = [&](int p) {  // x plane p with its halo, and b of the tile's nodes on it
+    const int slot = (p - k0 + 1 + RING) % RING;
+    const long base = nnb(L, 2, p) * sz;
+    cp_async_elem(&xs[slot][ty + 1][tx + 1], x + xo_own + base, true);
+    if (t < XH) cp_async_elem(&xs[slot][hxc][hxa], x + xo_halo + base, true);
+    cp_async_elem(&rs[slot][ty][tx], b + xo_own + base, true);
+  };
+  auto issue_b = [&](int c) {
+    const int slot = (c - k0 + 1 + RING) % RING;
+    const int ck = cnb(L, 2, c);
+    const long base = ck >= 0 ? ck * cz : 0;
+    cp_async_elem(&bs[slot][ty + 1][tx + 1], beta + bo_own + base, b_own_ok && ck >= 0);
+    if (t < BH) cp_async_elem(&bs[slot][hbc][hba], beta + bo_halo + base, b_halo_ok && ck >= 0);
+  };
+  // group 0: x planes k0-1 .. k0+1, cell planes k0-1, k0; then one group per further plane
+  issue_x(k0 - 1);
+  issue_x(k0);
+  issue_x(k0 + 1);
+  issue_b(k0 - 1);
+  issue_b(k0);
+  cp_async_commit();
+  issue_x(k0 + 2);
+  issue_b(k0 + 1);
+  cp_async_commit();
+  issue_x(k0 + 3);
+  issue_b(k0 + 2);
+  cp_async_commit();
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < L.nn[0] && j < L.nn[1];
+  const T s12 = cv<T>(L.s12, L.f_s12);
+  // Register window of the thread's column: three x planes (i-1..i+1, j-1..j+1) and two beta
+  // cell planes (the cells around the node below / above it).  The window moves up one plane
+  // per iteration by reading only the new plane from shared memory (shared-memory bandwidth,
+  // not DRAM, is the next limit of this kernel); the loop is unrolled so that the arrays change
+  // roles instead of being copied.
+  T Xa[3][3], Xb[3][3], Xc[3][3], Ba[2][2], Bb[2][2];
+  auto rd_x = [&](T (&P)[3][3], int slot) {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) P[c][a] = xs[slot][ty + c][tx + a];
+  };
+  auto rd_b = [&](T (&P)[2][2], int slot) {
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+#pragma unroll
+      for (int a = 0; a < 2; a++) P[c][a] = bs[slot][ty + c][tx + a];
+  };
+  const long ubase = (long)i + (long)j * sy;
+  int k = k0;
+  int sxp = 2, sbc = 1;  // ring slots of x plane k+1 and of cell plane k
+  // one plane: M, C, P = x planes k-1, k, k+1 (P is filled here), Bl, Bu = cell planes k-1, k
+  // (Bu is filled here)
+  auto plane = [&](T (&M)[3][3], T (&C)[3][3], T (&P)[3][3], T (&Bl)[2][2], T (&Bu)[2][2]) {
+    cp_async_wait<2>();  // x plane k+1 and cell plane k have landed (two newer groups may fly)
+    __syncthreads();     // ... for every thread; the slots refilled below were last read at
+                         // least one iteration ago, before this barrier
+    rd_x(P, sxp);
+    rd_b(Bu, sbc);
+    const T bcur = rs[sxp == 0 ? RING - 1 : sxp - 1][ty][tx];  // b of plane k (slot before k+1)
+    issue_x(k + 4);
+    issue_b(k + 3);
+    cp_async_commit();
+    sxp = sxp + 1 == RING ? 0 : sxp + 1;
+    sbc = sbc + 1 == RING ? 0 : sbc + 1;
+    if (own) {
+      const T bsum = (Bl[0][0] + Bl[0][1]) + (Bl[1][0] + Bl[1][1]) + ((Bu[0][0] + Bu[0][1]) + (Bu[1][0] + Bu[1][1]));
+      T acc = T(0);
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+        for (int qx = 0; qx < 2; qx++) acc += Bl[qy][qx] * M[2 * qy][2 * qx];
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+        for (int qx = 0; qx < 2; qx++) acc += Bu[qy][qx] * P[2 * qy][2 * qx];
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+        for (int qx = 0; qx < 2; qx++) acc += (Bl[qy][qx] + Bu[qy][qx]) * C[2 * qy][2 * qx];
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++) acc += (Bl[0][qx] + Bl[1][qx]) * M[1][2 * qx];
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++) acc += (Bu[0][qx] + Bu[1][qx]) * P[1][2 * qx];
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++) acc += (Bl[qy][0] + Bl[qy][1]) * M[2 * qy][1];
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++) acc += (Bu[qy][0] + Bu[qy][1]) * P[2 * qy][1];
+      const T xc = C[1][1];
+      const T diag = T(4) * bsum * s12;
+      const T ax = (T(4) * bsum * xc - acc) * s12;
+      const long u = ubase + (long)k * sz;
+      if constexpr (MODE == 0)
+        out[u] = diag > T(0) ? xc + w * (bcur - ax) / diag : xc;
+      else
+        out[u] = bcur - ax;
+    }
+    k++;
+  };
+  // planes k0-1, k0 and cell plane k0-1 start the window
+  cp_async_wait<2>();
+  __syncthreads();
+  rd_x(Xa, 0);
+  rd_x(Xb, 1);
+  rd_b(Ba, 0);
+  while (k < k1) {
+    plane(Xa, Xb, Xc, Ba, Bb);
+    if (k >= k1) break;
+    plane(Xb, Xc, Xa, Bb, Ba);
+    if (k >= k1) break;
+    plane(Xc, Xa, Xb, Ba, Bb);
+    if (k >= k1) break;
+    plane(Xa, Xb, Xc, Bb, Ba);
+    if (k >= k1) break;
+    plane(Xb, Xc, Xa, Ba, Bb);
+    if (k >= k1) break;
+    plane(Xc, Xa, Xb, Bb, Ba);
+  }
+  cp_async_wait<0>();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BX* BYMAX) k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b,
                                                    const T* __restrict__ rho, T* __restrict__ r) {
@@ -977,6 +1169,10 @@ void sum_ff(MGSolver* m, const float* h, const float* l, long n, double scale, d
   rmt_count_launches(1);
 }
 
+inline dim3 fe_grid(const Lv& L) {
+  return dim3((L.nn[0] + FX - 1) / FX, (L.nn[1] + FY - 1) / FY, (L.nn[2] + FZ - 1) / FZ);
+}
+
 template <typename T>
 void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   const Lv& L = m->lv[l];
@@ -994,8 +1190,7 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
       }
     } else {
       hk(m, l, 0, 1, s);
-      k_jacobi<T><<<grid3(L.nn[0], L.nn[1], L.nn[2], m->by), dim3(BX, m->by), 0, s>>>(L, T(m->omega), (const T*)m->x[l],
-                                                                              (T*)m->xt[l], b, rho);
+      k_fe_tile<T, 0><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(m->omega), (const T*)m->x[l], (T*)m->xt[l], b, rho);
       rmt_count_launches(1);
       hk(m, l, 0, 0, s);
       void* t = m->x[l];
@@ -1025,8 +1220,12 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
   const int ex = m->kind == 0 ? L.n[0] : L.nn[0], ey = m->kind == 0 ? L.n[1] : L.nn[1],
             ez = m->kind == 0 ? L.n[2] : L.nn[2];
   smooth<T>(m, l, m->pre, true, s);
-  k_resid<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
-                                                        (const T*)m->rho[l], (T*)m->r[l]);
+  if (m->kind == 0)
+    k_resid<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
+                                                                    (const T*)m->rho[l], (T*)m->r[l]);
+  else
+    k_fe_tile<T, 1><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
+                                                       (const T*)m->rho[l]);
   rmt_count_launches(1);
   const Lv& C = m->lv[l + 1];
   const int cx = m->kind == 0 ? C.n[0] : C.nn[0], cy = m->kind == 0 ? C.n[1] : C.nn[1],
