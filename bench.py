@@ -209,7 +209,8 @@ def plain_fp64_leg(cfg: dict, args, stream) -> dict:
 
     sc = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     sc.update(precision="fp64", mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe,
-              options={"fe_inner": args.fe_inner, "mac_warm": args.mac_warm, "graph": args.graph})
+              options={"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
+                       "graph": args.graph})
     g = rmt.Grid(sc, stream=stream.cuda_stream)
     g.step(3)
     k = max(3, args.steps // 2)
@@ -293,7 +294,7 @@ def serving_leg(args, stream) -> dict:
     for _, sc in jobs:
         sc.update(mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe)
     srv = rmt.Server(80 * 10**9, stream=stream.cuda_stream,
-                     options={"fe_inner": args.fe_inner, "mac_warm": args.mac_warm})
+                     options={"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm})
     t_start = time.perf_counter()
     pending = list(jobs)
     ids = []
@@ -353,14 +354,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
-    ap.add_argument("--mg-cycles-mac", type=int, default=4,
-                    help="V-cycles per MAC solve (fixed, no host sync; warm-started, 4 hold the 1e-6 relative "
-                         "residual that the adaptive solve needs in steady state)")
+    ap.add_argument("--mg-cycles-mac", type=int, default=5,
+                    help="V-cycles per MAC solve (fixed, no host sync; 5 reach the 1e-6 relative residual)")
     ap.add_argument("--mg-cycles-fe", type=int, default=4,
                     help="V-cycles per FE solve (fixed; 4 reach 1e-6 relative residual)")
+    ap.add_argument("--mac-inner", type=int, default=5,
+                    help="MAC V-cycles per high-precision residual (5: one residual, the first, per solve)")
     ap.add_argument("--fe-inner", type=int, default=2,
                     help="FE V-cycles per high-precision residual (mixed-precision refinement)")
-    ap.add_argument("--mac-warm", type=int, default=1, help="warm-start the MAC solve from the last step")
+    ap.add_argument("--mac-warm", type=int, default=0, help="warm-start the MAC solve from the last step")
     ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
@@ -401,7 +403,8 @@ def main():
     scene = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
-    scene["options"] = {"fe_inner": args.fe_inner, "mac_warm": args.mac_warm, "graph": args.graph}
+    scene["options"] = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
+                        "graph": args.graph}
     g = rmt.Grid(scene, stream=stream.cuda_stream)
     N = int(np.prod(scene["n"]))
     for _ in range(args.warmup):
@@ -504,7 +507,8 @@ def main():
                            "description": cfg["desc"], "grid": list(scene["n"]),
                            "bodies": len(scene["solids"]),
                            "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
-                                                   "fe_inner": args.fe_inner, "mac_warm_start": bool(args.mac_warm)},
+                                                   "mac_inner": args.mac_inner, "fe_inner": args.fe_inner,
+                                                   "mac_warm_start": bool(args.mac_warm)},
                            "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},

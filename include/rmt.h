@@ -135,7 +135,7 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
  * is not described).  On the right-hand sides of the grid's last step (RMT_ESTATE before the
  * first step) it tries, per solver, smoother sweeps before/after the coarse correction (1..4
  * for the 7-point solve, 1..3 for the nodal one), the Jacobi weight of the nodal smoother (0.8,
- * 0.9, 1.0) and 1 or 2 V-cycles per high-precision residual: for each, it counts the V-cycles
+ * 0.9, 1.0) and 1, 2 or 4 V-cycles per high-precision residual: for each, it counts the V-cycles
  * needed to reach the relative residual rtol and times that many with CUDA events.  It then
  * times the block height of the level kernels (1, 2, 4, 8 rows of 32 threads) for the fastest
  * schedule.  The winners are applied with rmt_set_option, including the cycle counts

@@ -258,6 +258,17 @@ __device__ __forceinline__ F2 mac_op_ff(const Lv& L, const float* __restrict__ x
   const long c = cix(L, i, j, k);
   const float rc = rho[c], ch = xh[c], cl = xl[c];
   float sh = 0.0f, sl = 0.0f;
+  if (i > 0 && i + 1 < L.n[0] && j > 0 && j + 1 < L.n[1] && k > 0 && k + 1 < L.n[2]) {
+    // interior: six neighbours at fixed offsets (2/(ra+rb) = 2 x the correctly rounded
+    // reciprocal, the same float as the division)
+    const int st[3] = {1, L.n[0], L.n[0] * L.n[1]};
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+      const long cn = c + ((f & 1) ? st[f >> 1] : -st[f >> 1]);
+      acc_wdiff(2.0f * __frcp_rn(rc + rho[cn]), ch, cl, xh[cn], xl[cn], sh, sl);
+    }
+    return ff_mul(sh, sl, L.f_ih2, L.f_ih2_lo);
+  }
   const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
 #pragma unroll
   for (int f = 0; f < 6; f++) {
@@ -267,7 +278,7 @@ __device__ __forceinline__ F2 mac_op_ff(const Lv& L, const float* __restrict__ x
     int q[3] = {i, j, k};
     q[d] = v;
     const long cn = cix(L, q[0], q[1], q[2]);
-    acc_wdiff(face_beta<false>(rc, rho[cn]), ch, cl, xh[cn], xl[cn], sh, sl);
+    acc_wdiff(2.0f * __frcp_rn(rc + rho[cn]), ch, cl, xh[cn], xl[cn], sh, sl);
   }
   return ff_mul(sh, sl, L.f_ih2, L.f_ih2_lo);
 }

@@ -1,10 +1,10 @@
 // Autotuner of the two multigrid solves (smoother schedule, cycle count, kernel block shape).
 //
 // For each solver it tries the smoother schedules of a small grid (sweeps before / after the
-// coarse correction, Jacobi weight for the nodal solve, V-cycles per high-precision residual)
-// on the right-hand side of the grid's last step: it counts the V-cycles a schedule needs to
-// reach the requested relative residual, times that many cycles with CUDA events, and keeps
-// the fastest.  Then it times the block heights of the level kernels with that schedule.  The
+// coarse correction, Jacobi weight for the nodal solve, 1, 2 or 4 V-cycles per high-precision
+// residual) on the right-hand side of the grid's last step: it counts the V-cycles a schedule
+// needs to reach the requested relative residual, times that many cycles with CUDA events, and
+// keeps the fastest.  Then it times the block heights of the level kernels with that schedule.  The
 // winner becomes the grid's fixed-cycle configuration (rmt_set_option), so later steps take no
 // host synchronisation.
 #include <cstdio>
@@ -52,7 +52,7 @@ int tune_one(MGSolver* m, int kind, double rtol, cudaStream_t s, cudaEvent_t a, 
   for (int pre = 1; pre <= nsw; pre++)
     for (int post = 1; post <= nsw; post++)
       for (int io = 0; io < nom; io++)
-        for (int inner = 1; inner <= 2; inner++) {
+        for (int inner : {1, 2, 4}) {
           const Sched c{pre, post, inner, 4, kind == 0 ? 1.0 : omegas_fe[io]};
           apply(m, c);
           cudaError_t e = cudaSuccess;

@@ -167,7 +167,7 @@ def test_full_size_properties(cfg):
     if cfg == "swimmers256_fp32":
         sc = S.swimmers(n=256, steps=1)
         # the launch configuration bench.py times
-        sc.update(mg_fixed_cycles=4, mg_fixed_cycles_fe=4, options={"fe_inner": 2, "mac_warm": 1, "graph": 1})
+        sc.update(mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options={"fe_inner": 2, "mac_inner": 5, "graph": 1})
         xtol = 1e-6  # FP32 fits of an affine map: a few units in the last place of x ~ O(1)
     else:
         sc = S.settling(n=128, steps=1)
@@ -222,3 +222,19 @@ def test_uneven_multigrid_hierarchies(n, prec):
                np.diff(um[2].reshape(n + 1, n, n), axis=0)) * n
         assert np.max(np.abs(div)) <= 1e-4 * max(np.abs(u).max() for u in um) * n
         assert np.all(np.isfinite(g.read(rmt.RMT_F_U)))
+
+
+def test_bench_cycle_counts_stay_close_to_the_converged_solve():
+    """The fixed-cycle configuration that bench.py times (5 MAC cycles after one two-float
+    residual, 4 FE cycles with a residual after every 2) against adaptive solves to 1e-9, on the
+    same FP32 swimmer scene over 6 steps."""
+    def run(**kw):
+        sc = S.swimmers(n=64, nbodies=2, seed=13, precision="fp32")
+        sc.update(kw)
+        g = rmt.Grid(sc)
+        g.step(6)
+        return g.read(rmt.RMT_F_U), g.read(rmt.RMT_F_P)
+    u_ref, p_ref = run(mg_rtol=1e-9, mg_max_cycles=60, options={"fe_inner": 2})
+    u, p = run(mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options={"fe_inner": 2, "mac_inner": 5, "graph": 1})
+    assert rel_l2(u, u_ref) <= 1e-5
+    assert rel_l2(p - p.mean(), p_ref - p_ref.mean()) <= 1e-5
