@@ -383,17 +383,14 @@ __device__ __forceinline__ void stage_boxes(const int* __restrict__ bbs, int str
     sbb[q] = bbs[(q / 6) * stride + q % 6];
   __syncthreads();
 }
+__device__ __forceinline__ bool in_box_axis(int v, int lo, int hi, int per, int n) {
+  int t = v - lo;
+  if (per && t < 0) t += n;
+  return lo <= hi && t >= 0 && t <= hi - lo;
+}
 __device__ __forceinline__ bool in_box(const Geo& g, const int* bb, int i, int j, int k) {
-  const int c[3] = {i, j, k};
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    const int lo = bb[d], hi = bb[3 + d];
-    if (lo > hi) return false;
-    int t = c[d] - lo;
-    if (g.per[d] && t < 0) t += g.n[d];
-    if (t < 0 || t > hi - lo) return false;
-  }
-  return true;
+  return in_box_axis(i, bb[0], bb[3], g.per[0], g.n[0]) && in_box_axis(j, bb[1], bb[4], g.per[1], g.n[1]) &&
+         in_box_axis(k, bb[2], bb[5], g.per[2], g.n[2]);
 }
 
 // grid-stride helper

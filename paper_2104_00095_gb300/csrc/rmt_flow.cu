@@ -72,8 +72,8 @@ __device__ __forceinline__ bool is_wall_face(const Geo& g, int d, int f) {
 }
 
 // transverse bar states at every e-face (SI "Tangential derivatives")
-template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, int e, const T* __restrict__ u, Slopes9 S,
+template <typename T, int e>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, const T* __restrict__ u, Slopes9 S,
                                                          T* __restrict__ ub0, T* __restrict__ ub1, T* __restrict__ ub2,
                                                          T* __restrict__ vadv) {
   const int ex = g.n[0] + (e == 0), ey = g.n[1] + (e == 1), ez = g.n[2] + (e == 2);
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_cellw(Geo g, const T* __rest
 }
 
 // normal-face states of the velocity and the Godunov choice (SI "Godunov-type upwinding")
-template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, int d, const T* __restrict__ u, Slopes9 S, Slopes9 W,
+template <typename T, int d>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, const T* __restrict__ u, Slopes9 S, Slopes9 W,
                                                           BarPtrs bp) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1), ez = g.n[2] + (d == 2);
   const T h = cv<T>(g.h, g.f.h), dt = cv<T>(g.dt, g.f.dt);
@@ -252,8 +252,8 @@ __global__ void k_mac_rhs(Geo g, FacePtrs3 un, MGVec b) {
   }
 }
 
-template <typename T>
-__global__ void k_mac_correct(Geo g, int d, const T* __restrict__ un, const T* __restrict__ rho, MGVec q,
+template <typename T, int d>
+__global__ void k_mac_correct(Geo g, const T* __restrict__ un, const T* __restrict__ rho, MGVec q,
                               T* __restrict__ umac) {
   const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
   const T fac = cv<T>(g.hdt_h, g.f.hdt_h);
@@ -461,7 +461,10 @@ void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ub
   rmt_count_launches(1);
   for (int e = 0; e < 3; e++) {
     const dim3 gr((g.n[0] + (e == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (e == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (e == 2));
-    k_bar<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, e, u, S, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]);
+    // the direction is a template argument: a runtime index into the pointer bundles would
+    // copy them to local memory in every thread
+    auto kb = e == 0 ? k_bar<T, 0> : (e == 1 ? k_bar<T, 1> : k_bar<T, 2>);
+    kb<<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, S, ubar[e][0], ubar[e][1], ubar[e][2], vadv[e]);
     rmt_count_launches(1);
   }
 }
@@ -484,7 +487,8 @@ void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, cons
   for (int d = 0; d < 3; d++) {
     for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
     const dim3 gr((g.n[0] + (d == 0) + TILE_X - 1) / TILE_X, (g.n[1] + (d == 1) + TILE_Y - 1) / TILE_Y, g.n[2] + (d == 2));
-    k_face<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, d, u, S, W, bp);
+    auto kf = d == 0 ? k_face<T, 0> : (d == 1 ? k_face<T, 1> : k_face<T, 2>);
+    kf<<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, S, W, bp);
     rmt_count_launches(1);
   }
 }
@@ -499,7 +503,8 @@ template <typename T>
 void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, MGVec q, T* const umac[3],
                         cudaStream_t s) {
   for (int d = 0; d < 3; d++) {
-    k_mac_correct<T><<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, d, uf[d][d], rho, q, umac[d]);
+    auto kc = d == 0 ? k_mac_correct<T, 0> : (d == 1 ? k_mac_correct<T, 1> : k_mac_correct<T, 2>);
+    kc<<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, uf[d][d], rho, q, umac[d]);
     rmt_count_launches(1);
   }
 }
