@@ -388,9 +388,45 @@ __device__ __forceinline__ bool in_box_axis(int v, int lo, int hi, int per, int 
   if (per && t < 0) t += n;
   return lo <= hi && t >= 0 && t <= hi - lo;
 }
+// does the cell range [a, b] of axis d (0 <= a <= b < n) meet the box's range on that axis?
+__device__ __forceinline__ bool tile_meets_box(const Geo& g, const int* bb, int d, int a, int b) {
+  const int lo = bb[d], hi = bb[3 + d];
+  if (lo > hi) return false;
+  if (!g.per[d]) return lo <= b && hi >= a;
+  const int n = g.n[d];
+  if (hi - lo + 1 >= n) return true;
+  // the box starts inside the range, or the range starts inside the box
+  int s = lo % n;
+  if (s < 0) s += n;
+  return (s >= a && s <= b) || in_box_axis(a, lo, hi, 1, n);
+}
 __device__ __forceinline__ bool in_box(const Geo& g, const int* bb, int i, int j, int k) {
   return in_box_axis(i, bb[0], bb[3], g.per[0], g.n[0]) && in_box_axis(j, bb[1], bb[4], g.per[1], g.n[1]) &&
          in_box_axis(k, bb[2], bb[5], g.per[2], g.n[2]);
+}
+
+// Bodies whose band box meets the block's tile (TILE_X x TILE_Y cells of plane blockIdx.z, the
+// THREAD_XYZ layout): only they need a per-cell test.  All threads of the block call it; warp 0
+// writes the mask to *slot.
+__device__ __forceinline__ unsigned long long tile_body_mask(const Geo& g, const int* sbb, int nb,
+                                                             unsigned long long* slot) {
+  if (threadIdx.y == 0) {
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y, kk = blockIdx.z;
+    const int i1 = min(i0 + TILE_X, g.n[0]) - 1, j1 = min(j0 + TILE_Y, g.n[1]) - 1;
+    unsigned long long mk = 0;
+    for (int base = 0; base < nb; base += 32) {
+      const int m = base + threadIdx.x;
+      bool hit = false;
+      if (m < nb) {
+        const int* b = sbb + 6 * m;
+        hit = tile_meets_box(g, b, 0, i0, i1) && tile_meets_box(g, b, 1, j0, j1) && tile_meets_box(g, b, 2, kk, kk);
+      }
+      mk |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << base;
+    }
+    if (threadIdx.x == 0) *slot = mk;
+  }
+  __syncthreads();
+  return *slot;
 }
 
 // grid-stride helper

@@ -315,25 +315,29 @@ __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
 // density by mixing (eq. mod_heaviside) and u*
 
 template <typename T>
-__global__ void k_density(Geo g, const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb,
-                          const int* __restrict__ bbs, int bstride, T* __restrict__ rho) {
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_density(Geo g, const Body* __restrict__ bodies,
+                                                             const BodyView<T>* __restrict__ views, int nb,
+                                                             const int* __restrict__ bbs, int bstride,
+                                                             T* __restrict__ rho) {
   __shared__ int sbb[6 * RMT_MAX_BODIES];
+  __shared__ unsigned long long tile_mask;
   stage_boxes(bbs, bstride, nb, sbb);
+  const unsigned long long tm = tile_body_mask(g, sbb, nb, &tile_mask);
   const T eps = cv<T>(g.eps, g.f.eps);
-  GRID_LOOP(c, g.N) {
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
-    T wsum = T(0), acc = T(0);
-    for (int m = 0; m < nb; m++) {
-      if (!in_box(g, sbb + 6 * m, i, j, k) || views[m].lay[c] < 0) continue;
-      const T w = T(1) - heavi(views[m].phi[c], eps);
-      acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
-      wsum += w;
-    }
-    const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
-    const T sc = wsum > T(1) ? T(1) / wsum : T(1);
-    rho[c] = Hf * cv<T>(g.rho_f, g.f.rho_f) + acc * sc;
+  THREAD_XYZ(i, j, k);
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const long c = cidx(g, i, j, k);
+  T wsum = T(0), acc = T(0);
+  for (unsigned long long r = tm; r; r &= r - 1) {
+    const int m = __ffsll((long long)r) - 1;
+    if (!in_box(g, sbb + 6 * m, i, j, k) || views[m].lay[c] < 0) continue;
+    const T w = T(1) - heavi(views[m].phi[c], eps);
+    acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
+    wsum += w;
   }
+  const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
+  const T sc = wsum > T(1) ? T(1) / wsum : T(1);
+  rho[c] = Hf * cv<T>(g.rho_f, g.f.rho_f) + acc * sc;
 }
 
 template <typename T>
@@ -520,7 +524,9 @@ void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cu
 template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
                     T* rho, cudaStream_t s) {
-  k_density<T><<<nblocks(g.N), TPB, 0, s>>>(g, bodies, views, nb, bbs, bstride, rho); rmt_count_launches(1);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  k_density<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, bodies, views, nb, bbs, bstride, rho);
+  rmt_count_launches(1);
 }
 template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h, T* ustar,

@@ -141,11 +141,17 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T*
                                                                   T* __restrict__ out, int* __restrict__ list,
                                                                   int* __restrict__ count) {
   __shared__ int sbb[6 * RMT_MAX_BODIES];
+  __shared__ unsigned long long tile_mask;
   stage_boxes(bbs, bstride, nb, sbb);
+  const unsigned long long tm = tile_body_mask(g, sbb, nb, &tile_mask);
   THREAD_XYZ(i, j, k);
   if (i >= g.n[0] || j >= g.n[1]) return;
   const long c = cidx(g, i, j, k);
-  const uint64_t bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+  uint64_t bm = 0;
+  for (unsigned long long r = tm; r; r &= r - 1) {
+    const int m = __ffsll((long long)r) - 1;
+    if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
+  }
   const unsigned act = __activemask();
   const unsigned want = __ballot_sync(act, bm != 0);
   if (bm != 0) {
