@@ -676,7 +676,9 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid(Lv L, int kind, const T* __
   int i, j, k;
   if (!thread_cell(ext, i, j, k)) return;
   T dg;
-  const T ax = kind == 0 ? mac_op<T>(L, x, rho, i, j, k, dg) : fe_op<T>(L, x, rho, i, j, k, dg);
+  // the V-cycle's operator: the smoother's coefficient (the high-precision residual outside the
+  // V-cycle uses the exactly rounded one)
+  const T ax = kind == 0 ? mac_op<T, true>(L, x, rho, i, j, k, dg) : fe_op<T>(L, x, rho, i, j, k, dg);
   const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
   r[u] = b[u] - ax;
 }
@@ -716,65 +718,91 @@ __global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, co
   xc[u] = T(0);
 }
 
-// trilinear prolongation of the coarse correction, added to the fine iterate
+// Trilinear prolongation of the coarse correction, added to the fine iterate; one thread per
+// coarse unknown writes its 2 x 2 x 2 fine children.
+// Cell-centred: along each axis a child takes 3/4 of its parent and 1/4 of the parent's
+// neighbour on the child's side (the parent itself beyond a wall: Neumann mirror), applied
+// axis by axis.
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_prolong(Lv F, Lv C, int kind, const T* __restrict__ xc,
-                                                     T* __restrict__ xf) {
-  const int ext[3] = {kind == 0 ? F.n[0] : F.nn[0], kind == 0 ? F.n[1] : F.nn[1], kind == 0 ? F.n[2] : F.nn[2]};
-  int i, j, k;
-  if (!thread_cell(ext, i, j, k)) return;
-  const int ff[3] = {i, j, k};
-  T v = T(0);
-  if (kind == 0) {
-    int own[3], oth[3];
-    T wo[3];
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
+  int I, J, K;
+  if (!thread_cell(C.n, I, J, K)) return;
+  int nx[3], ny[3], nz[3];  // coarse indices of I-1, I, I+1 (and for J, K)
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      own[d] = ff[d] >> 1;
-      int o = own[d] + ((ff[d] & 1) ? 1 : -1);
-      wo[d] = T(0.75);
-      if (o < 0 || o >= C.n[d]) {
-        if (C.per[d]) {
-          o = o < 0 ? o + C.n[d] : o - C.n[d];
-        } else {
-          o = own[d];
-          wo[d] = T(1);  // Neumann: the mirror value equals the boundary cell
-        }
-      }
-      oth[d] = o;
+  for (int q = 0; q < 3; q++) {
+    const int di = q - 1;
+    int a = I + di, b = J + di, c = K + di;
+    if (a < 0 || a >= C.n[0]) a = C.per[0] ? (a < 0 ? a + C.n[0] : a - C.n[0]) : I;
+    if (b < 0 || b >= C.n[1]) b = C.per[1] ? (b < 0 ? b + C.n[1] : b - C.n[1]) : J;
+    if (c < 0 || c >= C.n[2]) c = C.per[2] ? (c < 0 ? c + C.n[2] : c - C.n[2]) : K;
+    nx[q] = a;
+    ny[q] = b;
+    nz[q] = c;
+  }
+  const T w0 = T(0.75), w1 = T(0.25);
+  // along x: rx[z][y][child] for the 3 x 3 coarse rows around (J, K)
+  T rx[3][3][2];
+#pragma unroll
+  for (int qz = 0; qz < 3; qz++)
+#pragma unroll
+    for (int qy = 0; qy < 3; qy++) {
+      const long row = (long)C.n[0] * (ny[qy] + (long)C.n[1] * nz[qz]);
+      const T xm = xc[row + nx[0]], x0 = xc[row + nx[1]], xp = xc[row + nx[2]];
+      rx[qz][qy][0] = w0 * x0 + w1 * xm;
+      rx[qz][qy][1] = w0 * x0 + w1 * xp;
     }
+  const long sy = F.n[0], sz = (long)F.n[0] * F.n[1];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
-      const T w = (sx ? T(1) - wo[0] : wo[0]) * (sy ? T(1) - wo[1] : wo[1]) * (sz ? T(1) - wo[2] : wo[2]);
-      if (w == T(0)) continue;
-      v += w * xc[cix(C, sx ? oth[0] : own[0], sy ? oth[1] : own[1], sz ? oth[2] : own[2])];
-    }
-  } else {
-    int lo[3], hi[3];
-    T wl[3];
+  for (int cz = 0; cz < 2; cz++)
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      lo[d] = ff[d] >> 1;
-      if (ff[d] & 1) {
-        hi[d] = lo[d] + 1;
-        if (C.per[d] && hi[d] >= C.nn[d]) hi[d] -= C.nn[d];
-        wl[d] = T(0.5);
-      } else {
-        hi[d] = lo[d];
-        wl[d] = T(1);
+    for (int cy = 0; cy < 2; cy++) {
+      const long base = (long)(2 * I) + (long)(2 * J + cy) * sy + (long)(2 * K + cz) * sz;
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) {
+        // along y, then z
+        const T y0 = w0 * rx[1][1][cx] + w1 * rx[1][2 * cy][cx];
+        const T ym = w0 * rx[0][1][cx] + w1 * rx[0][2 * cy][cx];
+        const T yp = w0 * rx[2][1][cx] + w1 * rx[2][2 * cy][cx];
+        const T v = w0 * y0 + w1 * (cz ? yp : ym);
+        xf[base + cx] += v;
       }
     }
+}
+
+// Nodal: a fine node on a coarse node takes its value, one between two coarse nodes their mean
+// (per axis).
+template <typename T>
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong_fe(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
+  int I, J, K;
+  if (!thread_cell(C.nn, I, J, K)) return;
+  const int I1 = I + 1 < C.nn[0] ? I + 1 : (C.per[0] ? 0 : I);
+  const int J1 = J + 1 < C.nn[1] ? J + 1 : (C.per[1] ? 0 : J);
+  const int K1 = K + 1 < C.nn[2] ? K + 1 : (C.per[2] ? 0 : K);
+  const T c000 = xc[nix(C, I, J, K)], c100 = xc[nix(C, I1, J, K)], c010 = xc[nix(C, I, J1, K)],
+          c110 = xc[nix(C, I1, J1, K)], c001 = xc[nix(C, I, J, K1)], c101 = xc[nix(C, I1, J, K1)],
+          c011 = xc[nix(C, I, J1, K1)], c111 = xc[nix(C, I1, J1, K1)];
+  const T h = T(0.5);
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
-      const T w = (sx ? T(1) - wl[0] : wl[0]) * (sy ? T(1) - wl[1] : wl[1]) * (sz ? T(1) - wl[2] : wl[2]);
-      if (w == T(0)) continue;
-      v += w * xc[nix(C, sx ? hi[0] : lo[0], sy ? hi[1] : lo[1], sz ? hi[2] : lo[2])];
+  for (int cz = 0; cz < 2; cz++) {
+    const int fk = 2 * K + cz;
+    if (fk >= F.nn[2]) continue;
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++) {
+      const int fj = 2 * J + cy;
+      if (fj >= F.nn[1]) continue;
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) {
+        const int fi = 2 * I + cx;
+        if (fi >= F.nn[0]) continue;
+        // mean along each odd axis
+        T a0 = cx ? h * (c000 + c100) : c000, a1 = cx ? h * (c010 + c110) : c010;
+        T a2 = cx ? h * (c001 + c101) : c001, a3 = cx ? h * (c011 + c111) : c011;
+        T b0 = cy ? h * (a0 + a1) : a0, b1 = cy ? h * (a2 + a3) : a2;
+        const T v = cz ? h * (b0 + b1) : b0;
+        xf[nix(F, fi, fj, fk)] += v;
+      }
     }
   }
-  const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
-  xf[u] += v;
 }
 
 // FE coefficient beta = 1/rho per cell (finest level)
@@ -1245,7 +1273,12 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
                                                            (T*)m->x[l + 1]);
   rmt_count_launches(1);
   vcycle<T>(m, l + 1, s);
-  k_prolong<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, C, m->kind, (const T*)m->x[l + 1], (T*)m->x[l]);
+  if (m->kind == 0)
+    k_prolong_mac<T><<<grid3(C.n[0], C.n[1], C.n[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
+                                                                                      (T*)m->x[l]);
+  else
+    k_prolong_fe<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
+                                                                                        (T*)m->x[l]);
   rmt_count_launches(1);
   smooth<T>(m, l, m->post, false, s);
 }
