@@ -40,7 +40,7 @@ enum {
   P_USTAR, P_FE_SETUP, P_FE_SOLVE, P_FE_UPDATE, P_MAC_SMOOTH, P_MAC_RESID, P_FE_SMOOTH, P_FE_RESID, P_NUM
 };
 const char* const kProfNames[P_NUM] = {
-    "stress_n", "godunov_velocity", "mac_setup", "mac_solve", "mac_correct_advect", "xi_predict", "extrapolate",
+    "stress_n", "godunov_velocity", "mac_setup", "mac_solve", "mac_correct_advect", "xi_predict", "extrapolate_corrector",
     "corrector", "stress_half", "density_ustar", "fe_setup", "fe_solve", "fe_update_density",
     "k_rbgs(mac,level0,colour)", "k_resid64(mac)", "k_jacobi(fe,level0)", "k_resid64(fe)"};
 struct Prof {
@@ -77,6 +77,9 @@ struct rmt_grid {
   int* bb_all = nullptr;  // band boxes: body m, parity p at 12 m + 6 p
   int *slist = nullptr, *scount = nullptr;  // cells some band reaches (stress pass 2)
   double* t_d = nullptr;                      // simulated time (device copy of t)
+  std::vector<cudaStream_t> body_s;           // one stream per body (re-extrapolation, corrector)
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
   void* views_d = nullptr;  // BodyView<T>[2 parities][3 levels][nb]
   int par = 0;
   void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
@@ -399,6 +402,13 @@ rmt_status init_t(rmt_grid* g) {
   const int nb = (int)g->bodies.size();
   rmt_status st = alloc_t<T>(g);
   if (st != RMT_OK) return st;
+  CK(g, cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+  g->body_s.assign(nb, nullptr);
+  g->ev_join.assign(nb, nullptr);
+  for (int m = 0; m < nb; m++) {
+    CK(g, cudaStreamCreateWithFlags(&g->body_s[m], cudaStreamNonBlocking));
+    CK(g, cudaEventCreateWithFlags(&g->ev_join[m], cudaEventDisableTiming));
+  }
   // outside a body's band every per-body array reads "absent" (layer -1, NaN); the window
   // kernels rely on it, since they only ever touch the band's neighbourhood
   const T nanv = (T)NAN;
@@ -479,23 +489,32 @@ rmt_status step_t(rmt_grid* g) {
   // 4. advective term
   launch_advect<T>(G, uf, umac, (T*)g->adv, s);
   pe(g, P_MAC_CORR_ADV);
-  // 5.-7. predictor, re-extrapolation, corrector for every body
+  // 5. predictor of every body (they share the predictor's scratch, so one after another)
+  pb(g, P_XI_PRED);
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
-    const int* bbc = b.bb + 6 * cur;
-    pb(g, P_XI_PRED);
-    launch_xi_predict<T>(G, u, vadv, uf, umac, bbc, b.blocks, (const T*)b.X[cur], b.LAY[cur], (T* const*)g->xscr_s,
-                         (T* const*)g->xscr_b, g->xscr_ok, (T*)b.X[nxt], s);
-    pe(g, P_XI_PRED);
-    pb(g, P_EXTRAP);
-    launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[nxt],
-                          (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, s);
-    pe(g, P_EXTRAP);
-    pb(g, P_CORR);
-    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, WLS_BLOCKS, (const T*)b.X[cur], b.LAY[cur],
-                        (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, s);
-    pe(g, P_CORR);
+    launch_xi_predict<T>(G, u, vadv, uf, umac, b.bb + 6 * cur, b.blocks, (const T*)b.X[cur], b.LAY[cur],
+                         (T* const*)g->xscr_s, (T* const*)g->xscr_b, g->xscr_ok, (T*)b.X[nxt], s);
   }
+  pe(g, P_XI_PRED);
+  // 6.-7. re-extrapolation and corrector: the bodies are independent, so each runs on its own
+  // stream, forked from and joined back into the step's stream (parallel branches when the step
+  // is captured as a graph)
+  pb(g, P_EXTRAP);
+  if (nb > 0) CK(g, cudaEventRecord(g->ev_fork, s));
+  for (int m = 0; m < nb; m++) {
+    BodyMem& b = g->bm[m];
+    cudaStream_t bs = g->body_s[m];
+    CK(g, cudaStreamWaitEvent(bs, g->ev_fork, 0));
+    const int* bbc = b.bb + 6 * cur;
+    launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[nxt],
+                          (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, bs);
+    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, WLS_BLOCKS, (const T*)b.X[cur], b.LAY[cur],
+                        (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, bs);
+    CK(g, cudaEventRecord(g->ev_join[m], bs));
+  }
+  for (int m = 0; m < nb; m++) CK(g, cudaStreamWaitEvent(s, g->ev_join[m], 0));
+  pe(g, P_EXTRAP);
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
   pb(g, P_STRESS_H);
   launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t_d, 0.5 * G.dt,
@@ -849,6 +868,11 @@ rmt_status rmt_destroy_grid(rmt_grid* g) {
   else cudaDeviceSynchronize();
   drop_graphs(g);
   if (g->cap_s) cudaStreamDestroy(g->cap_s);
+  for (cudaStream_t b : g->body_s)
+    if (b) cudaStreamDestroy(b);
+  for (cudaEvent_t e : g->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   for (void* p : g->allocs) cudaFree(p);
   if (g->err_h) cudaFreeHost(g->err_h);
   mg_destroy(g->mac);
