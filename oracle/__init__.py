@@ -23,6 +23,7 @@ F_U, F_P, F_RHO, F_XI, F_PHI, F_LAYER = 1, 2, 3, 4, 5, 6
 F_DIVTAU_N, F_DIVTAU_H, F_UFACE_X, F_UFACE_Y, F_UFACE_Z = 20, 21, 22, 23, 24
 F_MAC_Q, F_ADV_U, F_USTAR, F_PSI, F_RHO_HALF, F_XI_HALF = 25, 26, 27, 28, 29, 30
 F_UMAC_X, F_UMAC_Y, F_UMAC_Z = 31, 32, 33
+F_REPULSION = 34
 
 BC_NOSLIP, BC_PERIODIC = 0, 1
 SHAPE_SPHERE, SHAPE_ELLIPSOID = 0, 1
@@ -34,6 +35,7 @@ class GridDesc(C.Structure):
         ("wall_u", (C.c_double * 3) * 6), ("rho_f", C.c_double), ("mu", C.c_double),
         ("eps_h", C.c_double), ("band_layers", C.c_int), ("dt", C.c_double),
         ("gravity", C.c_double * 3), ("solve_rtol", C.c_double), ("solve_max_iter", C.c_int),
+        ("wall_dw", C.c_double),
     ]
 
 
@@ -42,7 +44,7 @@ class SolidDesc(C.Structure):
         ("shape", C.c_int), ("center", C.c_double * 3), ("semi_axes", C.c_double * 3),
         ("rot", C.c_double * 9), ("rho_s", C.c_double), ("G", C.c_double), ("mu_a", C.c_double),
         ("gamma_t", C.c_double), ("active_A", C.c_double), ("active_omega", C.c_double),
-        ("active_len", C.c_double),
+        ("active_len", C.c_double), ("rep_A", C.c_double),
     ]
 
 
@@ -104,6 +106,8 @@ def lib():
         L.orc_fe_weak_div.restype = None
         L.orc_cell_grad.argtypes = [C.c_void_p, dp, dp]
         L.orc_cell_grad.restype = None
+        L.orc_rep_accel.argtypes = [C.c_double] * 8
+        L.orc_rep_accel.restype = C.c_double
         _lib = L
     return _lib
 
@@ -126,6 +130,7 @@ def make_grid_desc(scene: dict) -> GridDesc:
     d.gravity[:] = list(scene.get("gravity", (0.0, 0.0, 0.0)))
     d.solve_rtol = scene.get("oracle_rtol", 1e-14)
     d.solve_max_iter = scene.get("oracle_max_iter", 20000)
+    d.wall_dw = scene.get("wall_dw", 0.0)
     return d
 
 
@@ -139,6 +144,7 @@ def make_solid_desc(s: dict) -> SolidDesc:
     o.active_A = s.get("active_A", 0.0)
     o.active_omega = s.get("active_omega", 0.0)
     o.active_len = s.get("active_len", 1.0)
+    o.rep_A = s.get("rep_A", 0.0)
     return o
 
 

@@ -40,6 +40,7 @@ struct orc_grid {
   /* intermediates kept for inspection */
   double *divtau_n[3], *divtau_h[3], *uf[3][3], *umac[3], *q, *adv[3], *ustar[3], *psi, *rho_h;
   double *ub[3][3], *vadv[3];               /* transverse bar velocity states at e-faces */
+  double *rep[3];                           /* wall-repulsion acceleration used in u* */
   int nsol;
   solid* sol;
   int iters[2];
@@ -278,7 +279,7 @@ int orc_create(const orc_grid_desc* d, orc_grid** out) {
   for (int a = 0; a < 3; a++) g->NF[a] = g->N / g->n[a] * (g->n[a] + 1);
   for (int a = 0; a < 3; a++) {
     g->u[a] = dalloc(g->N); g->divtau_n[a] = dalloc(g->N); g->divtau_h[a] = dalloc(g->N);
-    g->adv[a] = dalloc(g->N); g->ustar[a] = dalloc(g->N);
+    g->adv[a] = dalloc(g->N); g->ustar[a] = dalloc(g->N); g->rep[a] = dalloc(g->N);
     g->umac[a] = dalloc(g->NF[a]); g->vadv[a] = dalloc(g->NF[a]);
     for (int b = 0; b < 3; b++) { g->uf[a][b] = dalloc(g->NF[a]); g->ub[a][b] = dalloc(g->NF[a]); }
   }
@@ -322,7 +323,7 @@ void orc_destroy(orc_grid* g) {
   }
   free(g->sol);
   for (int a = 0; a < 3; a++) {
-    free(g->u[a]); free(g->divtau_n[a]); free(g->divtau_h[a]); free(g->adv[a]); free(g->ustar[a]);
+    free(g->u[a]); free(g->divtau_n[a]); free(g->divtau_h[a]); free(g->adv[a]); free(g->ustar[a]); free(g->rep[a]);
     free(g->umac[a]); free(g->vadv[a]);
     for (int b = 0; b < 3; b++) { free(g->uf[a][b]); free(g->ub[a][b]); }
   }
@@ -770,12 +771,71 @@ static double trans_x(const orc_grid* g, const solid* S, int d, int a, int i, in
 
 /* normal-face states u^{n+1/2} (all components) and xi^{n+1/2} at every d-face
  * (eqs. taylor_left, time_partial, left_final, right_final, xi_taylor_final) */
+/* ------------------------------------------------------------------------------- */
+/* wall repulsion (SI "Contact with a wall")                                         */
+/* ------------------------------------------------------------------------------- */
+
+double orc_rep_accel(double V, double U, double dw, double Lmin, double rho_s, double rho_f, double gmag,
+                     double Usafe) {
+  const double vrep = dw * Lmin * Lmin;           /* conservative contact volume */
+  const double a_safe = Usafe * Usafe / dw;
+  const double a_stop = V * U * U / (2.0 * dw * vrep);
+  const double a_hold = fabs(rho_s - rho_f) * V * gmag / (rho_s * vrep);
+  double a = a_safe;
+  if (a_stop > a) a = a_stop;
+  if (a_hold > a) a = a_hold;
+  return a;
+}
+
+/* Acceleration a_rep at every cell from the bodies' level sets (which = 0: phi^n with the
+ * layers of step n; which = 1: phi^{n+1/2} with the layers of step n+1).  For a no-slip wall
+ * alpha with inward normal n_alpha, the cells whose centre is nearer than d_w to it get, from
+ * every body present there, A_rep n_alpha times the transition factor of eq. wall_acc in the
+ * body's phi with width Delta h_alpha = h; walls add up, and (Reading) so do bodies. */
+static void rep_accel(orc_grid* g, int which, double* out[3]) {
+  const double h = g->h, dw = g->d.wall_dw > 0.0 ? g->d.wall_dw : h;
+  for (int a = 0; a < 3; a++) memset(out[a], 0, sizeof(double) * g->N);
+  int any = 0;
+  for (int m = 0; m < g->nsol; m++) any |= g->sol[m].d.rep_A != 0.0;
+  if (!any) return;
+  for (int k = 0; k < g->n[2]; k++)
+    for (int j = 0; j < g->n[1]; j++)
+      for (int i = 0; i < g->n[0]; i++) {
+        const int ii[3] = {i, j, k};
+        double nsum[3] = {0.0, 0.0, 0.0};
+        int near = 0;
+        for (int d = 0; d < 3; d++) {
+          if (g->per[d]) continue;
+          const double dlo = (ii[d] + 0.5) * h, dhi = (g->n[d] - ii[d] - 0.5) * h;
+          if (dlo < dw) { nsum[d] += 1.0; near = 1; }  /* wall at lo: inward normal +e_d */
+          if (dhi < dw) { nsum[d] -= 1.0; near = 1; }  /* wall at hi: inward normal -e_d */
+        }
+        if (!near) continue;
+        const long c = cidx(g, i, j, k);
+        for (int m = 0; m < g->nsol; m++) {
+          const solid* S = &g->sol[m];
+          if (S->d.rep_A == 0.0) continue;
+          const signed char* L = which == 0 ? S->lay : S->layn;
+          if (L[c] < 0) continue;
+          const double ph = which == 0 ? S->phi[c] : S->phih[c];
+          double f;
+          if (ph <= -h) f = 1.0;
+          else if (ph < h) f = 0.5 - ph / (2.0 * h);
+          else f = 0.0;
+          for (int a = 0; a < 3; a++) out[a][c] += f * S->d.rep_A * nsum[a];
+        }
+      }
+}
+
 static void face_states(orc_grid* g) {
   const double h = g->h, dt = g->dt;
   const long N = g->N;
-  /* forcing F = -grad p^{n-1/2} + div tau^n + b^n at cells; Reading: b = (rho - rho_f) g */
+  /* forcing F = -grad p^{n-1/2} + div tau^n + b^n at cells; Reading: b = (rho - rho_f) g
+   * plus rho a_rep (wall repulsion, from phi^n) */
   double* F[3];
-  for (int a = 0; a < 3; a++) F[a] = dalloc(N);
+  double* A[3];
+  for (int a = 0; a < 3; a++) { F[a] = dalloc(N); A[a] = dalloc(N); }
+  rep_accel(g, 0, A);
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -783,8 +843,9 @@ static void face_states(orc_grid* g) {
         double gp[3];
         grad_at_cell(g, g->p, i, j, k, gp);
         for (int a = 0; a < 3; a++)
-          F[a][c] = -gp[a] + g->divtau_n[a][c] + (g->rho[c] - g->d.rho_f) * g->d.gravity[a];
+          F[a][c] = -gp[a] + g->divtau_n[a][c] + (g->rho[c] - g->d.rho_f) * g->d.gravity[a] + g->rho[c] * A[a][c];
       }
+  for (int a = 0; a < 3; a++) free(A[a]);
   for (int d = 0; d < 3; d++) {
     int ext[3] = {g->n[0], g->n[1], g->n[2]};
     ext[d] += 1;
@@ -1172,7 +1233,9 @@ static int one_step(orc_grid* g) {
   stress_divergence(g, 1, g->t + 0.5 * dt, g->divtau_h);
   /* 9. rho^{n+1/2} */
   mix_density(g, 1, g->rho_h);
-  /* 10. u* (Reading of the garbled item: eq. dis_full_mmt with p^{n-1/2}) */
+  /* 10. u* (Reading of the garbled item: eq. dis_full_mmt with p^{n-1/2}); the wall
+   * repulsion joins b^{n+1/2} as rho a_rep, from phi^{n+1/2} */
+  rep_accel(g, 1, g->rep);
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1181,7 +1244,8 @@ static int one_step(orc_grid* g) {
         grad_at_cell(g, g->p, i, j, k, gp);
         for (int a = 0; a < 3; a++)
           g->ustar[a][c] = g->u[a][c] - dt * g->adv[a][c] +
-                           dt / g->rho_h[c] * (g->divtau_h[a][c] - gp[a] + (g->rho_h[c] - g->d.rho_f) * g->d.gravity[a]);
+                           dt / g->rho_h[c] * (g->divtau_h[a][c] - gp[a] + (g->rho_h[c] - g->d.rho_f) * g->d.gravity[a] +
+                                               g->rho_h[c] * g->rep[a][c]);
       }
   /* 11. approximate projection of (u* - u^n)/dt, u^{n+1}, p^{n+1/2} */
   {
@@ -1231,7 +1295,7 @@ int orc_step(orc_grid* g, int nsteps) {
 long orc_field_len(orc_grid* g, int field) {
   switch (field) {
     case ORC_F_U: case ORC_F_XI: case ORC_F_DIVTAU_N: case ORC_F_DIVTAU_H: case ORC_F_ADV_U:
-    case ORC_F_USTAR: case ORC_F_XI_HALF: return 3 * g->N;
+    case ORC_F_USTAR: case ORC_F_XI_HALF: case ORC_F_REPULSION: return 3 * g->N;
     case ORC_F_P: case ORC_F_PSI: return g->NN;
     case ORC_F_RHO: case ORC_F_PHI: case ORC_F_LAYER: case ORC_F_MAC_Q: case ORC_F_RHO_HALF: return g->N;
     case ORC_F_UFACE_X: return 3 * g->NF[0];
@@ -1267,6 +1331,7 @@ int orc_read(orc_grid* g, int field, int sid, double* dst, long n) {
     case ORC_F_DIVTAU_H: for (int a = 0; a < 3; a++) memcpy(dst + a * N, g->divtau_h[a], sizeof(double) * N); break;
     case ORC_F_ADV_U: for (int a = 0; a < 3; a++) memcpy(dst + a * N, g->adv[a], sizeof(double) * N); break;
     case ORC_F_USTAR: for (int a = 0; a < 3; a++) memcpy(dst + a * N, g->ustar[a], sizeof(double) * N); break;
+    case ORC_F_REPULSION: for (int a = 0; a < 3; a++) memcpy(dst + a * N, g->rep[a], sizeof(double) * N); break;
     case ORC_F_PSI: memcpy(dst, g->psi, sizeof(double) * g->NN); break;
     case ORC_F_MAC_Q: memcpy(dst, g->q, sizeof(double) * N); break;
     case ORC_F_RHO_HALF: memcpy(dst, g->rho_h, sizeof(double) * N); break;

@@ -41,6 +41,7 @@ typedef struct {
   double gravity[3];
   double solve_rtol;       /* CG relative residual target */
   int solve_max_iter;
+  double wall_dw;          /* wall-repulsion threshold distance (<= 0: one grid spacing) */
 } orc_grid_desc;
 
 typedef struct {
@@ -48,6 +49,7 @@ typedef struct {
   double center[3], semi_axes[3], rot[9]; /* rot: body -> world, row-major */
   double rho_s, G, mu_a, gamma_t;
   double active_A, active_omega, active_len;
+  double rep_A;            /* wall-repulsion acceleration magnitude (0: none) */
 } orc_solid_desc;
 
 typedef struct orc_grid orc_grid;
@@ -59,7 +61,8 @@ enum {
   ORC_F_DIVTAU_N = 20, ORC_F_DIVTAU_H = 21, ORC_F_UFACE_X = 22, ORC_F_UFACE_Y = 23,
   ORC_F_UFACE_Z = 24, ORC_F_MAC_Q = 25, ORC_F_ADV_U = 26, ORC_F_USTAR = 27,
   ORC_F_PSI = 28, ORC_F_RHO_HALF = 29, ORC_F_XI_HALF = 30, ORC_F_UMAC_X = 31,
-  ORC_F_UMAC_Y = 32, ORC_F_UMAC_Z = 33
+  ORC_F_UMAC_Y = 32, ORC_F_UMAC_Z = 33,
+  ORC_F_REPULSION = 34     /* wall-repulsion acceleration of the last step's u* (3 N) */
 };
 
 int  orc_create(const orc_grid_desc* d, orc_grid** out);
@@ -75,6 +78,12 @@ double orc_last_true_residual(orc_grid* g, int which); /* true relative residual
 const char* orc_error(orc_grid* g);
 
 /* Building blocks exposed for the pin tests. */
+/* A_rep of SI "Contact with a wall": the largest of U_safe^2/d_w (safety floor), V U^2 /
+ * (2 d_w^2 L_min^2) (stops a body of volume V approaching at U within d_w, with the
+ * conservative contact volume d_w L_min^2) and |rho_s - rho_f| V g / (rho_s d_w L_min^2)
+ * (carries the body's weight at rest). */
+double orc_rep_accel(double V, double U, double dw, double Lmin, double rho_s, double rho_f, double gmag,
+                     double Usafe);
 double orc_heaviside(double phi, double eps);
 double orc_dheaviside(double phi, double eps);
 double orc_limited_slope(const double q[5], const int ok[5], double h);

@@ -46,13 +46,13 @@ def _box(n: int, periodic: bool, lid: float = 0.0) -> dict:
 
 
 def solid(shape=SPHERE, center=(0.5, 0.5, 0.5), semi_axes=(0.2, 0.2, 0.2), rot=None, rho_s=1.0,
-          G=0.1, mu_a=0.01, gamma_t=0.0, active_A=0.0, active_omega=0.0, active_len=1.0) -> dict:
+          G=0.1, mu_a=0.01, gamma_t=0.0, active_A=0.0, active_omega=0.0, active_len=1.0, rep_A=0.0) -> dict:
     return dict(shape=shape, center=tuple(float(c) for c in center),
                 semi_axes=tuple(float(a) for a in semi_axes),
                 rot=np.eye(3) if rot is None else np.asarray(rot, dtype=np.float64),
                 rho_s=float(rho_s), G=float(G), mu_a=float(mu_a), gamma_t=float(gamma_t),
                 active_A=float(active_A), active_omega=float(active_omega),
-                active_len=float(active_len))
+                active_len=float(active_len), rep_A=float(rep_A))
 
 
 def cavity_sphere(n: int = 32, steps: int = 20, precision: str = "fp64") -> dict:

@@ -487,3 +487,75 @@ def test_viscous_shear_wave_decays_at_the_right_rate():
         ex = np.sin(2 * np.pi * Z) * np.exp(-4 * np.pi**2 * nu * steps * dt)
         errs.append(np.sqrt(np.mean((u[0] - ex) ** 2)))
     assert errs[0] / errs[1] > 2.0 and errs[1] / errs[2] > 2.0
+
+
+# --------------------------------------------------------------------------- wall repulsion
+def test_repulsion_magnitude_meets_its_defining_conditions():
+    """A_rep (SI "Contact with a wall") is the largest of three accelerations, each fixed by a
+    condition the paper states: check each condition where its term is the largest."""
+    V, dw, Lmin, g = 4.0 / 3.0 * np.pi * 0.1 ** 3, 1.0 / 64, 0.2, 1.0
+    vrep = dw * Lmin ** 2
+    # approach at U: the centre of mass, decelerated by V_rep A / V, stops within d_w at t = 2 d_w / U
+    U = 3.0
+    a = L.orc_rep_accel(V, U, dw, Lmin, 1.0, 1.0, 0.0, 1e-6)
+    acm = vrep * a / V
+    ts = U / acm
+    assert ts == pytest.approx(2 * dw / U, rel=1e-12)
+    assert U * ts - 0.5 * acm * ts ** 2 == pytest.approx(dw, rel=1e-12)
+    # resting on the wall: the repulsion on the breached cells carries the body's net weight
+    rho_s = 3.0
+    a = L.orc_rep_accel(V, 1e-6, dw, Lmin, rho_s, 1.0, g, 1e-6)
+    assert rho_s * vrep * a == pytest.approx(abs(rho_s - 1.0) * V * g, rel=1e-12)
+    # neither: the safety floor U_safe^2 / d_w
+    assert L.orc_rep_accel(V, 1e-6, dw, Lmin, 1.0, 1.0, 0.0, 4.5) == pytest.approx(4.5 ** 2 / dw, rel=1e-15)
+    # and it is the maximum of the three
+    terms = [4.5 ** 2 / dw, V * U ** 2 / (2 * dw * vrep), abs(rho_s - 1.0) * V * g / (rho_s * vrep)]
+    assert L.orc_rep_accel(V, U, dw, Lmin, rho_s, 1.0, g, 4.5) == pytest.approx(max(terms), rel=1e-15)
+
+
+def _wall_sphere(n=16, rep=8.0, dw=0.0):
+    sc = S._box(n, periodic=False)
+    h = 1.0 / n
+    sc.update(dt=0.1 * h, wall_dw=dw)
+    sc["solids"] = [S.solid(S.SPHERE, (0.5, 0.5, 0.22 + 0.3 * h), (0.22,) * 3, rho_s=1.0, G=0.2, rep_A=rep)]
+    return sc
+
+
+@pytest.mark.parametrize("dw_cells", [0.0, 2.0])
+def test_repulsion_field_matches_eq_wall_acc(dw_cells):
+    """The acceleration the oracle adds to u* equals eq. wall_acc evaluated independently from
+    the body's half-step reference map: sphere phi = |xi - c| - R, transition width h, inward
+    normal of the breached wall (here the bottom one), zero elsewhere."""
+    n = 16
+    h = 1.0 / n
+    sc = _wall_sphere(n, rep=8.0, dw=dw_cells * h)
+    o = O.Oracle(sc)
+    assert o.step(1) == 0
+    a = o.read(O.F_REPULSION).reshape(3, n, n, n)
+    xh = o.read(O.F_XI_HALF, 0).reshape(3, n, n, n)
+    c = np.array(sc["solids"][0]["center"])
+    phi = np.sqrt(sum((xh[q] - c[q]) ** 2 for q in range(3))) - 0.22
+    f = np.where(phi <= -h, 1.0, np.where(phi < h, 0.5 - phi / (2 * h), 0.0))
+    f = np.where(np.isfinite(xh[0]), f, 0.0)
+    dw = dw_cells * h if dw_cells > 0 else h
+    kk = np.arange(n)
+    near_bottom = ((kk + 0.5) * h < dw)[:, None, None]
+    expect_z = np.where(near_bottom, 8.0 * f, 0.0)
+    assert np.allclose(a[2], expect_z, rtol=0, atol=1e-14)
+    assert np.count_nonzero(a[2]) > 0
+    # the sphere reaches no other wall: no x or y component
+    assert np.all(a[0] == 0.0) and np.all(a[1] == 0.0)
+
+
+def test_repulsion_pushes_the_body_off_the_wall():
+    """With repulsion the body near the bottom wall starts to move up; without it, at rest."""
+    n = 16
+    w = {}
+    for rep in (0.0, 8.0):
+        o = O.Oracle(_wall_sphere(n, rep=rep))
+        assert o.step(3) == 0
+        u = o.read(O.F_U).reshape(3, n, n, n)
+        lay = o.read(O.F_LAYER, 0).reshape(n, n, n)
+        w[rep] = u[2][lay == 0].mean()
+    assert abs(w[0.0]) < 1e-12
+    assert w[8.0] > 1e-4
