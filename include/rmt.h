@@ -62,6 +62,8 @@ typedef struct {
                              synchronisation inside rmt_step)                                 */
   int mg_fixed_cycles_fe; /* the same for the FE solve (<= 0: mg_fixed_cycles)                */
   void* cuda_stream;      /* cudaStream_t all work is ordered on (NULL: legacy stream)        */
+  double wall_dw;         /* wall-repulsion threshold distance d_w (<= 0: one grid spacing;
+                             SI "Contact with a wall")                                        */
 } rmt_grid_desc;
 
 /* One immersed body (main text "Hyperelastic formulation", "Swimming"). The reference
@@ -74,6 +76,11 @@ typedef struct {
                                          viscosity factor (Table pars)                       */
   double active_A, active_omega, active_len; /* active stress A sin(2 pi X/len - omega t)
                                          along the body x axis; A = 0: passive            */
+  double rep_A;                       /* wall-repulsion acceleration A_rep (0: none): cells of
+                                         the body nearer than d_w to a no-slip wall get
+                                         A_rep times the transition factor of eq. wall_acc
+                                         along the wall's inward normal (SI "Contact with a
+                                         wall"); see rmt_wall_repulsion                   */
 } rmt_solid_desc;
 
 /* Creates a grid.  Validates the descriptor; allocates the device state lazily on the first
@@ -95,7 +102,8 @@ enum {
   RMT_F_DIVTAU_N = 20, RMT_F_DIVTAU_H = 21, RMT_F_UFACE_X = 22, RMT_F_UFACE_Y = 23,
   RMT_F_UFACE_Z = 24, RMT_F_MAC_Q = 25, RMT_F_ADV_U = 26, RMT_F_USTAR = 27, RMT_F_PSI = 28,
   RMT_F_RHO_HALF = 29, RMT_F_XI_HALF = 30, RMT_F_UMAC_X = 31, RMT_F_UMAC_Y = 32,
-  RMT_F_UMAC_Z = 33
+  RMT_F_UMAC_Z = 33,
+  RMT_F_REPULSION = 34 /* wall-repulsion acceleration that entered the last step's u* (3 N) */
 };
 
 /* Number of FP64 values of a field (see layouts above), or -1 for an unknown field. */
@@ -130,6 +138,14 @@ double rmt_dt(rmt_grid* g);
  * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL, RMT_ESTATE for
  * a batch member. */
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
+
+/* A_rep of SI "Contact with a wall" for one body: the largest of U_safe^2/d_w (a safety
+ * floor; the paper uses U_safe about 4.5), V U^2 / (2 d_w^2 L_min^2) (stops a body of volume V
+ * approaching the wall at speed U within d_w, taking d_w L_min^2 as the breached volume, L_min
+ * the body's smallest length) and |rho_s - rho_f| V g / (rho_s d_w L_min^2) (carries its net
+ * weight when it rests on the wall).  Pure function; no grid needed. */
+double rmt_wall_repulsion(double V, double U, double d_w, double L_min, double rho_s, double rho_f, double g,
+                          double U_safe);
 
 /* Autotuner of the two multigrid solves (no paper counterpart: the paper's multigrid library
  * is not described).  On the right-hand sides of the grid's last step (RMT_ESTATE before the

@@ -468,7 +468,8 @@ rmt_status step_t(rmt_grid* g) {
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
   launch_bar_states<T>(G, u, slopes, ub, vadv, s);
-  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, slopes, wcell, ub, vadv, uf, s);
+  launch_face_states<T>(G, u, (const T*)g->p, (const T*)g->rho, (const T*)g->divn, g->bodies_d, views<T>(g, cur, 0),
+                        nb, slopes, wcell, ub, vadv, uf, s);
   pe(g, P_GODUNOV);
   // 3. MAC projection of the normal face velocities
   pb(g, P_MAC_SETUP);
@@ -522,7 +523,8 @@ rmt_status step_t(rmt_grid* g) {
   pe(g, P_STRESS_H);
   pb(g, P_USTAR);
   launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho_h, s);
-  launch_ustar<T>(G, u, (const T*)g->adv, (const T*)g->p, (const T*)g->rho_h, (const T*)g->divh, (T*)g->ustar, s);
+  launch_ustar<T>(G, u, (const T*)g->adv, (const T*)g->p, (const T*)g->rho_h, (const T*)g->divh, (T*)g->ustar,
+                  g->bodies_d, views<T>(g, cur, 1), nb, s);
   pe(g, P_USTAR);
   // 11. approximate projection, u^{n+1}, p^{n+1/2}
   pb(g, P_FE_SETUP);
@@ -570,9 +572,13 @@ rmt_status ensure_init(rmt_grid* g) {
     b.actA = s.active_A;
     b.actW = s.active_omega;
     b.actL = s.active_len;
+    b.repA = s.rep_A;
     body_finish(b);
     g->bodies.push_back(b);
+    if (s.rep_A != 0.0) g->g.any_rep = 1;
   }
+  g->g.dw = g->desc.wall_dw > 0.0 ? g->desc.wall_dw : g->g.h;
+  g->g.f.dw = (float)g->g.dw;
   g->inited = 1;
   rmt_status st = g->fp32 ? init_t<float>(g) : init_t<double>(g);
   if (st != RMT_OK) return st;
@@ -669,6 +675,9 @@ rmt_status gather_t(rmt_grid* g, int field, int sid, double* out) {
     case RMT_F_ADV_U: cvt(g->adv, 3 * N, 0); break;
     case RMT_F_USTAR: cvt(g->ustar, 3 * N, 0); break;
     case RMT_F_RHO_HALF: cvt(g->rho_h, N, 0); break;
+    case RMT_F_REPULSION:  // from the last step's half-level bodies
+      launch_rep_field<T>(G, g->bodies_d, views<T>(g, 1 - g->par, 1), (int)g->bodies.size(), out, s);
+      break;
     case RMT_F_MAC_Q:
       CK(g, cudaMemcpyAsync(out, mg_solution64(g->mac, s), N * sizeof(double), cudaMemcpyDeviceToDevice, s));
       break;
@@ -804,7 +813,7 @@ long rmt_field_len(rmt_grid* g, int field) {
   const Geo& G = g->g;
   switch (field) {
     case RMT_F_U: case RMT_F_XI: case RMT_F_DIVTAU_N: case RMT_F_DIVTAU_H: case RMT_F_ADV_U:
-    case RMT_F_USTAR: case RMT_F_XI_HALF: return 3 * G.N;
+    case RMT_F_USTAR: case RMT_F_XI_HALF: case RMT_F_REPULSION: return 3 * G.N;
     case RMT_F_P: case RMT_F_PSI: return G.NN;
     case RMT_F_RHO: case RMT_F_PHI: case RMT_F_LAYER: case RMT_F_MAC_Q: case RMT_F_RHO_HALF: return G.N;
     case RMT_F_UFACE_X: case RMT_F_UFACE_Y: case RMT_F_UFACE_Z: return 3 * nfaces(G, field - RMT_F_UFACE_X);
@@ -962,6 +971,16 @@ size_t rmt_grid_footprint(const rmt_grid_desc* d, int nsolids) {
 }
 
 size_t rmt_grid_device_bytes(const rmt_grid* g) { return g ? g->bytes : 0; }
+
+double rmt_wall_repulsion(double V, double U, double d_w, double L_min, double rho_s, double rho_f, double g,
+                          double U_safe) {
+  const double vrep = d_w * L_min * L_min;  // the breached volume the paper assumes
+  double a = U_safe * U_safe / d_w;
+  const double stop = V * U * U / (2.0 * d_w * vrep), hold = fabs(rho_s - rho_f) * V * g / (rho_s * vrep);
+  if (stop > a) a = stop;
+  if (hold > a) a = hold;
+  return a;
+}
 
 const char* rmt_profile_name(int entry) { return (entry >= 0 && entry < P_NUM) ? kProfNames[entry] : ""; }
 

@@ -22,12 +22,15 @@ struct Geo {
   double wall[6][3];
   double grav[3];
   int layers;      // extrapolation layers
+  double dw;       // wall-repulsion threshold distance
+  int any_rep;     // some body has a wall-repulsion acceleration
   // derived constants (host-computed by geo_finish) and float mirrors of everything a kernel
   // reads, so that FP32 kernels never convert or divide in FP64
   double ih, q4, hdt_h, two_dt, fe_rhs;  // 1/h, 0.25/h, dt/(2h), 2/dt, h^2/(4 dt)
   struct {
     float h, ih, q4, hdt_h, dt, eps, rho_f, mu, utol, wall[6][3], grav[3];
     float two_dt, two_dt_lo, fe_rhs, fe_rhs_lo;  // two-float pairs (value = hi + lo)
+    float dw;
   } f;
 };
 
@@ -36,9 +39,10 @@ struct Body {
   int shape;
   double c[3], a[3], R[9];
   double rho_s, G, mu_a, gamma_t, actA, actW, actL;
+  double repA;         // wall-repulsion acceleration (0: none)
   double a2[3], mina;  // squared semi-axes, smallest semi-axis (body_finish)
   struct {
-    float c[3], a[3], R[9], a2[3], mina, rho_s, G, mu_a, gamma_t, actA, actW, actL;
+    float c[3], a[3], R[9], a2[3], mina, rho_s, G, mu_a, gamma_t, actA, actW, actL, repA;
   } f;
 };
 
@@ -72,6 +76,7 @@ inline void geo_finish(Geo& g) {
   g.f.two_dt_lo = (float)(g.two_dt - (double)g.f.two_dt);
   g.f.fe_rhs = (float)g.fe_rhs;
   g.f.fe_rhs_lo = (float)(g.fe_rhs - (double)g.f.fe_rhs);
+  g.f.dw = (float)g.dw;
 }
 // fills the derived constants and float mirrors of a body (host)
 inline void body_finish(Body& b) {
@@ -93,6 +98,7 @@ inline void body_finish(Body& b) {
   b.f.actA = (float)b.actA;
   b.f.actW = (float)b.actW;
   b.f.actL = (float)b.actL;
+  b.f.repA = (float)b.repA;
 }
 
 // The reference-map fields of one body at one time level.
@@ -403,6 +409,46 @@ __device__ __forceinline__ bool tile_meets_box(const Geo& g, const int* bb, int 
 __device__ __forceinline__ bool in_box(const Geo& g, const int* bb, int i, int j, int k) {
   return in_box_axis(i, bb[0], bb[3], g.per[0], g.n[0]) && in_box_axis(j, bb[1], bb[4], g.per[1], g.n[1]) &&
          in_box_axis(k, bb[2], bb[5], g.per[2], g.n[2]);
+}
+
+// Wall-repulsion acceleration at cell (i,j,k), index c (SI "Contact with a wall", eq.
+// wall_acc): for every no-slip wall whose distance to the cell centre is below d_w, each body
+// present at the cell with a repulsion adds A_rep times the transition factor of its phi
+// (1 for phi <= -h, 1/2 - phi/(2h) for |phi| < h, 0 beyond) along the wall's inward normal.
+// Returns false (out untouched) for cells that no wall reaches.
+template <typename T>
+__device__ __forceinline__ bool rep_accel(const Geo& g, const Body* __restrict__ bodies,
+                                          const BodyView<T>* __restrict__ views, int nb, int i, int j, int k, long c,
+                                          T out[3]) {
+  const T h = cv<T>(g.h, g.f.h), dw = cv<T>(g.dw, g.f.dw);
+  const int ii[3] = {i, j, k};
+  T ns[3] = {T(0), T(0), T(0)};
+  bool near = false;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (g.per[d]) continue;
+    if ((T(ii[d]) + T(0.5)) * h < dw) {
+      ns[d] += T(1);
+      near = true;
+    }
+    if ((T(g.n[d] - ii[d]) - T(0.5)) * h < dw) {
+      ns[d] -= T(1);
+      near = true;
+    }
+  }
+  if (!near) return false;
+  out[0] = out[1] = out[2] = T(0);
+  for (int m = 0; m < nb; m++) {
+    const Body& B = bodies[m];
+    if (B.repA == 0.0) continue;
+    if (views[m].lay[c] < 0) continue;
+    const T ph = views[m].phi[c];
+    const T f = ph <= -h ? T(1) : (ph < h ? T(0.5) - ph / (T(2) * h) : T(0));
+    const T fa = f * cv<T>(B.repA, B.f.repA);
+#pragma unroll
+    for (int a = 0; a < 3; a++) out[a] += fa * ns[a];
+  }
+  return true;
 }
 
 // Bodies whose band box meets the block's tile (TILE_X x TILE_Y cells of plane blockIdx.z, the

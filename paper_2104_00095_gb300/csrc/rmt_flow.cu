@@ -123,7 +123,8 @@ struct BarPtrs {
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_cellw(Geo g, const T* __restrict__ u, const T* __restrict__ p,
                                                            const T* __restrict__ rho, const T* __restrict__ divtau,
-                                                           BarPtrs bp, Slopes9 W) {
+                                                           BarPtrs bp, Slopes9 W, const Body* __restrict__ bodies,
+                                                           const BodyView<T>* __restrict__ views, int nb) {
   THREAD_XYZ(i, j, k);
   if (i >= g.n[0] || j >= g.n[1]) return;
   const T dt = cv<T>(g.dt, g.f.dt), ih = cv<T>(g.ih, g.f.ih);
@@ -138,6 +139,9 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_cellw(Geo g, const T* __rest
     gp[2] += sc ? pv : -pv;
   }
   const T r = rho[c];
+  // wall repulsion joins b (SI "Contact with a wall"), from phi^n
+  T rep[3];
+  const bool has_rep = g.any_rep && rep_accel(g, bodies, views, nb, i, j, k, c, rep);
   T vavg[3];
   long lo[3], hi[3];
 #pragma unroll
@@ -148,8 +152,8 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_cellw(Geo g, const T* __rest
   }
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] +
-                (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
+    T F = -gp[a] * (T(0.25) * ih) + divtau[a * g.N + c] + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
+    if (has_rep) F = F + r * rep[a];
     T term[3];
 #pragma unroll
     for (int e = 0; e < 3; e++) {
@@ -342,7 +346,8 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_density(Geo g, const Body* _
 
 template <typename T>
 __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ adv, const T* __restrict__ p,
-                        const T* __restrict__ rho_h, const T* __restrict__ divtau_h, T* __restrict__ ustar) {
+                        const T* __restrict__ rho_h, const T* __restrict__ divtau_h, T* __restrict__ ustar,
+                        const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb) {
   const T dt = cv<T>(g.dt, g.f.dt), q4 = cv<T>(g.q4, g.f.q4);
   GRID_LOOP(c, g.N) {
     int i, j, k;
@@ -357,10 +362,15 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
       gp[2] += sc ? pv : -pv;
     }
     const T r = rho_h[c];
+    // wall repulsion joins b^{n+1/2} (SI "Contact with a wall"), from phi^{n+1/2}
+    T rep[3];
+    const bool has_rep = g.any_rep && rep_accel(g, bodies, views, nb, i, j, k, c, rep);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-      ustar[a * g.N + c] = u[a * g.N + c] - dt * adv[a * g.N + c] +
-                           dt / r * (divtau_h[a * g.N + c] - gp[a] * q4 + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]));
+    for (int a = 0; a < 3; a++) {
+      T f = divtau_h[a * g.N + c] - gp[a] * q4 + (r - cv<T>(g.rho_f, g.f.rho_f)) * cv<T>(g.grav[a], g.f.grav[a]);
+      if (has_rep) f = f + r * rep[a];
+      ustar[a * g.N + c] = u[a * g.N + c] - dt * adv[a * g.N + c] + dt / r * f;
+    }
   }
 }
 
@@ -448,6 +458,20 @@ __global__ void k_fe_update_p(long nn, MGVec psi, T* __restrict__ p, T* __restri
   }
 }
 
+// the wall-repulsion acceleration of every cell as FP64 (read-back of RMT_F_REPULSION)
+template <typename T>
+__global__ void k_rep_field(Geo g, const Body* __restrict__ bodies, const BodyView<T>* __restrict__ views, int nb,
+                            double* __restrict__ out) {
+  GRID_LOOP(c, g.N) {
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    T rep[3];
+    const bool has = g.any_rep && rep_accel(g, bodies, views, nb, i, j, k, c, rep);
+#pragma unroll
+    for (int a = 0; a < 3; a++) out[a * g.N + c] = has ? (double)rep[a] : 0.0;
+  }
+}
+
 template <typename T>
 __global__ void k_fill(T* a, T v, long n) {
   GRID_LOOP(i, n) a[i] = v;
@@ -473,7 +497,8 @@ void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ub
   }
 }
 template <typename T>
-void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, const Body* bodies,
+                        const BodyView<T>* views, int nb, T* const slopes[9],
                         T* const wcell[9], T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s) {
   BarPtrs bp;
   Slopes9 S, W;
@@ -486,7 +511,7 @@ void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, cons
     bp.vadv[e] = vadv[e];
   }
   const dim3 gc((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
-  k_cellw<T><<<gc, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, p, rho, divtau, bp, W);
+  k_cellw<T><<<gc, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, p, rho, divtau, bp, W, bodies, views, nb);
   rmt_count_launches(1);
   for (int d = 0; d < 3; d++) {
     for (int a = 0; a < 3; a++) bp.uf[a] = uf[d][a];
@@ -529,9 +554,15 @@ void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, 
   rmt_count_launches(1);
 }
 template <typename T>
+void launch_rep_field(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, double* out, cudaStream_t s) {
+  k_rep_field<T><<<nblocks(g.N), TPB, 0, s>>>(g, bodies, views, nb, out);
+  rmt_count_launches(1);
+}
+template <typename T>
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h, T* ustar,
-                  cudaStream_t s) {
-  k_ustar<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, adv, p, rho_h, divtau_h, ustar); rmt_count_launches(1);
+                  const Body* bodies, const BodyView<T>* views, int nb, cudaStream_t s) {
+  k_ustar<T><<<nblocks(g.N), TPB, 0, s>>>(g, u, adv, p, rho_h, divtau_h, ustar, bodies, views, nb);
+  rmt_count_launches(1);
 }
 template <typename T>
 void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b64, cudaStream_t s) {
@@ -551,7 +582,8 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
 
 #define INST(T)                                                                                                   \
   template void launch_bar_states<T>(const Geo&, const T*, T* const[9], T* const[3][3], T* const[3], cudaStream_t); \
-  template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, T* const[9],           \
+  template void launch_face_states<T>(const Geo&, const T*, const T*, const T*, const T*, const Body*,          \
+                                      const BodyView<T>*, int, T* const[9],                                   \
                                       T* const[9], T* const[3][3], T* const[3], T* const[3][3], cudaStream_t);   \
   template void launch_mac_setup<T>(const Geo&, T* const[3][3], MGVec, cudaStream_t);                            \
   template void launch_mac_correct<T>(const Geo&, T* const[3][3], const T*, MGVec, T* const[3],                 \
@@ -559,7 +591,9 @@ void launch_fill(T* a, T v, long n, cudaStream_t s) {
   template void launch_advect<T>(const Geo&, T* const[3][3], T* const[3], T*, cudaStream_t);                      \
   template void launch_density<T>(const Geo&, const Body*, const BodyView<T>*, int, const int*, int, T*,        \
                                   cudaStream_t);                                                                \
-  template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, cudaStream_t); \
+  template void launch_ustar<T>(const Geo&, const T*, const T*, const T*, const T*, const T*, T*, const Body*,  \
+                                const BodyView<T>*, int, cudaStream_t);                                       \
+  template void launch_rep_field<T>(const Geo&, const Body*, const BodyView<T>*, int, double*, cudaStream_t);   \
   template void launch_fe_setup<T>(const Geo&, const T*, const T*, MGVec, cudaStream_t);                        \
   template void launch_fe_update<T>(const Geo&, const T*, const T*, MGVec, T*, T*, T*, cudaStream_t);          \
   template void launch_fill<T>(T*, T, long, cudaStream_t);

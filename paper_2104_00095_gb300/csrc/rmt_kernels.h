@@ -36,8 +36,10 @@ void launch_bar_states(const Geo& g, const T* u, T* const slopes[9], T* const ub
                        cudaStream_t s);
 // wcell: nine cell arrays of scratch for the side-independent part of the face states
 template <typename T>
-void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, T* const slopes[9],
-                        T* const wcell[9], T* const ubar[3][3], T* const vadv[3], T* const uf[3][3], cudaStream_t s);
+// bodies / views / nb: the bodies at step n, for the wall-repulsion term of the forcing
+void launch_face_states(const Geo& g, const T* u, const T* p, const T* rho, const T* divtau, const Body* bodies,
+                        const BodyView<T>* views, int nb, T* const slopes[9], T* const wcell[9], T* const ubar[3][3],
+                        T* const vadv[3], T* const uf[3][3], cudaStream_t s);
 template <typename T>
 void launch_mac_setup(const Geo& g, T* const uf[3][3], MGVec b, cudaStream_t s);
 template <typename T>
@@ -55,8 +57,12 @@ template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
                     T* rho, cudaStream_t s);
 template <typename T>
+// bodies / views / nb: the bodies at step n+1/2, for the wall-repulsion term
 void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* rho_h, const T* divtau_h,
-                  T* ustar, cudaStream_t s);
+                  T* ustar, const Body* bodies, const BodyView<T>* views, int nb, cudaStream_t s);
+// the wall-repulsion acceleration of every cell from the given bodies' phi, as FP64 (3 N)
+template <typename T>
+void launch_rep_field(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, double* out, cudaStream_t s);
 template <typename T>
 void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b, cudaStream_t s);
 template <typename T>

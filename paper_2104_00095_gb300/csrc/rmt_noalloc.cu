@@ -92,6 +92,7 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   b.actA = s->active_A;
   b.actW = s->active_omega;
   b.actL = s->active_len;
+  b.repA = s->rep_A;
   body_finish(b);
   geo_finish(G);
 

@@ -21,6 +21,7 @@ RMT_F_U, RMT_F_P, RMT_F_RHO, RMT_F_XI, RMT_F_PHI, RMT_F_LAYER = 1, 2, 3, 4, 5, 6
 RMT_F_DIVTAU_N, RMT_F_DIVTAU_H, RMT_F_UFACE_X, RMT_F_UFACE_Y, RMT_F_UFACE_Z = 20, 21, 22, 23, 24
 RMT_F_MAC_Q, RMT_F_ADV_U, RMT_F_USTAR, RMT_F_PSI, RMT_F_RHO_HALF, RMT_F_XI_HALF = 25, 26, 27, 28, 29, 30
 RMT_F_UMAC_X, RMT_F_UMAC_Y, RMT_F_UMAC_Z = 31, 32, 33
+RMT_F_REPULSION = 34
 
 RMT_JOB_QUEUED, RMT_JOB_RUNNING, RMT_JOB_DONE, RMT_JOB_FAILED = 0, 1, 2, 3
 
@@ -32,7 +33,7 @@ EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt
            "rmt_batch_last_error", "rmt_server_create", "rmt_server_set_option", "rmt_server_submit",
            "rmt_server_poll", "rmt_server_job", "rmt_server_job_grid", "rmt_server_release",
            "rmt_server_resident_bytes", "rmt_server_clock", "rmt_server_cell_steps", "rmt_server_destroy",
-           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats")
+           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats", "rmt_wall_repulsion")
 
 
 class rmt_grid_desc(C.Structure):
@@ -42,7 +43,7 @@ class rmt_grid_desc(C.Structure):
         ("eps_h", C.c_double), ("band_layers", C.c_int), ("dt", C.c_double),
         ("gravity", C.c_double * 3), ("precision", C.c_int), ("mg_rtol", C.c_double),
         ("mg_max_cycles", C.c_int), ("mg_fixed_cycles", C.c_int), ("mg_fixed_cycles_fe", C.c_int),
-        ("cuda_stream", C.c_void_p),
+        ("cuda_stream", C.c_void_p), ("wall_dw", C.c_double),
     ]
 
 
@@ -74,7 +75,7 @@ class rmt_solid_desc(C.Structure):
         ("shape", C.c_int), ("center", C.c_double * 3), ("semi_axes", C.c_double * 3),
         ("rot", C.c_double * 9), ("rho_s", C.c_double), ("G", C.c_double), ("mu_a", C.c_double),
         ("gamma_t", C.c_double), ("active_A", C.c_double), ("active_omega", C.c_double),
-        ("active_len", C.c_double),
+        ("active_len", C.c_double), ("rep_A", C.c_double),
     ]
 
 
@@ -150,6 +151,8 @@ def load(build: bool = True):
     L.rmt_server_stats.argtypes = [vp, C.POINTER(rmt_server_stats_t)]
     L.rmt_server_stats.restype = C.c_int
     L.rmt_autotune.argtypes = [vp, C.c_double, C.POINTER(rmt_tune_result)]
+    L.rmt_wall_repulsion.argtypes = [C.c_double] * 8
+    L.rmt_wall_repulsion.restype = C.c_double
     for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
               "rmt_destroy_grid", "rmt_batch_create", "rmt_batch_add", "rmt_batch_remove", "rmt_batch_step",
               "rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy", "rmt_server_create", "rmt_server_set_option",
@@ -184,6 +187,7 @@ def make_grid_desc(scene: dict, stream: int = 0) -> rmt_grid_desc:
     d.mg_fixed_cycles = scene.get("mg_fixed_cycles", 0)
     d.mg_fixed_cycles_fe = scene.get("mg_fixed_cycles_fe", 0)
     d.cuda_stream = stream or None
+    d.wall_dw = scene.get("wall_dw", 0.0)
     return d
 
 
@@ -197,6 +201,7 @@ def make_solid_desc(s: dict) -> rmt_solid_desc:
     o.active_A = s.get("active_A", 0.0)
     o.active_omega = s.get("active_omega", 0.0)
     o.active_len = s.get("active_len", 1.0)
+    o.rep_A = s.get("rep_A", 0.0)
     return o
 
 

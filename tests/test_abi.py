@@ -5,6 +5,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2104_00095_gb300 import rmt, scenes
@@ -69,3 +70,16 @@ def test_add_solid_validation_is_host_side():
     assert L.rmt_field_len(g, rmt.RMT_F_P) == 17**3
     assert L.rmt_field_len(g, rmt.RMT_F_UFACE_X) == 3 * 17 * 16 * 16
     assert L.rmt_field_len(g, 999) == -1
+
+
+def test_wall_repulsion_helper_matches_the_oracle():
+    """rmt_wall_repulsion (host arithmetic, no GPU) and the oracle's A_rep agree."""
+    import oracle as O
+    from paper_2104_00095_gb300 import rmt
+
+    L = rmt.load()
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        args = [rng.uniform(1e-4, 1e-1), rng.uniform(0, 5), rng.uniform(1e-3, 0.1), rng.uniform(0.01, 0.3),
+                rng.uniform(0.2, 3), rng.uniform(0.5, 1.5), rng.uniform(0, 2), rng.uniform(0, 6)]
+        assert L.rmt_wall_repulsion(*args) == O.lib().orc_rep_accel(*args)

@@ -238,3 +238,23 @@ def test_bench_cycle_counts_stay_close_to_the_converged_solve():
     u, p = run(mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options={"fe_inner": 2, "mac_inner": 5, "graph": 1})
     assert rel_l2(u, u_ref) <= 1e-5
     assert rel_l2(p - p.mean(), p_ref - p_ref.mean()) <= 1e-5
+
+
+@pytest.mark.parametrize("dw_cells", [0.0, 2.0])
+def test_wall_repulsion_parity(dw_cells):
+    """A sphere close to the bottom wall with wall repulsion (SI "Contact with a wall"): state
+    and repulsion field against the oracle, step by step."""
+    n = 24
+    h = 1.0 / n
+    sc = S._box(n, periodic=False)
+    sc.update(dt=0.1 * h, wall_dw=dw_cells * h, gravity=(0.0, 0.0, -1.0))
+    sc["solids"] = [S.solid(S.SPHERE, (0.5, 0.45, 0.2 + 0.3 * h), (0.2,) * 3, rho_s=1.5, G=0.3, rep_A=12.0)]
+    g, o = pair(sc)
+    for s in range(4):
+        g.step(1)
+        assert o.step(1) == 0, o.error()
+        compare_state(g, o, 1, TOL64, tag=f"repulsion step {s + 1}")
+        ar, ao = g.read(rmt.RMT_F_REPULSION), o.read(O.F_REPULSION)
+        assert np.count_nonzero(ao) > 0
+        assert np.array_equal(ar != 0, ao != 0)
+        assert rel_l2(ar, ao) <= TOL64
