@@ -71,6 +71,7 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(GridDesc), C.POINTER(C.c_void_p)]
         L.orc_add_solid.argtypes = [C.c_void_p, C.POINTER(SolidDesc), ip]
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_init_pressure.argtypes = [C.c_void_p, C.c_int, C.c_double, ip]
         L.orc_field_len.argtypes = [C.c_void_p, C.c_int]
         L.orc_field_len.restype = C.c_long
         L.orc_read.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_long]
@@ -175,6 +176,12 @@ class Oracle:
 
     def step(self, nsteps: int = 1) -> int:
         return self._L.orc_step(self._g, nsteps)
+
+    def init_pressure(self, max_iters: int, tol: float):
+        """Initial pressure iterations; returns (status, iterations)."""
+        it = C.c_int()
+        rc = self._L.orc_init_pressure(self._g, max_iters, tol, C.byref(it))
+        return rc, it.value
 
     @property
     def dt(self) -> float:

@@ -1277,6 +1277,74 @@ static int one_step(orc_grid* g) {
   return rc;
 }
 
+/* Initial pressure iterations (SI "Initialization" item 2): a timestep from the initial state
+ * is run with the current estimate of p^{-1/2}; its p^{1/2} becomes the next estimate and
+ * every other change is discarded.  Reading of the stopping test (the paper names a tolerance
+ * on the divergence of u^0, which the iterations do not change): stop once the estimate moves
+ * by at most tol relative, ||p_k - p_{k-1}||_2 <= tol ||p_k||_2, or after max_iters
+ * iterations.  The projection computes pressure increments (p += psi), the variant the paper
+ * asks for. */
+int orc_init_pressure(orc_grid* g, int max_iters, double tol, int* iters_out) {
+  if (!g || max_iters < 0) return EINVAL_;
+  ensure_init(g);
+  if (g->step != 0) return ESTATE_;
+  const long N = g->N, NN = g->NN;
+  double* u0[3];
+  for (int a = 0; a < 3; a++) { u0[a] = dalloc(N); memcpy(u0[a], g->u[a], sizeof(double) * N); }
+  double* rho0 = dalloc(N);
+  memcpy(rho0, g->rho, sizeof(double) * N);
+  double** xi0 = (double**)calloc((size_t)(g->nsol > 0 ? g->nsol : 1) * 4, sizeof(double*));
+  signed char** lay0 = (signed char**)calloc((size_t)(g->nsol > 0 ? g->nsol : 1), sizeof(signed char*));
+  for (int m = 0; m < g->nsol; m++) {
+    solid* S = &g->sol[m];
+    for (int a = 0; a < 3; a++) { xi0[4 * m + a] = dalloc(N); memcpy(xi0[4 * m + a], S->xi[a], sizeof(double) * N); }
+    xi0[4 * m + 3] = dalloc(N);
+    memcpy(xi0[4 * m + 3], S->phi, sizeof(double) * N);
+    lay0[m] = calloc8(N);
+    memcpy(lay0[m], S->lay, (size_t)N);
+  }
+  double* prev = dalloc(NN);
+  int it = 0, rc = OK;
+  const int degen0 = g->degenerate;
+  while (it < max_iters) {
+    memcpy(prev, g->p, sizeof(double) * NN);
+    rc = one_step(g);
+    it++;
+    /* keep p^{1/2}; restore everything else */
+    for (int a = 0; a < 3; a++) memcpy(g->u[a], u0[a], sizeof(double) * N);
+    memcpy(g->rho, rho0, sizeof(double) * N);
+    for (int m = 0; m < g->nsol; m++) {
+      solid* S = &g->sol[m];
+      for (int a = 0; a < 3; a++) memcpy(S->xi[a], xi0[4 * m + a], sizeof(double) * N);
+      memcpy(S->phi, xi0[4 * m + 3], sizeof(double) * N);
+      memcpy(S->lay, lay0[m], (size_t)N);
+    }
+    g->t = 0.0;
+    g->step = 0;
+    if (rc != OK) break;
+    double dn = 0.0, pn = 0.0;
+    for (long i = 0; i < NN; i++) {
+      const double dv = g->p[i] - prev[i];
+      dn += dv * dv;
+      pn += g->p[i] * g->p[i];
+    }
+    if (dn <= tol * tol * pn) break;
+  }
+  g->degenerate = degen0 > g->degenerate ? degen0 : g->degenerate;
+  for (int a = 0; a < 3; a++) free(u0[a]);
+  free(rho0);
+  for (int m = 0; m < g->nsol; m++) {
+    for (int q = 0; q < 4; q++) free(xi0[4 * m + q]);
+    free(lay0[m]);
+  }
+  free(xi0);
+  free(lay0);
+  free(prev);
+  if (iters_out) *iters_out = it;
+  if (rc != OK) snprintf(g->err, sizeof g->err, "linear solve did not converge in the initial pressure iterations");
+  return rc;
+}
+
 int orc_step(orc_grid* g, int nsteps) {
   if (!g) return EINVAL_;
   ensure_init(g);

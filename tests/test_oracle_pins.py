@@ -559,3 +559,54 @@ def test_repulsion_pushes_the_body_off_the_wall():
         w[rep] = u[2][lay == 0].mean()
     assert abs(w[0.0]) < 1e-12
     assert w[8.0] > 1e-4
+
+
+# --------------------------------------------------------------------------- initial pressure
+def _taylor_green(n, iters, tol):
+    """2-D Taylor-Green vortex u = (sin x cos y, -cos x sin y, 0) in a periodic [0,2pi]^2 box
+    (4 cells deep); its pressure is p = (cos 2x + cos 2y)/4 (rho = 1)."""
+    Lx = 2 * np.pi
+    h = Lx / n
+    sc = S._box(n, periodic=True)
+    sc.update(n=(n, n, 4), hi=(Lx, Lx, 4 * h), mu=0.01, dt=0.1 * h)
+    o = O.Oracle(sc)
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u = np.zeros((3, 4, n, n))
+    u[0] = np.sin(X) * np.cos(Y)
+    u[1] = -np.cos(X) * np.sin(Y)
+    o.write(O.F_U, u.reshape(-1))
+    rc, it = o.init_pressure(iters, tol)
+    p = o.read(O.F_P).reshape(4, n, n)
+    xn = np.arange(n) * h
+    Xn, Yn = np.meshgrid(xn, xn, indexing="xy")
+    pe = 0.25 * (np.cos(2 * Xn) + np.cos(2 * Yn))
+    return rc, it, np.abs(p - (pe - pe.mean())[None]).max(), o, u
+
+
+def test_initial_pressure_iterations_recover_the_taylor_green_pressure():
+    """SI "Initialization" item 2: the iterations turn p = 0 into the pressure the velocity
+    field needs; for the Taylor-Green vortex that is known in closed form, and the error falls
+    at second order with h."""
+    rc16, it16, e16, o, u = _taylor_green(16, 30, 1e-6)
+    rc32, it32, e32, _, _ = _taylor_green(32, 30, 1e-6)
+    assert rc16 == 0 and rc32 == 0
+    assert it16 < 30 and it32 < 30  # the estimate converged before the cap
+    assert e16 < 0.02 and e32 < 0.006  # amplitude of p is 0.5
+    assert e16 / e32 > 3.0
+    # nothing but p changed
+    assert np.array_equal(o.read(O.F_U), u.reshape(-1))
+
+
+def test_initial_pressure_iterations_leave_a_quiescent_state_alone():
+    sc = S.cavity_sphere(16)
+    sc["wall_u"] = [[0.0] * 3 for _ in range(6)]
+    o = O.Oracle(sc)
+    before = {f: o.read(f) for f in (O.F_U, O.F_RHO)}
+    xi = o.read(O.F_XI, 0)
+    rc, it = o.init_pressure(5, 1e-8)
+    assert rc == 0 and 1 <= it <= 5
+    assert np.abs(o.read(O.F_P)).max() < 1e-10  # rounding noise of a state at rest
+    for f, v in before.items():
+        assert np.array_equal(o.read(f), v)
+    assert np.array_equal(o.read(O.F_XI, 0), xi, equal_nan=True)
