@@ -96,6 +96,16 @@ rmt_status rmt_add_solid(rmt_grid* g, const rmt_solid_desc* s, int* solid_id);
  * its residual norm back to the host once per cycle. */
 rmt_status rmt_step(rmt_grid* g, int nsteps);
 
+/* Initial pressure iterations (SI "Initialization" item 2), before the first step: a timestep
+ * from the initial state is run with the current estimate of p^{-1/2}; its p^{1/2} becomes
+ * the next estimate and every other change is undone (velocity, density, reference maps,
+ * time).  Stops once the estimate moves by at most tol relative (||p_k - p_{k-1}||_2 <=
+ * tol ||p_k||_2; the paper names a tolerance on the divergence of u^0, which these iterations
+ * do not change) or after max_iters iterations; iters_out receives the count.  Synchronous.
+ * Errors: RMT_EINVAL, RMT_ESTATE (after the first step, or for a batch member), and those of
+ * rmt_step. */
+rmt_status rmt_init_pressure(rmt_grid* g, int max_iters, double tol, int* iters_out);
+
 enum {
   RMT_F_U = 1, RMT_F_P = 2, RMT_F_RHO = 3, RMT_F_XI = 4, RMT_F_PHI = 5, RMT_F_LAYER = 6,
   /* intermediates of the last step (same meaning as the oracle's) */

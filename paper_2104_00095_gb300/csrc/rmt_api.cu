@@ -808,6 +808,72 @@ rmt_status rmt_step(rmt_grid* g, int nsteps) {
   return RMT_OK;
 }
 
+rmt_status rmt_init_pressure(rmt_grid* g, int max_iters, double tol, int* iters_out) {
+  if (!g || max_iters < 0 || !(tol >= 0.0)) return RMT_EINVAL;
+  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
+  if (g->sticky != RMT_OK) return RMT_ESTATE;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  if (g->step != 0) return refuse(g, "initial pressure iterations run before the first step");
+  const Geo& G = g->g;
+  const size_t e = g->esz;
+  void *u0 = nullptr, *rho0 = nullptr;
+  CK(g, cudaMalloc(&u0, 3 * G.N * e));
+  if (cudaMalloc(&rho0, G.N * e) != cudaSuccess) {
+    cudaFree(u0);
+    return fail(g, RMT_ENOMEM, "initial pressure iterations: no memory for the saved state");
+  }
+  std::vector<double> prev((size_t)G.NN), cur((size_t)G.NN);
+  auto read_p = [&](std::vector<double>& dst) -> rmt_status {
+    rmt_status s2 = g->fp32 ? gather_t<float>(g, RMT_F_P, 0, g->stage) : gather_t<double>(g, RMT_F_P, 0, g->stage);
+    if (s2 != RMT_OK) return s2;
+    CK(g, cudaMemcpyAsync(dst.data(), g->stage, G.NN * sizeof(double), cudaMemcpyDeviceToHost, g->s));
+    CK(g, cudaStreamSynchronize(g->s));
+    return RMT_OK;
+  };
+  int it = 0;
+  st = RMT_OK;
+  if (cudaMemcpyAsync(u0, g->u, 3 * G.N * e, cudaMemcpyDeviceToDevice, g->s) != cudaSuccess ||
+      cudaMemcpyAsync(rho0, g->rho, G.N * e, cudaMemcpyDeviceToDevice, g->s) != cudaSuccess)
+    st = fail(g, RMT_ECUDA, "initial pressure iterations: saving the state failed");
+  if (st == RMT_OK) st = read_p(prev);
+  while (st == RMT_OK && it < max_iters) {
+    // a step from the initial state with the current estimate of p^{-1/2} ...
+    const int prof = g->prof.on;
+    g->prof.on = 0;
+    st = g->fp32 ? step_t<float>(g) : step_t<double>(g);
+    g->prof.on = prof;
+    it++;
+    // ... keeps only p^{1/2}: u, rho, the reference maps (their parity), time and step count
+    // return to the initial state
+    g->par = 1 - g->par;
+    g->t = 0.0;
+    g->step = 0;
+    if (cudaMemcpyAsync(g->u, u0, 3 * G.N * e, cudaMemcpyDeviceToDevice, g->s) != cudaSuccess ||
+        cudaMemcpyAsync(g->rho, rho0, G.N * e, cudaMemcpyDeviceToDevice, g->s) != cudaSuccess ||
+        cudaMemsetAsync(g->t_d, 0, sizeof(double), g->s) != cudaSuccess) {
+      st = fail(g, RMT_ECUDA, "initial pressure iterations: restoring the state failed");
+      break;
+    }
+    if (st != RMT_OK) break;
+    if ((st = read_p(cur)) != RMT_OK) break;
+    double dn = 0.0, pn = 0.0;
+    for (long q = 0; q < G.NN; q++) {
+      const double dv = cur[q] - prev[q];
+      dn += dv * dv;
+      pn += cur[q] * cur[q];
+    }
+    if (dn <= tol * tol * pn) break;
+    prev.swap(cur);
+  }
+  cudaStreamSynchronize(g->s);
+  cudaFree(u0);
+  cudaFree(rho0);
+  if (iters_out) *iters_out = it;
+  if (st != RMT_OK) return st;
+  return check_err(g);
+}
+
 long rmt_field_len(rmt_grid* g, int field) {
   if (!g) return -1;
   const Geo& G = g->g;

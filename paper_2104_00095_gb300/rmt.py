@@ -33,7 +33,7 @@ EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt
            "rmt_batch_last_error", "rmt_server_create", "rmt_server_set_option", "rmt_server_submit",
            "rmt_server_poll", "rmt_server_job", "rmt_server_job_grid", "rmt_server_release",
            "rmt_server_resident_bytes", "rmt_server_clock", "rmt_server_cell_steps", "rmt_server_destroy",
-           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats", "rmt_wall_repulsion")
+           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats", "rmt_wall_repulsion", "rmt_init_pressure")
 
 
 class rmt_grid_desc(C.Structure):
@@ -151,6 +151,8 @@ def load(build: bool = True):
     L.rmt_server_stats.argtypes = [vp, C.POINTER(rmt_server_stats_t)]
     L.rmt_server_stats.restype = C.c_int
     L.rmt_autotune.argtypes = [vp, C.c_double, C.POINTER(rmt_tune_result)]
+    L.rmt_init_pressure.argtypes = [vp, C.c_int, C.c_double, C.POINTER(C.c_int)]
+    L.rmt_init_pressure.restype = C.c_int
     L.rmt_wall_repulsion.argtypes = [C.c_double] * 8
     L.rmt_wall_repulsion.restype = C.c_double
     for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
@@ -250,6 +252,12 @@ class Grid:
 
     def step(self, nsteps: int = 1):
         self._check("rmt_step", self._L.rmt_step(self._g, nsteps))
+
+    def init_pressure(self, max_iters: int, tol: float) -> int:
+        """Initial pressure iterations before the first step; returns the iteration count."""
+        it = C.c_int()
+        self._check("rmt_init_pressure", self._L.rmt_init_pressure(self._g, int(max_iters), float(tol), C.byref(it)))
+        return it.value
 
     def field_len(self, field: int) -> int:
         return self._L.rmt_field_len(self._g, field)

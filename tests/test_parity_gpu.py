@@ -258,3 +258,19 @@ def test_wall_repulsion_parity(dw_cells):
         assert np.count_nonzero(ao) > 0
         assert np.array_equal(ar != 0, ao != 0)
         assert rel_l2(ar, ao) <= TOL64
+
+
+def test_initial_pressure_iterations_parity():
+    """SI "Initialization" item 2 on both paths: same iteration count, same pressure, and the
+    steps after it stay in parity."""
+    sc = S.cavity_sphere(24)
+    g, o = pair(sc)
+    it_g = g.init_pressure(8, 1e-4)
+    rc, it_o = o.init_pressure(8, 1e-4)
+    assert rc == 0 and it_g == it_o >= 2
+    assert rel_l2(g.read(rmt.RMT_F_P), o.read(O.F_P)) <= TOL64
+    compare_state(g, o, 1, TOL64, tag="after the initial pressure iterations")
+    for s in range(2):
+        g.step(1)
+        assert o.step(1) == 0
+        compare_state(g, o, 1, TOL64, tag=f"step {s + 1} after them")
