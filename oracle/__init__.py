@@ -72,6 +72,7 @@ def lib():
         L.orc_add_solid.argtypes = [C.c_void_p, C.POINTER(SolidDesc), ip]
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_init_pressure.argtypes = [C.c_void_p, C.c_int, C.c_double, ip]
+        L.orc_body_stats.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_field_len.argtypes = [C.c_void_p, C.c_int]
         L.orc_field_len.restype = C.c_long
         L.orc_read.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_long]
@@ -176,6 +177,14 @@ class Oracle:
 
     def step(self, nsteps: int = 1) -> int:
         return self._L.orc_step(self._g, nsteps)
+
+    def body_stats(self, solid: int = 0) -> np.ndarray:
+        """[centroid velocity x, y, z, active power, volume] of one body."""
+        out = np.zeros(5)
+        rc = self._L.orc_body_stats(self._g, solid, _dp(out))
+        if rc != 0:
+            raise ValueError(f"orc_body_stats failed ({rc})")
+        return out
 
     def init_pressure(self, max_iters: int, tol: float):
         """Initial pressure iterations; returns (status, iterations)."""

@@ -1345,6 +1345,92 @@ int orc_init_pressure(orc_grid* g, int max_iters, double tol, int* iters_out) {
   return rc;
 }
 
+/* Swimmer diagnostics of one body at the current step (main text "Swimming"; SI "Swimming
+ * statistics"): out[0..2] the centroid velocity, out[3] the active power
+ * P = -int sigma_a : grad u dV, out[4] the body's volume.  Reading (the paper defines neither
+ * the centroid velocity nor the solid region of the integral on the grid): both weight each
+ * cell by the body's solid fraction 1 - H_eps(phi) (the blending weight of its stress), over
+ * the cells holding the body's xi; grad xi and grad u are centred differences over the two
+ * neighbouring cells (velocity ghosts at walls); sigma_a is the active stress of the stress
+ * calculation evaluated at the cell centre at the current time. */
+int orc_body_stats(orc_grid* g, int sid, double* out) {
+  if (!g || !out || sid < 0) return EINVAL_;
+  ensure_init(g);
+  if (sid >= g->nsol) return EINVAL_;
+  const solid* S = &g->sol[sid];
+  const double h = g->h;
+  double wu[3] = {0.0, 0.0, 0.0}, ws = 0.0, pw = 0.0;
+  for (int k = 0; k < g->n[2]; k++)
+    for (int j = 0; j < g->n[1]; j++)
+      for (int i = 0; i < g->n[0]; i++) {
+        const long c = cidx(g, i, j, k);
+        if (S->lay[c] < 0) continue;
+        const double w = 1.0 - orc_heaviside(S->phi[c], g->eps);
+        if (!(w > 0.0)) continue;
+        for (int a = 0; a < 3; a++) wu[a] += w * g->u[a][c];
+        ws += w;
+        if (S->d.active_A == 0.0) continue;
+        /* grad xi at the cell: A[3a+d] = d xi_a / d x_d */
+        double A[9];
+        int ok = 1;
+        const int ii[3] = {i, j, k};
+        for (int d = 0; d < 3 && ok; d++) {
+          int p[3] = {ii[0], ii[1], ii[2]}, m[3] = {ii[0], ii[1], ii[2]};
+          p[d]++; m[d]--;
+          double xp[3], xm[3];
+          if (!xval(g, S->xi, S->lay, 0, p[0], p[1], p[2], &xp[0]) || !xval(g, S->xi, S->lay, 0, m[0], m[1], m[2], &xm[0])) {
+            ok = 0;
+            break;
+          }
+          for (int a = 1; a < 3; a++) {
+            xval(g, S->xi, S->lay, a, p[0], p[1], p[2], &xp[a]);
+            xval(g, S->xi, S->lay, a, m[0], m[1], m[2], &xm[a]);
+          }
+          for (int a = 0; a < 3; a++) A[3 * a + d] = (xp[a] - xm[a]) / (2.0 * h);
+        }
+        if (!ok) continue;
+        const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                           A[2] * (A[3] * A[7] - A[4] * A[6]);
+        if (det == 0.0) continue;
+        double F[9];
+        F[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+        F[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+        F[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+        F[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+        F[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+        F[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+        F[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+        F[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+        F[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+        const double* R = S->d.rot;
+        const double r[3] = {S->xi[0][c] - S->d.center[0], S->xi[1][c] - S->d.center[1], S->xi[2][c] - S->d.center[2]};
+        const double Xb = R[0] * r[0] + R[3] * r[1] + R[6] * r[2];
+        const double Zb = R[2] * r[0] + R[5] * r[1] + R[8] * r[2];
+        const double s0 = S->d.active_A * sin(2.0 * M_PI * Xb / S->d.active_len - S->d.active_omega * g->t);
+        const double EX[3] = {R[0], R[3], R[6]};
+        double f[3];
+        for (int a = 0; a < 3; a++) f[a] = F[3 * a] * EX[0] + F[3 * a + 1] * EX[1] + F[3 * a + 2] * EX[2];
+        const double fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        const double amp = 1.5 * Zb * s0;
+        /* grad u at the cell: gu[3a+d] = d u_a / d x_d */
+        double sg = 0.0;
+        for (int a = 0; a < 3; a++)
+          for (int d = 0; d < 3; d++) {
+            int p[3] = {ii[0], ii[1], ii[2]}, m[3] = {ii[0], ii[1], ii[2]};
+            p[d]++; m[d]--;
+            const double gu = (uval(g, a, p[0], p[1], p[2]) - uval(g, a, m[0], m[1], m[2])) / (2.0 * h);
+            const double sig = amp * ((f[a] / fn) * (f[d] / fn) - (a == d ? 1.0 / 3.0 : 0.0));
+            sg += sig * gu;
+          }
+        pw += w * sg;
+      }
+  const double dv = h * h * h;
+  for (int a = 0; a < 3; a++) out[a] = ws > 0.0 ? wu[a] / ws : 0.0;
+  out[3] = -pw * dv;
+  out[4] = ws * dv;
+  return OK;
+}
+
 int orc_step(orc_grid* g, int nsteps) {
   if (!g) return EINVAL_;
   ensure_init(g);

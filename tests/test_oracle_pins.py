@@ -610,3 +610,78 @@ def test_initial_pressure_iterations_leave_a_quiescent_state_alone():
     for f, v in before.items():
         assert np.array_equal(o.read(f), v)
     assert np.array_equal(o.read(O.F_XI, 0), xi, equal_nan=True)
+
+
+# --------------------------------------------------------------------------- swimmer diagnostics
+def _solid_fraction(phi, eps):
+    """1 - H_eps(phi) of eq. sm_heavi, written out here."""
+    H = np.where(phi <= -eps, 0.0, np.where(phi >= eps, 1.0,
+                 0.5 * (1 + phi / eps + np.sin(np.pi * phi / eps) / np.pi)))
+    return 1.0 - H
+
+
+def test_body_stats_uniform_flow_and_volume():
+    """A uniform velocity is the centroid velocity of every body and does no active work; the
+    volume is the integral of the solid fraction (close to 4/3 pi R^3)."""
+    n = 24
+    sc = S._box(n, periodic=True)
+    sc.update(dt=0.2 / n)
+    R = 0.25
+    sc["solids"] = [S.solid(S.SPHERE, (0.5, 0.5, 0.5), (R,) * 3, active_A=0.7, active_omega=2 * np.pi,
+                            active_len=0.5)]
+    o = O.Oracle(sc)
+    U = np.array([0.3, -0.1, 0.2])
+    o.write(O.F_U, np.repeat(U, n ** 3))
+    st = o.body_stats(0)
+    assert np.allclose(st[:3], U, rtol=0, atol=1e-14)
+    assert st[3] == 0.0
+    phi, lay = o.read(O.F_PHI, 0), o.read(O.F_LAYER, 0)
+    w = np.where(lay >= 0, _solid_fraction(phi, 1.5 / n), 0.0)
+    assert st[4] == pytest.approx(w.sum() / n ** 3, rel=1e-13)
+    assert st[4] == pytest.approx(4 / 3 * np.pi * R ** 3, rel=0.05)  # blur of 1.5 h
+
+
+def test_body_stats_active_power_brute_force():
+    """u = (c X^2 Z, 0, 0) on an undeformed body aligned with the axes: only the xx active
+    stress acts, and sigma_a : grad u = (3/2) Z sigma_0(X) (2/3) 2 c X Z = 2 c X Z^2 sigma_0(X)
+    (the centred difference of a quadratic is exact), summed by hand over the solid fraction."""
+    n = 32
+    sc = S._box(n, periodic=True)
+    sc.update(dt=0.2 / n)
+    ctr = np.array([0.5, 0.5, 0.5])
+    A_, w_, l_ = 0.7, 2 * np.pi, 0.45
+    sc["solids"] = [S.solid(S.ELLIPSOID, ctr, (0.3, 0.12, 0.12), active_A=A_, active_omega=w_, active_len=l_)]
+    o = O.Oracle(sc)
+    x = (np.arange(n) + 0.5) / n
+    Z3, Y3, X3 = np.meshgrid(x, x, x, indexing="ij")
+    Xr, Zr = X3 - ctr[0], Z3 - ctr[2]
+    c = 0.8
+    u = np.zeros((3, n, n, n))
+    u[0] = c * Xr ** 2 * Zr
+    o.write(O.F_U, u.reshape(-1))
+    st = o.body_stats(0)
+    phi, lay = o.read(O.F_PHI, 0).reshape(n, n, n), o.read(O.F_LAYER, 0).reshape(n, n, n)
+    wfrac = np.where(lay >= 0, _solid_fraction(phi, 1.5 / n), 0.0)
+    s0 = A_ * np.sin(2 * np.pi * Xr / l_)  # t = 0
+    P = -np.sum(wfrac * 2 * c * Xr * Zr ** 2 * s0) / n ** 3
+    assert abs(P) > 1e-6
+    assert st[3] == pytest.approx(P, rel=1e-12)
+    # a flow whose stretching is odd in X does no net work on this symmetric body
+    u[0] = c * Xr * Zr
+    o.write(O.F_U, u.reshape(-1))
+    assert abs(o.body_stats(0)[3]) < 1e-12 * abs(P) + 1e-18
+
+
+def test_body_stats_rigid_rotation_has_no_centroid_velocity():
+    n = 24
+    sc = S._box(n, periodic=True)
+    sc.update(dt=0.2 / n)
+    sc["solids"] = [S.solid(S.SPHERE, (0.5, 0.5, 0.5), (0.25,) * 3)]
+    o = O.Oracle(sc)
+    x = (np.arange(n) + 0.5) / n - 0.5
+    Z3, Y3, X3 = np.meshgrid(x, x, x, indexing="ij")
+    om = np.array([0.3, -0.5, 0.8])
+    u = np.stack([om[1] * Z3 - om[2] * Y3, om[2] * X3 - om[0] * Z3, om[0] * Y3 - om[1] * X3])
+    o.write(O.F_U, u.reshape(-1))
+    st = o.body_stats(0)
+    assert np.abs(st[:3]).max() < 1e-14
