@@ -179,8 +179,9 @@ class Oracle:
         return self._L.orc_step(self._g, nsteps)
 
     def body_stats(self, solid: int = 0) -> np.ndarray:
-        """[centroid velocity x, y, z, active power, volume] of one body."""
-        out = np.zeros(5)
+        """[centroid velocity x, y, z, active power, volume, elastic energy, RMS of J - 1] of
+        one body."""
+        out = np.zeros(7)
         rc = self._L.orc_body_stats(self._g, solid, _dp(out))
         if rc != 0:
             raise ValueError(f"orc_body_stats failed ({rc})")

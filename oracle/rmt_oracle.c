@@ -1345,21 +1345,24 @@ int orc_init_pressure(orc_grid* g, int max_iters, double tol, int* iters_out) {
   return rc;
 }
 
-/* Swimmer diagnostics of one body at the current step (main text "Swimming"; SI "Swimming
- * statistics"): out[0..2] the centroid velocity, out[3] the active power
- * P = -int sigma_a : grad u dV, out[4] the body's volume.  Reading (the paper defines neither
- * the centroid velocity nor the solid region of the integral on the grid): both weight each
- * cell by the body's solid fraction 1 - H_eps(phi) (the blending weight of its stress), over
- * the cells holding the body's xi; grad xi and grad u are centred differences over the two
- * neighbouring cells (velocity ghosts at walls); sigma_a is the active stress of the stress
- * calculation evaluated at the cell centre at the current time. */
+/* Diagnostics of one body at the current step (main text "Swimming"; SI "Swimming
+ * statistics"; SI "Pre-stretched sphere", eq. elas): out[0..2] the centroid velocity, out[3]
+ * the active power P = -int sigma_a : grad u dV, out[4] the body's volume, out[5] its elastic
+ * energy int Phi_elas dV with Phi_elas = G/2 (tr(F^T F) - 3 - 2 ln J), out[6] the RMS of
+ * J - 1 over the body.  Reading (the paper defines neither the centroid velocity nor the solid
+ * region of the integrals on the grid): every sum weights a cell by the body's solid fraction
+ * 1 - H_eps(phi) (the blending weight of its stress), over the cells holding the body's xi;
+ * grad xi and grad u are centred differences over the two neighbouring cells (velocity ghosts
+ * at walls), F = (grad xi)^-1 and J = det F; a cell whose grad xi is missing or has det <= 0
+ * adds to the centroid velocity and the volume only; sigma_a is the active stress of the
+ * stress calculation evaluated at the cell centre at the current time. */
 int orc_body_stats(orc_grid* g, int sid, double* out) {
   if (!g || !out || sid < 0) return EINVAL_;
   ensure_init(g);
   if (sid >= g->nsol) return EINVAL_;
   const solid* S = &g->sol[sid];
-  const double h = g->h;
-  double wu[3] = {0.0, 0.0, 0.0}, ws = 0.0, pw = 0.0;
+  const double h = g->h, G = S->d.G;
+  double wu[3] = {0.0, 0.0, 0.0}, ws = 0.0, pw = 0.0, en = 0.0, wj = 0.0, jj = 0.0;
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1369,7 +1372,6 @@ int orc_body_stats(orc_grid* g, int sid, double* out) {
         if (!(w > 0.0)) continue;
         for (int a = 0; a < 3; a++) wu[a] += w * g->u[a][c];
         ws += w;
-        if (S->d.active_A == 0.0) continue;
         /* grad xi at the cell: A[3a+d] = d xi_a / d x_d */
         double A[9];
         int ok = 1;
@@ -1391,7 +1393,7 @@ int orc_body_stats(orc_grid* g, int sid, double* out) {
         if (!ok) continue;
         const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                            A[2] * (A[3] * A[7] - A[4] * A[6]);
-        if (det == 0.0) continue;
+        if (!(det > 0.0)) continue;
         double F[9];
         F[0] = (A[4] * A[8] - A[5] * A[7]) / det;
         F[1] = (A[2] * A[7] - A[1] * A[8]) / det;
@@ -1402,6 +1404,14 @@ int orc_body_stats(orc_grid* g, int sid, double* out) {
         F[6] = (A[3] * A[7] - A[4] * A[6]) / det;
         F[7] = (A[1] * A[6] - A[0] * A[7]) / det;
         F[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+        /* eq. elas: tr(C) = sum of the squares of F's entries; J = det F = 1 / det(grad xi) */
+        double trC = 0.0;
+        for (int q = 0; q < 9; q++) trC += F[q] * F[q];
+        const double J = 1.0 / det;
+        en += w * 0.5 * G * (trC - 3.0 - 2.0 * log(J));
+        wj += w;
+        jj += w * (J - 1.0) * (J - 1.0);
+        if (S->d.active_A == 0.0) continue;
         const double* R = S->d.rot;
         const double r[3] = {S->xi[0][c] - S->d.center[0], S->xi[1][c] - S->d.center[1], S->xi[2][c] - S->d.center[2]};
         const double Xb = R[0] * r[0] + R[3] * r[1] + R[6] * r[2];
@@ -1428,6 +1438,8 @@ int orc_body_stats(orc_grid* g, int sid, double* out) {
   for (int a = 0; a < 3; a++) out[a] = ws > 0.0 ? wu[a] / ws : 0.0;
   out[3] = -pw * dv;
   out[4] = ws * dv;
+  out[5] = en * dv;
+  out[6] = wj > 0.0 ? sqrt(jj / wj) : 0.0;
   return OK;
 }
 

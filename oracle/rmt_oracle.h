@@ -70,8 +70,9 @@ int  orc_add_solid(orc_grid* g, const orc_solid_desc* s, int* id);
 int  orc_step(orc_grid* g, int nsteps);
 /* initial pressure iterations before the first step; iters_out receives the count */
 int  orc_init_pressure(orc_grid* g, int max_iters, double tol, int* iters_out);
-/* swimmer diagnostics of one body: centroid velocity (3), active power, volume */
-int  orc_body_stats(orc_grid* g, int solid, double* out5);
+/* diagnostics of one body: centroid velocity (3), active power, volume, elastic energy,
+ * RMS of J - 1 */
+int  orc_body_stats(orc_grid* g, int solid, double* out7);
 long orc_field_len(orc_grid* g, int field);
 int  orc_read(orc_grid* g, int field, int solid, double* dst, long n);
 int  orc_write(orc_grid* g, int field, int solid, const double* src, long n);

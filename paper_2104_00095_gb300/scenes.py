@@ -190,3 +190,50 @@ def scaled(scene: dict, n: int) -> dict:
     if scene.get("dt", 0.0) > 0.0:
         s["dt"] = scene["dt"] * scene["n"][0] / n
     return s
+
+
+# Table str_params of the SI ("Pre-stretched sphere"): mu, rho_s / rho_f, R, G per case
+STR_PARAMS = {
+    "A1": (0.005, 1.0, 0.2, 0.25), "A2": (0.01, 1.0, 0.2, 1.0), "A3": (0.005, 1.0, 0.1, 1.0),
+    "A4": (0.0075, 1.0, 0.3, 0.25), "B1": (0.005, 1.0, 0.1, 0.25), "B2": (0.02, 1.0, 0.2, 2.5),
+    "B3": (0.005, 1.0, 0.3, 0.25), "C1": (0.005, 0.5625, 4.0 / 15.0, 0.25), "C2": (0.005, 2.25, 2.0 / 15.0, 0.25),
+}
+
+
+def prestretched_sphere(n: int = 32, case: str = "A2", dt: float = 0.0, precision: str = "fp64") -> dict:
+    """Pre-stretched sphere (SI "Pre-stretched sphere"; Table str_params): periodic unit box,
+    rho_f = 1, one neo-Hookean sphere of radius R at the centre with mu_a = mu and gamma_t = 0,
+    released from rest at t = 0 in a volume-preserving stretch (see prestretch_xi).  The
+    scene's sphere is the reference (unstretched) body."""
+    mu, rs, R, G = STR_PARAMS[case]
+    s = _box(n, periodic=True)
+    s.update(mu=mu, dt=dt, precision=precision)
+    s["solids"] = [solid(SPHERE, (0.5, 0.5, 0.5), (R, R, R), rho_s=rs, G=G, mu_a=mu)]
+    return s
+
+
+def prestretch_xi(scene: dict, lam: float = 1.21) -> np.ndarray:
+    """Initial reference map of a body stretched by lam along x and by 1/sqrt(lam) along y and
+    z about its centre: xi = c + diag(1/lam, sqrt(lam), sqrt(lam)) (x - c) at every cell centre
+    ([3][nz][ny][nx], the layout of the field reads and writes).  The SI text gives lam = 1.21;
+    the caption of its figure says 1.44."""
+    n = scene["n"]
+    c = np.asarray(scene["solids"][0]["center"])
+    h = (np.asarray(scene["hi"]) - np.asarray(scene["lo"])) / np.asarray(n)
+    ax = [scene["lo"][d] + (np.arange(n[d]) + 0.5) * h[d] for d in range(3)]
+    Z3, Y3, X3 = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    inv = (1.0 / lam, np.sqrt(lam), np.sqrt(lam))
+    return np.stack([c[0] + inv[0] * (X3 - c[0]), c[1] + inv[1] * (Y3 - c[1]),
+                     c[2] + inv[2] * (Z3 - c[2])]).reshape(-1)
+
+
+def stokes_sphere(n: int = 48, R: float = 0.1, mu: float = 0.05, rho_s: float = 1.5, G: float = 1.0,
+                  dt: float = 0.0, precision: str = "fp64") -> dict:
+    """One heavy sphere in a triply periodic unit box under gravity -1 in z (a simple cubic
+    array of settling spheres), set up like the main text's settling runs ("Settling sphere in
+    a square cylinder"): rho_f = 1, mu_a = mu, gamma_t = 0, a blur half-width of h/2 and G large
+    enough that the sphere stays nearly rigid."""
+    s = _box(n, periodic=True)
+    s.update(mu=mu, dt=dt, gravity=(0.0, 0.0, -1.0), precision=precision, eps_h=0.5)
+    s["solids"] = [solid(SPHERE, (0.5, 0.5, 0.5), (R, R, R), rho_s=rho_s, G=G, mu_a=mu)]
+    return s

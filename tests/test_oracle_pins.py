@@ -685,3 +685,75 @@ def test_body_stats_rigid_rotation_has_no_centroid_velocity():
     o.write(O.F_U, u.reshape(-1))
     st = o.body_stats(0)
     assert np.abs(st[:3]).max() < 1e-14
+
+
+def _affine_xi(n, ctr, M):
+    """xi = ctr + M (x - ctr) at every cell centre of the periodic unit box ([3][N] layout)."""
+    x = (np.arange(n) + 0.5) / n
+    Z3, Y3, X3 = np.meshgrid(x, x, x, indexing="ij")
+    r = np.stack([X3 - ctr[0], Y3 - ctr[1], Z3 - ctr[2]]).reshape(3, -1)
+    return (np.asarray(ctr)[:, None] + M @ r).reshape(-1)
+
+
+@pytest.mark.parametrize("stretch", ["isochoric", "rotated"])
+def test_body_stats_elastic_energy_of_a_uniform_stretch(stretch):
+    """SI "Pre-stretched sphere", eq. elas: a body deformed by a uniform F has the energy density
+    G/2 (sum_i lambda_i^2 - 3 - 2 ln(lambda_1 lambda_2 lambda_3)) everywhere (lambda_i the
+    principal stretches of F; tr(F^T F) is invariant under rotations), so the energy is that
+    density times the body's volume, and J - 1 = prod lambda_i - 1 at every cell.  The affine
+    reference map is xi = c + F^-1 (x - c)."""
+    n = 32
+    G_ = 1.7
+    sc = S._box(n, periodic=True)
+    sc.update(dt=0.2 / n)
+    ctr = np.array([0.5, 0.5, 0.5])
+    sc["solids"] = [S.solid(S.SPHERE, ctr, (0.2,) * 3, G=G_)]
+    o = O.Oracle(sc)
+    if stretch == "isochoric":  # the paper's pre-stretch: lambda along x, 1/sqrt(lambda) across
+        lam = np.array([1.21, 1.21 ** -0.5, 1.21 ** -0.5])
+        Q = np.eye(3)
+    else:
+        lam = np.array([1.1, 0.93, 1.04])
+        Q = S.random_rotation(np.random.default_rng(3))
+    F = Q @ np.diag(lam) @ Q.T
+    assert o.write(O.F_XI, _affine_xi(n, ctr, np.linalg.inv(F)), 0) == 0
+    st = o.body_stats(0)
+    phi_el = 0.5 * G_ * (np.sum(lam ** 2) - 3 - 2 * np.log(np.prod(lam)))
+    assert phi_el > 0
+    assert st[5] == pytest.approx(phi_el * st[4], rel=1e-10)
+    assert st[6] == pytest.approx(abs(np.prod(lam) - 1), abs=1e-11)
+    assert st[4] == pytest.approx(4 / 3 * np.pi * 0.2 ** 3 * np.prod(lam), rel=0.05)
+
+
+def test_body_stats_undeformed_body_has_no_elastic_energy():
+    n = 24
+    sc = S._box(n, periodic=True)
+    sc.update(dt=0.2 / n)
+    sc["solids"] = [S.solid(S.ELLIPSOID, (0.5, 0.5, 0.5), (0.3, 0.15, 0.1))]
+    o = O.Oracle(sc)
+    st = o.body_stats(0)
+    assert abs(st[5]) < 1e-12 * st[4] and st[6] < 1e-12
+
+
+def test_prestretched_sphere_scaling_is_exact():
+    """SI "Pre-stretched sphere" item 2 (Table str_params, cases A1 and A2): the two runs share
+    R and gamma = R sqrt(rho G) / mu, so with time scaled by tau_diss (A1's step twice A2's)
+    they are the same problem with u scaled by 1/2 and every stress and p by 1/4.  Each factor
+    is a power of two, so the discrete runs agree bit for bit under that scaling: a term with a
+    misplaced dt, mu, G or rho breaks it."""
+    n, h = 16, 1.0 / 16
+    runs = {}
+    for case, dt in (("A2", 0.1 * h), ("A1", 0.2 * h)):
+        sc = S.prestretched_sphere(n, case, dt=dt)
+        o = O.Oracle(sc)
+        assert o.write(O.F_XI, S.prestretch_xi(sc), 0) == 0
+        e0 = o.body_stats(0)[5]
+        assert o.step(3) == 0, o.error()
+        runs[case] = (o.read(O.F_U), o.read(O.F_P), o.read(O.F_XI, 0), e0, o.body_stats(0))
+    (u1, p1, x1, e01, s1), (u2, p2, x2, e02, s2) = runs["A1"], runs["A2"]
+    assert np.abs(u2).max() > 1e-3 and e02 > 0
+    assert np.array_equal(2 * u1, u2)
+    assert np.array_equal(4 * p1, p2)
+    assert np.array_equal(x1, x2, equal_nan=True)
+    assert 4 * e01 == e02 and 4 * s1[5] == s2[5]
+    assert s2[5] < e02  # the stretched sphere starts to relax
