@@ -157,6 +157,23 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
 double rmt_wall_repulsion(double V, double U, double d_w, double L_min, double rho_s, double rho_f, double g,
                           double U_safe);
 
+/* Diagnostics of body solid_id at the grid's current time (main text "Swimming"; SI "Swimming
+ * statistics"; SI "Pre-stretched sphere", eq. elas), written to out[7] (host memory):
+ *   out[0..3)  centroid velocity: sum w u / sum w over the cells that hold the body's reference
+ *              map, w = 1 - H_eps(phi) its solid fraction (eq. heaviside);
+ *   out[3]     active power: -sum w sigma_a : grad u h^3, sigma_a the active stress of the stress
+ *              model at the cell centre and time t (main text "Swimming"), built from F =
+ *              (grad xi)^-1 by centred differences of xi, grad u by centred differences of the
+ *              cell velocities (periodic wrap, mirrored ghost at a wall);
+ *   out[4]     volume: sum w h^3;
+ *   out[5]     elastic energy: sum w G/2 (tr(F^T F) - 3 - 2 ln J) h^3, J = det F (eq. elas);
+ *   out[6]     RMS of J - 1 over the body (weights w).
+ * A cell whose grad xi lacks a neighbour value or has det <= 0 adds to out[0..5) only.  The
+ * sums are taken in FP64 in a fixed order (deterministic).  A passive body (active_A = 0) gives
+ * zero power.  Synchronous (a batch member waits for its batch's queued steps).
+ * Errors: RMT_EINVAL (null, bad solid id), RMT_ECUDA. */
+rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]);
+
 /* Autotuner of the two multigrid solves (no paper counterpart: the paper's multigrid library
  * is not described).  On the right-hand sides of the grid's last step (RMT_ESTATE before the
  * first step) it tries, per solver, smoother sweeps before/after the coarse correction (1..4

@@ -909,6 +909,45 @@ rmt_status rmt_read_fields(rmt_grid* g, int field, int solid_id, void* dst, size
   return RMT_OK;
 }
 
+rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]) {
+  if (!g || !out) return RMT_EINVAL;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  if (solid_id < 0 || solid_id >= (int)g->bodies.size()) return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  if (g->in_batch && g->batch_s != g->s) CK(g, cudaStreamSynchronize(g->batch_s));
+  const Geo& G = g->g;
+  const size_t need = body_stats_scratch_bytes();
+  double* scratch = g->stage;
+  double* tmp = nullptr;
+  if ((size_t)g->stage_len * sizeof(double) < need) {
+    CK(g, cudaMalloc(&tmp, need));
+    scratch = tmp;
+  }
+  const Body& b = g->bodies[solid_id];
+  const BodyMem& m = g->bm[solid_id];
+  const int par = g->par;
+  if (g->fp32)
+    launch_body_stats<float>(G, (const float*)g->u, b, BodyView<float>{(const float*)m.X[par], (const float*)m.PHI[par], m.LAY[par]},
+                             g->t_d, scratch, g->s);
+  else
+    launch_body_stats<double>(G, (const double*)g->u, b,
+                              BodyView<double>{(const double*)m.X[par], (const double*)m.PHI[par], m.LAY[par]}, g->t_d,
+                              scratch, g->s);
+  double sums[8];
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sums, scratch, sizeof sums, cudaMemcpyDeviceToHost, g->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(g, RMT_ECUDA, "body statistics: %s", cudaGetErrorString(e));
+  const double dv = G.h * G.h * G.h;
+  for (int a = 0; a < 3; a++) out[a] = sums[3] > 0.0 ? sums[a] / sums[3] : 0.0;
+  out[3] = -sums[4] * dv;
+  out[4] = sums[3] * dv;
+  out[5] = sums[5] * dv;
+  out[6] = sums[6] > 0.0 ? sqrt(sums[7] / sums[6]) : 0.0;
+  return RMT_OK;
+}
+
 rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* src, size_t src_bytes, int src_is_device) {
   if (!g || !src) return RMT_EINVAL;
   if (g->sticky != RMT_OK) return RMT_ESTATE;

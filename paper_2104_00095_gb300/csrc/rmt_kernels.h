@@ -63,6 +63,14 @@ void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* r
 // the wall-repulsion acceleration of every cell from the given bodies' phi, as FP64 (3 N)
 template <typename T>
 void launch_rep_field(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, double* out, cudaStream_t s);
+
+// ---- swimmer diagnostics (rmt_diag.cu) ----------------------------------------------
+// one body's sums [w u (3), w, w sigma_a : grad u, w Phi_elas, w over cells with F, w (J-1)^2]
+// into scratch[0..8) (FP64); scratch holds body_stats_scratch_bytes(); t: device time
+size_t body_stats_scratch_bytes();
+template <typename T>
+void launch_body_stats(const Geo& g, const T* u, const Body& b, const BodyView<T>& v, const double* t, double* scratch,
+                       cudaStream_t s);
 template <typename T>
 void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b, cudaStream_t s);
 template <typename T>

@@ -33,7 +33,8 @@ EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt
            "rmt_batch_last_error", "rmt_server_create", "rmt_server_set_option", "rmt_server_submit",
            "rmt_server_poll", "rmt_server_job", "rmt_server_job_grid", "rmt_server_release",
            "rmt_server_resident_bytes", "rmt_server_clock", "rmt_server_cell_steps", "rmt_server_destroy",
-           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats", "rmt_wall_repulsion", "rmt_init_pressure")
+           "rmt_autotune", "rmt_server_last_error", "rmt_server_stats", "rmt_wall_repulsion", "rmt_init_pressure",
+           "rmt_body_stats")
 
 
 class rmt_grid_desc(C.Structure):
@@ -153,6 +154,8 @@ def load(build: bool = True):
     L.rmt_autotune.argtypes = [vp, C.c_double, C.POINTER(rmt_tune_result)]
     L.rmt_init_pressure.argtypes = [vp, C.c_int, C.c_double, C.POINTER(C.c_int)]
     L.rmt_init_pressure.restype = C.c_int
+    L.rmt_body_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_double)]
+    L.rmt_body_stats.restype = C.c_int
     L.rmt_wall_repulsion.argtypes = [C.c_double] * 8
     L.rmt_wall_repulsion.restype = C.c_double
     for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
@@ -258,6 +261,13 @@ class Grid:
         it = C.c_int()
         self._check("rmt_init_pressure", self._L.rmt_init_pressure(self._g, int(max_iters), float(tol), C.byref(it)))
         return it.value
+
+    def body_stats(self, solid: int = 0) -> np.ndarray:
+        """Diagnostics of one body at the current time: centroid velocity (3), active power,
+        volume, elastic energy, RMS of J - 1."""
+        out = (C.c_double * 7)()
+        self._check("rmt_body_stats", self._L.rmt_body_stats(self._g, int(solid), out))
+        return np.array(out[:], dtype=np.float64)
 
     def field_len(self, field: int) -> int:
         return self._L.rmt_field_len(self._g, field)

@@ -274,3 +274,36 @@ def test_initial_pressure_iterations_parity():
         g.step(1)
         assert o.step(1) == 0
         compare_state(g, o, 1, TOL64, tag=f"step {s + 1} after them")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_body_stats_parity(prec):
+    """Body diagnostics (main text "Swimming"; SI "Swimming statistics"; SI "Pre-stretched
+    sphere", eq. elas) of every active body after a few steps against the oracle's.  FP64: the
+    two states are in parity.  FP32: the GPU state (u and each body's xi) is written into the
+    oracle first, so both evaluate the diagnostics on the same FP32 state (the oracle
+    re-extrapolates the band of the written xi in FP64)."""
+    sc = S.swimmers(n=32, nbodies=2, seed=5, precision=prec)
+    g, o = pair(sc)
+    g.step(3)
+    assert o.step(3) == 0
+    assert o.write(O.F_U, g.read(rmt.RMT_F_U)) == 0
+    if prec == "fp32":
+        for m in range(len(sc["solids"])):
+            assert o.write(O.F_XI, g.read(rmt.RMT_F_XI, m), m) == 0
+    for m in range(len(sc["solids"])):
+        a, b = g.body_stats(m), o.body_stats(m)
+        assert a.shape == (7,) and np.all(np.isfinite(a))
+        assert b[3] != 0.0 and b[4] > 0.0 and b[5] > 0.0 and b[6] > 0.0
+        if prec == "fp64":
+            np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(b[:5]).max())
+        else:
+            # xi is stored to ~1e-7 absolute, so centred differences of it over 2h carry ~3e-6:
+            # J and the (second-order small) elastic energy are compared to that resolution
+            uscale = np.abs(g.read(rmt.RMT_F_U)).max()
+            np.testing.assert_allclose(a[:3], b[:3], rtol=0, atol=1e-6 * uscale)
+            np.testing.assert_allclose(a[3:5], b[3:5], rtol=1e-3)
+            assert abs(a[6] - b[6]) <= 1e-5
+            assert abs(a[5] - b[5]) <= 2e-2 * b[5]
+    # deterministic: the same call twice gives the same bits
+    assert np.array_equal(g.body_stats(0), g.body_stats(0))
