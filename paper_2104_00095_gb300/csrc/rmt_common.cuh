@@ -259,12 +259,14 @@ __device__ __forceinline__ T mc_lim(T qm, T q0, T qp) {
   const T a = qp - q0, b = q0 - qm;
   return (a * b > T(0)) ? T(2) * fmin(fabs(a), fabs(b)) : T(0);
 }
+// sgn(s) min(|x|, y) for y >= 0, written as copysign(min(|x|, y), s): equal to the product form
+// for every s (s = 0 makes the limiters' y vanish, so both give zero, up to the sign of zero)
 template <typename T>
-__device__ __forceinline__ T sgnv(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+__device__ __forceinline__ T sgn_min(T s, T x, T y) { return copysign(fmin(fabs(x), y), s); }
 template <typename T>
 __device__ __forceinline__ T dflim(T qm, T q0, T qp) {
   const T dc = T(0.5) * (qp - qm);
-  return sgnv(dc) * fmin(fabs(dc), mc_lim(qm, q0, qp));
+  return sgn_min(dc, dc, mc_lim(qm, q0, qp));
 }
 template <typename T>
 __device__ __forceinline__ T lim_slope(const T q[5], unsigned okmask, T inv_h) {
@@ -272,11 +274,14 @@ __device__ __forceinline__ T lim_slope(const T q[5], unsigned okmask, T inv_h) {
   if ((okmask & 0xE) != 0xE) return T(0);
   const T dc = T(0.5) * (q[3] - q[1]);
   const T dl = mc_lim(q[1], q[2], q[3]);
-  if ((okmask & 0x11) != 0x11) return sgnv(dc) * fmin(fabs(dc), dl) * inv_h;
+  if ((okmask & 0x11) != 0x11) return sgn_min(dc, dc, dl) * inv_h;
   const T dfp = dflim(q[2], q[3], q[4]);
   const T dfm = dflim(q[0], q[1], q[2]);
-  const T d4 = T(4.0 / 3.0) * dc - (dfp + dfm) / T(6);
-  return sgnv(dc) * fmin(fabs(d4), dl) * inv_h;
+  // FP32: the sixth as a product (a division per slope would dominate the kernel)
+  T d4;
+  if constexpr (sizeof(T) == 4) d4 = T(4.0 / 3.0) * dc - (dfp + dfm) * T(1.0 / 6.0);
+  else d4 = T(4.0 / 3.0) * dc - (dfp + dfm) / T(6);
+  return sgn_min(dc, d4, dl) * inv_h;
 }
 
 // Godunov choice of the normal velocity and upwinding of other quantities

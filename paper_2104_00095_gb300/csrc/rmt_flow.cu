@@ -35,7 +35,18 @@ __device__ __forceinline__ void cell_faces(const Geo& g, int e, int i, int j, in
 template <typename T>
 __device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int a, int d, int i, int j, int k) {
   T q[5];
-  if (inside<T>(g, d, i, j, k, 2)) {
+  if (d == 0 && g.per[0]) {
+    // periodic x: wrap by selects, one path for the whole row (no divergence at its ends)
+    const T* row = u + (long)a * g.N + cidx(g, 0, j, k);
+    const int n0 = g.n[0];
+#pragma unroll
+    for (int s = -2; s <= 2; s++) {
+      int ii = i + s;
+      ii += ii < 0 ? n0 : 0;
+      ii -= ii >= n0 ? n0 : 0;
+      q[s + 2] = row[ii];
+    }
+  } else if (inside<T>(g, d, i, j, k, 2)) {
     const long c = (long)a * g.N + cidx(g, i, j, k);
     const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
 #pragma unroll

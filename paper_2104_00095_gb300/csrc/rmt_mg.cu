@@ -80,21 +80,29 @@ __device__ __forceinline__ CT face_beta(CT ra, CT rb) {
   return CT(2) / (ra + rb);
 }
 
-// MAC at cell (i,j,k): returns (A x)_c (in AT) and its diagonal
+// MAC at cell (i,j,k): returns (A x)_c (in AT) and its diagonal.  Rows away from the y and z
+// boundaries share one path: the two x neighbours come from selects (periodic wrap, or a zero
+// weight at a wall), so a warp whose row reaches i = 0 or n-1 does not diverge.
 template <typename AT, bool FAST = false, typename XT, typename CT>
 __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ rho, int i, int j,
                                      int k, AT& diag) {
   const long c = cix(L, i, j, k);
   const CT rc = rho[c];
   AT off = AT(0), dg = AT(0);
-  if (i > 0 && i + 1 < L.n[0] && j > 0 && j + 1 < L.n[1] && k > 0 && k + 1 < L.n[2]) {
-    // interior: six neighbours at fixed offsets, no boundary rules
-    const long st[3] = {1, (long)L.n[0], (long)L.n[0] * L.n[1]};
+  if (j > 0 && j + 1 < L.n[1] && k > 0 && k + 1 < L.n[2]) {
+    // 32-bit offsets from the cell (a level holds fewer than 2^31 cells); a missing x neighbour
+    // reads the cell itself with weight 0
+    const int sy = L.n[0], sz = L.n[0] * L.n[1];
+    const bool lo = i > 0, hi = i + 1 < L.n[0];
+    const bool hasl = lo || L.per[0], hash = hi || L.per[0];
+    const int off6[6] = {lo ? -1 : (L.per[0] ? L.n[0] - 1 : 0), hi ? 1 : (L.per[0] ? 1 - L.n[0] : 0), -sy, sy, -sz, sz};
+    const CT* rp = rho + c;
+    const XT* xp = x + c;
 #pragma unroll
     for (int f = 0; f < 6; f++) {
-      const long cn = c + ((f & 1) ? st[f >> 1] : -st[f >> 1]);
-      const AT beta = (AT)face_beta<FAST>(rc, rho[cn]);
-      off += beta * (AT)x[cn];
+      const bool has = f == 0 ? hasl : (f == 1 ? hash : true);
+      const AT beta = has ? (AT)face_beta<FAST>(rc, rp[off6[f]]) : AT(0);
+      off += beta * (AT)xp[off6[f]];
       dg += beta;
     }
     const AT ih2 = cv<AT>(L.ih2, L.f_ih2);
@@ -928,7 +936,7 @@ __device__ __forceinline__ double block_sum(A v, double* red) {
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
   __syncthreads();
   double t = 0.0;
-  for (int w = 0; w < COARSE_TPB / 32; w++) t += red[w];
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
   return t;
 }
 
@@ -1219,7 +1227,7 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   const T* rho = (const T*)m->rho[l];
   for (int it = 0; it < sweeps; it++) {
     if (m->kind == 0) {
-      const dim3 gr((L.n[0] / 2 + 1 + BX - 1) / BX, (L.n[1] + m->by - 1) / m->by, L.n[2]);
+      const dim3 gr(((L.n[0] + 1) / 2 + BX - 1) / BX, (L.n[1] + m->by - 1) / m->by, L.n[2]);
       for (int q = 0; q < 2; q++) {
         const int col = forward ? q : 1 - q;
         hk(m, l, 0, 1, s);
@@ -1251,7 +1259,11 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     const int max_it = 8 * nmax + 64;
     const double tol = sizeof(T) == 4 ? 1e-5 : 1e-10;
     const size_t smem = coarse_smem(L, sizeof(T));  // opted in at creation
-    k_coarse_cg<T><<<1, COARSE_TPB, smem, s>>>(L, m->kind, max_it, tol, (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
+    // as many warps as the level has unknowns for (a small level's iterations are bound by the
+    // block's barriers and reductions, which cost less with fewer warps)
+    const long want = (L.nunk + 31) / 32 * 32;
+    const int tpb = want < COARSE_TPB ? (int)want : COARSE_TPB;
+    k_coarse_cg<T><<<1, tpb, smem, s>>>(L, m->kind, max_it, tol, (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
                                                (T*)m->r[l], (const T*)m->rho[l], smem > 0);
     rmt_count_launches(1);
     return;
