@@ -203,14 +203,22 @@ def timed_steps(g, steps: int, stream) -> float:
     return a.elapsed_time(b) / steps
 
 
+def solver_options(args, graph: bool = True) -> dict:
+    """The multigrid schedule of the timed configuration (rmt_set_option names)."""
+    o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
+         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse}
+    if graph:
+        o["graph"] = args.graph
+    return o
+
+
 def plain_fp64_leg(cfg: dict, args, stream) -> dict:
     """The same workload on the plain FP64 path (no mixed precision), same cycle counts."""
     from paper_2104_00095_gb300 import rmt
 
     sc = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     sc.update(precision="fp64", mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe,
-              options={"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
-                       "graph": args.graph})
+              options=solver_options(args))
     g = rmt.Grid(sc, stream=stream.cuda_stream)
     g.step(3)
     k = max(3, args.steps // 2)
@@ -293,8 +301,7 @@ def serving_leg(args, stream) -> dict:
     jobs = S.serving_stream(njobs=args.serve_jobs, steps=(lo, hi))
     for _, sc in jobs:
         sc.update(mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe)
-    srv = rmt.Server(80 * 10**9, stream=stream.cuda_stream,
-                     options={"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm})
+    srv = rmt.Server(80 * 10**9, stream=stream.cuda_stream, options=solver_options(args, graph=False))
     t_start = time.perf_counter()
     pending = list(jobs)
     ids = []
@@ -363,6 +370,8 @@ def main():
     ap.add_argument("--fe-inner", type=int, default=2,
                     help="FE V-cycles per high-precision residual (mixed-precision refinement)")
     ap.add_argument("--mac-warm", type=int, default=0, help="warm-start the MAC solve from the last step")
+    ap.add_argument("--mac-coarse", type=int, default=2,
+                    help="red-black sweeps before and after the coarse correction on the MAC levels below the finest")
     ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
@@ -403,8 +412,7 @@ def main():
     scene = make_scene(cfg, n=args.n, nbodies=args.nbodies)
     scene["mg_fixed_cycles"] = args.mg_cycles_mac
     scene["mg_fixed_cycles_fe"] = args.mg_cycles_fe
-    scene["options"] = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
-                        "graph": args.graph}
+    scene["options"] = solver_options(args)
     g = rmt.Grid(scene, stream=stream.cuda_stream)
     N = int(np.prod(scene["n"]))
     for _ in range(args.warmup):
@@ -508,6 +516,7 @@ def main():
                            "bodies": len(scene["solids"]),
                            "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
                                                    "mac_inner": args.mac_inner, "fe_inner": args.fe_inner,
+                                                   "mac_coarse_sweeps": args.mac_coarse,
                                                    "mac_warm_start": bool(args.mac_warm)},
                            "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",

@@ -143,7 +143,9 @@ double rmt_dt(rmt_grid* g);
  * default 1), "mac_block", "fe_block" (rows of 32 threads per block of the multigrid level
  * kernels: 1, 2, 4 or 8, default 4), "mac_cycles", "fe_cycles" (replace the descriptor's
  * mg_fixed_cycles / mg_fixed_cycles_fe), "mac_warm", "fe_warm" (nonzero: each solve starts from the
- * previous step's solution instead of zero; default 0), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
+ * previous step's solution instead of zero; default 0), "mac_coarse_pre", "mac_coarse_post",
+ * "fe_coarse_pre", "fe_coarse_post" (sweeps on the levels below the finest, 0..16; default: the
+ * finest level's), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
  * of the step instead of launching its kernels one by one; the results are the same).  Cycle
  * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL, RMT_ESTATE for
  * a batch member. */

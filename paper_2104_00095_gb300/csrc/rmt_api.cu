@@ -107,6 +107,7 @@ struct rmt_grid {
   HookCtx hctx[2];
   // smoother schedule (negative: solver default)
   int mac_pre = -1, mac_post = -1, fe_pre = -1, fe_post = -1, mac_inner = 1, fe_inner = 1;
+  int mac_cpre = -1, mac_cpost = -1, fe_cpre = -1, fe_cpost = -1;  // coarse levels (negative: as level 0)
   int mac_block = 4, fe_block = 4;  // block height of the multigrid level kernels
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
   double fe_omega = -1.0;
@@ -385,6 +386,8 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_hook(g->fe, mg_hook, &g->hctx[1]);
   mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
   mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+  mg_set_coarse_smoother(g->mac, g->mac_cpre, g->mac_cpost);
+  mg_set_coarse_smoother(g->fe, g->fe_cpre, g->fe_cpost);
   mg_set_inner(g->mac, g->mac_inner);
   mg_set_inner(g->fe, g->fe_inner);
   mg_set_block(g->mac, g->mac_block);
@@ -1031,6 +1034,10 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   else if (!strcmp(name, "fe_inner")) ip = &g->fe_inner;
   else if (!strcmp(name, "mac_warm")) ip = &g->mac_warm;
   else if (!strcmp(name, "fe_warm")) ip = &g->fe_warm;
+  else if (!strcmp(name, "mac_coarse_pre")) ip = &g->mac_cpre;
+  else if (!strcmp(name, "mac_coarse_post")) ip = &g->mac_cpost;
+  else if (!strcmp(name, "fe_coarse_pre")) ip = &g->fe_cpre;
+  else if (!strcmp(name, "fe_coarse_post")) ip = &g->fe_cpost;
   if (ip) {
     if (value < 0 || value > 16) return fail(g, RMT_EINVAL, "%s out of range", name);
     *ip = (int)value;
@@ -1053,6 +1060,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   if (g->inited) {
     mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
     mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
+    mg_set_coarse_smoother(g->mac, g->mac_cpre, g->mac_cpost);
+    mg_set_coarse_smoother(g->fe, g->fe_cpre, g->fe_cpost);
     mg_set_inner(g->mac, g->mac_inner);
     mg_set_inner(g->fe, g->fe_inner);
     mg_set_block(g->mac, g->mac_block);

@@ -113,6 +113,8 @@ const double* mg_solution64(MGSolver* m, cudaStream_t s);
 void mg_set_density(MGSolver* m, const void* rho);
 // smoother sweeps before/after the coarse correction and the Jacobi weight (negative: keep)
 void mg_set_smoother(MGSolver* m, int pre, int post, double omega);
+// sweeps on the levels below the finest (negative: the finest level's counts)
+void mg_set_coarse_smoother(MGSolver* m, int pre, int post);
 // V-cycles on the correction equation between FP64 residual evaluations (>= 1)
 void mg_set_inner(MGSolver* m, int inner);
 // block height (1, 2, 4 or 8 rows of 32 threads) of the level kernels

@@ -1025,6 +1025,7 @@ struct MGSolver {
   double* hpin = nullptr;
   size_t esz = 8;
   int pre = 2, post = 2;
+  int cpre = -1, cpost = -1;  // levels below the finest (negative: pre, post)
   int inner = 1;  // V-cycles on the storage-precision correction equation per high-precision residual
   int by = 4;     // block height of the level kernels
   int warm = 0;   // start from the last solution instead of zero
@@ -1042,6 +1043,10 @@ void mg_set_smoother(MGSolver* m, int pre, int post, double omega) {
   if (pre >= 0) m->pre = pre;
   if (post >= 0) m->post = post;
   if (omega > 0) m->omega = omega;
+}
+void mg_set_coarse_smoother(MGSolver* m, int pre, int post) {
+  m->cpre = pre;
+  m->cpost = post;
 }
 void mg_set_inner(MGSolver* m, int inner) {
   if (inner >= 1) m->inner = inner;
@@ -1270,7 +1275,8 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
   }
   const int ex = m->kind == 0 ? L.n[0] : L.nn[0], ey = m->kind == 0 ? L.n[1] : L.nn[1],
             ez = m->kind == 0 ? L.n[2] : L.nn[2];
-  smooth<T>(m, l, m->pre, true, s);
+  const int npre = l > 0 && m->cpre >= 0 ? m->cpre : m->pre, npost = l > 0 && m->cpost >= 0 ? m->cpost : m->post;
+  smooth<T>(m, l, npre, true, s);
   if (m->kind == 0)
     k_resid<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
                                                                     (const T*)m->rho[l], (T*)m->r[l]);
@@ -1292,7 +1298,7 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     k_prolong_fe<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
                                                                                         (T*)m->x[l]);
   rmt_count_launches(1);
-  smooth<T>(m, l, m->post, false, s);
+  smooth<T>(m, l, npost, false, s);
 }
 
 template <typename T>

@@ -133,7 +133,12 @@ __device__ __forceinline__ uint64_t cell_bodies(const Geo& g, const BodyView<T>*
 }
 
 // Pass 1, every cell: cells no body reaches take the pure-fluid divergence mu lap(u) here; the
-// others are appended to a list (one atomic per warp) for pass 2.
+// others are appended to a list (one atomic per warp and plane) for pass 2.  A block marches
+// over SFZ planes of a TILE_X x TILE_Y column, so the body boxes and the tile's body mask are
+// set up once per column, and keeps u of the planes below and above in registers.  Every
+// neighbour comes from selects (periodic wrap, or the mirrored ghost 2 u_wall - u at a no-slip
+// wall), so no warp takes a separate path at the domain's edges.
+constexpr int SFZ = 8;
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T* __restrict__ u,
                                                                   const BodyView<T>* __restrict__ views, int nb,
@@ -143,52 +148,97 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T*
   __shared__ int sbb[6 * RMT_MAX_BODIES];
   __shared__ unsigned long long tile_mask;
   stage_boxes(bbs, bstride, nb, sbb);
-  const unsigned long long tm = tile_body_mask(g, sbb, nb, &tile_mask);
-  THREAD_XYZ(i, j, k);
+  const int k0 = blockIdx.z * SFZ, k1 = min(k0 + SFZ, g.n[2]);
+  if (threadIdx.y == 0) {
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int i1 = min(i0 + TILE_X, g.n[0]) - 1, j1 = min(j0 + TILE_Y, g.n[1]) - 1;
+    unsigned long long mk = 0;
+    for (int base = 0; base < nb; base += 32) {
+      const int m = base + threadIdx.x;
+      bool hit = false;
+      if (m < nb) {
+        const int* b = sbb + 6 * m;
+        hit = tile_meets_box(g, b, 0, i0, i1) && tile_meets_box(g, b, 1, j0, j1) && tile_meets_box(g, b, 2, k0, k1 - 1);
+      }
+      mk |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << base;
+    }
+    if (threadIdx.x == 0) tile_mask = mk;
+  }
+  __syncthreads();
+  const unsigned long long tm = tile_mask;
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  const long c = cidx(g, i, j, k);
-  uint64_t bm = 0;
-  for (unsigned long long r = tm; r; r &= r - 1) {
-    const int m = __ffsll((long long)r) - 1;
-    if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
-  }
-  const unsigned act = __activemask();
-  const unsigned want = __ballot_sync(act, bm != 0);
-  if (bm != 0) {
-    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-    const int leader = __ffs(want) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(want));
-    base = __shfl_sync(want, base, leader);
-    list[base + __popc(want & ((1u << lane) - 1u))] = (int)c;
-    return;
-  }
-  // pure fluid around this cell: every face row is mu (u_b - u_a)/h
   const T ih = cv<T>(g.ih, g.f.ih);
   const T mu = cv<T>(g.mu, g.f.mu);
-  const bool in = i > 0 && i + 1 < g.n[0] && j > 0 && j + 1 < g.n[1] && k > 0 && k + 1 < g.n[2];
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long sy = n0, sz = (long)n0 * n1;
+  // x and y neighbours: offsets from the cell (the cell itself where a wall ghost is used)
+  const bool xl = i > 0, xh = i + 1 < n0, yl = j > 0, yh = j + 1 < n1;
+  const long oxl = xl ? -1 : (g.per[0] ? n0 - 1 : 0), oxh = xh ? 1 : (g.per[0] ? 1 - n0 : 0);
+  const long oyl = yl ? -sy : (g.per[1] ? (n1 - 1) * sy : 0), oyh = yh ? sy : (g.per[1] ? (1 - n1) * sy : 0);
+  const bool gxl = !xl && !g.per[0], gxh = !xh && !g.per[0], gyl = !yl && !g.per[1], gyh = !yh && !g.per[1];
+  // the plane below the first one and the first one
+  auto zoff = [&](int kk) -> long {  // plane index kk in [-1, n2] -> offset of (i, j, kk) (own plane at a wall)
+    if (kk < 0) return g.per[2] ? (long)(n2 - 1) * sz : -1;
+    if (kk >= n2) return g.per[2] ? 0 : -1;
+    return (long)kk * sz;
+  };
+  const long cij = i + (long)j * sy;
+  T win[3][3];  // win[a][0..2] = u_a at planes k-1, k, k+1
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const T* ua = u + (long)a * g.N;
-    const T uc = ua[c];
-    T acc = T(0);
+    const T* ua = u + (long)a * g.N + cij;
+    const T uk = ua[(long)k0 * sz];
+    const long ol = zoff(k0 - 1);
+    const T vl = ua[ol >= 0 ? ol : (long)k0 * sz];
+    win[a][0] = ol >= 0 ? vl : T(2) * cv<T>(g.wall[4][a], g.f.wall[4][a]) - uk;
+    win[a][1] = uk;
+  }
+  for (int k = k0; k < k1; k++) {
+    const long c = cij + (long)k * sz;
+    const long oh = zoff(k + 1);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      T up, um;
-      if (in) {
-        const long st = d == 0 ? 1 : (d == 1 ? (long)g.n[0] : (long)g.n[0] * g.n[1]);
-        up = ua[c + st];
-        um = ua[c - st];
-      } else {
-        int p[3] = {i, j, k}, q[3] = {i, j, k};
-        p[d] += 1;
-        q[d] -= 1;
-        up = uval(g, u, a, p[0], p[1], p[2]);
-        um = uval(g, u, a, q[0], q[1], q[2]);
-      }
-      acc += (mu * ((up - uc) * ih) - mu * ((uc - um) * ih)) * ih;
+    for (int a = 0; a < 3; a++) {
+      const T* ua = u + (long)a * g.N + cij;
+      const T vh = ua[oh >= 0 ? oh : (long)k * sz];
+      win[a][2] = oh >= 0 ? vh : T(2) * cv<T>(g.wall[5][a], g.f.wall[5][a]) - win[a][1];
     }
-    out[a * g.N + c] = acc;
+    uint64_t bm = 0;
+    for (unsigned long long r = tm; r; r &= r - 1) {
+      const int m = __ffsll((long long)r) - 1;
+      if (in_box(g, sbb + 6 * m, i, j, k) && views[m].lay[c] >= 0) bm |= (1ull << m);
+    }
+    const unsigned act = __activemask();
+    const unsigned want = __ballot_sync(act, bm != 0);
+    if (bm != 0) {
+      const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+      const int leader = __ffs(want) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(count, __popc(want));
+      base = __shfl_sync(want, base, leader);
+      list[base + __popc(want & ((1u << lane) - 1u))] = (int)c;
+    } else {
+      // pure fluid around this cell: every face row is mu (u_b - u_a)/h
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const T* ua = u + (long)a * g.N + c;
+        const T uc = win[a][1];
+        const T wxl = T(2) * cv<T>(g.wall[0][a], g.f.wall[0][a]) - uc, wxh = T(2) * cv<T>(g.wall[1][a], g.f.wall[1][a]) - uc;
+        const T wyl = T(2) * cv<T>(g.wall[2][a], g.f.wall[2][a]) - uc, wyh = T(2) * cv<T>(g.wall[3][a], g.f.wall[3][a]) - uc;
+        const T vxl = ua[oxl], vxh = ua[oxh], vyl = ua[oyl], vyh = ua[oyh];
+        const T nb6[6] = {gxl ? wxl : vxl, gxh ? wxh : vxh, gyl ? wyl : vyl, gyh ? wyh : vyh, win[a][0], win[a][2]};
+        T acc = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+          acc += (mu * ((nb6[2 * d + 1] - uc) * ih) - mu * ((uc - nb6[2 * d]) * ih)) * ih;
+        out[a * g.N + c] = acc;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      win[a][0] = win[a][1];
+      win[a][1] = win[a][2];
+    }
   }
 }
 
@@ -233,7 +283,7 @@ template <typename T>
 void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
                        const int* bbs, int bstride, const double* t, double toff, T* out, int* list, int* count,
                        cudaStream_t s) {
-  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + SFZ - 1) / SFZ);
   cudaMemsetAsync(count, 0, sizeof(int), s);
   k_stress_fluid<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, views, nb, bbs, bstride, out, list, count);
   rmt_count_launches(1);
