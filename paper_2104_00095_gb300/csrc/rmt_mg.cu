@@ -295,6 +295,58 @@ __device__ __forceinline__ F2 mac_op_ff(const Lv& L, const float* __restrict__ x
 // of c that differ from the node in two or three coordinates} (x_node - x_corner)
 __device__ __forceinline__ F2 fe_op_ff(const Lv& L, const float* __restrict__ xh, const float* __restrict__ xl,
                                        const float* __restrict__ beta, int i, int j, int k) {
+  if (i > 0 && i + 1 < L.nn[0] && j > 0 && j + 1 < L.nn[1] && k > 0 && k + 1 < L.nn[2] && i <= L.n[0] &&
+      j <= L.n[1] && k <= L.n[2]) {
+    // interior: the 8 cells and 26 neighbours at fixed offsets; a corner shared by two cells of
+    // the node (the 12 face diagonals) takes the sum of their coefficients, so 20 weighted
+    // differences instead of 32
+    const int sx = 1, sy = L.nn[0], sz = L.nn[0] * L.nn[1];
+    const int cy = L.n[0], cz = L.n[0] * L.n[1];
+    const float* bp = beta + cix(L, i - 1, j - 1, k - 1);
+    float b[2][2][2];
+#pragma unroll
+    for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+        for (int qx = 0; qx < 2; qx++) b[qx][qy][qz] = bp[qx + qy * cy + qz * cz];
+    const long n0 = nix(L, i, j, k);
+    const float* ph = xh + n0;
+    const float* pl = xl + n0;
+    const float ch = ph[0], cl = pl[0];
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+        for (int qx = 0; qx < 2; qx++) {
+          const int o = (2 * qx - 1) * sx + (2 * qy - 1) * sy + (2 * qz - 1) * sz;
+          acc_wdiff(b[qx][qy][qz], ch, cl, ph[o], pl[o], sh, sl);  // body diagonals
+        }
+#pragma unroll
+    for (int qy = 0; qy < 2; qy++)
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++) {
+        const int o = (2 * qx - 1) * sx + (2 * qy - 1) * sy;
+        acc_wdiff(__fadd_rn(b[qx][qy][0], b[qx][qy][1]), ch, cl, ph[o], pl[o], sh, sl);  // xy
+      }
+#pragma unroll
+    for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+      for (int qx = 0; qx < 2; qx++) {
+        const int o = (2 * qx - 1) * sx + (2 * qz - 1) * sz;
+        acc_wdiff(__fadd_rn(b[qx][0][qz], b[qx][1][qz]), ch, cl, ph[o], pl[o], sh, sl);  // xz
+      }
+#pragma unroll
+    for (int qz = 0; qz < 2; qz++)
+#pragma unroll
+      for (int qy = 0; qy < 2; qy++) {
+        const int o = (2 * qy - 1) * sy + (2 * qz - 1) * sz;
+        acc_wdiff(__fadd_rn(b[0][qy][qz], b[1][qy][qz]), ch, cl, ph[o], pl[o], sh, sl);  // yz
+      }
+    return ff_mul(sh, sl, L.f_s12, L.f_s12_lo);
+  }
   const int X[2] = {nnb(L, 0, i - 1), nnb(L, 0, i + 1)};
   const int Y[2] = {nnb(L, 1, j - 1), nnb(L, 1, j + 1)};
   const int Z[2] = {nnb(L, 2, k - 1), nnb(L, 2, k + 1)};
@@ -470,7 +522,12 @@ __global__ void __launch_bounds__(BX* BYMAX) k_rbgs(Lv L, int colour, T* __restr
   T dg;
   const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
   const long c = cix(L, i, j, k);
-  if (dg > T(0)) x[c] = x[c] + (b[c] - ax) / dg;
+  // the increment scales the residual, so an approximate FP32 quotient moves the sweep, not its
+  // fixed point
+  if (dg > T(0)) {
+    if constexpr (sizeof(T) == 4) x[c] = x[c] + __fdividef(b[c] - ax, dg);
+    else x[c] = x[c] + (b[c] - ax) / dg;
+  }
 }
 
 // weighted Jacobi pass (27-point): xo = xi + w (b - K xi)/diag
@@ -648,7 +705,9 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
       const T diag = T(4) * bsum * s12;
       const T ax = (T(4) * bsum * xc - acc) * s12;
       const long u = ubase + (long)k * sz;
-      if constexpr (MODE == 0)
+      if constexpr (MODE == 0 && sizeof(T) == 4)
+        out[u] = diag > T(0) ? xc + w * __fdividef(bcur - ax, diag) : xc;  // increment only (see k_rbgs)
+      else if constexpr (MODE == 0)
         out[u] = diag > T(0) ? xc + w * (bcur - ax) / diag : xc;
       else
         out[u] = bcur - ax;
@@ -677,18 +736,28 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
   cp_async_wait<0>();
 }
 
+// MAC: residual of the V-cycle's operator and its restriction in one pass: one thread per coarse
+// cell forms r = b - A x at its 8 fine cells and writes their mean (the 8-cell average of the
+// restriction), and zeroes the coarse iterate.  The operator is the smoothers' (approximate
+// coefficient quotient); the high-precision residual outside the V-cycle uses the exactly
+// rounded one.
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_resid(Lv L, int kind, const T* __restrict__ x, const T* __restrict__ b,
-                                                   const T* __restrict__ rho, T* __restrict__ r) {
-  const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
-  int i, j, k;
-  if (!thread_cell(ext, i, j, k)) return;
-  T dg;
-  // the V-cycle's operator: the smoother's coefficient (the high-precision residual outside the
-  // V-cycle uses the exactly rounded one)
-  const T ax = kind == 0 ? mac_op<T, true>(L, x, rho, i, j, k, dg) : fe_op<T>(L, x, rho, i, j, k, dg);
-  const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
-  r[u] = b[u] - ax;
+__global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, const T* __restrict__ x,
+                                                                const T* __restrict__ b, const T* __restrict__ rho,
+                                                                T* __restrict__ bc, T* __restrict__ xc) {
+  int I, J, K;
+  if (!thread_cell(C.n, I, J, K)) return;
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + ((q >> 2) & 1);
+    T dg;
+    const T ax = mac_op<T, true>(F, x, rho, i, j, k, dg);
+    s += b[cix(F, i, j, k)] - ax;
+  }
+  const long u = cix(C, I, J, K);
+  bc[u] = s * T(0.125);
+  xc[u] = T(0);
 }
 
 // restriction of the residual to the coarse right-hand side (coarse x zeroed)
@@ -1273,23 +1342,21 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     rmt_count_launches(1);
     return;
   }
-  const int ex = m->kind == 0 ? L.n[0] : L.nn[0], ey = m->kind == 0 ? L.n[1] : L.nn[1],
-            ez = m->kind == 0 ? L.n[2] : L.nn[2];
   const int npre = l > 0 && m->cpre >= 0 ? m->cpre : m->pre, npost = l > 0 && m->cpost >= 0 ? m->cpost : m->post;
   smooth<T>(m, l, npre, true, s);
-  if (m->kind == 0)
-    k_resid<T><<<grid3(ex, ey, ez, m->by), dim3(BX, m->by), 0, s>>>(L, m->kind, (const T*)m->x[l], (const T*)m->b[l],
-                                                                    (const T*)m->rho[l], (T*)m->r[l]);
-  else
+  const Lv& C = m->lv[l + 1];
+  if (m->kind == 0) {
+    k_resid_restrict_mac<T><<<grid3(C.n[0], C.n[1], C.n[2], m->by), dim3(BX, m->by), 0, s>>>(
+        L, C, (const T*)m->x[l], (const T*)m->b[l], (const T*)m->rho[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
+    rmt_count_launches(1);
+  } else {
     k_fe_tile<T, 1><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
                                                        (const T*)m->rho[l]);
-  rmt_count_launches(1);
-  const Lv& C = m->lv[l + 1];
-  const int cx = m->kind == 0 ? C.n[0] : C.nn[0], cy = m->kind == 0 ? C.n[1] : C.nn[1],
-            cz = m->kind == 0 ? C.n[2] : C.nn[2];
-  k_restrict<T><<<grid3(cx, cy, cz, m->by), dim3(BX, m->by), 0, s>>>(L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1],
-                                                           (T*)m->x[l + 1]);
-  rmt_count_launches(1);
+    rmt_count_launches(1);
+    k_restrict<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(
+        L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
+    rmt_count_launches(1);
+  }
   vcycle<T>(m, l + 1, s);
   if (m->kind == 0)
     k_prolong_mac<T><<<grid3(C.n[0], C.n[1], C.n[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
