@@ -138,7 +138,8 @@ double rmt_dt(rmt_grid* g);
 
 /* Solver schedule options (any time): "mac_pre", "mac_post" (red-black Gauss-Seidel sweeps
  * before / after the coarse correction, 0..16, default 3), "fe_pre", "fe_post" (weighted Jacobi
- * sweeps, default 2), "fe_omega" (Jacobi weight in (0,2), default 0.9), "mac_inner", "fe_inner"
+ * sweeps, default 2), "fe_omega" (Jacobi weight in (0,2), default 0.9), "mac_omega" (relaxation
+ * factor of the red-black sweeps in (0,2), default 1), "mac_inner", "fe_inner"
  * (V-cycles on the storage-precision correction equation per high-precision residual, 1..16,
  * default 1), "mac_block", "fe_block" (rows of 32 threads per block of the multigrid level
  * kernels: 1, 2, 4 or 8, default 4), "mac_cycles", "fe_cycles" (replace the descriptor's

@@ -110,7 +110,7 @@ struct rmt_grid {
   int mac_cpre = -1, mac_cpost = -1, fe_cpre = -1, fe_cpost = -1;  // coarse levels (negative: as level 0)
   int mac_block = 4, fe_block = 4;  // block height of the multigrid level kernels
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
-  double fe_omega = -1.0;
+  double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
   // captured step graphs (fixed-cycle mode): one per parity of the reference-map buffers
@@ -384,7 +384,7 @@ rmt_status alloc_t(rmt_grid* g) {
   g->hctx[1] = {g, 1};
   mg_set_hook(g->mac, mg_hook, &g->hctx[0]);
   mg_set_hook(g->fe, mg_hook, &g->hctx[1]);
-  mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
+  mg_set_smoother(g->mac, g->mac_pre, g->mac_post, g->mac_omega);
   mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
   mg_set_coarse_smoother(g->mac, g->mac_cpre, g->mac_cpost);
   mg_set_coarse_smoother(g->fe, g->fe_cpre, g->fe_cpost);
@@ -1048,9 +1048,9 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   } else if (!strcmp(name, "mac_cycles") || !strcmp(name, "fe_cycles")) {
     if (value < 0 || value > 1000) return fail(g, RMT_EINVAL, "%s out of range", name);
     (name[0] == 'm' ? g->desc.mg_fixed_cycles : g->desc.mg_fixed_cycles_fe) = (int)value;
-  } else if (!strcmp(name, "fe_omega")) {
-    if (!(value > 0.0 && value < 2.0)) return fail(g, RMT_EINVAL, "fe_omega out of range");
-    g->fe_omega = value;
+  } else if (!strcmp(name, "fe_omega") || !strcmp(name, "mac_omega")) {
+    if (!(value > 0.0 && value < 2.0)) return fail(g, RMT_EINVAL, "%s out of range", name);
+    (name[0] == 'f' ? g->fe_omega : g->mac_omega) = value;
   } else if (!strcmp(name, "graph")) {
     g->use_graph = value != 0.0;
   } else {
@@ -1058,7 +1058,7 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   }
   drop_graphs(g);
   if (g->inited) {
-    mg_set_smoother(g->mac, g->mac_pre, g->mac_post, -1.0);
+    mg_set_smoother(g->mac, g->mac_pre, g->mac_post, g->mac_omega);
     mg_set_smoother(g->fe, g->fe_pre, g->fe_post, g->fe_omega);
     mg_set_coarse_smoother(g->mac, g->mac_cpre, g->mac_cpost);
     mg_set_coarse_smoother(g->fe, g->fe_cpre, g->fe_cpost);

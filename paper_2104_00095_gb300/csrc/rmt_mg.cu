@@ -508,38 +508,30 @@ __global__ void k_ff_to64(const float* __restrict__ xh, const float* __restrict_
   GRID_LOOP(i, n) x[i] = (double)xh[i] + (double)xl[i];
 }
 
-// red-black Gauss-Seidel colour pass (7-point): each thread updates the cell of this colour
-// among x = 2p and 2p+1 of its row
+// red-black Gauss-Seidel update (7-point) of the cell of this colour among x = 2p and 2p+1 of
+// row (j, k); the increment scales the residual, so an approximate FP32 quotient moves the sweep,
+// not its fixed point
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_rbgs(Lv L, int colour, T* __restrict__ x, const T* __restrict__ b,
-                                                  const T* __restrict__ rho) {
-  const int p = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (j >= L.n[1]) return;
+__device__ __forceinline__ void rbgs_at(const Lv& L, int colour, T w, T* __restrict__ x, const T* __restrict__ b,
+                                        const T* __restrict__ rho, int p, int j, int k) {
   const int i = 2 * p + ((j + k + colour) & 1);
   if (i >= L.n[0]) return;
   T dg;
   const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
   const long c = cix(L, i, j, k);
-  // the increment scales the residual, so an approximate FP32 quotient moves the sweep, not its
-  // fixed point
   if (dg > T(0)) {
-    if constexpr (sizeof(T) == 4) x[c] = x[c] + __fdividef(b[c] - ax, dg);
-    else x[c] = x[c] + (b[c] - ax) / dg;
+    if constexpr (sizeof(T) == 4) x[c] = x[c] + w * __fdividef(b[c] - ax, dg);
+    else x[c] = x[c] + w * ((b[c] - ax) / dg);
   }
 }
-
-// weighted Jacobi pass (27-point): xo = xi + w (b - K xi)/diag
+// one colour pass: one thread per cell pair along x
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_jacobi(Lv L, T w, const T* __restrict__ xi, T* __restrict__ xo,
-                                                    const T* __restrict__ b, const T* __restrict__ rho) {
-  int i, j, k;
-  if (!thread_cell(L.nn, i, j, k)) return;
-  T dg;
-  const T ax = fe_op<T>(L, xi, rho, i, j, k, dg);
-  const long u = nix(L, i, j, k);
-  xo[u] = dg > T(0) ? xi[u] + w * (b[u] - ax) / dg : xi[u];
+__global__ void __launch_bounds__(BX* BYMAX) k_rbgs(Lv L, int colour, T w, T* __restrict__ x, const T* __restrict__ b,
+                                                  const T* __restrict__ rho) {
+  const int p = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (j >= L.n[1]) return;
+  rbgs_at(L, colour, w, x, b, rho, p, j, (int)blockIdx.z);
 }
 
 // Asynchronous global -> shared copies (cp.async, 4 or 8 bytes; size 0 fills zeros), so that
@@ -742,11 +734,9 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
 // coefficient quotient); the high-precision residual outside the V-cycle uses the exactly
 // rounded one.
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, const T* __restrict__ x,
-                                                                const T* __restrict__ b, const T* __restrict__ rho,
-                                                                T* __restrict__ bc, T* __restrict__ xc) {
-  int I, J, K;
-  if (!thread_cell(C.n, I, J, K)) return;
+__device__ __forceinline__ void resid_restrict_mac_at(const Lv& F, const Lv& C, const T* __restrict__ x,
+                                                      const T* __restrict__ b, const T* __restrict__ rho,
+                                                      T* __restrict__ bc, T* __restrict__ xc, int I, int J, int K) {
   T s = T(0);
 #pragma unroll
   for (int q = 0; q < 8; q++) {
@@ -759,14 +749,20 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, co
   bc[u] = s * T(0.125);
   xc[u] = T(0);
 }
-
-// restriction of the residual to the coarse right-hand side (coarse x zeroed)
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
-                                                      T* __restrict__ bc, T* __restrict__ xc) {
-  const int ext[3] = {kind == 0 ? C.n[0] : C.nn[0], kind == 0 ? C.n[1] : C.nn[1], kind == 0 ? C.n[2] : C.nn[2]};
+__global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, const T* __restrict__ x,
+                                                                const T* __restrict__ b, const T* __restrict__ rho,
+                                                                T* __restrict__ bc, T* __restrict__ xc) {
   int I, J, K;
-  if (!thread_cell(ext, I, J, K)) return;
+  if (!thread_cell(C.n, I, J, K)) return;
+  resid_restrict_mac_at(F, C, x, b, rho, bc, xc, I, J, K);
+}
+
+// restriction of the residual to the coarse right-hand side at coarse unknown (I, J, K) (coarse
+// x zeroed): MAC the 8-cell mean, FE full weighting
+template <typename T>
+__device__ __forceinline__ void restrict_at(const Lv& F, const Lv& C, int kind, const T* __restrict__ rf,
+                                            T* __restrict__ bc, T* __restrict__ xc, int I, int J, int K) {
   T s = T(0);
   if (kind == 0) {
 #pragma unroll
@@ -790,9 +786,17 @@ __global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, co
           s += w * rf[nix(F, ff[0], ff[1], ff[2])];
         }
   }
-  const long u = I + (long)ext[0] * (J + (long)ext[1] * K);
+  const long u = kind == 0 ? cix(C, I, J, K) : nix(C, I, J, K);
   bc[u] = s;
   xc[u] = T(0);
+}
+template <typename T>
+__global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
+                                                      T* __restrict__ bc, T* __restrict__ xc) {
+  const int ext[3] = {kind == 0 ? C.n[0] : C.nn[0], kind == 0 ? C.n[1] : C.nn[1], kind == 0 ? C.n[2] : C.nn[2]};
+  int I, J, K;
+  if (!thread_cell(ext, I, J, K)) return;
+  restrict_at(F, C, kind, rf, bc, xc, I, J, K);
 }
 
 // Trilinear prolongation of the coarse correction, added to the fine iterate; one thread per
@@ -801,9 +805,8 @@ __global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, co
 // neighbour on the child's side (the parent itself beyond a wall: Neumann mirror), applied
 // axis by axis.
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
-  int I, J, K;
-  if (!thread_cell(C.n, I, J, K)) return;
+__device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T* __restrict__ xc, T* __restrict__ xf,
+                                               int I, int J, int K) {
   int nx[3], ny[3], nz[3];  // coarse indices of I-1, I, I+1 (and for J, K)
 #pragma unroll
   for (int q = 0; q < 3; q++) {
@@ -845,13 +848,18 @@ __global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* 
       }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
+  int I, J, K;
+  if (!thread_cell(C.n, I, J, K)) return;
+  prolong_mac_at(F, C, xc, xf, I, J, K);
+}
 
 // Nodal: a fine node on a coarse node takes its value, one between two coarse nodes their mean
 // (per axis).
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_prolong_fe(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
-  int I, J, K;
-  if (!thread_cell(C.nn, I, J, K)) return;
+__device__ __forceinline__ void prolong_fe_at(const Lv& F, const Lv& C, const T* __restrict__ xc, T* __restrict__ xf,
+                                              int I, int J, int K) {
   const int I1 = I + 1 < C.nn[0] ? I + 1 : (C.per[0] ? 0 : I);
   const int J1 = J + 1 < C.nn[1] ? J + 1 : (C.per[1] ? 0 : J);
   const int K1 = K + 1 < C.nn[2] ? K + 1 : (C.per[2] ? 0 : K);
@@ -880,6 +888,12 @@ __global__ void __launch_bounds__(BX* BYMAX) k_prolong_fe(Lv F, Lv C, const T* _
       }
     }
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong_fe(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
+  int I, J, K;
+  if (!thread_cell(C.nn, I, J, K)) return;
+  prolong_fe_at(F, C, xc, xf, I, J, K);
 }
 
 // FE coefficient beta = 1/rho per cell (finest level)
@@ -1009,27 +1023,13 @@ __device__ __forceinline__ double block_sum(A v, double* red) {
   return t;
 }
 
+// Conjugate gradients on one level by the whole block: r holds the right-hand side on entry (it
+// is made mean-free), x receives the mean-free solution, p and q are scratch; every thread of the
+// block calls it.  red: COARSE_TPB / 32 doubles of shared memory.
 template <typename T>
-__global__ void __launch_bounds__(COARSE_TPB) k_coarse_cg(Lv L, int kind, int max_it, double rtol, T* __restrict__ gx,
-                                                         T* __restrict__ gp, T* __restrict__ gb,
-                                                         T* __restrict__ gq, const T* __restrict__ grho,
-                                                         int in_smem) {
-  __shared__ double red[COARSE_TPB / 32];
-  extern __shared__ unsigned char smem[];
+__device__ void cg_block(const Lv& L, int kind, int max_it, double rtol, T* x, T* r, T* p, T* q, const T* rho,
+                         double* red) {
   const long n = L.nunk;
-  T *x = gx, *r = gb, *p = gp, *q = gq;
-  const T* rho = grho;
-  if (in_smem) {
-    x = (T*)smem;
-    r = x + n;
-    p = r + n;
-    q = p + n;
-    T* c = q + n;
-    for (long u = threadIdx.x; u < n; u += blockDim.x) r[u] = gb[u];
-    for (long u = threadIdx.x; u < L.ncell; u += blockDim.x) c[u] = grho[u];
-    rho = c;
-    __syncthreads();
-  }
   using A = T;  // per-thread accumulation type
   A loc = A(0);
   for (long u = threadIdx.x; u < n; u += blockDim.x) loc += r[u];
@@ -1074,7 +1074,97 @@ __global__ void __launch_bounds__(COARSE_TPB) k_coarse_cg(Lv L, int kind, int ma
   loc = A(0);
   for (long u = threadIdx.x; u < n; u += blockDim.x) loc += x[u];
   const double xm = block_sum(loc, red) / (double)n;
-  for (long u = threadIdx.x; u < n; u += blockDim.x) gx[u] = (T)((double)x[u] - xm);
+  for (long u = threadIdx.x; u < n; u += blockDim.x) x[u] = (T)((double)x[u] - xm);
+  __syncthreads();
+}
+
+// The same iteration run by one warp (the calling warp; small levels, where the block's barriers
+// would dominate): reductions by shuffles only.
+template <typename T>
+__device__ void cg_warp(const Lv& L, int kind, int max_it, double rtol, T* x, T* r, T* p, T* q, const T* rho) {
+  const int lane = threadIdx.x & 31;
+  const long n = L.nunk;
+  auto wsum = [](T v) {
+    double d = (double)v;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
+  };
+  T loc = T(0);
+  for (long u = lane; u < n; u += 32) loc += r[u];
+  const double mean = wsum(loc) / (double)n;
+  loc = T(0);
+  for (long u = lane; u < n; u += 32) {
+    const T v = (T)((double)r[u] - mean);
+    r[u] = v;
+    p[u] = v;
+    x[u] = T(0);
+    loc += v * v;
+  }
+  double rr = wsum(loc);
+  const double stop = rtol * rtol * rr;
+  const int ex = kind == 0 ? L.n[0] : L.nn[0], ey = kind == 0 ? L.n[1] : L.nn[1];
+  for (int it = 0; it < max_it && rr > stop; it++) {
+    __syncwarp();  // p complete
+    loc = T(0);
+    for (int u = lane; u < (int)n; u += 32) {
+      const int rw = u / ex;
+      const int i = u - rw * ex, j = rw % ey, k = rw / ey;
+      T dg;
+      const T ap = kind == 0 ? mac_op<T>(L, p, rho, i, j, k, dg) : fe_op<T>(L, p, rho, i, j, k, dg);
+      q[u] = ap;
+      loc += p[u] * ap;
+    }
+    const double pq = wsum(loc);
+    if (!(pq > 0.0)) break;
+    const T a = (T)(rr / pq);
+    loc = T(0);
+    for (long u = lane; u < n; u += 32) {
+      x[u] += a * p[u];
+      const T v = r[u] - a * q[u];
+      r[u] = v;
+      loc += v * v;
+    }
+    const double rr2 = wsum(loc);
+    const T beta = (T)(rr2 / rr);
+    rr = rr2;
+    __syncwarp();  // every lane has read p for its q before p changes
+    for (long u = lane; u < n; u += 32) p[u] = r[u] + beta * p[u];
+  }
+  __syncwarp();
+  loc = T(0);
+  for (long u = lane; u < n; u += 32) loc += x[u];
+  const double xm = wsum(loc) / (double)n;
+  for (long u = lane; u < n; u += 32) x[u] = (T)((double)x[u] - xm);
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(COARSE_TPB) k_coarse_cg(Lv L, int kind, int max_it, double rtol, T* __restrict__ gx,
+                                                         T* __restrict__ gp, T* __restrict__ gb,
+                                                         T* __restrict__ gq, const T* __restrict__ grho,
+                                                         int in_smem) {
+  __shared__ double red[COARSE_TPB / 32];
+  extern __shared__ unsigned char smem[];
+  const long n = L.nunk;
+  T *x = gx, *r = gb, *p = gp, *q = gq;
+  const T* rho = grho;
+  if (in_smem) {
+    x = (T*)smem;
+    r = x + n;
+    p = r + n;
+    q = p + n;
+    T* c = q + n;
+    for (long u = threadIdx.x; u < n; u += blockDim.x) r[u] = gb[u];
+    for (long u = threadIdx.x; u < L.ncell; u += blockDim.x) c[u] = grho[u];
+    rho = c;
+    __syncthreads();
+  }
+  if (blockDim.x == 32)
+    cg_warp(L, kind, max_it, rtol, x, r, p, q, rho);
+  else
+    cg_block(L, kind, max_it, rtol, x, r, p, q, rho, red);
+  if (in_smem)
+    for (long u = threadIdx.x; u < n; u += blockDim.x) gx[u] = x[u];
 }
 
 }  // namespace
@@ -1305,7 +1395,7 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
       for (int q = 0; q < 2; q++) {
         const int col = forward ? q : 1 - q;
         hk(m, l, 0, 1, s);
-        k_rbgs<T><<<gr, dim3(BX, m->by), 0, s>>>(L, col, (T*)m->x[l], b, rho);
+        k_rbgs<T><<<gr, dim3(BX, m->by), 0, s>>>(L, col, T(m->omega), (T*)m->x[l], b, rho);
         rmt_count_launches(1);
         hk(m, l, 0, 0, s);
       }
@@ -1333,10 +1423,10 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     const int max_it = 8 * nmax + 64;
     const double tol = sizeof(T) == 4 ? 1e-5 : 1e-10;
     const size_t smem = coarse_smem(L, sizeof(T));  // opted in at creation
-    // as many warps as the level has unknowns for (a small level's iterations are bound by the
-    // block's barriers and reductions, which cost less with fewer warps)
+    // as many warps as the level has unknowns for, and a single warp (reductions by shuffles, no
+    // block barriers) up to 512 unknowns: a small level's iterations are bound by the reductions
     const long want = (L.nunk + 31) / 32 * 32;
-    const int tpb = want < COARSE_TPB ? (int)want : COARSE_TPB;
+    const int tpb = L.nunk <= 512 ? 32 : (want < COARSE_TPB ? (int)want : COARSE_TPB);
     k_coarse_cg<T><<<1, tpb, smem, s>>>(L, m->kind, max_it, tol, (T*)m->x[l], (T*)m->xt[l], (T*)m->b[l],
                                                (T*)m->r[l], (const T*)m->rho[l], smem > 0);
     rmt_count_launches(1);
