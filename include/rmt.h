@@ -146,7 +146,10 @@ double rmt_dt(rmt_grid* g);
  * mg_fixed_cycles / mg_fixed_cycles_fe), "mac_warm", "fe_warm" (nonzero: each solve starts from the
  * previous step's solution instead of zero; default 0), "mac_coarse_pre", "mac_coarse_post",
  * "fe_coarse_pre", "fe_coarse_post" (sweeps on the levels below the finest, 0..16; default: the
- * finest level's), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
+ * finest level's), "mac_sweep" (FP32 grids: 1, the default, runs each red-black sweep of a
+ * level with n_x % 4 == 0, even periodic sides, n_x >= 64 and at least 2^20 cells as one fused
+ * pass over both colours; 2 does so on every level with n_x % 4 == 0 and even periodic sides; 0
+ * runs one pass per colour everywhere; all give the same sweep), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
  * of the step instead of launching its kernels one by one; the results are the same).  Cycle
  * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL, RMT_ESTATE for
  * a batch member. */

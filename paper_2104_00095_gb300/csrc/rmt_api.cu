@@ -37,12 +37,13 @@ struct BodyMem {
 namespace {
 enum {
   P_STRESS_N, P_GODUNOV, P_MAC_SETUP, P_MAC_SOLVE, P_MAC_CORR_ADV, P_XI_PRED, P_EXTRAP, P_CORR, P_STRESS_H,
-  P_USTAR, P_FE_SETUP, P_FE_SOLVE, P_FE_UPDATE, P_MAC_SMOOTH, P_MAC_RESID, P_FE_SMOOTH, P_FE_RESID, P_NUM
+  P_USTAR, P_FE_SETUP, P_FE_SOLVE, P_FE_UPDATE, P_MAC_SMOOTH, P_MAC_RESID, P_FE_SMOOTH, P_FE_RESID, P_MAC_SWEEP, P_NUM
 };
 const char* const kProfNames[P_NUM] = {
     "stress_n", "godunov_velocity", "mac_setup", "mac_solve", "mac_correct_advect", "xi_predict", "extrapolate_corrector",
     "corrector", "stress_half", "density_ustar", "fe_setup", "fe_solve", "fe_update_density",
-    "k_rbgs(mac,level0,colour)", "k_resid64(mac)", "k_jacobi(fe,level0)", "k_resid64(fe)"};
+    "k_rbgs(mac,level0,colour)", "k_resid64(mac)", "k_jacobi(fe,level0)", "k_resid64(fe)",
+    "k_rbgs_sweep(mac,level0)"};
 struct Prof {
   int on = 0;
   std::vector<cudaEvent_t> pool;
@@ -110,6 +111,7 @@ struct rmt_grid {
   int mac_cpre = -1, mac_cpost = -1, fe_cpre = -1, fe_cpost = -1;  // coarse levels (negative: as level 0)
   int mac_block = 4, fe_block = 4;  // block height of the multigrid level kernels
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
+  int mac_sweep = 1;                // fused red-black sweeps (FP32 MAC)
   double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
@@ -187,14 +189,16 @@ void prof_flush(rmt_grid* g) {
 }
 void mg_hook(void* ctx, int which, int begin, cudaStream_t) {
   HookCtx* h = (HookCtx*)ctx;
-  const int e = h->kind == 0 ? (which == 0 ? P_MAC_SMOOTH : P_MAC_RESID) : (which == 0 ? P_FE_SMOOTH : P_FE_RESID);
+  const int e = h->kind == 0 ? (which == 0 ? P_MAC_SMOOTH : (which == 2 ? P_MAC_SWEEP : P_MAC_RESID))
+                             : (which == 0 ? P_FE_SMOOTH : P_FE_RESID);
   if (begin) pb(h->g, e);
   else pe(h->g, e);
 }
 // algorithmic bytes of one launch of the profiled multigrid kernels (w = bytes per word, N
 // cells, NN nodes): red-black colour pass (7-point): x and rho read once, b read and x written
 // for half the cells; Jacobi pass (27-point): x, b read and x written per node, rho per cell;
-// FP64 residual: x and b 8 bytes each, rho, and the residual copy in the storage type.
+// FP64 residual: x and b 8 bytes each, rho, and the residual copy in the storage type; fused
+// red-black sweep: x, rho and b read and x written once per cell.
 double prof_bytes(const rmt_grid* g, int e) {
   const double w = (double)g->esz, N = (double)g->g.N, NN = (double)g->g.NN;
   switch (e) {
@@ -202,6 +206,7 @@ double prof_bytes(const rmt_grid* g, int e) {
     case P_MAC_RESID: return 16.0 * N + 2.0 * N * w;
     case P_FE_SMOOTH: return 3.0 * NN * w + N * w;
     case P_FE_RESID: return 16.0 * NN + N * w + NN * w;
+    case P_MAC_SWEEP: return 4.0 * N * w;
   }
   return 0.0;
 }
@@ -393,6 +398,7 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_block(g->mac, g->mac_block);
   mg_set_block(g->fe, g->fe_block);
   mg_set_warm(g->mac, g->mac_warm);
+  mg_set_sweep(g->mac, g->mac_sweep);
   mg_set_warm(g->fe, g->fe_warm);
   g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
   return RMT_OK;
@@ -1033,6 +1039,7 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   else if (!strcmp(name, "mac_inner")) ip = &g->mac_inner;
   else if (!strcmp(name, "fe_inner")) ip = &g->fe_inner;
   else if (!strcmp(name, "mac_warm")) ip = &g->mac_warm;
+  else if (!strcmp(name, "mac_sweep")) ip = &g->mac_sweep;
   else if (!strcmp(name, "fe_warm")) ip = &g->fe_warm;
   else if (!strcmp(name, "mac_coarse_pre")) ip = &g->mac_cpre;
   else if (!strcmp(name, "mac_coarse_post")) ip = &g->mac_cpost;
@@ -1067,6 +1074,7 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     mg_set_block(g->mac, g->mac_block);
     mg_set_block(g->fe, g->fe_block);
     mg_set_warm(g->mac, g->mac_warm);
+    mg_set_sweep(g->mac, g->mac_sweep);
     mg_set_warm(g->fe, g->fe_warm);
   }
   return RMT_OK;

@@ -121,8 +121,12 @@ void mg_set_inner(MGSolver* m, int inner);
 void mg_set_block(MGSolver* m, int by);
 // start each solve from the previous solution (zero before the first) instead of from zero
 void mg_set_warm(MGSolver* m, int warm);
+// MAC in FP32: one fused red-black pass per sweep (1: on the large levels that allow it, the
+// default; 2: on every level that allows it; 0: never), else one pass per colour
+void mg_set_sweep(MGSolver* m, int fused);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
-// hook(ctx, which, begin, stream) with which = 0 (smoother colour) or 1 (FP64 residual).
+// hook(ctx, which, begin, stream) with which = 0 (smoother colour), 1 (FP64 residual) or 2 (fused
+// red-black sweep).
 typedef void (*mg_hook_fn)(void* ctx, int which, int begin, cudaStream_t s);
 void mg_set_hook(MGSolver* m, mg_hook_fn fn, void* ctx);
 // Solves to rtol (or a fixed cycle count); returns cycles used, -1 on non-convergence.

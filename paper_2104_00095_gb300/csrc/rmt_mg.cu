@@ -72,11 +72,17 @@ __device__ __forceinline__ int nnb(const Lv& L, int d, int v) {
 }
 
 // ----------------------------------------------------------------------------- operators
+// approximate FP32 reciprocal: the hardware's reciprocal instruction alone (PTX rcp.approx.ftz)
+__device__ __forceinline__ float rcp_approx(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
+}
 // MAC face coefficient 2/(rho_a + rho_b) in the coefficient type; FAST: approximate reciprocal
-// (smoothers only)
+// (smoothers and the V-cycle residual only)
 template <bool FAST, typename CT>
 __device__ __forceinline__ CT face_beta(CT ra, CT rb) {
-  if constexpr (FAST && sizeof(CT) == 4) return __fdividef(2.0f, ra + rb);
+  if constexpr (FAST && sizeof(CT) == 4) return 2.0f * rcp_approx(ra + rb);
   return CT(2) / (ra + rb);
 }
 
@@ -520,7 +526,7 @@ __device__ __forceinline__ void rbgs_at(const Lv& L, int colour, T w, T* __restr
   const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
   const long c = cix(L, i, j, k);
   if (dg > T(0)) {
-    if constexpr (sizeof(T) == 4) x[c] = x[c] + w * __fdividef(b[c] - ax, dg);
+    if constexpr (sizeof(T) == 4) x[c] = x[c] + w * ((b[c] - ax) * rcp_approx(dg));
     else x[c] = x[c] + w * ((b[c] - ax) / dg);
   }
 }
@@ -548,6 +554,205 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Full red-black sweep in one pass (FP32): both colours of a Gauss-Seidel sweep, out of place
+// (x_in -> x_out), marching up a z-chunk of a GX x GY tile.  At plane q the block updates the
+// first colour c0 on the tile and a one-cell ring around it (from x_in only), then the second
+// colour on the tile at plane q-1 (from the new c0 values of planes q-2..q, kept in shared
+// memory).  The ring is recomputed by the neighbouring block with the same arithmetic, so no
+// block reads another block's output, and each value equals that of two in-place colour
+// passes.  Per sweep, x, rho and b are read once and x written once (4 words per cell instead of
+// 6 for two colour passes).  Planes of x, rho and b (with a halo of 4 cells along x, for 16-byte
+// cp.async rows, and 2 rows along y) arrive through a ring of GR slots two planes ahead of use.
+// Warps cover 16 cell pairs of two adjacent rows: the cells of one colour then fall in opposite
+// bank parities in the two half-warps, so the stencil's shared-memory reads are conflict-free.
+// Cells outside a wall are staged as x = 0, rho = 0, and a face whose far density is 0 gets
+// coefficient 0 (the wall's Neumann condition).  Requires n_x % 4 == 0 and even periodic sides.
+constexpr int GX = 64, GY = 8;           // tile: cells along x, rows along y
+constexpr int GW = GX + 8, GH = GY + 4;  // staged plane: 4 halo cells each side along x, 2 rows along y
+constexpr int GP = GW * GH;              // floats per staged plane
+constexpr int GR = 6;                    // ring slots per staged array (planes q-2 .. q+3)
+constexpr int GCH = GW / 4;              // 16-byte chunks per staged row
+constexpr int GNCH = 3 * GH * GCH;       // chunks per plane over x, rho and b
+constexpr int GT = 256;                  // threads per block
+constexpr size_t SWEEP_SMEM = (size_t)(3 * GR + 3) * GP * sizeof(float);
+static_assert((GX / 2) * GY == GT, "one thread per cell pair of the tile");
+static_assert(GW % 4 == 0 && GNCH <= 3 * GT, "staging layout");
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+
+// wrapped index along an axis of n cells (periodic), or -1 outside a wall
+__device__ __forceinline__ int sweep_wrap(int v, int n, int per) {
+  if (per) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return (v >= 0 && v < n) ? v : -1;
+}
+
+// Gauss-Seidel update of one cell from staged planes: X, R = x (or new values) and rho at the
+// cell's plane, XM/XP, RM/RP the planes below/above, xc and bc the cell's x and b, o its offset
+// within a plane.  The face coefficient 2/(rho_c + rho_n) is carried as r = 1/(rho_c + rho_n)
+// with the 2 moved into ih2x2 = 2/h^2 (a power-of-two scaling, so every rounding is that of the
+// colour-pass kernel); WALLS: a staged rho of 0 (outside a wall) gives the face weight 0.
+template <bool WALLS>
+__device__ __forceinline__ float sweep_cell(const float* __restrict__ X, const float* __restrict__ XM,
+                                            const float* __restrict__ XP, const float* __restrict__ R,
+                                            const float* __restrict__ RM, const float* __restrict__ RP, float xc,
+                                            float bc, int o, float ih2x2, float w) {
+  const float rc = R[o];
+  const float rn[6] = {R[o - 1], R[o + 1], R[o - GW], R[o + GW], RM[o], RP[o]};
+  const float xn[6] = {X[o - 1], X[o + 1], X[o - GW], X[o + GW], XM[o], XP[o]};
+  float off = 0.f, dg = 0.f;
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    float r = rcp_approx(rc + rn[f]);
+    if constexpr (WALLS) r = rn[f] > 0.f ? r : 0.f;
+    off += r * xn[f];
+    dg += r;
+  }
+  const float ax = (dg * xc - off) * ih2x2;
+  const float diag = dg * ih2x2;
+  return diag > 0.f ? xc + w * ((bc - ax) * rcp_approx(diag)) : xc;
+}
+
+template <bool WALLS>
+__global__ void __launch_bounds__(GT, 3) k_rbgs_sweep(Lv L, int c0, float w, const float* __restrict__ xin,
+                                                      float* __restrict__ xout, const float* __restrict__ b,
+                                                      const float* __restrict__ rho, int zc) {
+  extern __shared__ float4 sweep_sm4[];
+  float* const sm = reinterpret_cast<float*>(sweep_sm4);
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+  const int i0 = blockIdx.x * GX, j0 = blockIdx.y * GY;
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, nz);
+  const long pst = (long)nx * ny;
+  const float ih2x2 = 2.0f * L.f_ih2;
+  // staging: this thread's chunks (up to 3 of the GNCH per plane): shared offset, and the
+  // source row in plane 0 (null outside a wall)
+  const float* c_src[3];
+  int c_sm[3];
+#pragma unroll
+  for (int s = 0; s < 3; s++) {
+    const int c = t + GT * s;
+    c_src[s] = nullptr;
+    c_sm[s] = -1;
+    if (c < GNCH) {
+      const int a = c / (GH * GCH), rc = c % (GH * GCH), r = rc / GCH, cc = rc % GCH;
+      const int gy = sweep_wrap(j0 - 2 + r, ny, L.per[1]);
+      const int gx = sweep_wrap(i0 - 4 + 4 * cc, nx, L.per[0]);
+      const float* base = a == 0 ? xin : (a == 1 ? rho : b);
+      c_sm[s] = a * GR * GP + r * GW + 4 * cc;
+      if (gy >= 0 && gx >= 0) c_src[s] = base + (long)gy * nx + gx;
+    }
+  }
+  // plane p of the staged arrays sits in ring slot (p - k0 + 2) % GR, its RED plane in slot
+  // (p - k0 + 3) % 3; the loop keeps both for plane q and derives the others by one add
+  auto adv = [](int s, int d, int m) { return s + d >= m ? s + d - m : s + d; };
+  const int perx = L.per[0], pery = L.per[1], perz = L.per[2];
+  auto issue = [&](int p, int slot) {
+    // p lies in [k0-2, k1+1], within two planes of the grid
+    const int pz = p < 0 ? (perz ? p + nz : -1) : (p >= nz ? (perz ? p - nz : -1) : p);
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+      if (c_sm[s] < 0) continue;
+      const bool ok = pz >= 0 && c_src[s] != nullptr;
+      cp_async16(sm + c_sm[s] + slot * GP, ok ? c_src[s] + (long)pz * pst : xin, ok);
+    }
+  };
+  // the thread's cell pair of the tile: 16 pairs of two adjacent rows per warp
+  const int pp = 16 * (wp & 1) + (lane & 15), jj = 2 * (wp >> 1) + (lane >> 4);
+  // its ring pair (first 84 threads): rows -1 and GY across pairs 0..31, then pairs -1 and 32
+  int hp = 0, hj = 0;
+  const bool has_ring = t < 2 * GX / 2 + 2 * (GY + 2);
+  if (t < GX) {
+    hp = 16 * (t >> 5) + (t & 15);
+    hj = (t & 16) ? GY : -1;
+  } else if (has_ring) {
+    const int r = t - GX;
+    hp = r < GY + 2 ? -1 : GX / 2;
+    hj = (r < GY + 2 ? r : r - (GY + 2)) - 1;
+  }
+  const int c1 = c0 ^ 1;
+  const bool tile_row = j0 + jj < ny;  // the thread's tile row lies in the grid
+  // prologue: planes k0-2 .. k0 in one group, k0+1 in the next
+  issue(k0 - 2, 0);
+  issue(k0 - 1, 1);
+  issue(k0, 2);
+  cp_async_commit();
+  issue(k0 + 1, 3);
+  cp_async_commit();
+  int sq = 1, rq = 2;  // slots of plane q = k0-1
+  for (int q = k0 - 1; q <= k1; q++, sq = adv(sq, 1, GR), rq = adv(rq, 1, 3)) {
+    cp_async_wait<1>();  // plane q+1 has landed (q+2 may still fly)
+    __syncthreads();     // ... for every thread; slot of plane q-3 and RED of q-2's store are free
+    if (q + 3 <= k1 + 1) issue(q + 3, adv(sq, 3, GR));
+    cp_async_commit();
+    const int sm1 = adv(sq, GR - 1, GR), sm2 = adv(sq, GR - 2, GR), sp1 = adv(sq, 1, GR);
+    const float* const X0 = sm + sq * GP;
+    const float* const Xm1 = sm + sm1 * GP;
+    const float* const Xp1 = sm + sp1 * GP;
+    const float* const R0 = sm + (GR + sq) * GP;
+    const float* const Rm1 = sm + (GR + sm1) * GP;
+    const float* const Rm2 = sm + (GR + sm2) * GP;
+    const float* const Rp1 = sm + (GR + sp1) * GP;
+    const float* const B0 = sm + (2 * GR + sq) * GP;
+    const float* const Bm1 = sm + (2 * GR + sm1) * GP;
+    float* const N0 = sm + (3 * GR + rq) * GP;                  // RED plane q
+    float* const Nm1 = sm + (3 * GR + adv(rq, 2, 3)) * GP;      // RED plane q-1
+    const float* const Nm2 = sm + (3 * GR + adv(rq, 1, 3)) * GP;  // RED plane q-2
+    // plane q-2's tile (both colours) to x_out: one 16-byte store per thread
+    if (q - 2 >= k0 && t < GX * GY / 4) {
+      const int r = t / (GX / 4), cc = t % (GX / 4);
+      const int gj = j0 + r, gi = i0 + 4 * cc;
+      if (gj < ny && gi < nx) {
+        const float4 v = *reinterpret_cast<const float4*>(Nm2 + (r + 2) * GW + 4 + 4 * cc);
+        *reinterpret_cast<float4*>(xout + (long)(q - 2) * pst + (long)gj * nx + gi) = v;
+      }
+    }
+    // first colour at plane q on the pair (p2, jr) of the extended tile (0 outside a wall)
+    const bool zin = perz || (q >= 0 && q < nz);
+    auto first = [&](int p2, int jr) {
+      const int e = (c0 + j0 + jr + q) & 1;
+      const int ci = 2 * p2 + e;
+      const int o = (jr + 2) * GW + ci + 4;
+      if constexpr (WALLS) {
+        const bool real = zin && (pery || (unsigned)(j0 + jr) < (unsigned)ny) &&
+                          (perx || (unsigned)(i0 + ci) < (unsigned)nx);
+        N0[o] = real ? sweep_cell<true>(X0, Xm1, Xp1, R0, Rm1, Rp1, X0[o], B0[o], o, ih2x2, w) : 0.f;
+      } else {
+        N0[o] = sweep_cell<false>(X0, Xm1, Xp1, R0, Rm1, Rp1, X0[o], B0[o], o, ih2x2, w);
+      }
+    };
+    first(pp, jj);
+    if (has_ring) first(hp, hj);
+    __syncthreads();
+    // second colour on the tile at plane q-1 (RED planes q-2..q hold the new first colour)
+    if (q - 1 >= k0) {
+      const int e = (c1 + j0 + jj + q - 1) & 1;
+      const int ci = 2 * pp + e;
+      const int o = (jj + 2) * GW + ci + 4;
+      if (tile_row && i0 + ci < nx)
+        Nm1[o] = sweep_cell<WALLS>(Nm1, Nm2, N0, Rm1, Rm2, R0, Xm1[o], Bm1[o], o, ih2x2, w);
+    }
+  }
+  // plane k1-1's tile (the last iteration's second colour)
+  cp_async_wait<0>();
+  __syncthreads();
+  if (k1 - 1 >= k0 && t < GX * GY / 4) {
+    const float* const Nl = sm + (3 * GR + adv(rq, 1, 3)) * GP;  // rq is now the slot of k1+1
+    const int r = t / (GX / 4), cc = t % (GX / 4);
+    const int gj = j0 + r, gi = i0 + 4 * cc;
+    if (gj < ny && gi < nx) {
+      const float4 v = *reinterpret_cast<const float4*>(Nl + (r + 2) * GW + 4 + 4 * cc);
+      *reinterpret_cast<float4*>(xout + (long)(k1 - 1) * pst + (long)gj * nx + gi) = v;
+    }
+  }
+}
 
 // 27-point FE sweeps on a plane-marching tile: a block owns FX x FY nodes of every plane of a
 // z-chunk and keeps a ring of RING planes of x and of beta (with a one-point halo) in shared
@@ -1188,6 +1393,11 @@ struct MGSolver {
   int inner = 1;  // V-cycles on the storage-precision correction equation per high-precision residual
   int by = 4;     // block height of the level kernels
   int warm = 0;   // start from the last solution instead of zero
+  // MAC (FP32): fused red-black sweeps (k_rbgs_sweep): 0 never, 1 on the large levels that allow
+  // them, 2 on every level that allows them
+  int sweep = 1;
+  int zc[16] = {};      // z-chunk of k_rbgs_sweep per level (0: the level's layout does not allow it)
+  bool big[16] = {};    // level large enough for the fused sweep to pay
   double omega = 0.9;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
@@ -1211,8 +1421,29 @@ void mg_set_inner(MGSolver* m, int inner) {
   if (inner >= 1) m->inner = inner;
 }
 void mg_set_warm(MGSolver* m, int warm) { m->warm = warm != 0; }
+void mg_set_sweep(MGSolver* m, int fused) { m->sweep = fused < 0 ? 0 : (fused > 2 ? 2 : fused); }
 void mg_set_block(MGSolver* m, int by) {
   if (by == 1 || by == 2 || by == 4 || by == 8) m->by = by;
+}
+
+// z-chunk of the fused sweep on level Q with `resident` blocks on the GPU at once: the chunk
+// count that best fills whole waves, discounted by the two extra first-colour planes a chunk
+// recomputes
+static int sweep_chunk(const Lv& Q, int resident) {
+  const long tiles = (long)((Q.n[0] + GX - 1) / GX) * ((Q.n[1] + GY - 1) / GY);
+  int best = Q.n[2];
+  double best_eff = -1.0;
+  for (int c = 1; c <= Q.n[2]; c++) {
+    const int zc = (Q.n[2] + c - 1) / c;
+    const long blocks = tiles * ((Q.n[2] + zc - 1) / zc);
+    const long waves = (blocks + resident - 1) / resident;
+    const double eff = (double)blocks / (double)(waves * resident) * (double)zc / (double)(zc + 2);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = zc;
+    }
+  }
+  return best;
 }
 
 static cudaError_t dmalloc(void** p, size_t bytes) {
@@ -1298,6 +1529,36 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
       else
         e = cudaFuncSetAttribute(k_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) opted[prec_fp32 ? 1 : 0] = smem;
+    }
+    // the fused sweep's staging ring (beyond the 48 KB default) with the largest shared-memory
+    // carveout, so that three blocks fit on an SM; once per process
+    static bool sweep_opted = false;
+    if (e == cudaSuccess && kind == 0 && prec_fp32 && !sweep_opted) {
+      for (int v = 0; v < 2 && e == cudaSuccess; v++) {
+        const void* fn = v ? (const void*)k_rbgs_sweep<true> : (const void*)k_rbgs_sweep<false>;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+      }
+      if (e == cudaSuccess) sweep_opted = true;
+    }
+    if (e == cudaSuccess && kind == 0 && prec_fp32) {
+      // levels that take the fused sweep: rows of whole 16-byte chunks and even periodic sides (a
+      // consistent two-colouring across the wrap); z-chunks sized to the blocks resident at once
+      int dev = 0, nsm = 152, per_sm = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep<true>, GT, SWEEP_SMEM) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+      for (int l = 0; l < m->nlev; l++) {
+        const Lv& Q = m->lv[l];
+        bool ok = Q.n[0] % 4 == 0;
+        for (int d = 0; d < 3; d++)
+          if (Q.per[d] && (Q.n[d] & 1)) ok = false;
+        m->zc[l] = ok ? sweep_chunk(Q, per_sm * nsm) : 0;
+        m->big[l] = Q.n[0] >= 64 && Q.ncell >= (1L << 20);
+      }
     }
   }
   if (err) *err = e;
@@ -1390,6 +1651,25 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   const T* b = (const T*)m->b[l];
   const T* rho = (const T*)m->rho[l];
   for (int it = 0; it < sweeps; it++) {
+    if constexpr (sizeof(T) == 4) {
+      if (m->kind == 0 && m->zc[l] > 0 && (m->sweep == 2 || (m->sweep == 1 && m->big[l]))) {
+        // both colours in one out-of-place pass: x[l] -> xt[l], then the two swap roles
+        const dim3 gr((L.n[0] + GX - 1) / GX, (L.n[1] + GY - 1) / GY, (L.n[2] + m->zc[l] - 1) / m->zc[l]);
+        hk(m, l, 2, 1, s);
+        if (L.per[0] && L.per[1] && L.per[2])
+          k_rbgs_sweep<false><<<gr, GT, SWEEP_SMEM, s>>>(L, forward ? 0 : 1, (float)m->omega, (const float*)m->x[l],
+                                                         (float*)m->xt[l], b, rho, m->zc[l]);
+        else
+          k_rbgs_sweep<true><<<gr, GT, SWEEP_SMEM, s>>>(L, forward ? 0 : 1, (float)m->omega, (const float*)m->x[l],
+                                                        (float*)m->xt[l], b, rho, m->zc[l]);
+        rmt_count_launches(1);
+        hk(m, l, 2, 0, s);
+        void* t = m->x[l];
+        m->x[l] = m->xt[l];
+        m->xt[l] = t;
+        continue;
+      }
+    }
     if (m->kind == 0) {
       const dim3 gr(((L.n[0] + 1) / 2 + BX - 1) / BX, (L.n[1] + m->by - 1) / m->by, L.n[2]);
       for (int q = 0; q < 2; q++) {

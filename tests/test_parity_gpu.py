@@ -74,10 +74,13 @@ def test_pure_fluid_cavity_parity():
         compare_state(g, o, 0, TOL64, tag=f"fluid step {s + 1}")
 
 
-def test_fp32_bulk_within_1e4_after_10_steps():
+@pytest.mark.parametrize("sweep", [1, 2])
+def test_fp32_bulk_within_1e4_after_10_steps(sweep):
+    """sweep 2 runs the fused red-black pass on every MAC level of the 32^3 cavity (32 down to 4,
+    no-slip walls on every side); sweep 1 leaves these small levels to one pass per colour."""
     sc = S.cavity_sphere(32, precision="fp32")
     sc64 = dict(sc, precision="fp64")
-    g = rmt.Grid(dict(sc, mg_rtol=1e-10, mg_max_cycles=200))
+    g = rmt.Grid(dict(sc, mg_rtol=1e-10, mg_max_cycles=200, options={"mac_sweep": sweep}))
     o = O.Oracle(sc64)
     g.step(10)
     assert o.step(10) == 0
@@ -89,6 +92,42 @@ def test_fp32_bulk_within_1e4_after_10_steps():
     assert np.count_nonzero(np.isfinite(xg) != np.isfinite(xo)) <= 0.01 * both.sum()
     assert eu <= 1e-4, eu
     assert ex <= 1e-4, ex
+
+
+def _ragged_walls_fp32():
+    sc = S._box(64, periodic=False, lid=1.0)
+    sc.update(n=(68, 60, 64), hi=(68 / 64, 60 / 64, 1.0), dt=0.2 / 64, mu=0.01, precision="fp32")
+    sc["solids"] = [S.solid(S.ELLIPSOID, (0.5, 0.45, 0.5), (0.2, 0.12, 0.15),
+                            S.random_rotation(np.random.default_rng(4)), rho_s=1.3, G=0.4, mu_a=0.01)]
+    return sc
+
+
+@pytest.mark.parametrize("name,sweep", [("cavity128", 1), ("swimmers128", 1), ("ragged68x60x64", 2)])
+def test_fused_sweep_matches_colour_passes(name, sweep):
+    """The fused red-black pass (both colours per launch, out of place, z-chunked tiles with a
+    recomputed first-colour ring) against one in-place pass per colour, on the fixed-cycle FP32
+    schedule of the bench: no-slip walls on every side (cavity), a triply periodic box
+    (swimmers), and walls with partial tiles along x and y (68 x 60 x 64).  The two compute the
+    same sweep with the same operations; only the compiler's contraction of products into FMAs
+    may differ, so the results agree far below the FP32 bar."""
+    if name == "cavity128":
+        sc = S.cavity_sphere(128, precision="fp32")
+    elif name == "swimmers128":
+        sc = S.swimmers(n=128, nbodies=2, seed=7, precision="fp32")
+    else:
+        sc = _ragged_walls_fp32()
+
+    def run(mode):
+        g = rmt.Grid(dict(sc, mg_fixed_cycles=5, mg_fixed_cycles_fe=4, options=dict(BENCH_OPTIONS, mac_sweep=mode)))
+        g.step(3)
+        out = [g.read(f) for f in (rmt.RMT_F_U, rmt.RMT_F_P, rmt.RMT_F_RHO)]
+        g.close()
+        return out
+
+    ref, fused = run(0), run(sweep)
+    for a, b in zip(fused, ref):
+        assert np.all(np.isfinite(a))
+        assert rel_l2(a, b) <= 1e-6, rel_l2(a, b)
 
 
 def test_runs_are_bit_identical():
