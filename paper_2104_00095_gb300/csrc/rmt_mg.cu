@@ -564,7 +564,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // passes.  Per sweep, x, rho and b are read once and x written once (4 words per cell instead of
 // 6 for two colour passes).  Planes of x, rho and b (with a halo of 4 cells along x, for 16-byte
 // cp.async rows, and 2 rows along y) arrive through a ring of GR slots two planes ahead of use.
-// Warps cover 16 cell pairs of two adjacent rows: the cells of one colour then fall in opposite
+// The second colour's cell at plane q-1 is the cell of the thread's first colour at plane q (the
+// colour alternates along z), so that update's own values stay in registers.  Warps cover 16 cell pairs of two adjacent rows: the cells of one colour then fall in opposite
 // bank parities in the two half-warps, so the stencil's shared-memory reads are conflict-free.
 // Cells outside a wall are staged as x = 0, rho = 0, and a face whose far density is 0 gets
 // coefficient 0 (the wall's Neumann condition).  Requires n_x % 4 == 0 and even periodic sides.
@@ -579,12 +580,6 @@ constexpr size_t SWEEP_SMEM = (size_t)(3 * GR + 3) * GP * sizeof(float);
 static_assert((GX / 2) * GY == GT, "one thread per cell pair of the tile");
 static_assert(GW % 4 == 0 && GNCH <= 3 * GT, "staging layout");
 
-__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
-}
-
 // wrapped index along an axis of n cells (periodic), or -1 outside a wall
 __device__ __forceinline__ int sweep_wrap(int v, int n, int per) {
   if (per) {
@@ -594,19 +589,14 @@ __device__ __forceinline__ int sweep_wrap(int v, int n, int per) {
   return (v >= 0 && v < n) ? v : -1;
 }
 
-// Gauss-Seidel update of one cell from staged planes: X, R = x (or new values) and rho at the
-// cell's plane, XM/XP, RM/RP the planes below/above, xc and bc the cell's x and b, o its offset
-// within a plane.  The face coefficient 2/(rho_c + rho_n) is carried as r = 1/(rho_c + rho_n)
-// with the 2 moved into ih2x2 = 2/h^2 (a power-of-two scaling, so every rounding is that of the
-// colour-pass kernel); WALLS: a staged rho of 0 (outside a wall) gives the face weight 0.
+// Gauss-Seidel update of one cell: rc, xc, bc its rho, x and b; rn, xn the rho and x of its six
+// face neighbours (-x, +x, -y, +y, -z, +z).  The face coefficient 2/(rho_c + rho_n) is carried as
+// r = 1/(rho_c + rho_n) with the 2 moved into ih2x2 = 2/h^2 (a power-of-two scaling, so every
+// rounding is that of the colour-pass kernel); WALLS: a staged rho of 0 (outside a wall) gives
+// the face weight 0.
 template <bool WALLS>
-__device__ __forceinline__ float sweep_cell(const float* __restrict__ X, const float* __restrict__ XM,
-                                            const float* __restrict__ XP, const float* __restrict__ R,
-                                            const float* __restrict__ RM, const float* __restrict__ RP, float xc,
-                                            float bc, int o, float ih2x2, float w) {
-  const float rc = R[o];
-  const float rn[6] = {R[o - 1], R[o + 1], R[o - GW], R[o + GW], RM[o], RP[o]};
-  const float xn[6] = {X[o - 1], X[o + 1], X[o - GW], X[o + GW], XM[o], XP[o]};
+__device__ __forceinline__ float sweep_update(float rc, const float (&rn)[6], const float (&xn)[6], float xc, float bc,
+                                              float ih2x2, float w) {
   float off = 0.f, dg = 0.f;
 #pragma unroll
   for (int f = 0; f < 6; f++) {
@@ -625,60 +615,67 @@ __global__ void __launch_bounds__(GT, 3) k_rbgs_sweep(Lv L, int c0, float w, con
                                                       float* __restrict__ xout, const float* __restrict__ b,
                                                       const float* __restrict__ rho, int zc) {
   extern __shared__ float4 sweep_sm4[];
-  float* const sm = reinterpret_cast<float*>(sweep_sm4);
+  float* const sm = reinterpret_cast<float*>(sweep_sm4);  // all shared reads index this base
   const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
   const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
   const int i0 = blockIdx.x * GX, j0 = blockIdx.y * GY;
   const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, nz);
   const long pst = (long)nx * ny;
   const float ih2x2 = 2.0f * L.f_ih2;
-  // staging: this thread's chunks (up to 3 of the GNCH per plane): shared offset, and the
-  // source row in plane 0 (null outside a wall)
+  const int perx = L.per[0], pery = L.per[1], perz = L.per[2];
+  // staging: this thread's chunks (up to 3 of the GNCH per plane): shared address in slot 0, and
+  // the source row in plane 0 (null outside a wall)
+  const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
   const float* c_src[3];
-  int c_sm[3];
+  unsigned c_sa[3];
+  bool c_on[3];
 #pragma unroll
   for (int s = 0; s < 3; s++) {
     const int c = t + GT * s;
     c_src[s] = nullptr;
-    c_sm[s] = -1;
+    c_sa[s] = 0;
+    c_on[s] = c < GNCH;
     if (c < GNCH) {
       const int a = c / (GH * GCH), rc = c % (GH * GCH), r = rc / GCH, cc = rc % GCH;
-      const int gy = sweep_wrap(j0 - 2 + r, ny, L.per[1]);
-      const int gx = sweep_wrap(i0 - 4 + 4 * cc, nx, L.per[0]);
+      const int gy = sweep_wrap(j0 - 2 + r, ny, pery);
+      const int gx = sweep_wrap(i0 - 4 + 4 * cc, nx, perx);
       const float* base = a == 0 ? xin : (a == 1 ? rho : b);
-      c_sm[s] = a * GR * GP + r * GW + 4 * cc;
+      c_sa[s] = sm_base + 4u * (unsigned)(a * GR * GP + r * GW + 4 * cc);
       if (gy >= 0 && gx >= 0) c_src[s] = base + (long)gy * nx + gx;
     }
   }
   // plane p of the staged arrays sits in ring slot (p - k0 + 2) % GR, its RED plane in slot
   // (p - k0 + 3) % 3; the loop keeps both for plane q and derives the others by one add
   auto adv = [](int s, int d, int m) { return s + d >= m ? s + d - m : s + d; };
-  const int perx = L.per[0], pery = L.per[1], perz = L.per[2];
   auto issue = [&](int p, int slot) {
     // p lies in [k0-2, k1+1], within two planes of the grid
     const int pz = p < 0 ? (perz ? p + nz : -1) : (p >= nz ? (perz ? p - nz : -1) : p);
 #pragma unroll
     for (int s = 0; s < 3; s++) {
-      if (c_sm[s] < 0) continue;
+      if (!c_on[s]) continue;
       const bool ok = pz >= 0 && c_src[s] != nullptr;
-      cp_async16(sm + c_sm[s] + slot * GP, ok ? c_src[s] + (long)pz * pst : xin, ok);
+      const float* g = ok ? c_src[s] + (long)pz * pst : xin;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(c_sa[s] + 4u * (unsigned)(slot * GP)),
+                   "l"(g), "r"(ok ? 16 : 0));
     }
   };
   // the thread's cell pair of the tile: 16 pairs of two adjacent rows per warp
   const int pp = 16 * (wp & 1) + (lane & 15), jj = 2 * (wp >> 1) + (lane >> 4);
-  // its ring pair (first 84 threads): rows -1 and GY across pairs 0..31, then pairs -1 and 32
+  // its ring pair (first 80 threads): rows -1 and GY across pairs 0..31, then pairs -1 and 32
+  // for rows 0..GY-1 (the corners are not needed)
+  constexpr int NRING = GX + 2 * GY;
   int hp = 0, hj = 0;
-  const bool has_ring = t < 2 * GX / 2 + 2 * (GY + 2);
+  const bool has_ring = t < NRING;
   if (t < GX) {
     hp = 16 * (t >> 5) + (t & 15);
     hj = (t & 16) ? GY : -1;
   } else if (has_ring) {
     const int r = t - GX;
-    hp = r < GY + 2 ? -1 : GX / 2;
-    hj = (r < GY + 2 ? r : r - (GY + 2)) - 1;
+    hp = r < GY ? -1 : GX / 2;
+    hj = r < GY ? r : r - GY;
   }
-  const int c1 = c0 ^ 1;
   const bool tile_row = j0 + jj < ny;  // the thread's tile row lies in the grid
+  const int orow = (jj + 2) * GW + 4, hrow = (hj + 2) * GW + 4;
   // prologue: planes k0-2 .. k0 in one group, k0+1 in the next
   issue(k0 - 2, 0);
   issue(k0 - 1, 1);
@@ -693,62 +690,69 @@ __global__ void __launch_bounds__(GT, 3) k_rbgs_sweep(Lv L, int c0, float w, con
     if (q + 3 <= k1 + 1) issue(q + 3, adv(sq, 3, GR));
     cp_async_commit();
     const int sm1 = adv(sq, GR - 1, GR), sm2 = adv(sq, GR - 2, GR), sp1 = adv(sq, 1, GR);
-    const float* const X0 = sm + sq * GP;
-    const float* const Xm1 = sm + sm1 * GP;
-    const float* const Xp1 = sm + sp1 * GP;
-    const float* const R0 = sm + (GR + sq) * GP;
-    const float* const Rm1 = sm + (GR + sm1) * GP;
-    const float* const Rm2 = sm + (GR + sm2) * GP;
-    const float* const Rp1 = sm + (GR + sp1) * GP;
-    const float* const B0 = sm + (2 * GR + sq) * GP;
-    const float* const Bm1 = sm + (2 * GR + sm1) * GP;
-    float* const N0 = sm + (3 * GR + rq) * GP;                  // RED plane q
-    float* const Nm1 = sm + (3 * GR + adv(rq, 2, 3)) * GP;      // RED plane q-1
-    const float* const Nm2 = sm + (3 * GR + adv(rq, 1, 3)) * GP;  // RED plane q-2
+    // plane bases (float offsets into sm): x, rho, b of planes q-2..q+1; RED of q-2..q
+    const int X0 = sq * GP, Xm1 = sm1 * GP, Xp1 = sp1 * GP;
+    const int R0 = (GR + sq) * GP, Rm1 = (GR + sm1) * GP, Rm2 = (GR + sm2) * GP, Rp1 = (GR + sp1) * GP;
+    const int B0 = (2 * GR + sq) * GP, Bm1 = (2 * GR + sm1) * GP;
+    const int N0 = (3 * GR + rq) * GP, Nm1 = (3 * GR + adv(rq, 2, 3)) * GP, Nm2 = (3 * GR + adv(rq, 1, 3)) * GP;
     // plane q-2's tile (both colours) to x_out: one 16-byte store per thread
     if (q - 2 >= k0 && t < GX * GY / 4) {
       const int r = t / (GX / 4), cc = t % (GX / 4);
       const int gj = j0 + r, gi = i0 + 4 * cc;
       if (gj < ny && gi < nx) {
-        const float4 v = *reinterpret_cast<const float4*>(Nm2 + (r + 2) * GW + 4 + 4 * cc);
+        const float4 v = *reinterpret_cast<const float4*>(sm + Nm2 + (r + 2) * GW + 4 + 4 * cc);
         *reinterpret_cast<float4*>(xout + (long)(q - 2) * pst + (long)gj * nx + gi) = v;
       }
     }
-    // first colour at plane q on the pair (p2, jr) of the extended tile (0 outside a wall)
-    const bool zin = perz || (q >= 0 && q < nz);
-    auto first = [&](int p2, int jr) {
-      const int e = (c0 + j0 + jr + q) & 1;
-      const int ci = 2 * p2 + e;
-      const int o = (jr + 2) * GW + ci + 4;
+    const bool zin = !WALLS || perz || (q >= 0 && q < nz);
+    // first colour at plane q: the thread's tile pair (its cell o is also the second colour's
+    // cell at plane q-1, so the values below are reused there)
+    const int e = (c0 + j0 + jj + q) & 1;
+    const int o = orow + 2 * pp + e;
+    const float rc = sm[R0 + o], rlo = sm[Rm1 + o], xlo = sm[Xm1 + o];
+    float vq;
+    {
+      const float rn[6] = {sm[R0 + o - 1], sm[R0 + o + 1], sm[R0 + o - GW], sm[R0 + o + GW], rlo, sm[Rp1 + o]};
+      const float xn[6] = {sm[X0 + o - 1], sm[X0 + o + 1], sm[X0 + o - GW], sm[X0 + o + GW], xlo, sm[Xp1 + o]};
+      vq = sweep_update<WALLS>(rc, rn, xn, sm[X0 + o], sm[B0 + o], ih2x2, w);
       if constexpr (WALLS) {
-        const bool real = zin && (pery || (unsigned)(j0 + jr) < (unsigned)ny) &&
-                          (perx || (unsigned)(i0 + ci) < (unsigned)nx);
-        N0[o] = real ? sweep_cell<true>(X0, Xm1, Xp1, R0, Rm1, Rp1, X0[o], B0[o], o, ih2x2, w) : 0.f;
-      } else {
-        N0[o] = sweep_cell<false>(X0, Xm1, Xp1, R0, Rm1, Rp1, X0[o], B0[o], o, ih2x2, w);
+        const bool real = zin && (pery || tile_row) && (perx || (unsigned)(i0 + o - orow) < (unsigned)nx);
+        vq = real ? vq : 0.f;
       }
-    };
-    first(pp, jj);
-    if (has_ring) first(hp, hj);
+      sm[N0 + o] = vq;
+    }
+    if (has_ring) {
+      const int eh = (c0 + j0 + hj + q) & 1;
+      const int oh = hrow + 2 * hp + eh;
+      const float rn[6] = {sm[R0 + oh - 1], sm[R0 + oh + 1], sm[R0 + oh - GW], sm[R0 + oh + GW], sm[Rm1 + oh],
+                           sm[Rp1 + oh]};
+      const float xn[6] = {sm[X0 + oh - 1], sm[X0 + oh + 1], sm[X0 + oh - GW], sm[X0 + oh + GW], sm[Xm1 + oh],
+                           sm[Xp1 + oh]};
+      float v = sweep_update<WALLS>(sm[R0 + oh], rn, xn, sm[X0 + oh], sm[B0 + oh], ih2x2, w);
+      if constexpr (WALLS) {
+        const bool real = zin && (pery || (unsigned)(j0 + hj) < (unsigned)ny) &&
+                          (perx || (unsigned)(i0 + oh - hrow) < (unsigned)nx);
+        v = real ? v : 0.f;
+      }
+      sm[N0 + oh] = v;
+    }
     __syncthreads();
-    // second colour on the tile at plane q-1 (RED planes q-2..q hold the new first colour)
-    if (q - 1 >= k0) {
-      const int e = (c1 + j0 + jj + q - 1) & 1;
-      const int ci = 2 * pp + e;
-      const int o = (jj + 2) * GW + ci + 4;
-      if (tile_row && i0 + ci < nx)
-        Nm1[o] = sweep_cell<WALLS>(Nm1, Nm2, N0, Rm1, Rm2, R0, Xm1[o], Bm1[o], o, ih2x2, w);
+    // second colour on the tile at plane q-1, cell o (RED planes q-2..q hold the new first colour)
+    if (q - 1 >= k0 && tile_row && i0 + o - orow < nx) {
+      const float rn[6] = {sm[Rm1 + o - 1], sm[Rm1 + o + 1], sm[Rm1 + o - GW], sm[Rm1 + o + GW], sm[Rm2 + o], rc};
+      const float xn[6] = {sm[Nm1 + o - 1], sm[Nm1 + o + 1], sm[Nm1 + o - GW], sm[Nm1 + o + GW], sm[Nm2 + o], vq};
+      sm[Nm1 + o] = sweep_update<WALLS>(rlo, rn, xn, xlo, sm[Bm1 + o], ih2x2, w);
     }
   }
   // plane k1-1's tile (the last iteration's second colour)
   cp_async_wait<0>();
   __syncthreads();
   if (k1 - 1 >= k0 && t < GX * GY / 4) {
-    const float* const Nl = sm + (3 * GR + adv(rq, 1, 3)) * GP;  // rq is now the slot of k1+1
+    const int Nl = (3 * GR + adv(rq, 1, 3)) * GP;  // rq is now the slot of k1+1
     const int r = t / (GX / 4), cc = t % (GX / 4);
     const int gj = j0 + r, gi = i0 + 4 * cc;
     if (gj < ny && gi < nx) {
-      const float4 v = *reinterpret_cast<const float4*>(Nl + (r + 2) * GW + 4 + 4 * cc);
+      const float4 v = *reinterpret_cast<const float4*>(sm + Nl + (r + 2) * GW + 4 + 4 * cc);
       *reinterpret_cast<float4*>(xout + (long)(k1 - 1) * pst + (long)gj * nx + gi) = v;
     }
   }
