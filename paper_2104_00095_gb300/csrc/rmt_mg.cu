@@ -766,14 +766,23 @@ __global__ void __launch_bounds__(GT, 3) k_rbgs_sweep(Lv L, int c0, float w, con
 // wall carry beta = 0, which makes the stencil uniform (the clamped x of an outside node always
 // meets a zero weight).  MODE 0: weighted Jacobi, out = x + w (b - K x) / diag (x where
 // diag = 0); MODE 1: residual, out = b - K x.
+// VEC (FP32, periodic x with n_x % 4 == 0): planes arrive as 16-byte rows, one copy per thread
+// per plane (x rows widened to 4 halo nodes on each side, beta rows to 4 halo cells on the left)
+// instead of one 4-byte copy per element.
 constexpr int FX = 32, FY = 8, FZ = 32, RING = 5;
 constexpr int XH = (FX + 2) * (FY + 2) - FX * FY;  // halo nodes of an x plane (84)
 constexpr int BH = (FX + 1) * (FY + 1) - FX * FY;  // halo cells of a beta plane (41)
-template <typename T, int MODE>
+constexpr int VXC = (FX + 8) / 4, VBC = (FX + 4) / 4, VRC = FX / 4;  // 16-byte chunks per staged row (VEC)
+constexpr int VNX = (FY + 2) * VXC, VNR = FY * VRC, VNB = (FY + 1) * VBC;  // chunks per plane (VEC)
+static_assert(VNX + VNR + VNB <= FX * FY, "one staged chunk per thread and plane");
+template <typename T, int MODE, bool VEC = false>
 __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restrict__ x, T* __restrict__ out,
                                                     const T* __restrict__ b, const T* __restrict__ beta) {
-  __shared__ __align__(16) T xs[RING][FY + 2][FX + 2];
-  __shared__ __align__(16) T bs[RING][FY + 1][FX + 1];
+  static_assert(!VEC || sizeof(T) == 4, "16-byte rows of floats");
+  constexpr int XW = VEC ? FX + 8 : FX + 2, BW = VEC ? FX + 4 : FX + 1;  // staged row lengths
+  constexpr int XO = VEC ? 3 : 0, BO = VEC ? 3 : 0;  // column of node i0-1 / cell i0-1
+  __shared__ __align__(16) T xs[RING][FY + 2][XW];
+  __shared__ __align__(16) T bs[RING][FY + 1][BW];
   __shared__ __align__(16) T rs[RING][FY][FX];  // right-hand side b of the tile's nodes
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * FX + tx;
   const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY;
@@ -813,20 +822,64 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
   const int ci_halo = cnb(L, 0, i0 - 1 + hba), cj_halo = cnb(L, 1, j0 - 1 + hbc);
   const bool b_own_ok = ci_own >= 0 && cj_own >= 0, b_halo_ok = ci_halo >= 0 && cj_halo >= 0;
   const long bo_own = b_own_ok ? ci_own + cj_own * cy : 0, bo_halo = b_halo_ok ? ci_halo + cj_halo * cy : 0;
+  // VEC: this thread's chunk of a plane (kind 0: an x row chunk, 1: a b row chunk, 2: a beta row
+  // chunk, -1: none), its in-plane source offset and its shared slot-0 address
+  int vk = -1;
+  long voff = 0;
+  bool vok = true;
+  T* vdst = nullptr;
+  size_t vslot = 0;  // elements between ring slots of the chunk's array
+  if constexpr (VEC) {
+    const int nx0 = L.n[0];  // = nn[0] on a periodic x axis
+    auto wx = [&](int v) { return ((v % nx0) + nx0) % nx0; };
+    if (t < VNX) {
+      const int r = t / VXC, cc = t % VXC;
+      vk = 0;
+      voff = nnb(L, 1, j0 - 1 + r) * sy + wx(i0 - 4 + 4 * cc);
+      vdst = &xs[0][r][4 * cc];
+      vslot = (size_t)(FY + 2) * XW;
+    } else if (t < VNX + VNR) {
+      const int u = t - VNX, r = u / VRC, cc = u % VRC;
+      vk = 1;
+      voff = (long)min(j0 + r, L.nn[1] - 1) * sy + wx(i0 + 4 * cc);
+      vdst = &rs[0][r][4 * cc];
+      vslot = (size_t)FY * FX;
+    } else if (t < VNX + VNR + VNB) {
+      const int u = t - VNX - VNR, r = u / VBC, cc = u % VBC;
+      const int cyv = cnb(L, 1, j0 - 1 + r);
+      vk = 2;
+      vok = cyv >= 0;
+      voff = vok ? (long)cyv * cy + wx(i0 - 4 + 4 * cc) : 0;
+      vdst = &bs[0][r][4 * cc];
+      vslot = (size_t)(FY + 1) * BW;
+    }
+  }
+  auto cp16 = [&](T* dst, const T* src, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(valid ? 16 : 0));
+  };
   // x plane p lives in ring slot (p - k0 + 1) % RING, beta cell plane c in (c - k0 + 1) % RING
   auto issue_x = [&](int p) {  // x plane p with its halo, and b of the tile's nodes on it
     const int slot = (p - k0 + 1 + RING) % RING;
     const long base = nnb(L, 2, p) * sz;
-    cp_async_elem(&xs[slot][ty + 1][tx + 1], x + xo_own + base, true);
-    if (t < XH) cp_async_elem(&xs[slot][hxc][hxa], x + xo_halo + base, true);
-    cp_async_elem(&rs[slot][ty][tx], b + xo_own + base, true);
+    if constexpr (VEC) {
+      if (vk == 0 || vk == 1) cp16(vdst + slot * vslot, (vk == 0 ? x : b) + base + voff, true);
+    } else {
+      cp_async_elem(&xs[slot][ty + 1][tx + 1], x + xo_own + base, true);
+      if (t < XH) cp_async_elem(&xs[slot][hxc][hxa], x + xo_halo + base, true);
+      cp_async_elem(&rs[slot][ty][tx], b + xo_own + base, true);
+    }
   };
   auto issue_b = [&](int c) {
     const int slot = (c - k0 + 1 + RING) % RING;
     const int ck = cnb(L, 2, c);
     const long base = ck >= 0 ? ck * cz : 0;
-    cp_async_elem(&bs[slot][ty + 1][tx + 1], beta + bo_own + base, b_own_ok && ck >= 0);
-    if (t < BH) cp_async_elem(&bs[slot][hbc][hba], beta + bo_halo + base, b_halo_ok && ck >= 0);
+    if constexpr (VEC) {
+      if (vk == 2) cp16(vdst + slot * vslot, beta + base + voff, vok && ck >= 0);
+    } else {
+      cp_async_elem(&bs[slot][ty + 1][tx + 1], beta + bo_own + base, b_own_ok && ck >= 0);
+      if (t < BH) cp_async_elem(&bs[slot][hbc][hba], beta + bo_halo + base, b_halo_ok && ck >= 0);
+    }
   };
   // group 0: x planes k0-1 .. k0+1, cell planes k0-1, k0; then one group per further plane
   issue_x(k0 - 1);
@@ -854,13 +907,13 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
 #pragma unroll
     for (int c = 0; c < 3; c++)
 #pragma unroll
-      for (int a = 0; a < 3; a++) P[c][a] = xs[slot][ty + c][tx + a];
+      for (int a = 0; a < 3; a++) P[c][a] = xs[slot][ty + c][tx + XO + a];
   };
   auto rd_b = [&](T (&P)[2][2], int slot) {
 #pragma unroll
     for (int c = 0; c < 2; c++)
 #pragma unroll
-      for (int a = 0; a < 2; a++) P[c][a] = bs[slot][ty + c][tx + a];
+      for (int a = 0; a < 2; a++) P[c][a] = bs[slot][ty + c][tx + BO + a];
   };
   const long ubase = (long)i + (long)j * sy;
   int k = k0;
@@ -1645,6 +1698,11 @@ void sum_ff(MGSolver* m, const float* h, const float* l, long n, double scale, d
   rmt_count_launches(1);
 }
 
+// the FE tile kernel stages 16-byte rows on FP32 levels with a periodic x axis of n_x % 4 == 0
+template <typename T>
+inline bool fe_vec(const Lv& L) {
+  return sizeof(T) == 4 && L.per[0] && L.n[0] % 4 == 0;
+}
 inline dim3 fe_grid(const Lv& L) {
   return dim3((L.nn[0] + FX - 1) / FX, (L.nn[1] + FY - 1) / FY, (L.nn[2] + FZ - 1) / FZ);
 }
@@ -1685,7 +1743,12 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
       }
     } else {
       hk(m, l, 0, 1, s);
-      k_fe_tile<T, 0><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(m->omega), (const T*)m->x[l], (T*)m->xt[l], b, rho);
+      if (fe_vec<T>(L))
+        k_fe_tile<float, 0, true><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, (float)m->omega, (const float*)m->x[l],
+                                                                      (float*)m->xt[l], (const float*)b,
+                                                                      (const float*)rho);
+      else
+        k_fe_tile<T, 0><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(m->omega), (const T*)m->x[l], (T*)m->xt[l], b, rho);
       rmt_count_launches(1);
       hk(m, l, 0, 0, s);
       void* t = m->x[l];
@@ -1724,8 +1787,12 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
         L, C, (const T*)m->x[l], (const T*)m->b[l], (const T*)m->rho[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
     rmt_count_launches(1);
   } else {
-    k_fe_tile<T, 1><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
-                                                       (const T*)m->rho[l]);
+    if (fe_vec<T>(L))
+      k_fe_tile<float, 1, true><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, 0.f, (const float*)m->x[l], (float*)m->r[l],
+                                                                    (const float*)m->b[l], (const float*)m->rho[l]);
+    else
+      k_fe_tile<T, 1><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
+                                                         (const T*)m->rho[l]);
     rmt_count_launches(1);
     k_restrict<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(
         L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
