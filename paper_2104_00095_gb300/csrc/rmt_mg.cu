@@ -759,9 +759,10 @@ __global__ void __launch_bounds__(GT, 3) k_rbgs_sweep(Lv L, int c0, float w, con
 }
 
 // 27-point FE sweeps on a plane-marching tile: a block owns FX x FY nodes of every plane of a
-// z-chunk and keeps a ring of RING planes of x and of beta (with a one-point halo) in shared
-// memory, and each thread a register window of its column (below); the next planes arrive by
-// cp.async while one is computed.
+// z-chunk (FZ planes, fewer on small levels; the grid's z extent sets it) and keeps a ring of
+// RING planes of x and of beta (with a one-point halo) in shared memory, and each thread a
+// register window of its column (below); the next planes arrive by cp.async while one is
+// computed.
 // Each value is read from global memory about once instead of up to 27 times.  Cells outside a
 // wall carry beta = 0, which makes the stencil uniform (the clamped x of an outside node always
 // meets a zero weight).  MODE 0: weighted Jacobi, out = x + w (b - K x) / diag (x where
@@ -786,7 +787,8 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
   __shared__ __align__(16) T rs[RING][FY][FX];  // right-hand side b of the tile's nodes
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * FX + tx;
   const int i0 = blockIdx.x * FX, j0 = blockIdx.y * FY;
-  const int k0 = blockIdx.z * FZ, k1 = min(k0 + FZ, L.nn[2]);
+  const int fz = (L.nn[2] + (int)gridDim.z - 1) / (int)gridDim.z;  // planes per block (FZ, or fewer on small levels)
+  const int k0 = blockIdx.z * fz, k1 = min(k0 + fz, L.nn[2]);
   const long sy = L.nn[0], sz = (long)L.nn[0] * L.nn[1];
   const long cy = L.n[0], cz = (long)L.n[0] * L.n[1];
   // this thread's elements of a plane: its own node (tx+1, ty+1) and, for the first XH threads,
@@ -1704,7 +1706,14 @@ inline bool fe_vec(const Lv& L) {
   return sizeof(T) == 4 && L.per[0] && L.n[0] % 4 == 0;
 }
 inline dim3 fe_grid(const Lv& L) {
-  return dim3((L.nn[0] + FX - 1) / FX, (L.nn[1] + FY - 1) / FY, (L.nn[2] + FZ - 1) / FZ);
+  // z-chunks of FZ planes, or more and shorter chunks on small levels, so that at least two
+  // blocks per SM march concurrently (a block's planes follow one another)
+  const int tx = (L.nn[0] + FX - 1) / FX, ty = (L.nn[1] + FY - 1) / FY;
+  int nch = (L.nn[2] + FZ - 1) / FZ;
+  const int want = (2 * 152 + tx * ty - 1) / (tx * ty);
+  if (want > nch) nch = want < L.nn[2] ? want : L.nn[2];
+  const int fz = (L.nn[2] + nch - 1) / nch;
+  return dim3(tx, ty, (L.nn[2] + fz - 1) / fz);
 }
 
 template <typename T>
