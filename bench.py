@@ -92,10 +92,25 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        self.skip = 0
+
+    def _rows(self) -> list:
+        with open(self.f.name) as f:
+            return [r for r in f.read().splitlines() if r.strip()]
+
+    def begin(self, timeout_s: float = 3.0):
+        """Waits until the sampler has printed (NVML is up), then marks the start of the timed
+        region: only samples taken after this point are reported."""
+        if self.p is None:
+            return
+        t0 = time.perf_counter()
+        while not self._rows() and time.perf_counter() - t0 < timeout_s and self.p.poll() is None:
+            time.sleep(0.01)
+        self.skip = len(self._rows())
 
     def stop(self) -> dict:
         if self.p is None:
@@ -105,9 +120,11 @@ class Clocks:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-        self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        lines = self._rows()
         os.unlink(self.f.name)
+        # the samples of the timed region (the last earlier one if the region ended before the next)
+        lines = lines[self.skip:] if len(lines) > self.skip else lines[-1:]
+        rows = [r.split(",") for r in lines]
         sm, smax, reasons, pw = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -425,6 +442,7 @@ def main():
     except Exception:
         uuid = str(local)
     clk = Clocks(uuid)
+    clk.begin()
     barrier()
     torch.cuda.synchronize()
     l0 = rmt.kernel_launches()
