@@ -118,9 +118,14 @@ __device__ bool solve4(AT A[4][4], AT B[4][3], AT X[4][3], AT tolfac) {
 // whole warp: the lanes split the (2 rs + 1)^3 candidate cells and the normal-equation sums are
 // combined by a butterfly (every lane ends with the same totals, in a fixed order).
 // mode 0: kernel 2^-(|di|+|dj|+|dk|); mode 1: times max(0, cos) against the normal n_e.
+// FP32 fits take the data as displacements from the identity map, xi_d - (ref + offset h), ref
+// the position of cell (i,j,k) in the body's periodic image: the fitted values are then small,
+// so the FP32 solve's error, which scales with the data, no longer carries O(1) positions into
+// the extrapolated maps.  The caller adds the identity back.  FP64 fits take xi_d itself.
 template <typename AT, typename T>
 __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j,
-                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, AT sol[4][3]) {
+                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, const AT ref[3],
+                             AT sol[4][3]) {
   const int lane = threadIdx.x & 31;
   AT a[10], bsum[12];
 #pragma unroll
@@ -144,7 +149,12 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
       if (!(wt > AT(0))) continue;
     }
     const AT v[4] = {AT(1), (AT)di, (AT)dj, (AT)dk};
-    const AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
+    AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
+    if constexpr (sizeof(AT) == 4) {
+      const AT hf = g.f.h;
+#pragma unroll
+      for (int d = 0; d < 3; d++) xv[d] -= ref[d] + v[1 + d] * hf;
+    }
     int q = 0;
 #pragma unroll
     for (int r = 0; r < 4; r++)
@@ -187,17 +197,33 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
                             int i, int j, int k, int le, double out[3]) {
   // FP64: the degeneracy threshold; FP32: also the point below which the fit is redone in FP64
   const AT tolfac = sizeof(AT) == 8 ? AT(1e-12) : AT(1e-4);
+  // FP32: the identity map's value at the cell, in the periodic image nearest the body centre
+  // (the image the reference map takes); the fits return displacements from it
+  double refd[3] = {0.0, 0.0, 0.0};
+  AT ref[3] = {AT(0), AT(0), AT(0)};
+  if constexpr (sizeof(AT) == 4) {
+    const int id[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+      const double xe = g.lo[d] + (id[d] + 0.5) * g.h;
+      refd[d] = g.per[d] ? xe + g.len[d] * rint((b.c[d] - xe) / g.len[d]) : xe;
+      ref[d] = (AT)refd[d];
+      refd[d] = (double)ref[d];
+    }
+  }
+  const AT hid = sizeof(AT) == 4 ? (AT)g.f.h : AT(0);  // identity's slope per cell offset
   for (int rs = 2; rs <= 4; rs++) {
     AT s1[4][3];
-    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, s1)) {
+    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, ref, s1)) {
       if (sizeof(AT) == 4) return -1;
       continue;
     }
     if (le <= 2) {
-      const AT c0[3] = {s1[0][0], s1[0][1], s1[0][2]};
+      const AT c0[3] = {s1[0][0] + ref[0], s1[0][1] + ref[1], s1[0][2] + ref[2]};
       AT gX[3], v[3];
       phi0_dir<AT>(b, c0, gX);
-      for (int q = 0; q < 3; q++) v[q] = s1[1 + q][0] * gX[0] + s1[1 + q][1] * gX[1] + s1[1 + q][2] * gX[2];
+      for (int q = 0; q < 3; q++)
+        v[q] = (s1[1 + q][0] + (q == 0 ? hid : AT(0))) * gX[0] + (s1[1 + q][1] + (q == 1 ? hid : AT(0))) * gX[1] +
+               (s1[1 + q][2] + (q == 2 ? hid : AT(0))) * gX[2];
       const AT nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
       if (!(nv > AT(0))) {
         if (sizeof(AT) == 4) return -1;
@@ -205,14 +231,14 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
       }
       const AT nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
       AT s2[4][3];
-      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, s2)) {
+      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, ref, s2)) {
         if (sizeof(AT) == 4) return -1;
         continue;
       }
-      out[0] = s2[0][0]; out[1] = s2[0][1]; out[2] = s2[0][2];
+      for (int d = 0; d < 3; d++) out[d] = refd[d] + (double)s2[0][d];
       return 1;
     }
-    out[0] = s1[0][0]; out[1] = s1[0][1]; out[2] = s1[0][2];
+    for (int d = 0; d < 3; d++) out[d] = refd[d] + (double)s1[0][d];
     return 1;
   }
   return 0;

@@ -126,11 +126,12 @@ def test_fp32_periodic_fluid_matches_fp64_oracle():
 
 def test_fp32_swimmers_error_against_the_fp64_oracle():
     """The FP32 form on the swimmer scene (2 active ellipsoids, 32^3) against the FP64 oracle after
-    10 steps.  Its velocity error (3e-3, already 6e-3 after the first step, the same with and
-    without the fused sweep and the 16-byte FE staging) comes from reference maps stored in FP32:
-    their rounding, and that of the FP32 extrapolation fits, enters the elastic stress, a
-    difference of O(1) terms, and the swimmers' weak active forcing does not dominate it as the
-    lid does in the cavity.  The test bounds that error and the reference-map error."""
+    10 steps.  Its velocity error was measured at 6.3e-4 (9e-4 after the first step; 3e-3 before
+    the FP32 extrapolation fits took displacements from the identity map), the same with and
+    without the fused sweep and the 16-byte FE staging.  What remains comes from reference maps
+    stored in FP32: their rounding enters the elastic stress, a difference of O(1) terms, and the
+    swimmers' weak active forcing does not dominate it as the lid does in the cavity.  The test
+    bounds that error and the reference-map error (measured 1.9e-7)."""
     sc = S.swimmers(n=32, nbodies=2, seed=5, precision="fp32")
     g = rmt.Grid(dict(sc, mg_rtol=1e-10, mg_max_cycles=200, options={"mac_sweep": 2}))
     o = O.Oracle(dict(sc, precision="fp64"))
@@ -143,8 +144,8 @@ def test_fp32_swimmers_error_against_the_fp64_oracle():
         both = np.isfinite(xg) & np.isfinite(xo)
         assert np.count_nonzero(np.isfinite(xg) != np.isfinite(xo)) <= 0.01 * both.sum()
         exs.append(np.linalg.norm(xg[both] - xo[both]) / np.linalg.norm(xo[both]))
-    assert eu <= 1e-2, (eu, exs)
-    assert max(exs) <= 1e-4, (eu, exs)
+    assert eu <= 2e-3, (eu, exs)
+    assert max(exs) <= 1e-5, (eu, exs)
 
 
 def _ragged_walls_fp32():
