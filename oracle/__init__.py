@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
 benchmark's CPU-baseline leg.  The product package never imports it.
 
-The oracle is plain C (rmt_oracle.c), built here with gcc -O2 -ffp-contract=off into
-liboracle.so and driven through ctypes.  The Python side only marshals arguments.
+The oracle is plain C (rmt_oracle.c), built here with gcc -O2 -ffp-contract=off -fopenmp into
+liboracle.so and driven through ctypes.  The Python side only marshals arguments.  Its cell
+loops run on all host cores (OMP_NUM_THREADS limits them); its sums use fixed chunks and its
+element loops fixed colours, so a result does not depend on the thread count.
 """
 from __future__ import annotations
 
@@ -49,11 +51,11 @@ class SolidDesc(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compiles liboracle.so (gcc, FP64, no FMA contraction)."""
+    """Compiles liboracle.so (gcc, FP64, no FMA contraction, OpenMP)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))):
         return _LIB
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-D_DEFAULT_SOURCE",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-std=c11", "-D_DEFAULT_SOURCE",
            "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(_LIB + ".tmp", _LIB)

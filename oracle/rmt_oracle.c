@@ -441,6 +441,7 @@ static int wls_cell(const orc_grid* g, const solid* S, double* const X[3], const
  * in X is a candidate primary value; layer 0 = candidates with phi_0(xi) < 0. */
 static void extrapolate(orc_grid* g, solid* S, double* X[3], double* PH, signed char* L, const signed char* cand) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < g->N; c++) {
     L[c] = -1;
     if (cand[c]) {
@@ -448,8 +449,10 @@ static void extrapolate(orc_grid* g, solid* S, double* X[3], double* PH, signed 
       if (orc_phi0(&S->d, xv) < 0.0) L[c] = 0;
     }
   }
-  /* layers: unmarked face neighbours of layer l-1; walls stop the march, periodic axes wrap */
+  /* layers: unmarked face neighbours of layer l-1; walls stop the march, periodic axes wrap
+   * (in place and race-free: a pass writes only l over -1 and tests only l-1) */
   for (int l = 1; l <= g->d.band_layers; l++)
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -462,8 +465,10 @@ static void extrapolate(orc_grid* g, solid* S, double* X[3], double* PH, signed 
             if (L[nb] == l - 1) { L[c] = (signed char)l; break; }
           }
         }
-  /* WLS, layer by layer in ascending order */
-  for (int l = 1; l <= g->d.band_layers; l++)
+  /* WLS, layer by layer in ascending order (the fits of one layer read only lower layers) */
+  for (int l = 1; l <= g->d.band_layers; l++) {
+    int bad = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(+ : bad)
     for (int k = 0; k < nz; k++)
       for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -474,9 +479,12 @@ static void extrapolate(orc_grid* g, solid* S, double* X[3], double* PH, signed 
             X[0][c] = out[0]; X[1][c] = out[1]; X[2][c] = out[2];
           } else {
             L[c] = -1;
-            g->degenerate++;
+            bad++;
           }
         }
+    g->degenerate += bad;
+  }
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < g->N; c++) {
     if (L[c] >= 0) {
       double xv[3] = {X[0][c], X[1][c], X[2][c]};
@@ -496,9 +504,10 @@ static void extrapolate(orc_grid* g, solid* S, double* X[3], double* PH, signed 
  * Reading: rho = H rho_f + sum_m w_m rho_m with the normalised weights of the stress rule. */
 static void mix_density(orc_grid* g, int which, double* out) {
   int S = g->nsol;
-  double Hm[64], w[64];
-  int ids[64];
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < g->N; c++) {
+    double Hm[64], w[64];
+    int ids[64];
     int cnt = 0;
     for (int m = 0; m < S; m++) {
       const solid* s = &g->sol[m];
@@ -610,6 +619,7 @@ static void face_traction(orc_grid* g, int d, int i, int j, int k, int which, do
 /* grad . tau at every cell: sum over directions of (row(+face) - row(-face)) / h */
 static void stress_divergence(orc_grid* g, int which, double tt, double* out[3]) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < nz; k++)
     for (int j = 0; j < ny; j++)
       for (int i = 0; i < nx; i++) {
@@ -645,6 +655,7 @@ static void grad_at_cell(const orc_grid* g, const double* P, int i, int j, int k
 }
 
 void orc_cell_grad(orc_grid* g, const double* nodal, double* out) {
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -691,6 +702,7 @@ static void bar_states(orc_grid* g) {
   for (int e = 0; e < 3; e++) {
     int ext[3] = {g->n[0], g->n[1], g->n[2]};
     ext[e] += 1;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < ext[2]; k++)
       for (int j = 0; j < ext[1]; j++)
         for (int i = 0; i < ext[0]; i++) {
@@ -798,6 +810,7 @@ static void rep_accel(orc_grid* g, int which, double* out[3]) {
   int any = 0;
   for (int m = 0; m < g->nsol; m++) any |= g->sol[m].d.rep_A != 0.0;
   if (!any) return;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -836,6 +849,7 @@ static void face_states(orc_grid* g) {
   double* A[3];
   for (int a = 0; a < 3; a++) { F[a] = dalloc(N); A[a] = dalloc(N); }
   rep_accel(g, 0, A);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -849,6 +863,7 @@ static void face_states(orc_grid* g) {
   for (int d = 0; d < 3; d++) {
     int ext[3] = {g->n[0], g->n[1], g->n[2]};
     ext[d] += 1;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < ext[2]; k++)
       for (int j = 0; j < ext[1]; j++)
         for (int i = 0; i < ext[0]; i++) {
@@ -908,15 +923,29 @@ static void face_states(orc_grid* g) {
 
 typedef void (*opfn)(orc_grid*, const double*, const double*, double*);
 
-static double dotp(const double* a, const double* b, long n) {
+/* Sums over fixed chunks of SUM_CHUNK entries, the chunk totals added in order: the same
+ * result for any number of threads. */
+#define SUM_CHUNK 4096L
+static double chunked_sum(const double* a, const double* b, long n) {
+  const long nch = (n + SUM_CHUNK - 1) / SUM_CHUNK;
+  double* part = dalloc(nch);
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < nch; q++) {
+    const long i1 = (q + 1) * SUM_CHUNK < n ? (q + 1) * SUM_CHUNK : n;
+    double s = 0.0;
+    for (long i = q * SUM_CHUNK; i < i1; i++) s += b ? a[i] * b[i] : a[i];
+    part[q] = s;
+  }
   double s = 0.0;
-  for (long i = 0; i < n; i++) s += a[i] * b[i];
+  for (long q = 0; q < nch; q++) s += part[q];
+  free(part);
   return s;
 }
+static double dotp(const double* a, const double* b, long n) { return chunked_sum(a, b, n); }
 static void demean(double* a, long n) {
-  double s = 0.0;
-  for (long i = 0; i < n; i++) s += a[i];
+  double s = chunked_sum(a, NULL, n);
   s /= (double)n;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; i++) a[i] -= s;
 }
 
@@ -939,17 +968,20 @@ static int cg(orc_grid* g, opfn A, const double* coef, const double* b_in, doubl
     double pAp = dotp(pv, Ap, n);
     if (!(pAp > 0.0)) break;
     double al = rr / pAp;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) { x[i] += al * pv[i]; r[i] -= al * Ap[i]; }
     it++;
     if (it % 50 == 0) {
       /* residual replacement: keep the recursive residual equal to the true one */
       A(g, coef, x, Ap);
+#pragma omp parallel for schedule(static)
       for (long i = 0; i < n; i++) r[i] = b[i] - Ap[i];
     }
     demean(r, n);
     double rr2 = dotp(r, r, n);
     double be = rr2 / rr;
     rr = rr2;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) pv[i] = r[i] + be * pv[i];
   }
 done:
@@ -967,6 +999,7 @@ done:
  * beta = 1/rho_face with rho_face the mean of the two cells (Reading), zero on walls. */
 static void mac_apply(orc_grid* g, const double* rho, const double* q, double* out) {
   const double h2 = g->h * g->h;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -990,6 +1023,7 @@ static void mac_apply(orc_grid* g, const double* rho, const double* q, double* o
 int orc_mac_project(orc_grid* g, const double* rho, double* ufx, double* ufy, double* ufz, double dt, double* q_out) {
   double* U[3] = {ufx, ufy, ufz};
   double* rhs = dalloc(g->N);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1008,6 +1042,7 @@ int orc_mac_project(orc_grid* g, const double* rho, double* ufx, double* ufy, do
   for (int d = 0; d < 3; d++) {
     int ext[3] = {g->n[0], g->n[1], g->n[2]};
     ext[d] += 1;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < ext[2]; k++)
       for (int j = 0; j < ext[1]; j++)
         for (int i = 0; i < ext[0]; i++) {
@@ -1030,11 +1065,23 @@ int orc_mac_project(orc_grid* g, const double* rho, double* ufx, double* ufy, do
  * Almgren et al. 1996): K_ij = sum_cells beta_c int_c grad N_i . grad N_j.  On a cube of
  * side h the element matrix is (h/12) * {4 same node, 0 edge, -1 face diagonal,
  * -1 body diagonal}.  beta lives on cells. */
+/* The element loops below add each cell's contributions into its 8 nodes.  They visit the
+ * cells in 8 colours of (i, j, k) parity: two cells of one colour share no node (on a periodic
+ * axis when its cell count is even), so a colour runs in parallel and every node's sum is
+ * taken in the same order for any number of threads. */
+static int colour_parallel(const orc_grid* g) {
+  for (int d = 0; d < 3; d++)
+    if (g->per[d] && (g->n[d] & 1)) return 0;
+  return 1;
+}
 void orc_fe_apply(orc_grid* g, const double* beta, const double* psi, double* out) {
   for (long i = 0; i < g->NN; i++) out[i] = 0.0;
-  for (int k = 0; k < g->n[2]; k++)
-    for (int j = 0; j < g->n[1]; j++)
-      for (int i = 0; i < g->n[0]; i++) {
+  const int par = colour_parallel(g);
+  for (int col = 0; col < 8; col++)
+#pragma omp parallel for collapse(2) schedule(static) if (par)
+  for (int k = (col >> 2) & 1; k < g->n[2]; k += 2)
+    for (int j = (col >> 1) & 1; j < g->n[1]; j += 2)
+      for (int i = col & 1; i < g->n[0]; i += 2) {
         long nd[8];
         double v[8];
         for (int q = 0; q < 8; q++) {
@@ -1060,9 +1107,12 @@ static void fe_apply_op(orc_grid* g, const double* beta, const double* x, double
 void orc_fe_weak_div(orc_grid* g, const double* V, double* out) {
   for (long i = 0; i < g->NN; i++) out[i] = 0.0;
   const double s = g->h * g->h / 4.0;
-  for (int k = 0; k < g->n[2]; k++)
-    for (int j = 0; j < g->n[1]; j++)
-      for (int i = 0; i < g->n[0]; i++) {
+  const int par = colour_parallel(g);
+  for (int col = 0; col < 8; col++)
+#pragma omp parallel for collapse(2) schedule(static) if (par)
+  for (int k = (col >> 2) & 1; k < g->n[2]; k += 2)
+    for (int j = (col >> 1) & 1; j < g->n[1]; j += 2)
+      for (int i = col & 1; i < g->n[0]; i += 2) {
         long c = cidx(g, i, j, k);
         for (int q = 0; q < 8; q++) {
           int a = q & 1, b = (q >> 1) & 1, e = (q >> 2) & 1;
@@ -1117,6 +1167,7 @@ static double pick_dt(orc_grid* g) {
  * nearest to the body's centre. */
 static void init_solid(orc_grid* g, solid* S) {
   signed char* cand = calloc8(g->N);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1157,6 +1208,7 @@ static int one_step(orc_grid* g) {
   for (int d = 0; d < 3; d++) memcpy(g->umac[d], g->uf[d][d], sizeof(double) * g->NF[d]);
   if (orc_mac_project(g, g->rho, g->umac[0], g->umac[1], g->umac[2], dt, g->q) != OK) rc = ENOCONV_;
   /* 4. advective terms (eq. adv_terms) and 5. predictor of xi (eq. dis_xi_adv) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1177,6 +1229,7 @@ static int one_step(orc_grid* g) {
   for (int m = 0; m < g->nsol; m++) {
     solid* S = &g->sol[m];
     signed char* cand = calloc8(N);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->n[2]; k++)
       for (int j = 0; j < g->n[1]; j++)
         for (int i = 0; i < g->n[0]; i++) {
@@ -1205,11 +1258,14 @@ static int one_step(orc_grid* g) {
      * Reading: a cell new to the band (no xi^n) gets xi^{n+1/2} by the same WLS
      * extrapolation, layer by layer (band of step n+1), from the corrected values of the
      * lower layers; this keeps affine maps exact. */
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; c++) {
       if (S->layn[c] < 0 || S->lay[c] < 0) { S->xh[0][c] = S->xh[1][c] = S->xh[2][c] = NAN; continue; }
       for (int a = 0; a < 3; a++) S->xh[a][c] = 0.5 * (S->xi[a][c] + S->xn[a][c]);
     }
-    for (int l = 1; l <= g->d.band_layers; l++)
+    for (int l = 1; l <= g->d.band_layers; l++) {
+      int bad = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) reduction(+ : bad)
       for (int k = 0; k < g->n[2]; k++)
         for (int j = 0; j < g->n[1]; j++)
           for (int i = 0; i < g->n[0]; i++) {
@@ -1219,10 +1275,13 @@ static int one_step(orc_grid* g) {
             if (!wls_cell(g, S, S->xh, S->layn, i, j, k, l, out)) {
               /* cannot happen when the same cell was extrapolated at step 6 from a superset */
               out[0] = S->xn[0][c]; out[1] = S->xn[1][c]; out[2] = S->xn[2][c];
-              g->degenerate++;
+              bad++;
             }
             S->xh[0][c] = out[0]; S->xh[1][c] = out[1]; S->xh[2][c] = out[2];
           }
+      g->degenerate += bad;
+    }
+#pragma omp parallel for schedule(static)
     for (long c = 0; c < N; c++) {
       if (S->layn[c] < 0) { S->phih[c] = NAN; continue; }
       double xv[3] = {S->xh[0][c], S->xh[1][c], S->xh[2][c]};
@@ -1236,6 +1295,7 @@ static int one_step(orc_grid* g) {
   /* 10. u* (Reading of the garbled item: eq. dis_full_mmt with p^{n-1/2}); the wall
    * repulsion joins b^{n+1/2} as rho a_rep, from phi^{n+1/2} */
   rep_accel(g, 1, g->rep);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n[2]; k++)
     for (int j = 0; j < g->n[1]; j++)
       for (int i = 0; i < g->n[0]; i++) {
@@ -1254,6 +1314,7 @@ static int one_step(orc_grid* g) {
       for (long c = 0; c < N; c++) V[a * N + c] = (g->ustar[a][c] - g->u[a][c]) / dt;
     if (orc_fe_solve(g, g->rho_h, V, g->psi) != OK) rc = ENOCONV_;
     free(V);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->n[2]; k++)
       for (int j = 0; j < g->n[1]; j++)
         for (int i = 0; i < g->n[0]; i++) {
