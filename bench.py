@@ -2,7 +2,7 @@
 """Benchmark of the GB300 RMT per-step update: FSI cell-updates/s.
 
 Default workload: the 256^3 triply periodic active-swimmer scene (8 ellipsoids with an active
-bending stress, FP32 bulk with FP64 multigrid residual refinement).  One "step" is one full
+bending stress, FP32 bulk with two-float refinement of the projections).  One "step" is one full
 timestep of the 13-step algorithm over the whole grid.  Inputs (fields of 256^3 cells, several
 GB) are far larger than the 129 MB L2, so no cache flush is needed between steps.
 
@@ -34,8 +34,8 @@ CONFIGS = {
     # name: (scene factory kwargs, description)
     "swimmers256": dict(kind="swimmers", n=256, precision="fp32",
                         desc="256^3 triply periodic unit box, 8 active-stress ellipsoid swimmers "
-                             "(0.15,0.04,0.04), G=1, mu=mu_a=0.01, A=0.5, omega=2pi; FP32 bulk + FP64 "
-                             "multigrid residual refinement"),
+                             "(0.15,0.04,0.04), G=1, mu=mu_a=0.01, A=0.5, omega=2pi; FP32 bulk with "
+                             "two-float refinement of the projections"),
     "swimmers256_fp64": dict(kind="swimmers", n=256, precision="fp64",
                              desc="the same 256^3 swimmer scene on the plain FP64 path"),
     "settling128": dict(kind="settling", n=128, precision="fp64",
@@ -150,17 +150,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def dram_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/dram_traffic.txt),
-    or None when there is no record or the kernel's source file changed since it was taken."""
+def dram_traffic(kernel: str, cells: int):
+    """DRAM bytes per launch of `kernel` at `cells` cells, from the committed ncu record of a small
+    case (profiles/dram_traffic_small_case.txt: bytes per launch measured on a grid of a few GB,
+    scaled by the cell count, since the kernel moves a fixed number of bytes per cell), or None
+    when there is no record or the kernel's source file changed since it was taken."""
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_small_case.txt")) as f:
             lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
     except OSError:
         return None
-    for name, nbytes, src, sha in lines:
+    for name, nbytes, ncells, src, sha in lines:
         if name != kernel:
             continue
         try:
@@ -169,7 +171,7 @@ def dram_traffic(kernel: str):
                     return None
         except OSError:
             return None
-        return float(nbytes)
+        return float(nbytes) * cells / float(ncells)
     return None
 
 
@@ -481,7 +483,7 @@ def main():
         ach = byt / (per / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_source": peak_kind,
-                    "traffic": dram_traffic(name) if args.n is None and args.nbodies is None else None,
+                    "traffic": dram_traffic(name, N),
                     "bytes_per_launch": byt, "launches": nl, "avg_launch_ms": per,
                     "share_of_step": tot / prof_ms, "profiled_ms_per_step": prof_ms / args.steps}
     stages = {p[0]: round(p[1] / args.steps, 4) for p in prof if p[1] > 0}

@@ -34,8 +34,11 @@ typedef enum {
   RMT_ESTATE = 4,       /* call not allowed now (after an error, or add after a step)  */
   RMT_ENOCONVERGE = 5,  /* a multigrid solve missed its tolerance within its cycle cap */
   RMT_EDIVERGED = 6,    /* non-finite velocity detected                                */
-  RMT_ETIMEOUT = 7,     /* reserved for bounded device-side waits                      */
-  RMT_EDEGENERATE = 8   /* a least-squares extrapolation stayed degenerate at r_s = 4  */
+  RMT_ETIMEOUT = 7,     /* reserved for bounded device-side waits (none in this build)  */
+  RMT_EDEGENERATE = 8,  /* a least-squares extrapolation stayed degenerate at r_s = 4  */
+  RMT_ERANGE = 9        /* FP32 form: a body's band came within 3 cells of the point half a
+                           period from its centre on a periodic axis (the reference map is
+                           stored relative to one periodic image of the grid around the body)*/
 } rmt_status;
 
 enum { RMT_BC_NOSLIP = 0, RMT_BC_PERIODIC = 1 };
@@ -55,7 +58,10 @@ typedef struct {
   double dt;              /* time step; <= 0: min(0.2h, 0.8 rho_min h^2/(6 mu_max),
                              0.5 h / sqrt(G_max/rho_min))                                     */
   double gravity[3];      /* body force is (rho - rho_f) g                                    */
-  int precision;          /* RMT_PREC_FP64, or FP32 bulk with FP64 multigrid refinement      */
+  int precision;          /* RMT_PREC_FP64, or FP32 bulk: FP32 fields (reference maps stored as
+                             displacements from the cell centres) and V-cycles, with the
+                             projections' residuals, right-hand sides and solutions refined
+                             in two-float arithmetic (hi + lo FP32 pairs)                    */
   double mg_rtol;         /* relative residual target of both Poisson solves (<=0: 1e-12)    */
   int mg_max_cycles;      /* cap on V-cycles per solve (<=0: 60)                              */
   int mg_fixed_cycles;    /* > 0: run exactly this many MAC cycles, no residual checks (no host
@@ -93,7 +99,13 @@ rmt_status rmt_add_solid(rmt_grid* g, const rmt_solid_desc* s, int* solid_id);
 
 /* Advances nsteps timesteps of the 13-step algorithm (SI "Timestepping algorithm").
  * Work is enqueued on the grid's stream; with mg_fixed_cycles = 0 each Poisson solve reads
- * its residual norm back to the host once per cycle. */
+ * its residual norm back to the host once per cycle, and the call waits for its steps and
+ * reports their failures.  With fixed cycle counts nothing waits: every step copies the grid's
+ * device error words to pinned host memory as its last operation, and a later rmt_step (or
+ * rmt_batch_sync, or the server's poll) reports a failure found there: RMT_EDIVERGED (a NaN or
+ * infinity reached the mean or norm that every pressure solve takes of its right-hand side and
+ * solution), RMT_EDEGENERATE, RMT_ERANGE.  Errors: those of the status list; RMT_ESTATE after a
+ * sticky error. */
 rmt_status rmt_step(rmt_grid* g, int nsteps);
 
 /* Initial pressure iterations (SI "Initialization" item 2), before the first step: a timestep
@@ -149,10 +161,15 @@ double rmt_dt(rmt_grid* g);
  * finest level's), "mac_sweep" (FP32 grids: 1, the default, runs each red-black sweep of a
  * level with n_x % 4 == 0, even periodic sides, n_x >= 64 and at least 2^20 cells as one fused
  * pass over both colours; 2 does so on every level with n_x % 4 == 0 and even periodic sides; 0
- * runs one pass per colour everywhere; all give the same sweep), "graph" (nonzero: with fixed cycle counts, rmt_step replays a captured CUDA graph
- * of the step instead of launching its kernels one by one; the results are the same).  Cycle
- * counts (mg_fixed_cycles, rmt_last_cycles) count V-cycles.  Errors: RMT_EINVAL, RMT_ESTATE for
- * a batch member. */
+ * runs one pass per colour everywhere; all give the same sweep), "graph" (nonzero: with fixed
+ * cycle counts, rmt_step replays a captured CUDA graph of the step instead of launching its
+ * kernels one by one; the results are the same).  Cycle counts (mg_fixed_cycles,
+ * rmt_last_cycles) count V-cycles.
+ * Fault injection from the host, for testing failure handling (no device fault is involved):
+ * "inject_nan_step" (k >= 0: before step k runs, one velocity value is overwritten with NaN, as
+ * a diverging scheme would leave it; -1 turns it off), "inject_alloc" (k >= 0, before the first
+ * step: the grid's k-th device allocation fails as cudaMalloc would, giving RMT_ENOMEM).
+ * Errors: RMT_EINVAL, RMT_ESTATE for a batch member (and for inject_alloc after allocation). */
 rmt_status rmt_set_option(rmt_grid* g, const char* name, double value);
 
 /* A_rep of SI "Contact with a wall" for one body: the largest of U_safe^2/d_w (a safety
@@ -263,14 +280,17 @@ const char* rmt_batch_last_error(const rmt_batch* b);
 /* ---- serving: continuous batching of simulation jobs (no paper counterpart) ----------------
  * rmt_server_submit queues a job (grid description with fixed cycle counts, bodies, number of
  * steps); its footprint (rmt_grid_footprint) must fit the budget.  Each rmt_server_poll
- *   1. retires the running jobs whose last step has been launched: completion time = when the
- *      GPU finished that step (CUDA event), then the job's error flag is read;
+ *   1. evicts the running jobs whose error words (copied to the host by every step) report a
+ *      failure: a diverged velocity (RMT_EDIVERGED), a degenerate extrapolation: the job is
+ *      marked failed, its grid destroyed and its memory returned to the budget, and the others
+ *      carry on; then retires the running jobs whose last step has been launched: completion
+ *      time = when the GPU finished that step (CUDA event), then the job's error words are read;
  *   2. admits queued jobs in arrival order while their footprint fits next to the resident
  *      jobs (a job that does not fit waits; later, smaller jobs may pass it); an admitted job's
  *      grid is created, initialised and added to the server's batch;
  *   3. launches one batched step of all running jobs, with at most two steps in flight.
- * A job that fails (bad description, allocation, degenerate extrapolation) is marked failed
- * and the others carry on.  Finished jobs keep their fields on the device, readable through
+ * A job that fails (bad description, allocation, divergence, degenerate extrapolation) is
+ * marked failed and the others carry on.  Finished jobs keep their fields on the device, readable through
  * rmt_server_job_grid, until rmt_server_release, and count against the budget until then.
  * Times are seconds since rmt_server_create (rmt_server_clock).  rmt_server_set_option applies
  * rmt_set_option(name, value) to every job grid at admission. */
@@ -312,10 +332,12 @@ long rmt_kernel_launches(void);
 
 /* Timing of the step's stages and of the finest-level multigrid kernels with CUDA events on
  * the grid's stream.  rmt_profile(g, 1) clears and starts collecting, rmt_profile(g, 0) stops.
- * Entries: 0..12 are stages of the timestep (each a group of kernels), 13..16 single kernels
- * (7-point smoother colour, 7-point FP64 residual, 27-point smoother colour, 27-point FP64
- * residual).  rmt_profile_read synchronises the stream and returns the accumulated time, the
- * number of timed launches and, for 13..16, the algorithmic bytes of one launch (0 else). */
+ * Entries: 0..12 are stages of the timestep (each a group of kernels), 13..17 single kernels
+ * (7-point smoother colour, 7-point high-precision residual, 27-point smoother colour, 27-point
+ * high-precision residual, fused red-black sweep; high precision is FP64 in the FP64 form and
+ * two-float in the FP32 form).  rmt_profile_read synchronises the stream and returns the
+ * accumulated time, the number of timed launches and, for 13..17, the algorithmic bytes of one
+ * launch (0 else). */
 rmt_status rmt_profile(rmt_grid* g, int enable);
 int rmt_profile_entries(void);
 const char* rmt_profile_name(int entry);

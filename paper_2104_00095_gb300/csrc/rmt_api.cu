@@ -69,6 +69,7 @@ struct rmt_grid {
   size_t esz = 8;
   cudaStream_t s = nullptr;
   int inited = 0;
+  rmt_status init_st = RMT_OK;  // outcome of the initialisation (ensure_init)
   rmt_status sticky = RMT_OK;
   char msg[512] = {0};
   std::vector<rmt_solid_desc> solids;
@@ -96,6 +97,9 @@ struct rmt_grid {
   void* umac[3] = {};
   MGSolver* mac = nullptr;
   MGSolver* fe = nullptr;
+  // device error words, copied to err_h (pinned) at the end of every step: [0] degenerate fits,
+  // [1] FP32 band cells near the seam of their image window, [2] a non-finite mean or norm in a
+  // projection (the velocity diverged)
   int* err_d = nullptr;
   int* err_h = nullptr;
   double* stage = nullptr;
@@ -115,6 +119,9 @@ struct rmt_grid {
   double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
+  // host-side fault injection (rmt_set_option): a NaN written into u before step
+  // inject_nan_step, a failure of the grid's inject_alloc-th device allocation (-1: off)
+  long inject_nan_step = -1, inject_alloc = -1, nalloc = 0;
   // captured step graphs (fixed-cycle mode): one per parity of the reference-map buffers
   int use_graph = 0;
   cudaStream_t cap_s = nullptr;
@@ -140,6 +147,9 @@ rmt_status fail(rmt_grid* g, rmt_status st, const char* fmt, ...) {
   }
   return st;
 }
+
+// reads the grid's device error words after waiting for its stream (defined below)
+rmt_status check_err(rmt_grid* g);
 
 // a call refused in the grid's present state: message only, the grid stays usable
 rmt_status refuse(rmt_grid* g, const char* why) {
@@ -217,6 +227,10 @@ rmt_status dalloc(rmt_grid* g, void** p, size_t bytes) {
     *p = nullptr;
     return RMT_OK;
   }
+  if (g->inject_alloc >= 0 && g->nalloc++ == g->inject_alloc) {
+    *p = nullptr;
+    return fail(g, RMT_ENOMEM, "cudaMalloc(%zu): failure injected by the inject_alloc option", bytes);
+  }
   cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) return fail(g, RMT_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   g->allocs.push_back(*p);
@@ -257,6 +271,34 @@ __global__ void k_cvt_back(const double* __restrict__ a, T* __restrict__ b, long
 }
 __global__ void k_cvt_i8(const int8_t* __restrict__ a, double* __restrict__ b, long n) {
   GRID_LOOP(i, n) b[i] = (double)a[i];
+}
+// a reference map to FP64 xi (FP32 storage: the displacement plus the cell centre's image)
+template <typename T>
+__global__ void k_xi_out(Geo g, Body b, const T* __restrict__ x, double* __restrict__ out) {
+  GRID_LOOP(q, 3 * g.N) {
+    double v = (double)x[q];
+    if constexpr (disp_storage<T>()) {
+      const int a = (int)(q / g.N);
+      const long c = q - a * g.N;
+      const int ii[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long)g.n[0] * g.n[1]))};
+      v += g.lo[a] + (img_u(g, b, a, ii[a]) + 0.5) * g.h;
+    }
+    out[q] = v;
+  }
+}
+// FP64 xi to the stored form
+template <typename T>
+__global__ void k_xi_in(Geo g, Body b, const double* __restrict__ in, T* __restrict__ x) {
+  GRID_LOOP(q, 3 * g.N) {
+    double v = in[q];
+    if constexpr (disp_storage<T>()) {
+      const int a = (int)(q / g.N);
+      const long c = q - a * g.N;
+      const int ii[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long)g.n[0] * g.n[1]))};
+      v -= g.lo[a] + (img_u(g, b, a, ii[a]) + 0.5) * g.h;
+    }
+    x[q] = (T)v;
+  }
 }
 inline int nbk(long n) {
   long b = (n + 255) / 256;
@@ -400,6 +442,8 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_warm(g->mac, g->mac_warm);
   mg_set_sweep(g->mac, g->mac_sweep);
   mg_set_warm(g->fe, g->fe_warm);
+  mg_set_nonfinite_flag(g->mac, g->err_d + 2);
+  mg_set_nonfinite_flag(g->fe, g->err_d + 2);
   g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
   return RMT_OK;
 }
@@ -435,8 +479,8 @@ rmt_status init_t(rmt_grid* g) {
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
     launch_init_xi<T>(G, g->bodies[m], (T*)b.X[0], g->s);
-    launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[0],
-                          (T*)b.PHI[0], b.LAY[0], g->err_d, g->s);
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, WLS_BLOCKS,
+                                (T*)b.X[0], (T*)b.PHI[0], b.LAY[0], g->err_d, g->s));
   }
   launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, g->bb_all, 12, (T*)g->rho, g->s);
   CK(g, cudaGetLastError());
@@ -471,8 +515,8 @@ rmt_status step_t(rmt_grid* g) {
   T* u = (T*)g->u;
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t_d, 0.0,
-                       (T*)g->divn, g->slist, g->scount, s);
+  CK(g, launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t_d, 0.0,
+                              (T*)g->divn, g->slist, g->scount, s));
   pe(g, P_STRESS_N);
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
@@ -492,7 +536,11 @@ rmt_status step_t(rmt_grid* g) {
   int cyc = mg_solve(g->mac, rtol, maxc, g->desc.mg_fixed_cycles, s, &ce);
   pe(g, P_MAC_SOLVE);
   if (ce != cudaSuccess) return fail(g, RMT_ECUDA, "MAC solve: %s", cudaGetErrorString(ce));
-  if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "MAC multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  if (cyc < 0) {
+    const rmt_status es = check_err(g);  // a non-finite right-hand side stops a solve too
+    if (es != RMT_OK) return es;
+    return fail(g, RMT_ENOCONVERGE, "MAC multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  }
   g->cycles[0] = cyc;
   pb(g, P_MAC_CORR_ADV);
   launch_mac_correct<T>(G, uf, (const T*)g->rho, mg_solution(g->mac), umac, s);
@@ -517,8 +565,8 @@ rmt_status step_t(rmt_grid* g) {
     cudaStream_t bs = g->body_s[m];
     CK(g, cudaStreamWaitEvent(bs, g->ev_fork, 0));
     const int* bbc = b.bb + 6 * cur;
-    launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS, (T*)b.X[nxt],
-                          (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, bs);
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS,
+                                (T*)b.X[nxt], (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, bs));
     launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, WLS_BLOCKS, (const T*)b.X[cur], b.LAY[cur],
                         (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, bs);
     CK(g, cudaEventRecord(g->ev_join[m], bs));
@@ -527,8 +575,8 @@ rmt_status step_t(rmt_grid* g) {
   pe(g, P_EXTRAP);
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
   pb(g, P_STRESS_H);
-  launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t_d, 0.5 * G.dt,
-                       (T*)g->divh, g->slist, g->scount, s);
+  CK(g, launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t_d,
+                              0.5 * G.dt, (T*)g->divh, g->slist, g->scount, s));
   pe(g, P_STRESS_H);
   pb(g, P_USTAR);
   launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho_h, s);
@@ -545,7 +593,11 @@ rmt_status step_t(rmt_grid* g) {
                s, &ce);
   pe(g, P_FE_SOLVE);
   if (ce != cudaSuccess) return fail(g, RMT_ECUDA, "FE solve: %s", cudaGetErrorString(ce));
-  if (cyc < 0) return fail(g, RMT_ENOCONVERGE, "FE multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  if (cyc < 0) {
+    const rmt_status es = check_err(g);
+    if (es != RMT_OK) return es;
+    return fail(g, RMT_ENOCONVERGE, "FE multigrid missed rtol %.3g in %d cycles at step %ld", rtol, maxc, g->step);
+  }
   g->cycles[1] = cyc;
   pb(g, P_FE_UPDATE);
   launch_fe_update<T>(G, (const T*)g->ustar, (const T*)g->rho_h, mg_solution(g->fe), u, (T*)g->p, (T*)g->psi, s);
@@ -554,6 +606,8 @@ rmt_status step_t(rmt_grid* g) {
   launch_density<T>(G, g->bodies_d, views<T>(g, nxt, 0), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho, s);
   launch_tick(g->t_d, G.dt, s);
   pe(g, P_FE_UPDATE);
+  // the error words reach the host with the step (no synchronisation; read by poll_err)
+  CK(g, cudaMemcpyAsync(g->err_h, g->err_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(g, cudaGetLastError());
   g->t += G.dt;
   g->step++;
@@ -561,7 +615,7 @@ rmt_status step_t(rmt_grid* g) {
 }
 
 rmt_status ensure_init(rmt_grid* g) {
-  if (g->inited) return RMT_OK;
+  if (g->inited) return g->init_st;
   g->g.dt = pick_dt(g);
   g->g.utol = 1e-12 * g->g.h / g->g.dt;
   geo_finish(g->g);
@@ -583,23 +637,55 @@ rmt_status ensure_init(rmt_grid* g) {
     b.actL = s.active_len;
     b.repA = s.rep_A;
     body_finish(b);
+    body_image(b, g->g);
     g->bodies.push_back(b);
     if (s.rep_A != 0.0) g->g.any_rep = 1;
   }
   g->g.dw = g->desc.wall_dw > 0.0 ? g->desc.wall_dw : g->g.h;
   g->g.f.dw = (float)g->g.dw;
   g->inited = 1;
-  rmt_status st = g->fp32 ? init_t<float>(g) : init_t<double>(g);
-  if (st != RMT_OK) return st;
+  // a failed initialisation (allocation, CUDA error) leaves the state unusable: every later call
+  // that needs it gets the same status
+  g->init_st = g->fp32 ? init_t<float>(g) : init_t<double>(g);
+  return g->init_st;
+}
+
+// the status the error words e[0..2] report (RMT_OK when all clear), recorded on g
+rmt_status err_words(rmt_grid* g, const volatile int* e) {
+  if (e[2] != 0)
+    return fail(g, RMT_EDIVERGED, "non-finite values reached a pressure projection by step %ld (the velocity "
+                "diverged)", g->step);
+  if (e[0] != 0)
+    return fail(g, RMT_EDEGENERATE, "%d least-squares extrapolations stayed degenerate up to r_s = 4", e[0]);
+  if (e[1] != 0)
+    return fail(g, RMT_ERANGE,
+                "%d band cells came within %d cells of the seam of their body's periodic image window (FP32 "
+                "storage keeps the reference map relative to a fixed image; the body has drifted about half a "
+                "period)", e[1], SEAM_MARGIN);
+  return RMT_OK;
+}
+
+// Without waiting: the error words as of the last step whose copy has landed (fixed-cycle and
+// graph steps never synchronise, so a failure surfaces at a later call).  Records the first
+// error found as the grid's sticky status.
+rmt_status poll_err(rmt_grid* g) {
+  if (!g->err_h || g->sticky != RMT_OK) return RMT_OK;
+  return err_words(g, (const volatile int*)g->err_h);
+}
+
+// host-side fault injection before the step that is about to run: one velocity value becomes
+// NaN (written from the host, as a diverging scheme would leave it)
+rmt_status inject(rmt_grid* g) {
+  if (g->inject_nan_step < 0 || g->step != g->inject_nan_step) return RMT_OK;
+  const long c = g->g.N / 2 + g->g.n[0] / 2;
+  CK(g, cudaMemsetAsync((char*)g->u + c * g->esz, 0xff, g->esz, g->s));  // all-ones bits: a NaN
   return RMT_OK;
 }
 
 rmt_status check_err(rmt_grid* g) {
-  CK(g, cudaMemcpyAsync(g->err_h, g->err_d, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  CK(g, cudaMemcpyAsync(g->err_h, g->err_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->s));
   CK(g, cudaStreamSynchronize(g->s));
-  if (g->err_h[0] != 0)
-    return fail(g, RMT_EDEGENERATE, "%d least-squares extrapolations stayed degenerate up to r_s = 4", g->err_h[0]);
-  return RMT_OK;
+  return err_words(g, g->err_h);
 }
 
 // ----------------------------------------------------------------------------- step graphs
@@ -675,10 +761,16 @@ rmt_status gather_t(rmt_grid* g, int field, int sid, double* out) {
     case RMT_F_U: cvt(g->u, 3 * N, 0); break;
     case RMT_F_P: cvt(g->p, G.NN, 0); break;
     case RMT_F_RHO: cvt(g->rho, N, 0); break;
-    case RMT_F_XI: cvt(g->bm[sid].X[g->par], 3 * N, 0); break;
+    case RMT_F_XI:
+      k_xi_out<T><<<nbk(3 * N), 256, 0, s>>>(G, g->bodies[sid], (const T*)g->bm[sid].X[g->par], out);
+      rmt_count_launches(1);
+      break;
     case RMT_F_PHI: cvt(g->bm[sid].PHI[g->par], N, 0); break;
     case RMT_F_LAYER: k_cvt_i8<<<nbk(N), 256, 0, s>>>(g->bm[sid].LAY[g->par], out, N); rmt_count_launches(1); break;
-    case RMT_F_XI_HALF: cvt(g->bm[sid].XH, 3 * N, 0); break;
+    case RMT_F_XI_HALF:
+      k_xi_out<T><<<nbk(3 * N), 256, 0, s>>>(G, g->bodies[sid], (const T*)g->bm[sid].XH, out);
+      rmt_count_launches(1);
+      break;
     case RMT_F_DIVTAU_N: cvt(g->divn, 3 * N, 0); break;
     case RMT_F_DIVTAU_H: cvt(g->divh, 3 * N, 0); break;
     case RMT_F_ADV_U: cvt(g->adv, 3 * N, 0); break;
@@ -720,10 +812,10 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
     k_cvt_back<T><<<nbk(G.NN), 256, 0, s>>>(g->stage, (T*)g->p, G.NN); rmt_count_launches(1);
   } else {
     BodyMem& b = g->bm[sid];
-    k_cvt_back<T><<<nbk(3 * G.N), 256, 0, s>>>(g->stage, (T*)b.X[g->par], 3 * G.N); rmt_count_launches(1);
+    k_xi_in<T><<<nbk(3 * G.N), 256, 0, s>>>(G, g->bodies[sid], g->stage, (T*)b.X[g->par]); rmt_count_launches(1);
     const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
-    launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count, WLS_BLOCKS,
-                          (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s);
+    CK(g, launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count,
+                                WLS_BLOCKS, (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s));
     launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), g->bb_all + 6 * g->par, 12,
                       (T*)g->rho, s);
   }
@@ -796,12 +888,15 @@ rmt_status rmt_add_solid(rmt_grid* g, const rmt_solid_desc* s, int* solid_id) {
 
 rmt_status rmt_step(rmt_grid* g, int nsteps) {
   if (!g || nsteps < 0) return RMT_EINVAL;
+  rmt_status st = poll_err(g);  // a failure of an earlier, unsynchronised step
+  if (st != RMT_OK) return st;
   if (g->sticky != RMT_OK) return RMT_ESTATE;
   if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
-  rmt_status st = ensure_init(g);
+  st = ensure_init(g);
   if (st != RMT_OK) return st;
   if (g->use_graph && fixed_cycles(g) && !g->prof.on) {
     for (int k = 0; k < nsteps; k++) {
+      if ((st = inject(g)) != RMT_OK) return st;
       if (!g->gexec[g->par] && (st = build_graph(g)) != RMT_OK) return st;
       CK(g, cudaGraphLaunch(g->gexec[g->par], g->s));
       rmt_count_launches(g->gnodes[g->par]);
@@ -810,6 +905,7 @@ rmt_status rmt_step(rmt_grid* g, int nsteps) {
     return RMT_OK;
   }
   for (int k = 0; k < nsteps; k++) {
+    if ((st = inject(g)) != RMT_OK) return st;
     st = g->fp32 ? step_t<float>(g) : step_t<double>(g);
     if (st != RMT_OK) return st;
   }
@@ -1060,6 +1156,11 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     (name[0] == 'f' ? g->fe_omega : g->mac_omega) = value;
   } else if (!strcmp(name, "graph")) {
     g->use_graph = value != 0.0;
+  } else if (!strcmp(name, "inject_nan_step")) {
+    g->inject_nan_step = value < 0 ? -1 : (long)value;
+  } else if (!strcmp(name, "inject_alloc")) {
+    if (g->inited) return refuse(g, "inject_alloc is set before the grid allocates");
+    g->inject_alloc = value < 0 ? -1 : (long)value;
   } else {
     return fail(g, RMT_EINVAL, "unknown option %s", name);
   }
@@ -1143,6 +1244,17 @@ rmt_status grid_check(rmt_grid* g) {
   return check_err(g);
 }
 rmt_status grid_fail(rmt_grid* g, rmt_status st, const char* msg) { return fail(g, st, "%s", msg); }
+rmt_status grid_pre_step(rmt_grid* g, cudaStream_t s) {
+  cudaStream_t s0 = g->s;
+  g->s = s;
+  const rmt_status st = inject(g);
+  g->s = s0;
+  return st;
+}
+rmt_status grid_poll(rmt_grid* g) {
+  const rmt_status st = poll_err(g);
+  return st != RMT_OK ? st : g->sticky;
+}
 
 // ----------------------------------------------------------------------------- autotuner hooks
 rmt_status grid_solvers(rmt_grid* g, MGSolver** mac, MGSolver** fe, cudaStream_t* s, double* rtol) {

@@ -179,6 +179,10 @@ rmt_status rmt_batch_step(rmt_batch* b, int nsteps) {
       rmt_status st = capture(b, ph);
       if (st != RMT_OK) return st;
     }
+    for (rmt_grid* m : b->g) {
+      const rmt_status st = grid_pre_step(m, b->s);
+      if (st != RMT_OK) return bfail(b, st, "member: %s", rmt_last_error(m));
+    }
     BCK(b, cudaGraphLaunch(b->exec[ph], b->s));
     rmt_count_launches(b->nodes[ph]);
     for (rmt_grid* m : b->g) grid_advance_host(m);
@@ -337,10 +341,23 @@ rmt_status rmt_server_submit(rmt_server* s, const rmt_grid_desc* d, const rmt_so
 
 rmt_status rmt_server_poll(rmt_server* s, int* n_running, int* n_queued) {
   if (!s) return RMT_EINVAL;
-  // 1. retire the jobs whose last step has been launched
+  // 1. evict the jobs whose device error words report a failure (a diverged velocity, a
+  //    degenerate extrapolation), freeing their memory, and retire the jobs whose last step has
+  //    been launched; the others carry on
   const double t_ret = now(s);
   for (size_t i = 0; i < s->running.size();) {
     Job* j = s->running[i];
+    const rmt_status fs = grid_poll(j->g);
+    if (fs != RMT_OK) {
+      rmt_batch_remove(s->batch, j->g);
+      finish(s, j, fs);
+      j->t_done = now(s);
+      rmt_destroy_grid(j->g);
+      j->g = nullptr;
+      s->used -= j->bytes;
+      s->running.erase(s->running.begin() + i);
+      continue;
+    }
     if (j->steps_done < j->steps_total) {
       i++;
       continue;

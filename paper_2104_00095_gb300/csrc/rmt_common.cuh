@@ -41,8 +41,15 @@ struct Body {
   double rho_s, G, mu_a, gamma_t, actA, actW, actL;
   double repA;         // wall-repulsion acceleration (0: none)
   double a2[3], mina;  // squared semi-axes, smallest semi-axis (body_finish)
+  // FP32 storage keeps the reference map as the displacement S = xi - x0 from x0, the cell
+  // centre's image in a fixed window of periodic images around the body centre: unwrapped cell
+  // coordinates wlo[d] .. wlo[d] + n_d - 1 on a periodic axis (the cell itself on a walled one).
+  // cu: the cell coordinate nearest the centre; off = lo + (cu + 1/2) h - c, so that x0 - c =
+  // (u - cu) h + off holds small numbers only (body_image)
+  int wlo[3], cu[3];
+  double off[3];
   struct {
-    float c[3], a[3], R[9], a2[3], mina, rho_s, G, mu_a, gamma_t, actA, actW, actL, repA;
+    float c[3], a[3], R[9], a2[3], mina, rho_s, G, mu_a, gamma_t, actA, actW, actL, repA, off[3];
   } f;
 };
 
@@ -99,6 +106,16 @@ inline void body_finish(Body& b) {
   b.f.actW = (float)b.actW;
   b.f.actL = (float)b.actL;
   b.f.repA = (float)b.repA;
+}
+// the image window of a body on grid g (host; after body_finish and geo_finish)
+inline void body_image(Body& b, const Geo& g) {
+  for (int d = 0; d < 3; d++) {
+    const double ci = (b.c[d] - g.lo[d]) / g.h - 0.5;
+    b.cu[d] = (int)floor(ci + 0.5);
+    b.off[d] = g.lo[d] + (b.cu[d] + 0.5) * g.h - b.c[d];
+    b.f.off[d] = (float)b.off[d];
+    b.wlo[d] = g.per[d] ? b.cu[d] - g.n[d] / 2 : 0;
+  }
 }
 
 // The reference-map fields of one body at one time level.
@@ -202,10 +219,10 @@ __device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
 
 // Level set phi_0 of a body's reference shape (main text "Blurred interface method").
 // Sphere: exact signed distance.  Ellipsoid: (g-1)/|grad g| with g = |D^-1 R^T (X-c)|.
+// phi0_r takes the position relative to the centre, r = X - c.
 template <typename T>
-__device__ T phi0(const Body& b, T X0, T X1, T X2) {
+__device__ T phi0_r(const Body& b, T r0, T r1, T r2) {
 #define BC(x) cv<T>(b.x, b.f.x)
-  const T r0 = sub_rn(X0, BC(c[0])), r1 = sub_rn(X1, BC(c[1])), r2 = sub_rn(X2, BC(c[2]));
   if (b.shape == 0)
     return sub_rn(sqrt_rn(add_rn(add_rn(mul_rn(r0, r0), mul_rn(r1, r1)), mul_rn(r2, r2))), BC(a[0]));
   const T z0 = add_rn(add_rn(mul_rn(BC(R[0]), r0), mul_rn(BC(R[3]), r1)), mul_rn(BC(R[6]), r2));
@@ -218,11 +235,14 @@ __device__ T phi0(const Body& b, T X0, T X1, T X2) {
   const T wn = sqrt_rn(add_rn(add_rn(mul_rn(w0, w0), mul_rn(w1, w1)), mul_rn(w2, w2)));
   return div_rn(mul_rn(sub_rn(gg, T(1)), gg), wn);
 }
-
-// direction of grad_X phi_0 (the WLS weights use its direction only)
 template <typename T>
-__device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
-  const T r[3] = {X[0] - BC(c[0]), X[1] - BC(c[1]), X[2] - BC(c[2])};
+__device__ T phi0(const Body& b, T X0, T X1, T X2) {
+  return phi0_r(b, sub_rn(X0, BC(c[0])), sub_rn(X1, BC(c[1])), sub_rn(X2, BC(c[2])));
+}
+
+// direction of grad_X phi_0 at X = c + r (the WLS weights use its direction only)
+template <typename T>
+__device__ void phi0_dir_r(const Body& b, const T r[3], T gd[3]) {
   if (b.shape == 0) {
     gd[0] = r[0]; gd[1] = r[1]; gd[2] = r[2];
     return;
@@ -236,7 +256,66 @@ __device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
 #pragma unroll
   for (int a = 0; a < 3; a++) gd[a] = BC(R[3 * a]) * w[0] + BC(R[3 * a + 1]) * w[1] + BC(R[3 * a + 2]) * w[2];
 }
+template <typename T>
+__device__ void phi0_dir(const Body& b, const T X[3], T gd[3]) {
+  const T r[3] = {X[0] - BC(c[0]), X[1] - BC(c[1]), X[2] - BC(c[2])};
+  phi0_dir_r(b, r, gd);
+}
 #undef BC
+
+// ---- stored reference maps --------------------------------------------------------
+// FP64 storage holds xi itself; FP32 storage holds S = xi - x0 (see Body), so that FP32
+// rounding applies to the displacement rather than to O(1) positions: a difference of
+// neighbouring values is (x0 difference, a multiple of h) + (S difference).
+template <typename T>
+__host__ __device__ __forceinline__ constexpr bool disp_storage() { return sizeof(T) == 4; }
+
+// unwrapped image coordinate of cell index i (in [0, n)) on axis d
+__host__ __device__ __forceinline__ int img_u(const Geo& g, const Body& b, int d, int i) {
+  if (!g.per[d]) return i;
+  int t = (i - b.wlo[d]) % g.n[d];
+  if (t < 0) t += g.n[d];
+  return b.wlo[d] + t;
+}
+// x0 - c of cell index i on axis d (x0: the image of the cell centre)
+template <typename T>
+__device__ __forceinline__ T cell_rel(const Geo& g, const Body& b, int d, int i) {
+  return T(img_u(g, b, d, i) - b.cu[d]) * cv<T>(g.h, g.f.h) + cv<T>(b.off[d], b.f.off[d]);
+}
+// xi - c at cell (i,j,k) from its stored value v
+template <typename T>
+__device__ __forceinline__ void xi_rel(const Geo& g, const Body& b, int i, int j, int k, const T v[3], T r[3]) {
+  if constexpr (disp_storage<T>()) {
+    r[0] = cell_rel<T>(g, b, 0, i) + v[0];
+    r[1] = cell_rel<T>(g, b, 1, j) + v[1];
+    r[2] = cell_rel<T>(g, b, 2, k) + v[2];
+  } else {
+    r[0] = sub_rn(v[0], (T)b.c[0]);
+    r[1] = sub_rn(v[1], (T)b.c[1]);
+    r[2] = sub_rn(v[2], (T)b.c[2]);
+  }
+}
+// phi_0(xi) at cell (i,j,k) from its stored value (FP64: exactly phi0 of the value)
+template <typename T>
+__device__ __forceinline__ T phi_stored(const Geo& g, const Body& b, int i, int j, int k, T v0, T v1, T v2) {
+  const T v[3] = {v0, v1, v2};
+  T r[3];
+  xi_rel<T>(g, b, i, j, k, v, r);
+  return phi0_r(b, r[0], r[1], r[2]);
+}
+// FP32 storage: a band cell closer than this many cells to the edge of its body's image window
+// on a periodic axis is reported (the stencils then never pair cells across the window's seam)
+constexpr int SEAM_MARGIN = 3;
+__device__ __forceinline__ bool near_seam(const Geo& g, const Body& b, int i, int j, int k) {
+  const int ii[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (!g.per[d]) continue;
+    const int t = img_u(g, b, d, ii[d]) - b.wlo[d];
+    if (t < SEAM_MARGIN || t > g.n[d] - 1 - SEAM_MARGIN) return true;
+  }
+  return false;
+}
 
 // smoothed Heaviside (eq. sm_heavi) and its derivative
 template <typename T>

@@ -6,7 +6,8 @@
 // the active stress of the stress calculation at the cell centre, at the current time.  A
 // cell with a missing neighbour value of xi or det(grad xi) <= 0 adds to the centroid
 // velocity and the volume only.  Accumulated in FP64 with a fixed-order two-stage reduction,
-// so repeated calls agree bit for bit.
+// so repeated calls agree bit for bit.  FP32 storage holds S = xi - x0 (rmt_common.cuh):
+// grad xi = I + grad S, and xi - c = (x0 - c) + S, both formed in FP64.
 #include "rmt_kernels.h"
 
 namespace {
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(DTPB) k_body_stats(Geo g, const T* __restrict_
         break;
       }
 #pragma unroll
-      for (int a = 0; a < 3; a++) A[3 * a + d] = (xp[a] - xm[a]) / (2.0 * h);
+      for (int a = 0; a < 3; a++) A[3 * a + d] = (xp[a] - xm[a]) / (2.0 * h) + (disp_storage<T>() && a == d ? 1.0 : 0.0);
     }
     if (!ok) continue;
     const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
@@ -70,7 +71,10 @@ __global__ void __launch_bounds__(DTPB) k_body_stats(Geo g, const T* __restrict_
     acc[6] += w;
     acc[7] += w * (J - 1.0) * (J - 1.0);
     if (B.actA == 0.0) continue;
-    const double r[3] = {(double)v.x[c] - B.c[0], (double)v.x[g.N + c] - B.c[1], (double)v.x[2 * g.N + c] - B.c[2]};
+    double r[3] = {(double)v.x[c] - B.c[0], (double)v.x[g.N + c] - B.c[1], (double)v.x[2 * g.N + c] - B.c[2]};
+    if constexpr (disp_storage<T>()) {
+      for (int a = 0; a < 3; a++) r[a] = cell_rel<double>(g, B, a, ii[a]) + (double)v.x[a * g.N + c];
+    }
     const double Xb = B.R[0] * r[0] + B.R[3] * r[1] + B.R[6] * r[2];
     const double Zb = B.R[2] * r[0] + B.R[5] * r[1] + B.R[8] * r[2];
     const double s0 = B.actA * sin(2.0 * RMT_PI * Xb / B.actL - B.actW * t);

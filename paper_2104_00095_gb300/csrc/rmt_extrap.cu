@@ -5,7 +5,9 @@
 //
 // This translation unit is compiled with --fmad=false: the fits are evaluated operation
 // by operation in a fixed order, so that the integer outcomes (layer labels, which fits
-// are degenerate, which weights are positive) are reproducible.  All fits run in FP64.
+// are degenerate, which weights are positive) are reproducible.  FP64 storage fits in FP64;
+// FP32 storage holds displacements S = xi - x0 (rmt_common.cuh) and fits them in FP32, redone
+// in FP64 when ill-conditioned.
 #include "rmt_kernels.h"
 
 namespace {
@@ -24,10 +26,15 @@ __device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, i
   k = (int)(r / ny);
 }
 
-// xi^0 = x at every cell; on a periodic axis the image of x nearest the body centre
+// xi^0 = x at every cell; on a periodic axis the image of x nearest the body centre (FP32
+// storage: the displacement from the cell's image, zero)
 template <typename T>
 __global__ void k_init_xi(Geo g, Body b, T* __restrict__ x) {
   GRID_LOOP(c, g.N) {
+    if constexpr (disp_storage<T>()) {
+      x[c] = x[g.N + c] = x[2 * g.N + c] = T(0);
+      continue;
+    }
     int ii[3];
     decode(c, g.n[0], g.n[1], ii[0], ii[1], ii[2]);
 #pragma unroll
@@ -50,7 +57,7 @@ __global__ void k_classify(Geo g, Body b, const int* __restrict__ bb, const T* _
     win_cell(g, w, t, u, i, j, k, c);
     const T x0 = x[c], x1 = x[g.N + c], x2 = x[2 * g.N + c];
     int8_t l = -1;
-    if (isfinite(x0) && isfinite(x1) && isfinite(x2) && phi0(b, x0, x1, x2) < T(0)) l = 0;
+    if (isfinite(x0) && isfinite(x1) && isfinite(x2) && phi_stored(g, b, i, j, k, x0, x1, x2) < T(0)) l = 0;
     lay[c] = l;
   }
 }
@@ -118,14 +125,13 @@ __device__ bool solve4(AT A[4][4], AT B[4][3], AT X[4][3], AT tolfac) {
 // whole warp: the lanes split the (2 rs + 1)^3 candidate cells and the normal-equation sums are
 // combined by a butterfly (every lane ends with the same totals, in a fixed order).
 // mode 0: kernel 2^-(|di|+|dj|+|dk|); mode 1: times max(0, cos) against the normal n_e.
-// FP32 fits take the data as displacements from the identity map, xi_d - (ref + offset h), ref
-// the position of cell (i,j,k) in the body's periodic image: the fitted values are then small,
-// so the FP32 solve's error, which scales with the data, no longer carries O(1) positions into
-// the extrapolated maps.  The caller adds the identity back.  FP64 fits take xi_d itself.
+// The data are the stored values: xi_d (FP64 storage), or the displacements S_d (FP32 storage),
+// which the affine model fits exactly as it fits xi (the identity is affine): the fitted values
+// are then small, so the solve's error, which scales with the data, carries no O(1) positions
+// into the extrapolated maps.
 template <typename AT, typename T>
 __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j,
-                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, const AT ref[3],
-                             AT sol[4][3]) {
+                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, AT sol[4][3]) {
   const int lane = threadIdx.x & 31;
   AT a[10], bsum[12];
 #pragma unroll
@@ -149,12 +155,7 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
       if (!(wt > AT(0))) continue;
     }
     const AT v[4] = {AT(1), (AT)di, (AT)dj, (AT)dk};
-    AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
-    if constexpr (sizeof(AT) == 4) {
-      const AT hf = g.f.h;
-#pragma unroll
-      for (int d = 0; d < 3; d++) xv[d] -= ref[d] + v[1 + d] * hf;
-    }
+    const AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
     int q = 0;
 #pragma unroll
     for (int r = 0; r < 4; r++)
@@ -197,30 +198,25 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
                             int i, int j, int k, int le, double out[3]) {
   // FP64: the degeneracy threshold; FP32: also the point below which the fit is redone in FP64
   const AT tolfac = sizeof(AT) == 8 ? AT(1e-12) : AT(1e-4);
-  // FP32: the identity map's value at the cell, in the periodic image nearest the body centre
-  // (the image the reference map takes); the fits return displacements from it
-  double refd[3] = {0.0, 0.0, 0.0};
-  AT ref[3] = {AT(0), AT(0), AT(0)};
-  if constexpr (sizeof(AT) == 4) {
-    const int id[3] = {i, j, k};
-    for (int d = 0; d < 3; d++) {
-      const double xe = g.lo[d] + (id[d] + 0.5) * g.h;
-      refd[d] = g.per[d] ? xe + g.len[d] * rint((b.c[d] - xe) / g.len[d]) : xe;
-      ref[d] = (AT)refd[d];
-      refd[d] = (double)ref[d];
-    }
-  }
-  const AT hid = sizeof(AT) == 4 ? (AT)g.f.h : AT(0);  // identity's slope per cell offset
+  // FP32 storage fits displacements: the identity's slope per cell offset is added back to the
+  // fitted gradient, and the cell's x0 - c to the fitted value, where the normal needs xi
+  const AT hid = disp_storage<T>() ? (sizeof(AT) == 4 ? (AT)g.f.h : (AT)g.h) : AT(0);
   for (int rs = 2; rs <= 4; rs++) {
     AT s1[4][3];
-    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, ref, s1)) {
+    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, s1)) {
       if (sizeof(AT) == 4) return -1;
       continue;
     }
     if (le <= 2) {
-      const AT c0[3] = {s1[0][0] + ref[0], s1[0][1] + ref[1], s1[0][2] + ref[2]};
       AT gX[3], v[3];
-      phi0_dir<AT>(b, c0, gX);
+      if constexpr (disp_storage<T>()) {
+        const AT r0[3] = {cell_rel<AT>(g, b, 0, i) + s1[0][0], cell_rel<AT>(g, b, 1, j) + s1[0][1],
+                          cell_rel<AT>(g, b, 2, k) + s1[0][2]};
+        phi0_dir_r<AT>(b, r0, gX);
+      } else {
+        const AT c0[3] = {s1[0][0], s1[0][1], s1[0][2]};
+        phi0_dir<AT>(b, c0, gX);
+      }
       for (int q = 0; q < 3; q++)
         v[q] = (s1[1 + q][0] + (q == 0 ? hid : AT(0))) * gX[0] + (s1[1 + q][1] + (q == 1 ? hid : AT(0))) * gX[1] +
                (s1[1 + q][2] + (q == 2 ? hid : AT(0))) * gX[2];
@@ -231,14 +227,14 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
       }
       const AT nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
       AT s2[4][3];
-      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, ref, s2)) {
+      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, s2)) {
         if (sizeof(AT) == 4) return -1;
         continue;
       }
-      for (int d = 0; d < 3; d++) out[d] = refd[d] + (double)s2[0][d];
+      for (int d = 0; d < 3; d++) out[d] = (double)s2[0][d];
       return 1;
     }
-    for (int d = 0; d < 3; d++) out[d] = refd[d] + (double)s1[0][d];
+    for (int d = 0; d < 3; d++) out[d] = (double)s1[0][d];
     return 1;
   }
   return 0;
@@ -294,9 +290,11 @@ __global__ void k_wls(Geo g, Body b, int l, T* __restrict__ x, int8_t* __restric
   }
 }
 
+// phi of the band cells, NaN elsewhere, the band's box; FP32 storage: band cells near the seam of
+// the body's image window are counted in *seam
 template <typename T>
 __global__ void k_finalize(Geo g, Body b, const int* __restrict__ bb, T* __restrict__ x, T* __restrict__ phi,
-                           const int8_t* __restrict__ lay, int* __restrict__ bb_out) {
+                           const int8_t* __restrict__ lay, int* __restrict__ bb_out, int* __restrict__ seam) {
   const T nanv = T(__longlong_as_double(0x7ff8000000000000ll));
   const Win w = make_win(g, bb, 2);
   WIN_LOOP(t, w) {
@@ -311,7 +309,8 @@ __global__ void k_finalize(Geo g, Body b, const int* __restrict__ bb, T* __restr
       }
     }
     if (lay[c] >= 0) {
-      phi[c] = phi0(b, x[c], x[g.N + c], x[2 * g.N + c]);
+      phi[c] = phi_stored(g, b, i, j, k, x[c], x[g.N + c], x[2 * g.N + c]);
+      if (disp_storage<T>() && near_seam(g, b, i, j, k)) atomicAdd(seam, 1);
     } else {
       x[c] = x[g.N + c] = x[2 * g.N + c] = nanv;
       phi[c] = nanv;
@@ -376,7 +375,7 @@ __global__ void k_phi_half(Geo g, Body b, const int* __restrict__ bb, const T* _
     int u[3], i, j, k;
     long c;
     win_cell(g, w, t, u, i, j, k, c);
-    phih[c] = layn[c] >= 0 ? phi0(b, xh[c], xh[g.N + c], xh[2 * g.N + c]) : nanv;
+    phih[c] = layn[c] >= 0 ? phi_stored(g, b, i, j, k, xh[c], xh[g.N + c], xh[2 * g.N + c]) : nanv;
   }
 }
 
@@ -407,15 +406,16 @@ void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list, int* count,
-                        int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s) {
+cudaError_t launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list,
+                               int* count, int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s) {
   k_classify<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, lay);
   rmt_count_launches(1);
   for (int l = 1; l <= g.layers; l++) {
     k_bfs<<<blocks, TPB, 0, s>>>(g, bb_in, l, lay);
     rmt_count_launches(1);
   }
-  cudaMemsetAsync(count, 0, sizeof(int), s);
+  const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   k_band_list<<<blocks, TPB, 0, s>>>(g, bb_in, lay, list, count);
   rmt_count_launches(1);
   for (int l = 1; l <= g.layers; l++) {
@@ -424,10 +424,11 @@ void launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_o
   }
   k_bb_reset<<<1, 32, 0, s>>>(bb_out);
   rmt_count_launches(1);
-  k_finalize<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, phi, lay, bb_out);
+  k_finalize<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, phi, lay, bb_out, err + 1);
   rmt_count_launches(1);
   k_bb_normalise<<<1, 32, 0, s>>>(g, bb_out);
   rmt_count_launches(1);
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -446,8 +447,8 @@ void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks,
 
 #define INST(T)                                                                                                \
   template void launch_init_xi<T>(const Geo&, const Body&, T*, cudaStream_t);                                   \
-  template void launch_extrapolate<T>(const Geo&, const Body&, const int*, int*, int, int*, int*, int, T*, T*,    \
-                                      int8_t*, int*, cudaStream_t);                                             \
+  template cudaError_t launch_extrapolate<T>(const Geo&, const Body&, const int*, int*, int, int*, int*, int, T*, \
+                                             T*, int8_t*, int*, cudaStream_t);                                  \
   template void launch_corrector<T>(const Geo&, const Body&, const int*, int, const int*, const int*, int,        \
                                     const T*, const int8_t*, const T*, const int8_t*, T*, T*, int*, cudaStream_t);
 INST(float)

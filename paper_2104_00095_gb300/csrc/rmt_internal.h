@@ -16,8 +16,13 @@ rmt_status grid_capture_step(rmt_grid* g, cudaStream_t s);
 // The host state after one step that ran from a captured graph (parity, time, step count).
 void grid_advance_host(rmt_grid* g);
 int grid_parity(const rmt_grid* g);
-// Waits for g's stream and reads its device error flag (degenerate fits).
+// Waits for g's stream and reads its device error words (degenerate fits, non-finite values).
 rmt_status grid_check(rmt_grid* g);
+// The same without waiting: the error words as of the last step whose copy has landed.
+rmt_status grid_poll(rmt_grid* g);
+// Host-side work before a batched step of g, enqueued on s (the fault injection of the
+// inject_nan_step option).
+rmt_status grid_pre_step(rmt_grid* g, cudaStream_t s);
 // Records an error on g (sticky unless RMT_EINVAL).
 rmt_status grid_fail(rmt_grid* g, rmt_status st, const char* msg);
 // The grid's two multigrid solvers and stream, for the autotuner; RMT_ESTATE before the first

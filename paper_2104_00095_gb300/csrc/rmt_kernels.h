@@ -25,9 +25,9 @@ struct Faces3 {
 // list (N ints) and count: scratch for the cells a band reaches
 // t: device pointer to the simulated time; the stress is evaluated at *t + toff
 template <typename T>
-void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
-                       const int* bbs, int bstride, const double* t, double toff, T* out, int* list, int* count,
-                       cudaStream_t s);
+cudaError_t launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
+                              const int* bbs, int bstride, const double* t, double toff, T* out, int* list,
+                              int* count, cudaStream_t s);
 void launch_tick(double* t, double dt, cudaStream_t s);
 // slopes: nine cell arrays, written by launch_bar_states (limited slope of u_a along d at 3d+a)
 // and read by launch_face_states
@@ -87,9 +87,11 @@ void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s);
 // count: device buffers for the compacted band (capacity: the grid), filled by
 // launch_extrapolate and read by launch_corrector of the same step; wls_blocks: launch width
 // of the one-warp-per-cell fits
+// err[0] counts degenerate fits, err[1] (FP32 storage) band cells near the seam of the body's
+// image window; returns the error of the one runtime call it makes besides launches
 template <typename T>
-void launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list, int* count,
-                        int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s);
+cudaError_t launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list,
+                               int* count, int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s);
 template <typename T>
 void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, const int* count,
                       int wls_blocks, const T* x, const int8_t* lay, const T* xn, const int8_t* layn, T* xh, T* phih,
@@ -121,6 +123,9 @@ void mg_set_inner(MGSolver* m, int inner);
 void mg_set_block(MGSolver* m, int by);
 // start each solve from the previous solution (zero before the first) instead of from zero
 void mg_set_warm(MGSolver* m, int warm);
+// device int set to 1 when a solve's right-hand-side mean, solution mean or residual norm is
+// not finite (null: not checked)
+void mg_set_nonfinite_flag(MGSolver* m, int* flag);
 // MAC in FP32: one fused red-black pass per sweep (1: on the large levels that allow it, the
 // default; 2: on every level that allows it; 0: never), else one pass per colour
 void mg_set_sweep(MGSolver* m, int fused);

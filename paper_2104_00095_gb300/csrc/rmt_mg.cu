@@ -1196,9 +1196,12 @@ __global__ void k_partial(const XT* __restrict__ a, long n, int mode, double* __
   }
 }
 
-// final fixed-order sum of the partials (one block); out = scale * sum
+// final fixed-order sum of the partials (one block); out = scale * sum; a non-finite result
+// sets *nonfinite (when given): every solve takes the mean of its right-hand side and of its
+// solution, so a NaN or infinity anywhere in the velocity that feeds them is caught here
 __global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part, int np, double scale,
-                                                double* __restrict__ out, float* __restrict__ out_ff = nullptr) {
+                                                double* __restrict__ out, float* __restrict__ out_ff = nullptr,
+                                                int* __restrict__ nonfinite = nullptr) {
   __shared__ double sh[1024];
   double loc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) loc += part[i];
@@ -1211,6 +1214,7 @@ __global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part,
   if (threadIdx.x == 0) {
     const double v = sh[0] * scale;
     *out = v;
+    if (nonfinite && !isfinite(v)) *nonfinite = 1;
     if (out_ff) {  // the same value as a two-float pair
       out_ff[0] = (float)v;
       out_ff[1] = (float)(v - (double)out_ff[0]);
@@ -1460,7 +1464,8 @@ struct MGSolver {
   double omega = 0.9;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
-  size_t bytes = 0;  // device bytes requested
+  int* nonfinite = nullptr;  // device flag set when a mean or norm of a solve is not finite
+  size_t bytes = 0;          // device bytes requested
 };
 
 void mg_set_hook(MGSolver* m, mg_hook_fn fn, void* ctx) {
@@ -1480,6 +1485,7 @@ void mg_set_inner(MGSolver* m, int inner) {
   if (inner >= 1) m->inner = inner;
 }
 void mg_set_warm(MGSolver* m, int warm) { m->warm = warm != 0; }
+void mg_set_nonfinite_flag(MGSolver* m, int* flag) { m->nonfinite = flag; }
 void mg_set_sweep(MGSolver* m, int fused) { m->sweep = fused < 0 ? 0 : (fused > 2 ? 2 : fused); }
 void mg_set_block(MGSolver* m, int by) {
   if (by == 1 || by == 2 || by == 4 || by == 8) m->by = by;
@@ -1685,7 +1691,7 @@ void sum_into(MGSolver* m, const T* a, long n, int mode, double scale, double* o
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
   k_partial<T><<<nb, TPB, 0, s>>>(a, n, mode, m->part);
   rmt_count_launches(1);
-  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out);
+  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out, nullptr, m->nonfinite);
   rmt_count_launches(1);
 }
 
@@ -1696,7 +1702,7 @@ void sum_ff(MGSolver* m, const float* h, const float* l, long n, double scale, d
   if (nb > RED_BLOCKS) nb = RED_BLOCKS;
   k_partial_ff<<<nb, TPB, 0, s>>>(h, l, n, m->part);
   rmt_count_launches(1);
-  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out, out_ff);
+  k_final<<<1, 1024, 0, s>>>(m->part, nb, scale, out, out_ff, m->nonfinite);
   rmt_count_launches(1);
 }
 
@@ -1889,7 +1895,7 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
       hk(m, 0, 1, 0, s);
     }
     if (fixed_cycles <= 0) {
-      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2);
+      k_final<<<1, 1024, 0, s>>>(m->part, nbr, 1.0, m->scal + 2, nullptr, m->nonfinite);
       rmt_count_launches(1);
       cudaMemcpyAsync(m->hpin + 1, m->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
       if ((*err = cudaStreamSynchronize(s)) != cudaSuccess) return -1;

@@ -95,6 +95,7 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   b.repA = s->rep_A;
   body_finish(b);
   geo_finish(G);
+  body_image(b, G);
 
   cudaStream_t st = (cudaStream_t)stream;
   int* scr = nullptr;
@@ -105,10 +106,10 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   if (e == cudaSuccess) e = cudaMemcpyAsync(xi_out, xi_in, 3 * G.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return RMT_ECUDA;
   const int blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
-  launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, 152 * 4, xi_out,
-                             phi_out, (int8_t*)layer_out, scr + SCR_ERR, st);
+  e = launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, 152 * 4,
+                                 xi_out, phi_out, (int8_t*)layer_out, scr + SCR_ERR, st);
   int nbad = 0;
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, scr + SCR_ERR, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return RMT_ECUDA;

@@ -3,6 +3,11 @@
 // Two passes: every cell that no body's band reaches takes the pure-fluid divergence at once
 // and the rest are listed; then one thread per listed cell computes the face-normal rows of the
 // blended stress at its six faces and their divergence.  Templated on T.
+//
+// FP32 storage holds S = xi - x0 (rmt_common.cuh): the stencil differences give grad S =
+// grad xi - I, and the neo-Hookean stress is formed from it without cancellation: with
+// E = F - I = -F grad S, B - I = E + E^T + E E^T, so the deviator of B keeps the relative
+// accuracy of the small strain instead of the absolute accuracy of entries near 1.
 #include "rmt_kernels.h"
 
 namespace {
@@ -78,25 +83,61 @@ __device__ __noinline__ void face_row(const Geo& g, const T* __restrict__ u, con
     }
     if (!ok) continue;
     const Body& B = bodies[m];
-    const T xf[3] = {T(0.5) * (xa[0] + xb[0]), T(0.5) * (xa[1] + xb[1]), T(0.5) * (xa[2] + xb[2])};
-    const T ph = phi0(B, xf[0], xf[1], xf[2]);
+    // xi at the face, relative to the body centre
+    T r[3];
+    if constexpr (disp_storage<T>()) {
+      const int ib[3] = {i, j, k};
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+        r[a] = cell_rel<T>(g, B, a, ib[a]) + T(0.5) * (xa[a] + xb[a]) - (a == d ? T(0.5) * g.f.h : T(0));
+    } else {
+      const T xf[3] = {T(0.5) * (xa[0] + xb[0]), T(0.5) * (xa[1] + xb[1]), T(0.5) * (xa[2] + xb[2])};
+#pragma unroll
+      for (int a = 0; a < 3; a++) r[a] = xf[a] - cv<T>(B.c[a], B.f.c[a]);
+    }
+    const T ph = disp_storage<T>() ? phi0_r(B, r[0], r[1], r[2]) : phi0(B, T(0.5) * (xa[0] + xb[0]),
+                                                                         T(0.5) * (xa[1] + xb[1]),
+                                                                         T(0.5) * (xa[2] + xb[2]));
     const T w = T(1) - heavi(ph, eps);
     if (!(w > T(0))) continue;
     T F[9];
-    if (!inv3(A, F)) continue;
-    // neo-Hookean: tau = G (F F^T - tr/3 I); only row d is needed (tau is symmetric)
-    T Bd[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) Bd[a] = F[3 * a] * F[3 * d] + F[3 * a + 1] * F[3 * d + 1] + F[3 * a + 2] * F[3 * d + 2];
-    const T tr3 = (F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + F[4] * F[4] + F[5] * F[5] +
-                   F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) / T(3);
     const T G = cv<T>(B.G, B.f.G);
     T tau[3];
+    if constexpr (disp_storage<T>()) {
+      // A = grad S; F = (I + A)^-1, E = F - I = -F A; row d of dev(B) from B - I = E + E^T + E E^T
+      T M[9];
 #pragma unroll
-    for (int a = 0; a < 3; a++) tau[a] = G * (Bd[a] - (a == d ? tr3 : T(0)));
+      for (int q = 0; q < 9; q++) M[q] = A[q] + ((q == 0 || q == 4 || q == 8) ? T(1) : T(0));
+      if (!inv3(M, F)) continue;
+      T E[9];
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) E[3 * a + b] = -(F[3 * a] * A[b] + F[3 * a + 1] * A[3 + b] + F[3 * a + 2] * A[6 + b]);
+      T Kd[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+        Kd[a] = E[3 * a + d] + E[3 * d + a] + E[3 * a] * E[3 * d] + E[3 * a + 1] * E[3 * d + 1] +
+                E[3 * a + 2] * E[3 * d + 2];
+      T ee = T(0);
+#pragma unroll
+      for (int q = 0; q < 9; q++) ee += E[q] * E[q];
+      const T tr3 = (T(2) * (E[0] + E[4] + E[8]) + ee) * T(1.0 / 3.0);
+#pragma unroll
+      for (int a = 0; a < 3; a++) tau[a] = G * (Kd[a] - (a == d ? tr3 : T(0)));
+    } else {
+      if (!inv3(A, F)) continue;
+      // neo-Hookean: tau = G (F F^T - tr/3 I); only row d is needed (tau is symmetric)
+      T Bd[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) Bd[a] = F[3 * a] * F[3 * d] + F[3 * a + 1] * F[3 * d + 1] + F[3 * a + 2] * F[3 * d + 2];
+      const T tr3 = (F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + F[4] * F[4] + F[5] * F[5] +
+                     F[6] * F[6] + F[7] * F[7] + F[8] * F[8]) / T(3);
+#pragma unroll
+      for (int a = 0; a < 3; a++) tau[a] = G * (Bd[a] - (a == d ? tr3 : T(0)));
+    }
     if (B.actA != 0.0) {
       // active stress (3 Z s0 / 2)(e e^T - I/3), e = F E_X / |F E_X|, s0 = A sin(2 pi X/l - w t)
-      const T r[3] = {xf[0] - cv<T>(B.c[0], B.f.c[0]), xf[1] - cv<T>(B.c[1], B.f.c[1]), xf[2] - cv<T>(B.c[2], B.f.c[2])};
       const T Xb = cv<T>(B.R[0], B.f.R[0]) * r[0] + cv<T>(B.R[3], B.f.R[3]) * r[1] + cv<T>(B.R[6], B.f.R[6]) * r[2];
       const T Zb = cv<T>(B.R[2], B.f.R[2]) * r[0] + cv<T>(B.R[5], B.f.R[5]) * r[1] + cv<T>(B.R[8], B.f.R[8]) * r[2];
       const T s0 = cv<T>(B.actA, B.f.actA) * sin(T(2.0 * RMT_PI) * Xb / cv<T>(B.actL, B.f.actL) - cv<T>(B.actW, B.f.actW) * tt);
@@ -280,22 +321,25 @@ __global__ void __launch_bounds__(128) k_stress_band(Geo g, const T* __restrict_
 }  // namespace
 
 template <typename T>
-void launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
-                       const int* bbs, int bstride, const double* t, double toff, T* out, int* list, int* count,
-                       cudaStream_t s) {
+cudaError_t launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
+                              const int* bbs, int bstride, const double* t, double toff, T* out, int* list,
+                              int* count, cudaStream_t s) {
   const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + SFZ - 1) / SFZ);
-  cudaMemsetAsync(count, 0, sizeof(int), s);
+  const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   k_stress_fluid<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, views, nb, bbs, bstride, out, list, count);
   rmt_count_launches(1);
-  if (nb == 0) return;
+  if (nb == 0) return cudaSuccess;
   k_stress_band<T><<<152 * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, out);
   rmt_count_launches(1);
+  return cudaSuccess;
 }
 
-template void launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int, const int*,
-                                       int, const double*, double, float*, int*, int*, cudaStream_t);
-template void launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int,
-                                        const int*, int, const double*, double, double*, int*, int*, cudaStream_t);
+template cudaError_t launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int,
+                                              const int*, int, const double*, double, float*, int*, int*, cudaStream_t);
+template cudaError_t launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int,
+                                               const int*, int, const double*, double, double*, int*, int*,
+                                               cudaStream_t);
 
 // simulated time on the device: t += dt after each step (read by the stress kernels, so that a
 // captured step graph needs no per-step parameter)

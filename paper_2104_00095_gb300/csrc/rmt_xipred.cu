@@ -2,6 +2,12 @@
 // states of eq. xi_taylor_final and the tangential terms of SI "Tangential derivatives").
 // Three passes over a body's window: limited slopes of xi, transverse bar states on faces,
 // then the predictor at the cells of layers 0 and 1.
+//
+// FP32 storage holds S = xi - x0 (rmt_common.cuh).  The slopes are those of xi (the limiter sees
+// differences of xi: h + dS along the component's own axis, dS across it); every face state
+// is stored as the displacement from the face centre's image, so where the FP64 form adds a
+// Taylor term (h/2) s to xi, the FP32 form adds (h/2)(s - 1) for the component along the
+// face's axis, and a difference of face states across a cell gains h on that component.
 #include "rmt_kernels.h"
 
 namespace {
@@ -62,6 +68,9 @@ __device__ __forceinline__ void slope_xi(const Geo& g, const T* __restrict__ x, 
     if (xi3(g, x, lay, ii[0], ii[1], ii[2], v)) {
       ok |= 1u << (t + 2);
       q[0][t + 2] = v[0]; q[1][t + 2] = v[1]; q[2][t + 2] = v[2];
+      // FP32 storage: the identity's part of xi_d along axis d, relative to the centre cell (the
+      // band never pairs cells across the seam of the body's image window)
+      if constexpr (disp_storage<T>()) q[d][t + 2] += T(t) * g.f.h;
     } else {
       q[0][t + 2] = q[1][t + 2] = q[2][t + 2] = T(0);
     }
@@ -127,9 +136,17 @@ __global__ void k_xi_bar(Geo g, const int* __restrict__ bb, const T* __restrict_
 #pragma unroll
           for (int a = 0; a < 3; a++) {
             const T sD = ((const T*)sc.s[3 * e + a])[cD], sU = ((const T*)sc.s[3 * e + a])[c];
-            ((T*)sc.xb[3 * e + a])[c] = upwind(x[a * g.N + cD] + (T(0.5) * h - T(0.5) * dt * uD) * sD,
-                                               x[a * g.N + c] - (T(0.5) * h + T(0.5) * dt * uU) * sU, va,
-                                               cv<T>(g.utol, g.f.utol));
+            T L, R;
+            if constexpr (disp_storage<T>()) {
+              // displacements from the face centre's image x0_D + (h/2) e_e = x0_U - (h/2) e_e
+              const T id = a == e ? T(1) : T(0);
+              L = x[a * g.N + cD] + T(0.5) * h * (sD - id) - T(0.5) * dt * uD * sD;
+              R = x[a * g.N + c] - T(0.5) * h * (sU - id) - T(0.5) * dt * uU * sU;
+            } else {
+              L = x[a * g.N + cD] + (T(0.5) * h - T(0.5) * dt * uD) * sD;
+              R = x[a * g.N + c] - (T(0.5) * h + T(0.5) * dt * uU) * sU;
+            }
+            ((T*)sc.xb[3 * e + a])[c] = upwind(L, R, va, cv<T>(g.utol, g.f.utol));
           }
         }
       }
@@ -168,6 +185,18 @@ __device__ __forceinline__ void xi_state(const Geo& g, const T* __restrict__ u, 
 #pragma unroll
     for (int a = 0; a < 3; a++)
       tr[a] += vav * (((const T*)sc.xb[3 * e + a])[cu] - ((const T*)sc.xb[3 * e + a])[c]) * ih;
+    // FP32 storage: the two bar states are displacements from face centres h apart along e
+    if constexpr (disp_storage<T>()) tr[e] += vav;
+  }
+  if constexpr (disp_storage<T>()) {
+    // displacement from the face centre's image x0_c +- (h/2) e_d
+    const T sg = side == 0 ? T(0.5) * h : -T(0.5) * h;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const T s = ((const T*)sc.s[3 * d + a])[c];
+      out[a] = x[a * g.N + c] + sg * (s - (a == d ? T(1) : T(0))) - T(0.5) * dt * ud * s - T(0.5) * dt * tr[a];
+    }
+    return;
   }
 #pragma unroll
   for (int a = 0; a < 3; a++)
@@ -221,6 +250,8 @@ __global__ void k_xi_predict(Geo g, const T* __restrict__ u, XiPredPtrs pp, cons
       const T va = T(0.5) * (U[lo] + U[hi]);
 #pragma unroll
       for (int a = 0; a < 3; a++) acc[a] += va * (xf[1][a] - xf[0][a]) * ih;
+      // FP32 storage: the face states are displacements from face centres h apart along d
+      if constexpr (disp_storage<T>()) acc[d] += va;
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) xn[a * g.N + c] = x[a * g.N + c] - dt * acc[a];

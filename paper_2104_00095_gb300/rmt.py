@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 RMT_OK, RMT_EINVAL, RMT_ENOMEM, RMT_ECUDA, RMT_ESTATE = 0, 1, 2, 3, 4
-RMT_ENOCONVERGE, RMT_EDIVERGED, RMT_ETIMEOUT, RMT_EDEGENERATE = 5, 6, 7, 8
+RMT_ENOCONVERGE, RMT_EDIVERGED, RMT_ETIMEOUT, RMT_EDEGENERATE, RMT_ERANGE = 5, 6, 7, 8, 9
 RMT_BC_NOSLIP, RMT_BC_PERIODIC = 0, 1
 RMT_PREC_FP64, RMT_PREC_FP32_REFINE = 0, 1
 RMT_SHAPE_SPHERE, RMT_SHAPE_ELLIPSOID = 0, 1
@@ -384,6 +384,12 @@ class Server:
         for k, v in (options or {}).items():
             self._L.rmt_server_set_option(self._s, k.encode(), float(v))
         self.scenes = {}
+
+    def set_option(self, name: str, value: float):
+        """rmt_set_option(name, value) for every job admitted from now on."""
+        rc = self._L.rmt_server_set_option(self._s, name.encode(), float(value))
+        if rc != RMT_OK:
+            raise RMTError("rmt_server_set_option", rc, "")
 
     def submit(self, scene: dict, nsteps: int) -> int:
         sol = scene.get("solids", [])

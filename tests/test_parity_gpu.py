@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
 Bar: integer outputs (layer labels) bit-exact; FP64 fields within rel-L2 1e-10 per step;
-FP32 bulk + FP64 refinement within rel-L2 1e-4 on u and xi after 10 steps."""
+FP32 bulk with two-float refinement of the projections within rel-L2 1e-4 on u and xi after 10
+steps."""
 import numpy as np
 import pytest
 from scipy import ndimage
@@ -124,28 +125,49 @@ def test_fp32_periodic_fluid_matches_fp64_oracle():
     assert ep <= 1e-3, (eu, ep)
 
 
-def test_fp32_swimmers_error_against_the_fp64_oracle():
-    """The FP32 form on the swimmer scene (2 active ellipsoids, 32^3) against the FP64 oracle after
-    10 steps.  Its velocity error was measured at 6.3e-4 (9e-4 after the first step; 3e-3 before
-    the FP32 extrapolation fits took displacements from the identity map), the same with and
-    without the fused sweep and the 16-byte FE staging.  What remains comes from reference maps
-    stored in FP32: their rounding enters the elastic stress, a difference of O(1) terms, and the
-    swimmers' weak active forcing does not dominate it as the lid does in the cavity.  The test
-    bounds that error and the reference-map error (measured 1.9e-7)."""
-    sc = S.swimmers(n=32, nbodies=2, seed=5, precision="fp32")
-    g = rmt.Grid(dict(sc, mg_rtol=1e-10, mg_max_cycles=200, options={"mac_sweep": 2}))
-    o = O.Oracle(dict(sc, precision="fp64"))
-    g.step(10)
-    assert o.step(10) == 0
+def _fp32_against_oracle(sc, steps=10):
+    """Relative L2 error of u and of every body's xi (cells holding xi on both paths) of the FP32
+    form against the FP64 oracle after `steps` steps; band presence may differ only on a thin
+    shell where phi is within float rounding of zero."""
+    g = rmt.Grid(dict(sc, precision="fp32", mg_rtol=1e-10, mg_max_cycles=200, options={"mac_sweep": 2}))
+    o = O.Oracle(dict(sc, precision="fp64", mg_rtol=1e-13, mg_max_cycles=200))
+    g.step(steps)
+    assert o.step(steps) == 0, o.error()
     eu = rel_l2(g.read(rmt.RMT_F_U), o.read(O.F_U))
     exs = []
-    for m in range(2):
+    for m in range(len(sc["solids"])):
         xg, xo = g.read(rmt.RMT_F_XI, m), o.read(O.F_XI, m)
         both = np.isfinite(xg) & np.isfinite(xo)
         assert np.count_nonzero(np.isfinite(xg) != np.isfinite(xo)) <= 0.01 * both.sum()
         exs.append(np.linalg.norm(xg[both] - xo[both]) / np.linalg.norm(xo[both]))
-    assert eu <= 2e-3, (eu, exs)
-    assert max(exs) <= 1e-5, (eu, exs)
+    g.close()
+    return eu, max(exs)
+
+
+def test_fp32_swimmers_within_1e4_of_the_fp64_oracle():
+    """The FP32 form on the swimmer scene (2 active ellipsoids, 32^3) after 10 steps.  Reference
+    maps are stored as displacements from the cell centres, so FP32 rounding no longer enters
+    the elastic stress at the level of O(1) positions (measured 4e-7 on u)."""
+    eu, ex = _fp32_against_oracle(S.swimmers(n=32, nbodies=2, seed=5))
+    assert eu <= 1e-4, (eu, ex)
+    assert ex <= 1e-4, (eu, ex)
+
+
+def test_fp32_swimmer_scene_64_eight_bodies_within_1e4():
+    """The benchmark's swimmer scene (8 active ellipsoids, seed of the 256^3 scene) on a 64^3
+    copy, FP32 against the FP64 oracle after 10 steps."""
+    eu, ex = _fp32_against_oracle(S.swimmers(n=64, nbodies=8))
+    assert eu <= 1e-4, (eu, ex)
+    assert ex <= 1e-4, (eu, ex)
+
+
+def test_fp32_settling_within_1e4():
+    """The settling mixture (heavy and buoyant ellipsoids under gravity between no-slip walls) on
+    a 48^3 copy with the 10 bodies that fit at this resolution, FP32 against the FP64 oracle after
+    10 steps."""
+    eu, ex = _fp32_against_oracle(S.settling(n=48, nbodies=10))
+    assert eu <= 1e-4, (eu, ex)
+    assert ex <= 1e-4, (eu, ex)
 
 
 def _ragged_walls_fp32():
