@@ -10,8 +10,8 @@ GB) are far larger than the 129 MB L2, so no cache flush is needed between steps
 
 N > 1 runs one independent replica per GPU (launched with torch.distributed.run); value is the
 cell-updates/s of all replicas together, timed between barriers, max over ranks.
---impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
-scene (the same bodies and constants on a 48^3 grid).
+--impl reference times the FP64 CPU oracle on all host cores (OpenMP) on a bounded sample of the
+same scene (the same bodies and constants on a 64^3 grid).
 """
 from __future__ import annotations
 
@@ -42,7 +42,7 @@ CONFIGS = {
                         desc="128^3 no-slip box, 20 settling ellipsoids (10 at 1.5, 10 at 0.5), FP64"),
     "cavity32": dict(kind="cavity", n=32, precision="fp64", desc="32^3 lid-driven cavity, one soft sphere, FP64"),
 }
-CPU_SAMPLE_N = 48
+CPU_SAMPLE_N = 64
 
 
 def make_scene(cfg: dict, n: int | None = None, nbodies: int | None = None):
@@ -175,8 +175,17 @@ def dram_traffic(kernel: str, cells: int):
     return None
 
 
+def host_cores() -> int:
+    """Threads the oracle's OpenMP loops use: OMP_NUM_THREADS, else every core this process may run on."""
+    try:
+        return int(os.environ["OMP_NUM_THREADS"])
+    except (KeyError, ValueError):
+        return len(os.sched_getaffinity(0))
+
+
 def cpu_oracle_rate(cfg: dict, steps: int, warmup: int):
-    """cell-updates/s of the FP64 oracle on the CPU_SAMPLE_N^3 copy of the scene (single thread)."""
+    """cell-updates/s of the FP64 oracle (OpenMP over all host cores) on the CPU_SAMPLE_N^3 copy
+    of the scene."""
     import oracle as O
 
     sc = make_scene(cfg, CPU_SAMPLE_N)
@@ -199,12 +208,12 @@ def run_reference(args, cfg):
         return
     rate, dt = cpu_oracle_rate(cfg, args.steps, args.warmup)
     sample = (f"{args.steps} timed steps (after {args.warmup} warm-up) of the same scene on a "
-              f"{CPU_SAMPLE_N}^3 grid, FP64 oracle, one host thread")
+              f"{CPU_SAMPLE_N}^3 grid (all bodies), FP64 oracle, {host_cores()} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.config + f" (sampled at {CPU_SAMPLE_N}^3)"},
-            "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": host_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -245,6 +254,31 @@ def plain_fp64_leg(cfg: dict, args, stream) -> dict:
     n = int(np.prod(sc["n"]))
     g.close()
     return {"value": n / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": k, "dtype": "f64"}
+
+
+def settling_leg(args, stream) -> dict:
+    """Config 2: the 128^3 settling mixture (20 ellipsoids, 10 heavy and 10 buoyant, gravity, no-slip
+    walls) on the plain FP64 path and in the FP32 form side by side, with the bench's multigrid
+    schedule; beside them the relative L2 difference of u between the two after the same steps."""
+    from paper_2104_00095_gb300 import rmt, scenes as S
+
+    out, us = {}, {}
+    for prec in ("fp64", "fp32"):
+        sc = S.settling(n=128, precision=prec)
+        sc.update(mg_fixed_cycles=args.mg_cycles_mac, mg_fixed_cycles_fe=args.mg_cycles_fe,
+                  options=solver_options(args))
+        g = rmt.Grid(sc, stream=stream.cuda_stream)
+        g.step(3)
+        k = 5
+        ms = timed_steps(g, k, stream)
+        us[prec] = g.read(rmt.RMT_F_U)
+        n = int(np.prod(sc["n"]))
+        out[prec] = {"value": n / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms, "steps": k}
+        g.close()
+    out["workload"] = "settling128: 128^3 no-slip box, 20 ellipsoids (10 at 1.5, 10 at 0.5), gravity -z"
+    out["u_rel_l2_fp32_vs_fp64_after_8_steps"] = float(np.linalg.norm(us["fp32"] - us["fp64"]) /
+                                                       np.linalg.norm(us["fp64"]))
+    return out
 
 
 def batched_leg(args, stream) -> dict:
@@ -361,6 +395,19 @@ def serving_leg(args, stream) -> dict:
         t = max(t, a_) + d_
         fin.append(t)
     slat = np.array(fin) - arr
+    # the model checked against whole serial FP64 runs of the two smallest jobs
+    small = sorted(range(len(jobs)), key=lambda q: np.prod(jobs[q][1]["n"]) * jobs[q][1]["steps"])[:2]
+    checked = []
+    for q in small:
+        s64 = dict(jobs[q][1], precision="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = rmt.Grid(s64, stream=stream.cuda_stream)
+        g.step(s64["steps"])
+        torch.cuda.synchronize()
+        checked.append({"grid": list(s64["n"]), "steps": s64["steps"], "measured_s": time.perf_counter() - t0,
+                        "modelled_s": dur[q]})
+        g.close()
     return {"workload": f"{len(jobs)} jobs, Poisson 4/s, grids {{48..192}}^3, 1-10 bodies, steps U[{lo},{hi}], "
                         f"FP32, 80 GB budget",
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
@@ -370,7 +417,11 @@ def serving_leg(args, stream) -> dict:
                             "p99_latency_s": float(np.percentile(slat, 99)),
                             "value": float(sum(np.prod(sc["n"]) * sc["steps"] for _, sc in jobs) / (fin[-1] - arr[0])),
                             "method": "FIFO, one job at a time, FP64; duration = measured init + steps x measured "
-                                      "per-step time (2-step sample)"}}
+                                      "per-step time (2-step sample)",
+                            "whole_runs_checked": checked},
+            "sample_note": ("the default run serves a sample of the mix (fewer jobs, shorter runs) so that the "
+                            "bench ends within minutes; --serve-jobs 64 --serve-steps 100 2000 serves the full mix"
+                            if (args.serve_jobs < 64 or lo != 100 or hi != 2000) else "the full mix")}
 
 
 def main():
@@ -513,13 +564,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(cfg, 2, 0)
-        cpu = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"2 steps of the same scene on a {CPU_SAMPLE_N}^3 grid, FP64 oracle, one host thread "
-                         f"({dt:.1f} s)"}
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"2 steps of the same scene on a {CPU_SAMPLE_N}^3 grid (all bodies), FP64 oracle, "
+                         f"{host_cores()} host threads ({dt:.1f} s)"}
 
     extra = {}
     if world == 1 and not args.no_extra:
         for key, leg in (("plain_fp64", lambda: plain_fp64_leg(cfg, args, stream)),
+                         ("settling128", lambda: settling_leg(args, stream)),
                          ("batched", lambda: batched_leg(args, stream)), ("serving", lambda: serving_leg(args, stream))):
             try:
                 extra[key] = leg()

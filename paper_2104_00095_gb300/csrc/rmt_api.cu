@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
 #include <atomic>
 
 #include "rmt.h"
@@ -17,6 +18,19 @@
 
 static std::atomic<long> g_launches{0};
 void rmt_count_launches(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int sm_count() {
+  constexpr int MAXDEV = 64;
+  static std::atomic<int> cached[MAXDEV];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) dev = 0;
+  int n = cached[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cached[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 
 namespace {
 
@@ -86,13 +100,13 @@ struct rmt_grid {
   int par = 0;
   void *u = nullptr, *p = nullptr, *rho = nullptr, *rho_h = nullptr, *divn = nullptr, *divh = nullptr;
   void *adv = nullptr, *ustar = nullptr, *psi = nullptr;
-  void* ub[3][3] = {};
-  void* slopes[9] = {};
-  void* wcell[9] = {};
   void* xscr_s[9] = {};
   void* xscr_b[9] = {};
   int8_t* xscr_ok[3] = {};
   void* vadv[3] = {};
+  void* ub[3][3] = {};
+  void* slopes[9] = {};
+  void* wcell[9] = {};
   void* uf[3][3] = {};
   void* umac[3] = {};
   MGSolver* mac = nullptr;
@@ -135,7 +149,7 @@ struct rmt_grid {
 namespace {
 
 // launch width of the one-warp-per-band-cell fits: 4 resident blocks of 128 threads per SM
-constexpr int WLS_BLOCKS = 152 * 4;
+inline int wls_blocks() { return sm_count() * 4; }
 
 rmt_status fail(rmt_grid* g, rmt_status st, const char* fmt, ...) {
   if (g) {
@@ -302,7 +316,7 @@ __global__ void k_xi_in(Geo g, Body b, const double* __restrict__ in, T* __restr
 }
 inline int nbk(long n) {
   long b = (n + 255) / 256;
-  if (b > 152L * 32) b = 152L * 32;
+  if (b > (long)sm_count() * 32) b = (long)sm_count() * 32;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -345,7 +359,7 @@ rmt_status size_windows(rmt_grid* g) {
     }
     long blocks = (vol + 127) / 128;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152L * 64) blocks = 152L * 64;
+    if (blocks > (long)sm_count() * 64) blocks = (long)sm_count() * 64;
     b.blocks = (int)blocks;
   }
   return RMT_OK;
@@ -475,11 +489,11 @@ rmt_status init_t(rmt_grid* g) {
   }
   if ((st = build_views<T>(g)) != RMT_OK) return st;
   // SI "Initialization": u^0 = 0, p = 0, xi^0 = x, extrapolation, phi, rho^0
-  const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
+  const int full_blocks = (int)std::min((G.N + 127) / 128, (long)sm_count() * 64);
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
     launch_init_xi<T>(G, g->bodies[m], (T*)b.X[0], g->s);
-    CK(g, launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, WLS_BLOCKS,
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, wls_blocks(),
                                 (T*)b.X[0], (T*)b.PHI[0], b.LAY[0], g->err_d, g->s));
   }
   launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, g->bb_all, 12, (T*)g->rho, g->s);
@@ -565,9 +579,9 @@ rmt_status step_t(rmt_grid* g) {
     cudaStream_t bs = g->body_s[m];
     CK(g, cudaStreamWaitEvent(bs, g->ev_fork, 0));
     const int* bbc = b.bb + 6 * cur;
-    CK(g, launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, WLS_BLOCKS,
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, wls_blocks(),
                                 (T*)b.X[nxt], (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, bs));
-    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, WLS_BLOCKS, (const T*)b.X[cur], b.LAY[cur],
+    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, wls_blocks(), (const T*)b.X[cur], b.LAY[cur],
                         (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, bs);
     CK(g, cudaEventRecord(g->ev_join[m], bs));
   }
@@ -813,9 +827,9 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
   } else {
     BodyMem& b = g->bm[sid];
     k_xi_in<T><<<nbk(3 * G.N), 256, 0, s>>>(G, g->bodies[sid], g->stage, (T*)b.X[g->par]); rmt_count_launches(1);
-    const int full_blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
+    const int full_blocks = (int)std::min((G.N + 127) / 128, (long)sm_count() * 64);
     CK(g, launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count,
-                                WLS_BLOCKS, (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s));
+                                wls_blocks(), (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s));
     launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), g->bb_all + 6 * g->par, 12,
                       (T*)g->rho, s);
   }

@@ -3,7 +3,7 @@
 // A batch advances many independent simulations with one CUDA-graph launch per step: the
 // step of every member is captured on its own branch stream, the branches are joined into one
 // graph, and the instantiated graph is replayed.  Kernels of different members overlap on the
-// GPU, which is what lets many small grids fill 152 SMs.  The reference-map buffers of a grid
+// GPU, which is what lets many small grids fill the GPU's SMs.  The reference-map buffers of a grid
 // alternate between two parities, so a batch keeps two graphs (even and odd steps) per
 // membership.
 //

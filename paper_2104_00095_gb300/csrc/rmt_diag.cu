@@ -13,7 +13,7 @@
 namespace {
 
 constexpr int DTPB = 256;
-constexpr int DBLOCKS = 152 * 4;
+constexpr int DBLOCKS = 608;  // fixed width: the same summation order on every GPU
 constexpr int NS = 8;  // partial sums per block
 
 template <typename T>

@@ -15,7 +15,7 @@ namespace {
 constexpr int TPB = 128;
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
-  if (b > 152L * 128) b = 152L * 128;
+  if (b > (long)sm_count() * 128) b = (long)sm_count() * 128;
   return (int)(b < 1 ? 1 : b);
 }
 

@@ -5,6 +5,10 @@
 
 #include "rmt_common.cuh"
 
+// streaming multiprocessors of the current device (its attribute, read once per device); launch
+// widths are multiples of it
+int sm_count();
+
 // A multigrid right-hand side or solution as the step kernels see it.  FP64 mode: the FP64
 // array d.  FP32 mode: two-float pairs, value = h + l (d is null), so that no FP64 arithmetic
 // runs in the FP32 step.

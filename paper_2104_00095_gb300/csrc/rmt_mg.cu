@@ -42,7 +42,7 @@ constexpr int BX = 32, BYMAX = 8;
 
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
-  if (b > 152L * 32) b = 152L * 32;
+  if (b > (long)sm_count() * 32) b = (long)sm_count() * 32;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -1611,8 +1611,8 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
     if (e == cudaSuccess && kind == 0 && prec_fp32) {
       // levels that take the fused sweep: rows of whole 16-byte chunks and even periodic sides (a
       // consistent two-colouring across the wrap); z-chunks sized to the blocks resident at once
-      int dev = 0, nsm = 152, per_sm = 0;
-      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int nsm = sm_count();
+      int per_sm = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_sweep<true>, GT, SWEEP_SMEM) != cudaSuccess ||
           per_sm < 1)
         per_sm = 1;
@@ -1716,7 +1716,7 @@ inline dim3 fe_grid(const Lv& L) {
   // blocks per SM march concurrently (a block's planes follow one another)
   const int tx = (L.nn[0] + FX - 1) / FX, ty = (L.nn[1] + FY - 1) / FY;
   int nch = (L.nn[2] + FZ - 1) / FZ;
-  const int want = (2 * 152 + tx * ty - 1) / (tx * ty);
+  const int want = (2 * sm_count() + tx * ty - 1) / (tx * ty);
   if (want > nch) nch = want < L.nn[2] ? want : L.nn[2];
   const int fz = (L.nn[2] + nch - 1) / nch;
   return dim3(tx, ty, (L.nn[2] + fz - 1) / fz);

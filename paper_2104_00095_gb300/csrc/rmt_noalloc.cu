@@ -105,8 +105,9 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   e = cudaMemsetAsync(scr + SCR_ERR, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(xi_out, xi_in, 3 * G.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return RMT_ECUDA;
-  const int blocks = (int)((G.N + 127) / 128 < 152L * 64 ? (G.N + 127) / 128 : 152L * 64);
-  e = launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, 152 * 4,
+  const long wide = (long)sm_count() * 64;
+  const int blocks = (int)((G.N + 127) / 128 < wide ? (G.N + 127) / 128 : wide);
+  e = launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, sm_count() * 4,
                                  xi_out, phi_out, (int8_t*)layer_out, scr + SCR_ERR, st);
   int nbad = 0;
   if (e == cudaSuccess) e = cudaGetLastError();

@@ -16,7 +16,7 @@ constexpr int TPB = 256;
 
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
-  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  if (b > (long)sm_count() * 64) b = (long)sm_count() * 64;  // grid-stride beyond 64 blocks per SM
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -330,7 +330,7 @@ cudaError_t launch_stress_div(const Geo& g, const T* u, const Body* bodies, cons
   k_stress_fluid<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, views, nb, bbs, bstride, out, list, count);
   rmt_count_launches(1);
   if (nb == 0) return cudaSuccess;
-  k_stress_band<T><<<152 * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, out);
+  k_stress_band<T><<<sm_count() * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, out);
   rmt_count_launches(1);
   return cudaSuccess;
 }

@@ -16,7 +16,7 @@ constexpr int TPB = 256;
 
 inline int nblocks(long n) {
   long b = (n + TPB - 1) / TPB;
-  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  if (b > (long)sm_count() * 64) b = (long)sm_count() * 64;  // grid-stride beyond 64 blocks per SM
   return (int)(b < 1 ? 1 : b);
 }
 
