@@ -302,7 +302,7 @@ def batched_leg(args, stream) -> dict:
             tuned[n] = g.autotune(1e-6)
     tune_s = time.perf_counter() - t0
     keys = ("mac_pre", "mac_post", "mac_inner", "mac_block", "mac_cycles", "fe_pre", "fe_post", "fe_inner",
-            "fe_block", "fe_omega", "fe_cycles")
+            "fe_block", "fe_omega", "fe_cycles", "mac_zchunk", "fe_zchunk")
     for g, sc in zip(grids, scenes):
         for k in keys:
             g.set_option(k, tuned[sc["n"][0]][k])
@@ -538,6 +538,14 @@ def main():
                     "bytes_per_launch": byt, "launches": nl, "avg_launch_ms": per,
                     "share_of_step": tot / prof_ms, "profiled_ms_per_step": prof_ms / args.steps}
     stages = {p[0]: round(p[1] / args.steps, 4) for p in prof if p[1] > 0}
+    # the whole step against the same peak, by the algorithmic byte model of one cell-step: 55 words
+    # for the stages outside the projections plus 24 per V-cycle (six finest-level passes over x,
+    # b and rho and one write), k_MAC + k_FE cycles, and 1/7 more for the coarse levels
+    word = 4 if cfg["precision"] == "fp32" else 8
+    model_words = 55 + 24 * (args.mg_cycles_mac + args.mg_cycles_fe) * 8.0 / 7.0
+    step_achieved = model_words * word * N / (ms / args.steps / 1e3) / 1e9
+    step_roofline = {"model_bytes_per_cell_step": model_words * word, "achieved": step_achieved, "peak": peak,
+                     "unit": "GB/s", "frac": step_achieved / peak, "peak_source": peak_kind}
 
     # end to end through the C ABI with host buffers: every step uploads u from pinned host
     # memory, advances one step and reads u back
@@ -593,7 +601,8 @@ def main():
                            "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
-                "gpu_launches": launches, "gpu_launches_before_timed": l0, "clocks": clocks, "roofline": roofline, "stages_ms_per_step": stages,
+                "gpu_launches": launches, "gpu_launches_before_timed": l0, "clocks": clocks, "roofline": roofline,
+                "step_roofline": step_roofline, "stages_ms_per_step": stages,
                 "e2e": e2e, "cpu_baseline": cpu}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -156,7 +156,9 @@ double rmt_dt(rmt_grid* g);
  * default 1), "mac_block", "fe_block" (rows of 32 threads per block of the multigrid level
  * kernels: 1, 2, 4 or 8, default 4), "mac_cycles", "fe_cycles" (replace the descriptor's
  * mg_fixed_cycles / mg_fixed_cycles_fe), "mac_warm", "fe_warm" (nonzero: each solve starts from the
- * previous step's solution instead of zero; default 0), "mac_coarse_pre", "mac_coarse_post",
+ * previous step's solution instead of zero; default 0), "mac_zchunk", "fe_zchunk" (planes a block
+ * of the finest level's fused red-black sweep / FE tiles marches; 0, the default, picks the
+ * length that fills whole waves of resident blocks), "mac_coarse_pre", "mac_coarse_post",
  * "fe_coarse_pre", "fe_coarse_post" (sweeps on the levels below the finest, 0..16; default: the
  * finest level's), "mac_sweep" (FP32 grids: 1, the default, runs each red-black sweep of a
  * level with n_x % 4 == 0, even periodic sides, n_x >= 64 and at least 2^20 cells as one fused
@@ -204,9 +206,11 @@ rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]);
  * 0.9, 1.0) and 1, 2 or 4 V-cycles per high-precision residual: for each, it counts the V-cycles
  * needed to reach the relative residual rtol and times that many with CUDA events.  It then
  * times the block height of the level kernels (1, 2, 4, 8 rows of 32 threads) for the fastest
- * schedule.  The winners are applied with rmt_set_option, including the cycle counts
- * ("mac_cycles", "fe_cycles"), so that later steps run fixed-cycle without host
- * synchronisation.  The solvers' solution buffers are overwritten (fields MAC_Q and PSI read
+ * schedule, and the z-chunk length of the finest level's plane-marching stencil tiles (the fused
+ * red-black sweep, the FE tiles: the wave-filling default, 8, 16, 32, 64, 128 planes).  The
+ * winners are applied with rmt_set_option, including the cycle counts ("mac_cycles",
+ * "fe_cycles") and the chunks ("mac_zchunk", "fe_zchunk"), so that later steps run fixed-cycle
+ * without host synchronisation.  The solvers' solution buffers are overwritten (fields MAC_Q and PSI read
  * afterwards show a tuning solve); the simulation state is not changed.  Synchronous.
  * Errors: RMT_EINVAL (rtol outside (0,1)), RMT_ESTATE, RMT_ENOCONVERGE (no schedule reached rtol
  * within 40 cycles), RMT_ECUDA. */
@@ -216,6 +220,7 @@ typedef struct {
   double fe_omega;
   double mac_ms, fe_ms; /* time of one solve with the chosen settings */
   int trials;           /* schedules and shapes tried */
+  int mac_zchunk, fe_zchunk; /* z-chunk of the finest level's plane-marching tiles (0: default) */
 } rmt_tune_result;
 rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* out);
 

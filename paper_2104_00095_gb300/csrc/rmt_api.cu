@@ -130,6 +130,7 @@ struct rmt_grid {
   int mac_block = 4, fe_block = 4;  // block height of the multigrid level kernels
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
   int mac_sweep = 1;                // fused red-black sweeps (FP32 MAC)
+  int mac_zchunk = 0, fe_zchunk = 0;  // finest-level stencil tile z-chunks (0: heuristic)
   double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
@@ -456,6 +457,8 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_warm(g->mac, g->mac_warm);
   mg_set_sweep(g->mac, g->mac_sweep);
   mg_set_warm(g->fe, g->fe_warm);
+  mg_set_zchunk(g->mac, g->mac_zchunk);
+  mg_set_zchunk(g->fe, g->fe_zchunk);
   mg_set_nonfinite_flag(g->mac, g->err_d + 2);
   mg_set_nonfinite_flag(g->fe, g->err_d + 2);
   g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
@@ -1168,6 +1171,9 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
   } else if (!strcmp(name, "fe_omega") || !strcmp(name, "mac_omega")) {
     if (!(value > 0.0 && value < 2.0)) return fail(g, RMT_EINVAL, "%s out of range", name);
     (name[0] == 'f' ? g->fe_omega : g->mac_omega) = value;
+  } else if (!strcmp(name, "mac_zchunk") || !strcmp(name, "fe_zchunk")) {
+    if (value < 0 || value > 65536) return fail(g, RMT_EINVAL, "%s out of range", name);
+    (name[0] == 'm' ? g->mac_zchunk : g->fe_zchunk) = (int)value;
   } else if (!strcmp(name, "graph")) {
     g->use_graph = value != 0.0;
   } else if (!strcmp(name, "inject_nan_step")) {
@@ -1191,6 +1197,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     mg_set_warm(g->mac, g->mac_warm);
     mg_set_sweep(g->mac, g->mac_sweep);
     mg_set_warm(g->fe, g->fe_warm);
+    mg_set_zchunk(g->mac, g->mac_zchunk);
+    mg_set_zchunk(g->fe, g->fe_zchunk);
   }
   return RMT_OK;
 }

@@ -130,6 +130,11 @@ void mg_set_warm(MGSolver* m, int warm);
 // device int set to 1 when a solve's right-hand-side mean, solution mean or residual norm is
 // not finite (null: not checked)
 void mg_set_nonfinite_flag(MGSolver* m, int* flag);
+// z-chunk length (planes a block marches) of the finest level's stencil tiles: the fused
+// red-black sweep (MAC; ignored where the level does not take it) or the FE tile kernels;
+// 0 restores the wave-filling heuristic.  mg_zchunk returns the length in use.
+void mg_set_zchunk(MGSolver* m, int zchunk);
+int mg_zchunk(const MGSolver* m);
 // MAC in FP32: one fused red-black pass per sweep (1: on the large levels that allow it, the
 // default; 2: on every level that allows it; 0: never), else one pass per colour
 void mg_set_sweep(MGSolver* m, int fused);

@@ -1465,6 +1465,8 @@ struct MGSolver {
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
   int* nonfinite = nullptr;  // device flag set when a mean or norm of a solve is not finite
+  int zc0_auto = 0;          // z-chunk of the finest level's fused sweep from the wave heuristic
+  int fe_zc0 = 0;            // z-chunk of the finest level's FE tiles (0: the heuristic)
   size_t bytes = 0;          // device bytes requested
 };
 
@@ -1622,6 +1624,7 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
         for (int d = 0; d < 3; d++)
           if (Q.per[d] && (Q.n[d] & 1)) ok = false;
         m->zc[l] = ok ? sweep_chunk(Q, per_sm * nsm) : 0;
+        if (l == 0) m->zc0_auto = m->zc[0];
         m->big[l] = Q.n[0] >= 64 && Q.ncell >= (1L << 20);
       }
     }
@@ -1711,13 +1714,15 @@ template <typename T>
 inline bool fe_vec(const Lv& L) {
   return sizeof(T) == 4 && L.per[0] && L.n[0] % 4 == 0;
 }
-inline dim3 fe_grid(const Lv& L) {
+inline dim3 fe_grid(const Lv& L, int zchunk = 0) {
   // z-chunks of FZ planes, or more and shorter chunks on small levels, so that at least two
-  // blocks per SM march concurrently (a block's planes follow one another)
+  // blocks per SM march concurrently (a block's planes follow one another); zchunk > 0 sets the
+  // chunk length instead (the autotuner's choice); the kernel takes its chunk from the grid
   const int tx = (L.nn[0] + FX - 1) / FX, ty = (L.nn[1] + FY - 1) / FY;
   int nch = (L.nn[2] + FZ - 1) / FZ;
   const int want = (2 * sm_count() + tx * ty - 1) / (tx * ty);
   if (want > nch) nch = want < L.nn[2] ? want : L.nn[2];
+  if (zchunk > 0) nch = (L.nn[2] + zchunk - 1) / zchunk;
   const int fz = (L.nn[2] + nch - 1) / nch;
   return dim3(tx, ty, (L.nn[2] + fz - 1) / fz);
 }
@@ -1758,12 +1763,13 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
       }
     } else {
       hk(m, l, 0, 1, s);
+      const dim3 fg = fe_grid(L, l == 0 ? m->fe_zc0 : 0);
       if (fe_vec<T>(L))
-        k_fe_tile<float, 0, true><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, (float)m->omega, (const float*)m->x[l],
+        k_fe_tile<float, 0, true><<<fg, dim3(FX, FY), 0, s>>>(L, (float)m->omega, (const float*)m->x[l],
                                                                       (float*)m->xt[l], (const float*)b,
                                                                       (const float*)rho);
       else
-        k_fe_tile<T, 0><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(m->omega), (const T*)m->x[l], (T*)m->xt[l], b, rho);
+        k_fe_tile<T, 0><<<fg, dim3(FX, FY), 0, s>>>(L, T(m->omega), (const T*)m->x[l], (T*)m->xt[l], b, rho);
       rmt_count_launches(1);
       hk(m, l, 0, 0, s);
       void* t = m->x[l];
@@ -1802,11 +1808,12 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
         L, C, (const T*)m->x[l], (const T*)m->b[l], (const T*)m->rho[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
     rmt_count_launches(1);
   } else {
+    const dim3 fg = fe_grid(L, l == 0 ? m->fe_zc0 : 0);
     if (fe_vec<T>(L))
-      k_fe_tile<float, 1, true><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, 0.f, (const float*)m->x[l], (float*)m->r[l],
+      k_fe_tile<float, 1, true><<<fg, dim3(FX, FY), 0, s>>>(L, 0.f, (const float*)m->x[l], (float*)m->r[l],
                                                                     (const float*)m->b[l], (const float*)m->rho[l]);
     else
-      k_fe_tile<T, 1><<<fe_grid(L), dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
+      k_fe_tile<T, 1><<<fg, dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
                                                          (const T*)m->rho[l]);
     rmt_count_launches(1);
     k_restrict<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(
@@ -1953,6 +1960,26 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
 }
 
 }  // namespace
+
+// does the finest MAC level run the fused red-black sweep?
+static bool mac_fused0(const MGSolver* m) {
+  return m->fp32 && m->zc[0] > 0 && (m->sweep == 2 || (m->sweep == 1 && m->big[0]));
+}
+void mg_set_zchunk(MGSolver* m, int zchunk) {
+  const Lv& L = m->lv[0];
+  if (m->kind == 0) {
+    if (!mac_fused0(m)) return;  // the finest level does not take the fused sweep
+    m->zc[0] = zchunk > 0 ? (zchunk < L.n[2] ? zchunk : L.n[2]) : m->zc0_auto;
+  } else {
+    m->fe_zc0 = zchunk > 0 ? (zchunk < L.nn[2] ? zchunk : L.nn[2]) : 0;
+  }
+}
+int mg_zchunk(const MGSolver* m) {
+  if (m->kind == 0) return mac_fused0(m) ? m->zc[0] : 0;
+  const Lv& L = m->lv[0];
+  const dim3 g = fe_grid(L, m->fe_zc0);
+  return (L.nn[2] + (int)g.z - 1) / (int)g.z;
+}
 
 int mg_solve(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStream_t s, cudaError_t* err) {
   cudaError_t e = cudaSuccess;

@@ -1,12 +1,15 @@
-// Autotuner of the two multigrid solves (smoother schedule, cycle count, kernel block shape).
+// Autotuner of the two multigrid solves (smoother schedule, cycle count, kernel block shapes
+// and the z-extent of the finest level's stencil tiles).
 //
 // For each solver it tries the smoother schedules of a small grid (sweeps before / after the
 // coarse correction, Jacobi weight for the nodal solve, 1, 2 or 4 V-cycles per high-precision
 // residual) on the right-hand side of the grid's last step: it counts the V-cycles a schedule
 // needs to reach the requested relative residual, times that many cycles with CUDA events, and
-// keeps the fastest.  Then it times the block heights of the level kernels with that schedule.  The
-// winner becomes the grid's fixed-cycle configuration (rmt_set_option), so later steps take no
-// host synchronisation.
+// keeps the fastest.  Then it times the block heights of the level kernels with that schedule,
+// and the z-chunk length (planes one block marches) of the finest level's plane-marching tiles
+// (the fused red-black sweep, the FE Jacobi / residual tiles): the wave-filling default against
+// 8, 16, 32, 64 and 128 planes.  The winner becomes the grid's fixed-cycle configuration
+// (rmt_set_option), so later steps take no host synchronisation.
 #include <cstdio>
 
 #include "rmt.h"
@@ -43,7 +46,7 @@ void apply(MGSolver* m, const Sched& c) {
 
 // best schedule of one solver: returns its cycles (-1: nothing converged), fills best and ms
 int tune_one(MGSolver* m, int kind, double rtol, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, Sched& best,
-             double& best_ms, int& trials) {
+             double& best_ms, int& trials, int& zchunk) {
   const int nsw = kind == 0 ? 4 : 3;
   const double omegas_fe[3] = {0.8, 0.9, 1.0};
   const int nom = kind == 0 ? 1 : 3;
@@ -79,6 +82,22 @@ int tune_one(MGSolver* m, int kind, double rtol, cudaStream_t s, cudaEvent_t a, 
     }
   }
   apply(m, best);
+  // z-chunk of the finest level's tiles (0: the wave-filling default)
+  zchunk = 0;
+  mg_set_zchunk(m, 0);
+  const int def = mg_zchunk(m);
+  for (int zc : {8, 16, 32, 64, 128}) {
+    if (zc == def) continue;
+    mg_set_zchunk(m, zc);
+    if (mg_zchunk(m) != zc) continue;  // the level is shorter, or takes no plane-marching tile
+    const double ms = time_solve(m, best_cyc, s, a, b);
+    trials++;
+    if (ms > 0 && ms < best_ms) {
+      best_ms = ms;
+      zchunk = zc;
+    }
+  }
+  mg_set_zchunk(m, zchunk);
   return best_cyc;
 }
 
@@ -98,9 +117,9 @@ extern "C" rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* ou
   }
   Sched bm{}, bf{};
   double ms_mac = 0, ms_fe = 0;
-  int trials = 0;
-  const int cm = tune_one(mac, 0, rtol, s, a, b, bm, ms_mac, trials);
-  const int cf = tune_one(fe, 1, rtol, s, a, b, bf, ms_fe, trials);
+  int trials = 0, zm = 0, zf = 0;
+  const int cm = tune_one(mac, 0, rtol, s, a, b, bm, ms_mac, trials, zm);
+  const int cf = tune_one(fe, 1, rtol, s, a, b, bf, ms_fe, trials, zf);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (cm < 0 || cf < 0) return grid_fail(g, RMT_ENOCONVERGE, "autotune: no schedule reached the tolerance");
@@ -111,7 +130,8 @@ extern "C" rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* ou
   } opts[] = {{"mac_pre", (double)bm.pre}, {"mac_post", (double)bm.post}, {"mac_inner", (double)bm.inner},
               {"mac_block", (double)bm.block}, {"mac_cycles", (double)cm}, {"fe_pre", (double)bf.pre},
               {"fe_post", (double)bf.post}, {"fe_inner", (double)bf.inner}, {"fe_block", (double)bf.block},
-              {"fe_omega", bf.omega}, {"fe_cycles", (double)cf}};
+              {"fe_omega", bf.omega}, {"fe_cycles", (double)cf}, {"mac_zchunk", (double)zm},
+              {"fe_zchunk", (double)zf}};
   for (const auto& o : opts)
     if ((st = rmt_set_option(g, o.name, o.v)) != RMT_OK) return st;
   if (out) {
@@ -129,6 +149,8 @@ extern "C" rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* ou
     out->fe_omega = bf.omega;
     out->fe_ms = ms_fe;
     out->trials = trials;
+    out->mac_zchunk = zm;
+    out->fe_zchunk = zf;
   }
   return RMT_OK;
 }

@@ -143,8 +143,8 @@ def test_autotune_picks_a_schedule_that_meets_the_tolerance():
     # the tuned grid now steps fixed-cycle; the same options set by hand give the same result
     twin = rmt.Grid(sc)
     twin.step(1)
-    for k in ("mac_pre", "mac_post", "mac_inner", "mac_block", "mac_cycles", "fe_pre", "fe_post", "fe_inner",
-              "fe_block", "fe_omega", "fe_cycles"):
+    for k in ("mac_pre", "mac_post", "mac_inner", "mac_block", "mac_cycles", "mac_zchunk", "fe_zchunk", "fe_pre",
+              "fe_post", "fe_inner", "fe_block", "fe_omega", "fe_cycles"):
         twin.set_option(k, r[k])
     g.step(2)
     twin.step(2)
@@ -154,3 +154,23 @@ def test_autotune_picks_a_schedule_that_meets_the_tolerance():
     div = (np.diff(um[0].reshape(n, n, n + 1), axis=2) + np.diff(um[1].reshape(n, n + 1, n), axis=1) +
            np.diff(um[2].reshape(n + 1, n, n), axis=0)) * n
     assert np.max(np.abs(div)) <= 1e-4 * max(np.abs(u).max() for u in um) * n
+
+
+def test_tile_z_chunks_do_not_change_the_result():
+    """The z-chunk length of the plane-marching tiles (fused red-black sweep, FE tiles) only
+    changes how the planes are split among blocks: a block recomputes the first-colour ring of its
+    chunk's lower boundary with the same arithmetic, so every chunking gives the same bits."""
+    sc = S.swimmers(n=128, nbodies=2, seed=7, precision="fp32")
+
+    def run(mz, fz):
+        g = rmt.Grid(dict(sc, mg_fixed_cycles=4, mg_fixed_cycles_fe=4,
+                          options={"graph": 1, "mac_sweep": 2, "mac_zchunk": mz, "fe_zchunk": fz}))
+        g.step(2)
+        out = [g.read(f) for f in (rmt.RMT_F_U, rmt.RMT_F_P)]
+        g.close()
+        return out
+
+    ref = run(0, 0)
+    for mz, fz in ((16, 8), (48, 64)):
+        for a, b in zip(run(mz, fz), ref):
+            assert np.array_equal(a, b)
