@@ -233,8 +233,9 @@ def timed_steps(g, steps: int, stream) -> float:
 
 def solver_options(args, graph: bool = True) -> dict:
     """The multigrid schedule of the timed configuration (rmt_set_option names)."""
-    o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm,
-         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse}
+    o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm, "fe_warm": args.fe_warm,
+         "mac_pre": args.mac_sweeps, "mac_post": args.mac_sweeps,
+         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse, "mg_tail": args.mg_tail}
     if graph:
         o["graph"] = args.graph
     return o
@@ -432,17 +433,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="swimmers256", choices=sorted(CONFIGS))
     ap.add_argument("--mg-cycles-mac", type=int, default=5,
-                    help="V-cycles per MAC solve (fixed, no host sync; 5 reach the 1e-6 relative residual)")
+                    help="V-cycles per MAC solve (fixed, no host sync; 5 keep the MAC velocities divergence-free "
+                         "to 1e-4 of their scale from the first step)")
     ap.add_argument("--mg-cycles-fe", type=int, default=4,
-                    help="V-cycles per FE solve (fixed; 4 reach 1e-6 relative residual)")
+                    help="V-cycles per FE solve (fixed)")
     ap.add_argument("--mac-inner", type=int, default=5,
-                    help="MAC V-cycles per high-precision residual (5: one residual, the first, per solve)")
-    ap.add_argument("--fe-inner", type=int, default=2,
+                    help="MAC V-cycles per high-precision residual (at least the cycle count: one residual, the "
+                         "first, per solve)")
+    ap.add_argument("--fe-inner", type=int, default=4,
                     help="FE V-cycles per high-precision residual (mixed-precision refinement)")
     ap.add_argument("--mac-warm", type=int, default=0, help="warm-start the MAC solve from the last step")
+    ap.add_argument("--fe-warm", type=int, default=0, help="warm-start the FE solve from the last step")
+    ap.add_argument("--mac-sweeps", type=int, default=3,
+                    help="red-black sweeps before and after the coarse correction on the finest MAC level")
     ap.add_argument("--mac-coarse", type=int, default=2,
                     help="red-black sweeps before and after the coarse correction on the MAC levels below the finest")
     ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
+    ap.add_argument("--mg-tail", type=int, default=0,
+                    help="run the multigrid levels below 40000 unknowns as one cluster launch per V-cycle")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
     ap.add_argument("--n", type=int, default=None,
@@ -596,8 +604,10 @@ def main():
                            "bodies": len(scene["solids"]),
                            "mg_cycles_per_solve": {"mac": args.mg_cycles_mac, "fe": args.mg_cycles_fe,
                                                    "mac_inner": args.mac_inner, "fe_inner": args.fe_inner,
-                                                   "mac_coarse_sweeps": args.mac_coarse,
-                                                   "mac_warm_start": bool(args.mac_warm)},
+                                                   "mac_sweeps": args.mac_sweeps, "mac_coarse_sweeps": args.mac_coarse,
+                                                   "mac_warm_start": bool(args.mac_warm),
+                                                   "fe_warm_start": bool(args.fe_warm),
+                                                   "coarse_tail_launch": bool(args.mg_tail)},
                            "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},

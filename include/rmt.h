@@ -156,14 +156,20 @@ double rmt_dt(rmt_grid* g);
  * default 1), "mac_block", "fe_block" (rows of 32 threads per block of the multigrid level
  * kernels: 1, 2, 4 or 8, default 4), "mac_cycles", "fe_cycles" (replace the descriptor's
  * mg_fixed_cycles / mg_fixed_cycles_fe), "mac_warm", "fe_warm" (nonzero: each solve starts from the
- * previous step's solution instead of zero; default 0), "mac_zchunk", "fe_zchunk" (planes a block
+ * previous step's solution instead of zero; default 0; both projections solve for increments of
+ * the pressure, which change quickly while the flow starts up, so this helps only once they vary
+ * slowly from step to step), "mac_zchunk", "fe_zchunk" (planes a block
  * of the finest level's fused red-black sweep / FE tiles marches; 0, the default, picks the
  * length that fills whole waves of resident blocks), "mac_coarse_pre", "mac_coarse_post",
  * "fe_coarse_pre", "fe_coarse_post" (sweeps on the levels below the finest, 0..16; default: the
  * finest level's), "mac_sweep" (FP32 grids: 1, the default, runs each red-black sweep of a
  * level with n_x % 4 == 0, even periodic sides, n_x >= 64 and at least 2^20 cells as one fused
  * pass over both colours; 2 does so on every level with n_x % 4 == 0 and even periodic sides; 0
- * runs one pass per colour everywhere; all give the same sweep), "graph" (nonzero: with fixed
+ * runs one pass per colour everywhere; all give the same sweep), "mg_tail" (nonzero: the levels
+ * of each V-cycle with at most 40000 unknowns, from the first of them below the finest level
+ * down to the coarsest and back, run as one launch of a thread-block cluster, MAC levels there
+ * smoothed by one pass per colour; 0, the default, launches them level by level; both compute
+ * the same V-cycle), "graph" (nonzero: with fixed
  * cycle counts, rmt_step replays a captured CUDA graph of the step instead of launching its
  * kernels one by one; the results are the same).  Cycle counts (mg_fixed_cycles,
  * rmt_last_cycles) count V-cycles.

@@ -38,7 +38,8 @@ struct BodyMem {
   int* bb = nullptr;  // band bounding boxes of the two parities (2 x 6 ints, device)
   int blocks = 1;     // launch width of the body's window kernels
   int* list = nullptr;   // compacted band cells of the current step (capacity N)
-  int* count = nullptr;  // its length (device)
+  int* count = nullptr;  // per-layer counts of the list and the redo lists' lengths (device)
+  int* redo = nullptr;   // FP32: cells whose fits are redone in FP64 (device)
   void* X[2] = {nullptr, nullptr};
   void* PHI[2] = {nullptr, nullptr};
   int8_t* LAY[2] = {nullptr, nullptr};
@@ -131,6 +132,7 @@ struct rmt_grid {
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
   int mac_sweep = 1;                // fused red-black sweeps (FP32 MAC)
   int mac_zchunk = 0, fe_zchunk = 0;  // finest-level stencil tile z-chunks (0: heuristic)
+  int mg_tail = 0;                    // coarse levels of a V-cycle in one cluster launch
   double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
@@ -415,7 +417,8 @@ rmt_status alloc_t(rmt_grid* g) {
     AL(b.PHIH, N * e);
     b.bb = nullptr;  // set below: all bodies' boxes are contiguous
     AL(b.list, N * sizeof(int));
-    AL(b.count, 16);
+    AL(b.count, BAND_COUNTERS * sizeof(int));
+    if (e == 4) AL(b.redo, N * sizeof(int));
   }
   AL(g->bb_all, (nb > 0 ? nb : 1) * 12 * sizeof(int));
   AL(g->slist, (nb > 0 ? N : 1) * sizeof(int));
@@ -459,6 +462,8 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_warm(g->fe, g->fe_warm);
   mg_set_zchunk(g->mac, g->mac_zchunk);
   mg_set_zchunk(g->fe, g->fe_zchunk);
+  mg_set_tail(g->mac, g->mg_tail);
+  mg_set_tail(g->fe, g->mg_tail);
   mg_set_nonfinite_flag(g->mac, g->err_d + 2);
   mg_set_nonfinite_flag(g->fe, g->err_d + 2);
   g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
@@ -496,7 +501,7 @@ rmt_status init_t(rmt_grid* g) {
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
     launch_init_xi<T>(G, g->bodies[m], (T*)b.X[0], g->s);
-    CK(g, launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, wls_blocks(),
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], nullptr, b.bb, full_blocks, b.list, b.count, b.redo, wls_blocks(),
                                 (T*)b.X[0], (T*)b.PHI[0], b.LAY[0], g->err_d, g->s));
   }
   launch_density<T>(G, g->bodies_d, views<T>(g, 0, 0), nb, g->bb_all, 12, (T*)g->rho, g->s);
@@ -582,9 +587,9 @@ rmt_status step_t(rmt_grid* g) {
     cudaStream_t bs = g->body_s[m];
     CK(g, cudaStreamWaitEvent(bs, g->ev_fork, 0));
     const int* bbc = b.bb + 6 * cur;
-    CK(g, launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, wls_blocks(),
+    CK(g, launch_extrapolate<T>(G, g->bodies[m], bbc, b.bb + 6 * nxt, b.blocks, b.list, b.count, b.redo, wls_blocks(),
                                 (T*)b.X[nxt], (T*)b.PHI[nxt], b.LAY[nxt], g->err_d, bs));
-    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, wls_blocks(), (const T*)b.X[cur], b.LAY[cur],
+    launch_corrector<T>(G, g->bodies[m], bbc, b.blocks, b.list, b.count, b.redo, wls_blocks(), (const T*)b.X[cur], b.LAY[cur],
                         (const T*)b.X[nxt], b.LAY[nxt], (T*)b.XH, (T*)b.PHIH, g->err_d, bs);
     CK(g, cudaEventRecord(g->ev_join[m], bs));
   }
@@ -831,7 +836,7 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
     BodyMem& b = g->bm[sid];
     k_xi_in<T><<<nbk(3 * G.N), 256, 0, s>>>(G, g->bodies[sid], g->stage, (T*)b.X[g->par]); rmt_count_launches(1);
     const int full_blocks = (int)std::min((G.N + 127) / 128, (long)sm_count() * 64);
-    CK(g, launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count,
+    CK(g, launch_extrapolate<T>(G, g->bodies[sid], nullptr, b.bb + 6 * g->par, full_blocks, b.list, b.count, b.redo,
                                 wls_blocks(), (T*)b.X[g->par], (T*)b.PHI[g->par], b.LAY[g->par], g->err_d, s));
     launch_density<T>(G, g->bodies_d, views<T>(g, g->par, 0), (int)g->bodies.size(), g->bb_all + 6 * g->par, 12,
                       (T*)g->rho, s);
@@ -1176,6 +1181,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     (name[0] == 'm' ? g->mac_zchunk : g->fe_zchunk) = (int)value;
   } else if (!strcmp(name, "graph")) {
     g->use_graph = value != 0.0;
+  } else if (!strcmp(name, "mg_tail")) {
+    g->mg_tail = value != 0.0;
   } else if (!strcmp(name, "inject_nan_step")) {
     g->inject_nan_step = value < 0 ? -1 : (long)value;
   } else if (!strcmp(name, "inject_alloc")) {
@@ -1199,6 +1206,8 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     mg_set_warm(g->fe, g->fe_warm);
     mg_set_zchunk(g->mac, g->mac_zchunk);
     mg_set_zchunk(g->fe, g->fe_zchunk);
+    mg_set_tail(g->mac, g->mg_tail);
+    mg_set_tail(g->fe, g->mg_tail);
   }
   return RMT_OK;
 }

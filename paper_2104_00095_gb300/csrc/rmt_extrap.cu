@@ -8,6 +8,8 @@
 // are degenerate, which weights are positive) are reproducible.  FP64 storage fits in FP64;
 // FP32 storage holds displacements S = xi - x0 (rmt_common.cuh) and fits them in FP32, redone
 // in FP64 when ill-conditioned.
+#include <type_traits>
+
 #include "rmt_kernels.h"
 
 namespace {
@@ -62,10 +64,21 @@ __global__ void k_classify(Geo g, Body b, const int* __restrict__ bb, const T* _
   }
 }
 
-// unmarked face neighbours of layer l-1 become layer l (walls stop, periodic axes wrap);
-// in place is race-free: only -1 -> l writes, and only l-1 is tested
-__global__ void k_bfs(Geo g, const int* __restrict__ bb, int l, int8_t* __restrict__ lay) {
+// The band list is sorted by layer: cnt[l] (l = 1..L) counts the cells of layer l, and they sit
+// at list[base_l ...], base_l = cnt[1] + ... + cnt[l-1] (the earlier passes have finished).
+__device__ __forceinline__ int layer_base(const int* __restrict__ cnt, int l) {
+  int b = 0;
+  for (int q = 1; q < l; q++) b += cnt[q];
+  return b;
+}
+
+// unmarked face neighbours of layer l-1 become layer l (walls stop, periodic axes wrap) and are
+// appended to layer l's segment of the band list; in place is race-free: only -1 -> l writes,
+// and only l-1 is tested
+__global__ void k_bfs(Geo g, const int* __restrict__ bb, int l, int8_t* __restrict__ lay, int* __restrict__ list,
+                      int* __restrict__ cnt) {
   const Win w = make_win(g, bb, 2);
+  const int base = layer_base(cnt, l);
   WIN_LOOP(t, w) {
     int u[3], i, j, k;
     long c;
@@ -77,6 +90,7 @@ __global__ void k_bfs(Geo g, const int* __restrict__ bb, int l, int8_t* __restri
       if (!cell_at(g, i + off[f][0], j + off[f][1], k + off[f][2], nb)) continue;
       if (lay[nb] == l - 1) {
         lay[c] = (int8_t)l;
+        list[base + atomicAdd(&cnt[l], 1)] = (int)c;
         break;
       }
     }
@@ -121,6 +135,49 @@ __device__ bool solve4(AT A[4][4], AT B[4][3], AT X[4][3], AT tolfac) {
   return true;
 }
 
+// The candidate cells of the radius-2 search box around one cell, loaded once per cell for
+// every fit that uses that box (the kernel-only fit, the normal-weighted fit and an FP64 redo):
+// lane L holds the candidates t = L + 32 q (q < 4) of the 5^3 box, a bit per slot that says
+// whether the candidate is a cell of a lower layer, and its stored values.  The layer bytes of
+// the four slots are read first and the values of the usable ones after them, so a cell costs
+// two dependent memory round trips instead of two per slot and fit.
+constexpr int RS0 = 2, NC0 = (2 * RS0 + 1) * (2 * RS0 + 1) * (2 * RS0 + 1), NQ0 = (NC0 + 31) / 32;
+template <typename T>
+struct Cand {
+  unsigned ok;
+  T v[NQ0][3];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_cand(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                                          int i, int j, int k, int le, Cand<T>& cd) {
+  const int lane = threadIdx.x & 31;
+  long cc[NQ0];
+  int ld[NQ0];
+#pragma unroll
+  for (int q = 0; q < NQ0; q++) {
+    const int t = lane + 32 * q, w = 2 * RS0 + 1;
+    ld[q] = -1;
+    cc[q] = 0;
+    long c;
+    if (t < NC0 && cell_at(g, i + t % w - RS0, j + (t / w) % w - RS0, k + t / (w * w) - RS0, c)) {
+      cc[q] = c;
+      ld[q] = lay[c];
+    }
+  }
+  cd.ok = 0u;
+#pragma unroll
+  for (int q = 0; q < NQ0; q++) {
+    cd.v[q][0] = cd.v[q][1] = cd.v[q][2] = T(0);
+    if (ld[q] >= 0 && ld[q] < le) {
+      cd.ok |= 1u << q;
+      cd.v[q][0] = x[cc[q]];
+      cd.v[q][1] = x[g.N + cc[q]];
+      cd.v[q][2] = x[2 * g.N + cc[q]];
+    }
+  }
+}
+
 // One affine WLS fit centred at cell (i,j,k) of layer le with search radius rs, computed by a
 // whole warp: the lanes split the (2 rs + 1)^3 candidate cells and the normal-equation sums are
 // combined by a butterfly (every lane ends with the same totals, in a fixed order).
@@ -128,10 +185,12 @@ __device__ bool solve4(AT A[4][4], AT B[4][3], AT X[4][3], AT tolfac) {
 // The data are the stored values: xi_d (FP64 storage), or the displacements S_d (FP32 storage),
 // which the affine model fits exactly as it fits xi (the identity is affine): the fitted values
 // are then small, so the solve's error, which scales with the data, carries no O(1) positions
-// into the extrapolated maps.
+// into the extrapolated maps.  With cd (rs = 2 only) the candidates come from the registers that
+// load_cand filled, in the same order, so the sums are the same to the last bit.
 template <typename AT, typename T>
 __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t* __restrict__ lay, int i, int j,
-                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, AT sol[4][3]) {
+                             int k, int le, int rs, int mode, const AT nrm[3], AT tolfac, AT sol[4][3],
+                             const Cand<T>* cd = nullptr) {
   const int lane = threadIdx.x & 31;
   AT a[10], bsum[12];
 #pragma unroll
@@ -140,22 +199,18 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
   for (int q = 0; q < 12; q++) bsum[q] = AT(0);
   int npos = 0;
   const int w = 2 * rs + 1, nc = w * w * w;
-  for (int t = lane; t < nc; t += 32) {
-    const int di = t % w - rs, dj = (t / w) % w - rs, dk = t / (w * w) - rs;
-    long c;
-    if (!cell_at(g, i + di, j + dj, k + dk, c)) continue;
-    const int ld = lay[c];
-    if (ld < 0 || ld >= le) continue;
+  // one candidate's contribution; false when its weight is not positive
+  auto add = [&](int di, int dj, int dk, T x0, T x1, T x2) {
     const int sr = abs(di) + abs(dj) + abs(dk);
     AT wt = sizeof(AT) == 4 ? (AT)ldexpf(1.0f, -sr) : (AT)ldexp(1.0, -sr);
     if (mode == 1) {
       const AT len = sqrt((AT)(di * di + dj * dj + dk * dk));
       const AT cs = -((AT)di * nrm[0] + (AT)dj * nrm[1] + (AT)dk * nrm[2]) / len;
       wt = cs * wt;
-      if (!(wt > AT(0))) continue;
+      if (!(wt > AT(0))) return;
     }
     const AT v[4] = {AT(1), (AT)di, (AT)dj, (AT)dk};
-    const AT xv[3] = {(AT)x[c], (AT)x[g.N + c], (AT)x[2 * g.N + c]};
+    const AT xv[3] = {(AT)x0, (AT)x1, (AT)x2};
     int q = 0;
 #pragma unroll
     for (int r = 0; r < 4; r++)
@@ -166,6 +221,23 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
 #pragma unroll
       for (int d = 0; d < 3; d++) bsum[3 * r + d] += wt * v[r] * xv[d];
     npos++;
+  };
+  if (cd) {
+#pragma unroll
+    for (int q = 0; q < NQ0; q++) {
+      if (!(cd->ok >> q & 1u)) continue;
+      const int t = lane + 32 * q;
+      add(t % w - rs, (t / w) % w - rs, t / (w * w) - rs, cd->v[q][0], cd->v[q][1], cd->v[q][2]);
+    }
+  } else {
+    for (int t = lane; t < nc; t += 32) {
+      const int di = t % w - rs, dj = (t / w) % w - rs, dk = t / (w * w) - rs;
+      long c;
+      if (!cell_at(g, i + di, j + dj, k + dk, c)) continue;
+      const int ld = lay[c];
+      if (ld < 0 || ld >= le) continue;
+      add(di, dj, dk, x[c], x[g.N + c], x[2 * g.N + c]);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -192,18 +264,20 @@ __device__ bool wls_fit_warp(const Geo& g, const T* __restrict__ x, const int8_t
 // Extrapolates one cell (whole warp) with fits accumulated in AT: kernel-only fit, then (layers
 // 1 and 2) the fit weighted by the normal n_e = normalised (grad xi)^T grad_X phi_0(xi_e) of that
 // first fit; the search radius grows up to 4 while the system stays degenerate.  Returns 1 on
-// success, 0 when degenerate, -1 when an FP32 attempt was too ill-conditioned to trust.
+// success, 0 when degenerate, -1 when an FP32 attempt was too ill-conditioned to trust.  cd: the
+// preloaded candidates of the radius-2 box.
 template <typename AT, typename T>
 __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
-                            int i, int j, int k, int le, double out[3]) {
+                            int i, int j, int k, int le, const Cand<T>& cd, double out[3]) {
   // FP64: the degeneracy threshold; FP32: also the point below which the fit is redone in FP64
   const AT tolfac = sizeof(AT) == 8 ? AT(1e-12) : AT(1e-4);
   // FP32 storage fits displacements: the identity's slope per cell offset is added back to the
   // fitted gradient, and the cell's x0 - c to the fitted value, where the normal needs xi
   const AT hid = disp_storage<T>() ? (sizeof(AT) == 4 ? (AT)g.f.h : (AT)g.h) : AT(0);
-  for (int rs = 2; rs <= 4; rs++) {
+  for (int rs = RS0; rs <= 4; rs++) {
+    const Cand<T>* cp = rs == RS0 ? &cd : nullptr;
     AT s1[4][3];
-    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, s1)) {
+    if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 0, (const AT*)nullptr, tolfac, s1, cp)) {
       if (sizeof(AT) == 4) return -1;
       continue;
     }
@@ -227,7 +301,7 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
       }
       const AT nrm[3] = {v[0] / nv, v[1] / nv, v[2] / nv};
       AT s2[4][3];
-      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, s2)) {
+      if (!wls_fit_warp<AT>(g, x, lay, i, j, k, le, rs, 1, nrm, tolfac, s2, cp)) {
         if (sizeof(AT) == 4) return -1;
         continue;
       }
@@ -240,51 +314,49 @@ __device__ int wls_cell_try(const Geo& g, const Body& b, const T* __restrict__ x
   return 0;
 }
 
-// FP64 storage: FP64 fits.  FP32 storage: FP32 fits, redone in FP64 when ill-conditioned.
-template <typename T>
-__device__ bool wls_cell_warp(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
-                              int i, int j, int k, int le, double out[3]) {
-  if (sizeof(T) == 4) {
-    const int r = wls_cell_try<float>(g, b, x, lay, i, j, k, le, out);
-    if (r >= 0) return r == 1;
-  }
-  return wls_cell_try<double>(g, b, x, lay, i, j, k, le, out) == 1;
+// One cell's fits in the accumulation type of the storage: FP64 storage fits in FP64 (1:
+// extrapolated, 0: degenerate); FP32 storage fits in FP32 and returns -1 when the system was too
+// ill-conditioned to trust, for the FP64 redo kernel (a separate kernel, so that the FP32 one
+// keeps the register budget of FP32 fits).  FP64: the redo itself.
+template <typename AT, typename T>
+__device__ int wls_cell_warp(const Geo& g, const Body& b, const T* __restrict__ x, const int8_t* __restrict__ lay,
+                             int i, int j, int k, int le, double out[3]) {
+  Cand<T> cd;
+  load_cand(g, x, lay, i, j, k, le, cd);
+  return wls_cell_try<AT>(g, b, x, lay, i, j, k, le, cd, out);
 }
 
-// compacted list of the band cells (layers 1..L) of a body's window
-__global__ void k_band_list(Geo g, const int* __restrict__ bb, const int8_t* __restrict__ lay, int* __restrict__ list,
-                            int* __restrict__ count) {
-  const Win w = make_win(g, bb, 2);
-  WIN_LOOP(t, w) {
-    int u[3], i, j, k;
-    long c;
-    win_cell(g, w, t, u, i, j, k, c);
-    const int l = lay[c];
-    if (l >= 1) list[atomicAdd(count, 1)] = (int)c;
-  }
-}
+// FP32 fits run at six blocks per SM (80 registers a thread, 8 bytes spilled); FP64 fits take what
+// they need
+#define WLS_MINB(T, REDO) ((sizeof(T) == 4 && !(REDO)) ? 6 : 1)
 
-// one warp per listed cell of layer l
-template <typename T>
-__global__ void k_wls(Geo g, Body b, int l, T* __restrict__ x, int8_t* __restrict__ lay, const int* __restrict__ list,
-                      const int* __restrict__ count, int* __restrict__ err) {
+// one warp per cell of layer l (its segment of the band list).  REDO: the FP64 pass over the
+// cells whose FP32 fits were too ill-conditioned (redo[0 .. cnt[0]), filtered by layer);
+// otherwise the storage type's pass, which lists such cells in redo (FP32 storage).
+template <typename T, bool REDO>
+__global__ void __launch_bounds__(TPB, WLS_MINB(T, REDO)) k_wls(Geo g, Body b, int l, T* __restrict__ x, int8_t* __restrict__ lay, const int* __restrict__ list,
+                      int* __restrict__ cnt, int* __restrict__ redo, int* __restrict__ err) {
+  using AT = typename std::conditional<REDO || sizeof(T) == 8, double, float>::type;
   const int lane = threadIdx.x & 31;
-  const int n = *count;
+  const int base = REDO ? 0 : layer_base(cnt, l), n = REDO ? cnt[0] : cnt[l];
+  const int* src = REDO ? redo : list + base;
   for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
-    const long c = list[e];
-    if (lay[c] != l) continue;
+    const long c = src[e];
+    if (REDO && lay[c] != l) continue;  // listed by an earlier layer's pass
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
     double out[3];
-    const bool ok = wls_cell_warp(g, b, x, lay, i, j, k, l, out);
+    const int r = wls_cell_warp<AT>(g, b, x, lay, i, j, k, l, out);
     __syncwarp();
     if (lane == 0) {
-      if (ok) {
+      if (r == 1) {
         x[c] = (T)out[0];
         x[g.N + c] = (T)out[1];
         x[2 * g.N + c] = (T)out[2];
-      } else {
+      } else if (r == 0) {
         lay[c] = -1;
         atomicAdd(err, 1);
+      } else {
+        redo[atomicAdd(&cnt[0], 1)] = (int)c;
       }
     }
   }
@@ -337,22 +409,27 @@ __global__ void k_corr(Geo g, const int* __restrict__ bb, const T* __restrict__ 
   }
 }
 
-// cells new to the band: xi^{n+1/2} by the same WLS from the corrected lower layers
-template <typename T>
-__global__ void k_wls_half(Geo g, Body b, int l, const int8_t* __restrict__ lay, const int8_t* __restrict__ layn,
+// cells new to the band: xi^{n+1/2} by the same WLS from the corrected lower layers (layer l's
+// segment of the new band's list; REDO as for k_wls, with its own redo count cnt[9])
+template <typename T, bool REDO>
+__global__ void __launch_bounds__(TPB, WLS_MINB(T, REDO)) k_wls_half(Geo g, Body b, int l, const int8_t* __restrict__ lay, const int8_t* __restrict__ layn,
                            const T* __restrict__ xn, T* __restrict__ xh, const int* __restrict__ list,
-                           const int* __restrict__ count, int* __restrict__ err) {
+                           int* __restrict__ cnt, int* __restrict__ redo, int* __restrict__ err) {
+  using AT = typename std::conditional<REDO || sizeof(T) == 8, double, float>::type;
   const int lane = threadIdx.x & 31;
-  const int n = *count;
+  const int base = REDO ? 0 : layer_base(cnt, l), n = REDO ? cnt[9] : cnt[l];
+  const int* src = REDO ? redo : list + base;
   for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
-    const long c = list[e];
+    const long c = src[e];
     if (layn[c] != l || lay[c] >= 0) continue;
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
     double out[3];
-    const bool ok = wls_cell_warp(g, b, xh, layn, i, j, k, l, out);
+    const int r = wls_cell_warp<AT>(g, b, xh, layn, i, j, k, l, out);
     __syncwarp();
     if (lane == 0) {
-      if (ok) {
+      if (r < 0) {
+        redo[atomicAdd(&cnt[9], 1)] = (int)c;
+      } else if (r == 1) {
         xh[c] = (T)out[0];
         xh[g.N + c] = (T)out[1];
         xh[2 * g.N + c] = (T)out[2];
@@ -405,22 +482,26 @@ void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s) {
   k_init_xi<T><<<nblocks(g.N), TPB, 0, s>>>(g, b, x); rmt_count_launches(1);
 }
 
+// cnt: BAND_COUNTERS ints (see rmt_kernels.h); redo: FP32 storage, a list of the grid's size
 template <typename T>
 cudaError_t launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list,
-                               int* count, int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s) {
+                               int* cnt, int* redo, int wls_blocks, T* x, T* phi, int8_t* lay, int* err,
+                               cudaStream_t s) {
+  const cudaError_t e = cudaMemsetAsync(cnt, 0, BAND_COUNTERS * sizeof(int), s);
+  if (e != cudaSuccess) return e;
   k_classify<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, x, lay);
   rmt_count_launches(1);
   for (int l = 1; l <= g.layers; l++) {
-    k_bfs<<<blocks, TPB, 0, s>>>(g, bb_in, l, lay);
+    k_bfs<<<blocks, TPB, 0, s>>>(g, bb_in, l, lay, list, cnt);
     rmt_count_launches(1);
   }
-  const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  k_band_list<<<blocks, TPB, 0, s>>>(g, bb_in, lay, list, count);
-  rmt_count_launches(1);
   for (int l = 1; l <= g.layers; l++) {
-    k_wls<T><<<wls_blocks, TPB, 0, s>>>(g, b, l, x, lay, list, count, err);
+    k_wls<T, false><<<wls_blocks, TPB, 0, s>>>(g, b, l, x, lay, list, cnt, redo, err);
     rmt_count_launches(1);
+    if (sizeof(T) == 4) {
+      k_wls<T, true><<<sm_count(), TPB, 0, s>>>(g, b, l, x, lay, list, cnt, redo, err);
+      rmt_count_launches(1);
+    }
   }
   k_bb_reset<<<1, 32, 0, s>>>(bb_out);
   rmt_count_launches(1);
@@ -432,14 +513,18 @@ cudaError_t launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, in
 }
 
 template <typename T>
-void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, const int* count,
+void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, int* cnt, int* redo,
                       int wls_blocks, const T* x, const int8_t* lay, const T* xn, const int8_t* layn, T* xh, T* phih,
                       int* err, cudaStream_t s) {
   k_corr<T><<<blocks, TPB, 0, s>>>(g, bb_in, x, lay, xn, layn, xh);
   rmt_count_launches(1);
   for (int l = 1; l <= g.layers; l++) {
-    k_wls_half<T><<<wls_blocks, TPB, 0, s>>>(g, b, l, lay, layn, xn, xh, list, count, err);
+    k_wls_half<T, false><<<wls_blocks, TPB, 0, s>>>(g, b, l, lay, layn, xn, xh, list, cnt, redo, err);
     rmt_count_launches(1);
+    if (sizeof(T) == 4) {
+      k_wls_half<T, true><<<sm_count(), TPB, 0, s>>>(g, b, l, lay, layn, xn, xh, list, cnt, redo, err);
+      rmt_count_launches(1);
+    }
   }
   k_phi_half<T><<<blocks, TPB, 0, s>>>(g, b, bb_in, xh, layn, phih);
   rmt_count_launches(1);
@@ -447,9 +532,9 @@ void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks,
 
 #define INST(T)                                                                                                \
   template void launch_init_xi<T>(const Geo&, const Body&, T*, cudaStream_t);                                   \
-  template cudaError_t launch_extrapolate<T>(const Geo&, const Body&, const int*, int*, int, int*, int*, int, T*, \
-                                             T*, int8_t*, int*, cudaStream_t);                                  \
-  template void launch_corrector<T>(const Geo&, const Body&, const int*, int, const int*, const int*, int,        \
+  template cudaError_t launch_extrapolate<T>(const Geo&, const Body&, const int*, int*, int, int*, int*, int*, int, \
+                                             T*, T*, int8_t*, int*, cudaStream_t);                              \
+  template void launch_corrector<T>(const Geo&, const Body&, const int*, int, const int*, int*, int*, int,        \
                                     const T*, const int8_t*, const T*, const int8_t*, T*, T*, int*, cudaStream_t);
 INST(float)
 INST(double)

@@ -87,17 +87,22 @@ void launch_fill(T* a, T v, long n, cudaStream_t s);
 template <typename T>
 void launch_init_xi(const Geo& g, const Body& b, T* x, cudaStream_t s);
 // bb_in: band bounding box of the step (null: whole grid); bb_out receives the new band's box;
-// blocks: launch width for the body's window (kernels stride over the whole window); list and
-// count: device buffers for the compacted band (capacity: the grid), filled by
-// launch_extrapolate and read by launch_corrector of the same step; wls_blocks: launch width
-// of the one-warp-per-cell fits
+// blocks: launch width for the body's window (kernels stride over the whole window); list: the
+// band's cells sorted by layer (capacity: the grid), written by the layer passes of
+// launch_extrapolate and read by launch_corrector of the same step; cnt: BAND_COUNTERS ints,
+// cnt[l] the cells of layer l (l = 1..8), cnt[0] and cnt[9] the lengths of the FP64 redo lists
+// of the two fitting passes; redo: FP32 storage, a list of the grid's size for the cells whose
+// FP32 fits were too ill-conditioned (null for FP64 storage); wls_blocks: launch width of the
+// one-warp-per-cell fits.
 // err[0] counts degenerate fits, err[1] (FP32 storage) band cells near the seam of the body's
 // image window; returns the error of the one runtime call it makes besides launches
+constexpr int BAND_COUNTERS = 10;
 template <typename T>
 cudaError_t launch_extrapolate(const Geo& g, const Body& b, const int* bb_in, int* bb_out, int blocks, int* list,
-                               int* count, int wls_blocks, T* x, T* phi, int8_t* lay, int* err, cudaStream_t s);
+                               int* cnt, int* redo, int wls_blocks, T* x, T* phi, int8_t* lay, int* err,
+                               cudaStream_t s);
 template <typename T>
-void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, const int* count,
+void launch_corrector(const Geo& g, const Body& b, const int* bb_in, int blocks, const int* list, int* cnt, int* redo,
                       int wls_blocks, const T* x, const int8_t* lay, const T* xn, const int8_t* layn, T* xh, T* phih,
                       int* err, cudaStream_t s);
 
@@ -137,6 +142,10 @@ void mg_set_zchunk(MGSolver* m, int zchunk);
 int mg_zchunk(const MGSolver* m);
 // MAC in FP32: one fused red-black pass per sweep (1: on the large levels that allow it, the
 // default; 2: on every level that allows it; 0: never), else one pass per colour
+// run the levels below the coarse-tail threshold as one cluster launch per V-cycle (default off);
+// mg_tail_levels: how many levels that launch covers (0: none)
+void mg_set_tail(MGSolver* m, int on);
+int mg_tail_levels(const MGSolver* m);
 void mg_set_sweep(MGSolver* m, int fused);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
 // hook(ctx, which, begin, stream) with which = 0 (smoother colour), 1 (FP64 residual) or 2 (fused

@@ -21,9 +21,10 @@ namespace {
 // largest grid (cells) the static scratch serves: every band cell needs one list entry and a
 // band never holds more cells than the grid
 constexpr long NOALLOC_MAX_CELLS = 1L << 21;  // 2,097,152 cells, e.g. 128^3
-// layout of the scratch (ints): [0, 8) count, bounding box (6), degenerate-fit counter;
-// [64, 64 + NOALLOC_MAX_CELLS) the band list
-constexpr long SCR_COUNT = 0, SCR_BB = 1, SCR_ERR = 7, SCR_LIST = 64;
+// layout of the scratch (ints): [0, 16) the band list's counters (BAND_COUNTERS of them),
+// [16, 22) bounding box, [22] degenerate-fit counter; [64, 64 + NOALLOC_MAX_CELLS) the band list
+constexpr long SCR_COUNT = 0, SCR_BB = 16, SCR_ERR = 22, SCR_LIST = 64;
+static_assert(BAND_COUNTERS <= SCR_BB && SCR_ERR < SCR_LIST, "scratch layout");
 constexpr int MAX_DEVICES = 64;
 
 __device__ __align__(256) int g_noalloc_scratch[SCR_LIST + NOALLOC_MAX_CELLS];
@@ -107,7 +108,8 @@ rmt_status rmt_extrapolate_noalloc(const rmt_grid_desc* d, const rmt_solid_desc*
   if (e != cudaSuccess) return RMT_ECUDA;
   const long wide = (long)sm_count() * 64;
   const int blocks = (int)((G.N + 127) / 128 < wide ? (G.N + 127) / 128 : wide);
-  e = launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, sm_count() * 4,
+  e = launch_extrapolate<double>(G, b, nullptr, scr + SCR_BB, blocks, scr + SCR_LIST, scr + SCR_COUNT, nullptr,
+                                 sm_count() * 4,
                                  xi_out, phi_out, (int8_t*)layer_out, scr + SCR_ERR, st);
   int nbad = 0;
   if (e == cudaSuccess) e = cudaGetLastError();
