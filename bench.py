@@ -235,7 +235,7 @@ def solver_options(args, graph: bool = True) -> dict:
     """The multigrid schedule of the timed configuration (rmt_set_option names)."""
     o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm, "fe_warm": args.fe_warm,
          "mac_pre": args.mac_sweeps, "mac_post": args.mac_sweeps,
-         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse, "mg_tail": args.mg_tail}
+         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse}
     if graph:
         o["graph"] = args.graph
     return o
@@ -449,8 +449,6 @@ def main():
     ap.add_argument("--mac-coarse", type=int, default=2,
                     help="red-black sweeps before and after the coarse correction on the MAC levels below the finest")
     ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
-    ap.add_argument("--mg-tail", type=int, default=0,
-                    help="run the multigrid levels below 40000 unknowns as one cluster launch per V-cycle")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
     ap.add_argument("--n", type=int, default=None,
@@ -606,8 +604,7 @@ def main():
                                                    "mac_inner": args.mac_inner, "fe_inner": args.fe_inner,
                                                    "mac_sweeps": args.mac_sweeps, "mac_coarse_sweeps": args.mac_coarse,
                                                    "mac_warm_start": bool(args.mac_warm),
-                                                   "fe_warm_start": bool(args.fe_warm),
-                                                   "coarse_tail_launch": bool(args.mg_tail)},
+                                                   "fe_warm_start": bool(args.fe_warm)},
                            "step_graph": bool(args.graph),
                            "dt": g.dt, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},

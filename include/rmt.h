@@ -165,11 +165,7 @@ double rmt_dt(rmt_grid* g);
  * finest level's), "mac_sweep" (FP32 grids: 1, the default, runs each red-black sweep of a
  * level with n_x % 4 == 0, even periodic sides, n_x >= 64 and at least 2^20 cells as one fused
  * pass over both colours; 2 does so on every level with n_x % 4 == 0 and even periodic sides; 0
- * runs one pass per colour everywhere; all give the same sweep), "mg_tail" (nonzero: the levels
- * of each V-cycle with at most 40000 unknowns, from the first of them below the finest level
- * down to the coarsest and back, run as one launch of a thread-block cluster, MAC levels there
- * smoothed by one pass per colour; 0, the default, launches them level by level; both compute
- * the same V-cycle), "graph" (nonzero: with fixed
+ * runs one pass per colour everywhere; all give the same sweep), "graph" (nonzero: with fixed
  * cycle counts, rmt_step replays a captured CUDA graph of the step instead of launching its
  * kernels one by one; the results are the same).  Cycle counts (mg_fixed_cycles,
  * rmt_last_cycles) count V-cycles.

@@ -132,7 +132,6 @@ struct rmt_grid {
   int mac_warm = 0, fe_warm = 0;    // warm-started solves
   int mac_sweep = 1;                // fused red-black sweeps (FP32 MAC)
   int mac_zchunk = 0, fe_zchunk = 0;  // finest-level stencil tile z-chunks (0: heuristic)
-  int mg_tail = 0;                    // coarse levels of a V-cycle in one cluster launch
   double fe_omega = -1.0, mac_omega = -1.0;
   size_t bytes = 0;  // device bytes requested by dalloc
   int dry = 0;       // dalloc only counts (footprint model)
@@ -462,8 +461,6 @@ rmt_status alloc_t(rmt_grid* g) {
   mg_set_warm(g->fe, g->fe_warm);
   mg_set_zchunk(g->mac, g->mac_zchunk);
   mg_set_zchunk(g->fe, g->fe_zchunk);
-  mg_set_tail(g->mac, g->mg_tail);
-  mg_set_tail(g->fe, g->mg_tail);
   mg_set_nonfinite_flag(g->mac, g->err_d + 2);
   mg_set_nonfinite_flag(g->fe, g->err_d + 2);
   g->bytes += mg_device_bytes(g->mac) + mg_device_bytes(g->fe);
@@ -1181,8 +1178,6 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     (name[0] == 'm' ? g->mac_zchunk : g->fe_zchunk) = (int)value;
   } else if (!strcmp(name, "graph")) {
     g->use_graph = value != 0.0;
-  } else if (!strcmp(name, "mg_tail")) {
-    g->mg_tail = value != 0.0;
   } else if (!strcmp(name, "inject_nan_step")) {
     g->inject_nan_step = value < 0 ? -1 : (long)value;
   } else if (!strcmp(name, "inject_alloc")) {
@@ -1206,8 +1201,6 @@ rmt_status rmt_set_option(rmt_grid* g, const char* name, double value) {
     mg_set_warm(g->fe, g->fe_warm);
     mg_set_zchunk(g->mac, g->mac_zchunk);
     mg_set_zchunk(g->fe, g->fe_zchunk);
-    mg_set_tail(g->mac, g->mg_tail);
-    mg_set_tail(g->fe, g->mg_tail);
   }
   return RMT_OK;
 }

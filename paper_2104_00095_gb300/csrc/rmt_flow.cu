@@ -67,11 +67,45 @@ __device__ __forceinline__ T slope_u(const Geo& g, const T* __restrict__ u, int 
 struct Slopes9 {
   void* s[9];
 };
+// A cell whose five-point stencils reach no wall ghost (all points inside, or wrapped across
+// periodic sides: every cell of a periodic box) takes the offsets of its +-1, +-2 neighbours
+// along each axis once and reads the three components through them; the others go through
+// slope_u's boundary rules.  The same values reach the same limiter either way.
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_slopes(Geo g, const T* __restrict__ u, Slopes9 S) {
   THREAD_XYZ(i, j, k);
   if (i >= g.n[0] || j >= g.n[1]) return;
   const long c = cidx(g, i, j, k);
+  const int ii[3] = {i, j, k};
+  const long st[3] = {1, (long)g.n[0], (long)g.n[0] * g.n[1]};
+  long off[3][4];  // neighbours -2, -1, +1, +2 along each axis
+  bool fast = true;
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int sft = q < 2 ? q - 2 : q - 1;
+      int v = ii[d] + sft;
+      if (v < 0 || v >= g.n[d]) {
+        fast = fast && g.per[d];
+        v += v < 0 ? g.n[d] : -g.n[d];
+      }
+      off[d][q] = (long)(v - ii[d]) * st[d];
+    }
+  if (fast) {
+    const T ih = cv<T>(g.ih, g.f.ih);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const T* pc = u + (long)a * g.N + c;
+      const T x0 = pc[0];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        const T q[5] = {pc[off[d][0]], pc[off[d][1]], x0, pc[off[d][2]], pc[off[d][3]]};
+        ((T*)S.s[3 * d + a])[c] = lim_slope(q, 0x1Fu, ih);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int d = 0; d < 3; d++)
 #pragma unroll

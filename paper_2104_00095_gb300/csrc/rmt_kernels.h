@@ -142,10 +142,6 @@ void mg_set_zchunk(MGSolver* m, int zchunk);
 int mg_zchunk(const MGSolver* m);
 // MAC in FP32: one fused red-black pass per sweep (1: on the large levels that allow it, the
 // default; 2: on every level that allows it; 0: never), else one pass per colour
-// run the levels below the coarse-tail threshold as one cluster launch per V-cycle (default off);
-// mg_tail_levels: how many levels that launch covers (0: none)
-void mg_set_tail(MGSolver* m, int on);
-int mg_tail_levels(const MGSolver* m);
 void mg_set_sweep(MGSolver* m, int fused);
 // Optional timing hook around the finest-level smoother and FP64-residual launches:
 // hook(ctx, which, begin, stream) with which = 0 (smoother colour), 1 (FP64 residual) or 2 (fused

@@ -24,7 +24,6 @@
 // (cell-centred), full weighting / trilinear (nodal).  Coarse densities are 8-cell means.
 // The coarsest level is solved by one block with conjugate gradients.  Norms use fixed-order
 // two-stage reductions, so results are deterministic.
-#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -73,15 +72,6 @@ __device__ __forceinline__ int nnb(const Lv& L, int d, int v) {
 }
 
 // ----------------------------------------------------------------------------- operators
-// Loads of values that another block of the same launch may have written (the coarse-level
-// kernel below runs a whole V-cycle tail in one launch): CG = true reads them from L2
-// (ld.global.cg), never from a block's L1 or the read-only path; CG = false is a plain load.
-template <bool CG, typename T>
-__device__ __forceinline__ T ldv(const T* p, long i) {
-  if constexpr (CG) return __ldcg(p + i);
-  else return p[i];
-}
-
 // approximate FP32 reciprocal: the hardware's reciprocal instruction alone (PTX rcp.approx.ftz)
 __device__ __forceinline__ float rcp_approx(float y) {
   float r;
@@ -99,7 +89,7 @@ __device__ __forceinline__ CT face_beta(CT ra, CT rb) {
 // MAC at cell (i,j,k): returns (A x)_c (in AT) and its diagonal.  Rows away from the y and z
 // boundaries share one path: the two x neighbours come from selects (periodic wrap, or a zero
 // weight at a wall), so a warp whose row reaches i = 0 or n-1 does not diverge.
-template <typename AT, bool FAST = false, bool CG = false, typename XT, typename CT>
+template <typename AT, bool FAST = false, typename XT, typename CT>
 __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, const CT* __restrict__ rho, int i, int j,
                                      int k, AT& diag) {
   const long c = cix(L, i, j, k);
@@ -118,12 +108,12 @@ __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, cons
     for (int f = 0; f < 6; f++) {
       const bool has = f == 0 ? hasl : (f == 1 ? hash : true);
       const AT beta = has ? (AT)face_beta<FAST>(rc, rp[off6[f]]) : AT(0);
-      off += beta * (AT)ldv<CG>(xp, off6[f]);
+      off += beta * (AT)xp[off6[f]];
       dg += beta;
     }
     const AT ih2 = cv<AT>(L.ih2, L.f_ih2);
     diag = dg * ih2;
-    return (dg * (AT)ldv<CG>(x, c) - off) * ih2;
+    return (dg * (AT)x[c] - off) * ih2;
   }
   const int nb[6][3] = {{i - 1, j, k}, {i + 1, j, k}, {i, j - 1, k}, {i, j + 1, k}, {i, j, k - 1}, {i, j, k + 1}};
 #pragma unroll
@@ -135,12 +125,12 @@ __device__ __forceinline__ AT mac_op(const Lv& L, const XT* __restrict__ x, cons
     q[d] = v;
     const long cn = cix(L, q[0], q[1], q[2]);
     const AT beta = (AT)face_beta<FAST>(rc, rho[cn]);
-    off += beta * (AT)ldv<CG>(x, cn);
+    off += beta * (AT)x[cn];
     dg += beta;
   }
   const AT ih2 = cv<AT>(L.ih2, L.f_ih2);
   diag = dg * ih2;
-  return (dg * (AT)ldv<CG>(x, c) - off) * ih2;
+  return (dg * (AT)x[c] - off) * ih2;
 }
 
 // FE at node (i,j,k): returns (K x)_i and its diagonal
@@ -527,18 +517,17 @@ __global__ void k_ff_to64(const float* __restrict__ xh, const float* __restrict_
 // red-black Gauss-Seidel update (7-point) of the cell of this colour among x = 2p and 2p+1 of
 // row (j, k); the increment scales the residual, so an approximate FP32 quotient moves the sweep,
 // not its fixed point
-template <typename T, bool CG = false>
+template <typename T>
 __device__ __forceinline__ void rbgs_at(const Lv& L, int colour, T w, T* __restrict__ x, const T* __restrict__ b,
                                         const T* __restrict__ rho, int p, int j, int k) {
   const int i = 2 * p + ((j + k + colour) & 1);
   if (i >= L.n[0]) return;
   T dg;
-  const T ax = mac_op<T, true, CG>(L, x, rho, i, j, k, dg);
+  const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
   const long c = cix(L, i, j, k);
   if (dg > T(0)) {
-    const T xc = ldv<CG>(x, c), bc = ldv<CG>(b, c);
-    if constexpr (sizeof(T) == 4) x[c] = xc + w * ((bc - ax) * rcp_approx(dg));
-    else x[c] = xc + w * ((bc - ax) / dg);
+    if constexpr (sizeof(T) == 4) x[c] = x[c] + w * ((b[c] - ax) * rcp_approx(dg));
+    else x[c] = x[c] + w * ((b[c] - ax) / dg);
   }
 }
 // one colour pass: one thread per cell pair along x
@@ -1008,7 +997,7 @@ __global__ void __launch_bounds__(FX* FY) k_fe_tile(Lv L, T w, const T* __restri
 // restriction), and zeroes the coarse iterate.  The operator is the smoothers' (approximate
 // coefficient quotient); the high-precision residual outside the V-cycle uses the exactly
 // rounded one.
-template <typename T, bool CG = false>
+template <typename T>
 __device__ __forceinline__ void resid_restrict_mac_at(const Lv& F, const Lv& C, const T* __restrict__ x,
                                                       const T* __restrict__ b, const T* __restrict__ rho,
                                                       T* __restrict__ bc, T* __restrict__ xc, int I, int J, int K) {
@@ -1017,8 +1006,8 @@ __device__ __forceinline__ void resid_restrict_mac_at(const Lv& F, const Lv& C, 
   for (int q = 0; q < 8; q++) {
     const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + ((q >> 2) & 1);
     T dg;
-    const T ax = mac_op<T, true, CG>(F, x, rho, i, j, k, dg);
-    s += ldv<CG>(b, cix(F, i, j, k)) - ax;
+    const T ax = mac_op<T, true>(F, x, rho, i, j, k, dg);
+    s += b[cix(F, i, j, k)] - ax;
   }
   const long u = cix(C, I, J, K);
   bc[u] = s * T(0.125);
@@ -1035,14 +1024,13 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, co
 
 // restriction of the residual to the coarse right-hand side at coarse unknown (I, J, K) (coarse
 // x zeroed): MAC the 8-cell mean, FE full weighting
-template <typename T, bool CG = false>
+template <typename T>
 __device__ __forceinline__ void restrict_at(const Lv& F, const Lv& C, int kind, const T* __restrict__ rf,
                                             T* __restrict__ bc, T* __restrict__ xc, int I, int J, int K) {
   T s = T(0);
   if (kind == 0) {
 #pragma unroll
-    for (int q = 0; q < 8; q++)
-      s += ldv<CG>(rf, cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1)));
+    for (int q = 0; q < 8; q++) s += rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
     s *= T(0.125);
   } else {
     for (int oz = -1; oz <= 1; oz++)
@@ -1059,7 +1047,7 @@ __device__ __forceinline__ void restrict_at(const Lv& F, const Lv& C, int kind, 
           }
           if (!in) continue;
           const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
-          s += w * ldv<CG>(rf, nix(F, ff[0], ff[1], ff[2]));
+          s += w * rf[nix(F, ff[0], ff[1], ff[2])];
         }
   }
   const long u = kind == 0 ? cix(C, I, J, K) : nix(C, I, J, K);
@@ -1080,7 +1068,7 @@ __global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, co
 // Cell-centred: along each axis a child takes 3/4 of its parent and 1/4 of the parent's
 // neighbour on the child's side (the parent itself beyond a wall: Neumann mirror), applied
 // axis by axis.
-template <typename T, bool CG = false>
+template <typename T>
 __device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T* __restrict__ xc, T* __restrict__ xf,
                                                int I, int J, int K) {
   int nx[3], ny[3], nz[3];  // coarse indices of I-1, I, I+1 (and for J, K)
@@ -1103,7 +1091,7 @@ __device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T
 #pragma unroll
     for (int qy = 0; qy < 3; qy++) {
       const long row = (long)C.n[0] * (ny[qy] + (long)C.n[1] * nz[qz]);
-      const T xm = ldv<CG>(xc, row + nx[0]), x0 = ldv<CG>(xc, row + nx[1]), xp = ldv<CG>(xc, row + nx[2]);
+      const T xm = xc[row + nx[0]], x0 = xc[row + nx[1]], xp = xc[row + nx[2]];
       rx[qz][qy][0] = w0 * x0 + w1 * xm;
       rx[qz][qy][1] = w0 * x0 + w1 * xp;
     }
@@ -1120,7 +1108,7 @@ __device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T
         const T ym = w0 * rx[0][1][cx] + w1 * rx[0][2 * cy][cx];
         const T yp = w0 * rx[2][1][cx] + w1 * rx[2][2 * cy][cx];
         const T v = w0 * y0 + w1 * (cz ? yp : ym);
-        xf[base + cx] = ldv<CG>(xf, base + cx) + v;
+        xf[base + cx] += v;
       }
     }
 }
@@ -1133,16 +1121,15 @@ __global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* 
 
 // Nodal: a fine node on a coarse node takes its value, one between two coarse nodes their mean
 // (per axis).
-template <typename T, bool CG = false>
+template <typename T>
 __device__ __forceinline__ void prolong_fe_at(const Lv& F, const Lv& C, const T* __restrict__ xc, T* __restrict__ xf,
                                               int I, int J, int K) {
   const int I1 = I + 1 < C.nn[0] ? I + 1 : (C.per[0] ? 0 : I);
   const int J1 = J + 1 < C.nn[1] ? J + 1 : (C.per[1] ? 0 : J);
   const int K1 = K + 1 < C.nn[2] ? K + 1 : (C.per[2] ? 0 : K);
-  const T c000 = ldv<CG>(xc, nix(C, I, J, K)), c100 = ldv<CG>(xc, nix(C, I1, J, K)),
-          c010 = ldv<CG>(xc, nix(C, I, J1, K)), c110 = ldv<CG>(xc, nix(C, I1, J1, K)),
-          c001 = ldv<CG>(xc, nix(C, I, J, K1)), c101 = ldv<CG>(xc, nix(C, I1, J, K1)),
-          c011 = ldv<CG>(xc, nix(C, I, J1, K1)), c111 = ldv<CG>(xc, nix(C, I1, J1, K1));
+  const T c000 = xc[nix(C, I, J, K)], c100 = xc[nix(C, I1, J, K)], c010 = xc[nix(C, I, J1, K)],
+          c110 = xc[nix(C, I1, J1, K)], c001 = xc[nix(C, I, J, K1)], c101 = xc[nix(C, I1, J, K1)],
+          c011 = xc[nix(C, I, J1, K1)], c111 = xc[nix(C, I1, J1, K1)];
   const T h = T(0.5);
 #pragma unroll
   for (int cz = 0; cz < 2; cz++) {
@@ -1161,8 +1148,7 @@ __device__ __forceinline__ void prolong_fe_at(const Lv& F, const Lv& C, const T*
         T a2 = cx ? h * (c001 + c101) : c001, a3 = cx ? h * (c011 + c111) : c011;
         T b0 = cy ? h * (a0 + a1) : a0, b1 = cy ? h * (a2 + a3) : a2;
         const T v = cz ? h * (b0 + b1) : b0;
-        const long u = nix(F, fi, fj, fk);
-        xf[u] = ldv<CG>(xf, u) + v;
+        xf[nix(F, fi, fj, fk)] += v;
       }
     }
   }
@@ -1283,6 +1269,12 @@ __global__ void k_add_to64(const T* __restrict__ a, double* __restrict__ b, long
 // positive semi-definite with the constants as null space; the right-hand side is made
 // mean-free and so is the result)
 constexpr int COARSE_TPB = 512;
+// relative tolerance of the coarsest solve: FP64 solves to 1e-10; an FP32 V-cycle needs its
+// coarse correction to well below its own convergence factor (about 0.1), and FP32 CG on the
+// periodic coarsest levels stalls on rounding near 1e-5 (it then ran to its iteration cap), so
+// FP32 stops at 1e-3
+template <typename T>
+constexpr double coarse_tol() { return sizeof(T) == 4 ? 1e-3 : 1e-10; }
 // dynamic shared memory of the coarse solve: x, r, p, q = A p and the coefficient of the level,
 // or 0 when they do not fit next to the kernel's static shared memory (it then works on global
 // memory)
@@ -1292,15 +1284,17 @@ inline size_t coarse_smem(const Lv& L, size_t esz) {
   return need <= avail ? need : 0;
 }
 
-// sum over the block (every thread gets it): float or double per thread, FP64 across threads
-template <typename A>
-__device__ __forceinline__ double block_sum(A v, double* red) {
-  double d = (double)v;
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+// Reductions and scalars of the coarsest solve run in the storage type: FP32 levels sum and divide
+// in FP32 (the solve is a correction inside an FP32 V-cycle; FP64 shuffles and divisions on
+// GB300's narrow FP64 pipe made each iteration a long latency chain), FP64 levels in FP64.
+// sum over the block (every thread gets it), in R; red: COARSE_TPB / 32 values of shared memory
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();  // red may still be read by the previous call
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
+  R t = R(0);
   for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
   return t;
 }
@@ -1310,26 +1304,26 @@ __device__ __forceinline__ double block_sum(A v, double* red) {
 // block calls it.  red: COARSE_TPB / 32 doubles of shared memory.
 template <typename T>
 __device__ void cg_block(const Lv& L, int kind, int max_it, double rtol, T* x, T* r, T* p, T* q, const T* rho,
-                         double* red) {
+                         double* redd) {
   const long n = L.nunk;
-  using A = T;  // per-thread accumulation type
-  A loc = A(0);
+  T* red = reinterpret_cast<T*>(redd);
+  T loc = T(0);
   for (long u = threadIdx.x; u < n; u += blockDim.x) loc += r[u];
-  const double mean = block_sum(loc, red) / (double)n;
-  loc = A(0);
+  const T mean = block_sum(loc, red) / T(n);
+  loc = T(0);
   for (long u = threadIdx.x; u < n; u += blockDim.x) {
-    const T v = (T)((double)r[u] - mean);
+    const T v = r[u] - mean;
     r[u] = v;
     p[u] = v;
     x[u] = T(0);
     loc += v * v;
   }
-  double rr = block_sum(loc, red);
-  const double stop = rtol * rtol * rr;
+  T rr = block_sum(loc, red);
+  const T stop = T(rtol * rtol) * rr;
   const int ex = kind == 0 ? L.n[0] : L.nn[0], ey = kind == 0 ? L.n[1] : L.nn[1];
   for (int it = 0; it < max_it && rr > stop; it++) {
     __syncthreads();  // p complete
-    loc = A(0);
+    loc = T(0);
     for (long u = threadIdx.x; u < n; u += blockDim.x) {
       const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
       T dg;
@@ -1337,26 +1331,26 @@ __device__ void cg_block(const Lv& L, int kind, int max_it, double rtol, T* x, T
       q[u] = ap;
       loc += p[u] * ap;
     }
-    const double pq = block_sum(loc, red);
-    if (!(pq > 0.0)) break;
-    const T a = (T)(rr / pq);
-    loc = A(0);
+    const T pq = block_sum(loc, red);
+    if (!(pq > T(0))) break;
+    const T a = rr / pq;
+    loc = T(0);
     for (long u = threadIdx.x; u < n; u += blockDim.x) {
       x[u] += a * p[u];
       const T v = r[u] - a * q[u];
       r[u] = v;
       loc += v * v;
     }
-    const double rr2 = block_sum(loc, red);
-    const T beta = (T)(rr2 / rr);
+    const T rr2 = block_sum(loc, red);
+    const T beta = rr2 / rr;
     rr = rr2;
     for (long u = threadIdx.x; u < n; u += blockDim.x) p[u] = r[u] + beta * p[u];
   }
   __syncthreads();
-  loc = A(0);
+  loc = T(0);
   for (long u = threadIdx.x; u < n; u += blockDim.x) loc += x[u];
-  const double xm = block_sum(loc, red) / (double)n;
-  for (long u = threadIdx.x; u < n; u += blockDim.x) x[u] = (T)((double)x[u] - xm);
+  const T xm = block_sum(loc, red) / T(n);
+  for (long u = threadIdx.x; u < n; u += blockDim.x) x[u] = x[u] - xm;
   __syncthreads();
 }
 
@@ -1365,30 +1359,29 @@ __device__ void cg_block(const Lv& L, int kind, int max_it, double rtol, T* x, T
 template <typename T>
 __device__ void cg_warp(const Lv& L, int kind, int max_it, double rtol, T* x, T* r, T* p, T* q, const T* rho) {
   const int lane = threadIdx.x & 31;
-  const long n = L.nunk;
+  const int n = (int)L.nunk;
   auto wsum = [](T v) {
-    double d = (double)v;
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    return d;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
   };
   T loc = T(0);
-  for (long u = lane; u < n; u += 32) loc += r[u];
-  const double mean = wsum(loc) / (double)n;
+  for (int u = lane; u < n; u += 32) loc += r[u];
+  const T mean = wsum(loc) / T(n);
   loc = T(0);
-  for (long u = lane; u < n; u += 32) {
-    const T v = (T)((double)r[u] - mean);
+  for (int u = lane; u < n; u += 32) {
+    const T v = r[u] - mean;
     r[u] = v;
     p[u] = v;
     x[u] = T(0);
     loc += v * v;
   }
-  double rr = wsum(loc);
-  const double stop = rtol * rtol * rr;
+  T rr = wsum(loc);
+  const T stop = T(rtol * rtol) * rr;
   const int ex = kind == 0 ? L.n[0] : L.nn[0], ey = kind == 0 ? L.n[1] : L.nn[1];
   for (int it = 0; it < max_it && rr > stop; it++) {
     __syncwarp();  // p complete
     loc = T(0);
-    for (int u = lane; u < (int)n; u += 32) {
+    for (int u = lane; u < n; u += 32) {
       const int rw = u / ex;
       const int i = u - rw * ex, j = rw % ey, k = rw / ey;
       T dg;
@@ -1396,27 +1389,27 @@ __device__ void cg_warp(const Lv& L, int kind, int max_it, double rtol, T* x, T*
       q[u] = ap;
       loc += p[u] * ap;
     }
-    const double pq = wsum(loc);
-    if (!(pq > 0.0)) break;
-    const T a = (T)(rr / pq);
+    const T pq = wsum(loc);
+    if (!(pq > T(0))) break;
+    const T a = rr / pq;
     loc = T(0);
-    for (long u = lane; u < n; u += 32) {
+    for (int u = lane; u < n; u += 32) {
       x[u] += a * p[u];
       const T v = r[u] - a * q[u];
       r[u] = v;
       loc += v * v;
     }
-    const double rr2 = wsum(loc);
-    const T beta = (T)(rr2 / rr);
+    const T rr2 = wsum(loc);
+    const T beta = rr2 / rr;
     rr = rr2;
     __syncwarp();  // every lane has read p for its q before p changes
-    for (long u = lane; u < n; u += 32) p[u] = r[u] + beta * p[u];
+    for (int u = lane; u < n; u += 32) p[u] = r[u] + beta * p[u];
   }
   __syncwarp();
   loc = T(0);
-  for (long u = lane; u < n; u += 32) loc += x[u];
-  const double xm = wsum(loc) / (double)n;
-  for (long u = lane; u < n; u += 32) x[u] = (T)((double)x[u] - xm);
+  for (int u = lane; u < n; u += 32) loc += x[u];
+  const T xm = wsum(loc) / T(n);
+  for (int u = lane; u < n; u += 32) x[u] = x[u] - xm;
   __syncwarp();
 }
 
@@ -1447,217 +1440,6 @@ __global__ void __launch_bounds__(COARSE_TPB) k_coarse_cg(Lv L, int kind, int ma
     cg_block(L, kind, max_it, rtol, x, r, p, q, rho, red);
   if (in_smem)
     for (long u = threadIdx.x; u < n; u += blockDim.x) gx[u] = x[u];
-}
-
-// ----------------------------------------------------------------------------- coarse tail
-// The levels of a V-cycle below TAIL_MAX_UNK unknowns, from the first of them down to the
-// coarsest and back, in ONE launch of a thread-block cluster: every smoothing pass, residual,
-// transfer and the coarsest solve of those levels is one step of the kernel, separated from the
-// next by a cluster barrier (release / acquire at cluster scope; values another block wrote in
-// this launch are read from L2).  On these levels each launch of the level-by-level V-cycle is a
-// few microseconds of latency for a few thousand unknowns; here a pass costs one L2 round trip
-// and one barrier.  Each step applies the per-cell arithmetic of the corresponding level kernel
-// (rbgs_at, resid_restrict_mac_at, restrict_at, prolong_*_at, fe_node_at, cg_warp / cg_block), so
-// the tail computes the V-cycle of the level-by-level launches; MAC levels are always smoothed by
-// colour passes there.
-constexpr int TAIL_CTAS = 8, TAIL_TPB = 512, TAIL_MAXL = 8;
-constexpr long TAIL_MAX_UNK = 40000;  // 32^3 cells, 33^3 nodes
-static_assert(TAIL_TPB == COARSE_TPB, "the coarsest solve's block reductions match k_coarse_cg's");
-
-// One node of k_fe_tile's sweep (MODE 0: weighted Jacobi into out; MODE 1: residual b - K x into
-// out) with the tile's window read from global memory: the same staged values (x wrapped or
-// clamped like the tile's rows, beta 0 outside a wall) and the same order of operations.
-template <typename T, int MODE, bool CG>
-__device__ __forceinline__ void fe_node_at(const Lv& L, T w, const T* x, T* out, const T* b, const T* beta, int i,
-                                           int j, int k) {
-  const long sy = L.nn[0], sz = (long)L.nn[0] * L.nn[1];
-  const long cy = L.n[0], cz = (long)L.n[0] * L.n[1];
-  const int X[3] = {nnb(L, 0, i - 1), i, nnb(L, 0, i + 1)};
-  const int Y[3] = {nnb(L, 1, j - 1), j, nnb(L, 1, j + 1)};
-  const int Z[3] = {nnb(L, 2, k - 1), k, nnb(L, 2, k + 1)};
-  T M[3][3], C[3][3], P[3][3], Bl[2][2], Bu[2][2];
-#pragma unroll
-  for (int c = 0; c < 3; c++)
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const long r = X[a] + Y[c] * sy;
-      M[c][a] = ldv<CG>(x, r + Z[0] * sz);
-      C[c][a] = ldv<CG>(x, r + Z[1] * sz);
-      P[c][a] = ldv<CG>(x, r + Z[2] * sz);
-    }
-  const int ci[2] = {cnb(L, 0, i - 1), cnb(L, 0, i)}, cj[2] = {cnb(L, 1, j - 1), cnb(L, 1, j)};
-  const int ckl = cnb(L, 2, k - 1), cku = cnb(L, 2, k);
-#pragma unroll
-  for (int c = 0; c < 2; c++)
-#pragma unroll
-    for (int a = 0; a < 2; a++) {
-      const bool in = ci[a] >= 0 && cj[c] >= 0;
-      const long r = in ? ci[a] + cj[c] * cy : 0;
-      Bl[c][a] = in && ckl >= 0 ? beta[r + ckl * cz] : T(0);
-      Bu[c][a] = in && cku >= 0 ? beta[r + cku * cz] : T(0);
-    }
-  const T bcur = ldv<CG>(b, i + j * sy + k * sz);
-  const T s12 = cv<T>(L.s12, L.f_s12);
-  const T bsum = (Bl[0][0] + Bl[0][1]) + (Bl[1][0] + Bl[1][1]) + ((Bu[0][0] + Bu[0][1]) + (Bu[1][0] + Bu[1][1]));
-  T acc = T(0);
-#pragma unroll
-  for (int qy = 0; qy < 2; qy++)
-#pragma unroll
-    for (int qx = 0; qx < 2; qx++) acc += Bl[qy][qx] * M[2 * qy][2 * qx];
-#pragma unroll
-  for (int qy = 0; qy < 2; qy++)
-#pragma unroll
-    for (int qx = 0; qx < 2; qx++) acc += Bu[qy][qx] * P[2 * qy][2 * qx];
-#pragma unroll
-  for (int qy = 0; qy < 2; qy++)
-#pragma unroll
-    for (int qx = 0; qx < 2; qx++) acc += (Bl[qy][qx] + Bu[qy][qx]) * C[2 * qy][2 * qx];
-#pragma unroll
-  for (int qx = 0; qx < 2; qx++) acc += (Bl[0][qx] + Bl[1][qx]) * M[1][2 * qx];
-#pragma unroll
-  for (int qx = 0; qx < 2; qx++) acc += (Bu[0][qx] + Bu[1][qx]) * P[1][2 * qx];
-#pragma unroll
-  for (int qy = 0; qy < 2; qy++) acc += (Bl[qy][0] + Bl[qy][1]) * M[2 * qy][1];
-#pragma unroll
-  for (int qy = 0; qy < 2; qy++) acc += (Bu[qy][0] + Bu[qy][1]) * P[2 * qy][1];
-  const T xc = C[1][1];
-  const T diag = T(4) * bsum * s12;
-  const T ax = (T(4) * bsum * xc - acc) * s12;
-  const long u = i + j * sy + k * sz;
-  if constexpr (MODE == 0 && sizeof(T) == 4)
-    out[u] = diag > T(0) ? xc + w * __fdividef(bcur - ax, diag) : xc;
-  else if constexpr (MODE == 0)
-    out[u] = diag > T(0) ? xc + w * (bcur - ax) / diag : xc;
-  else
-    out[u] = bcur - ax;
-}
-
-template <typename T>
-struct TailArgs {
-  int kind, nl;      // solver kind; levels in the tail (the last one is the coarsest)
-  int npre, npost;   // sweeps before / after the coarse correction on the tail's other levels
-  T w;               // smoother weight
-  int cg_max_it;     // coarsest solve: iteration cap, one warp (<= 512 unknowns) or the whole block
-  int cg_warp;
-  double cg_tol;
-  Lv lv[TAIL_MAXL];
-  T* x[TAIL_MAXL];   // iterate (FE: the buffer that is current when the tail starts)
-  T* xt[TAIL_MAXL];  // FE: the other buffer of the out-of-place Jacobi sweeps
-  T* b[TAIL_MAXL];
-  T* r[TAIL_MAXL];   // FE residual
-  const T* rho[TAIL_MAXL];
-};
-
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
-}
-
-template <typename T>
-__global__ void __cluster_dims__(TAIL_CTAS, 1, 1) __launch_bounds__(TAIL_TPB, 1)
-    k_mg_tail(const __grid_constant__ TailArgs<T> A) {
-  __shared__ double red[TAIL_TPB / 32];
-  extern __shared__ __align__(16) unsigned char tail_sm[];
-  unsigned rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(rank));
-  const int tid = (int)rank * TAIL_TPB + threadIdx.x, nth = TAIL_CTAS * TAIL_TPB;  // levels hold < 2^31 unknowns
-  const int kind = A.kind, last = A.nl - 1;
-  T* xc[TAIL_MAXL];
-  T* xo[TAIL_MAXL];
-  for (int l = 0; l < A.nl; l++) {
-    xc[l] = A.x[l];
-    xo[l] = A.xt[l];
-  }
-  // sweeps on level l: MAC colour passes in place, FE Jacobi out of place (the buffers swap)
-  auto smooth = [&](int l, int sweeps, bool forward) {
-    const Lv& L = A.lv[l];
-    for (int it = 0; it < sweeps; it++) {
-      if (kind == 0) {
-        const int np = (L.n[0] + 1) / 2;
-        const int items = np * L.n[1] * L.n[2];
-        for (int q = 0; q < 2; q++) {
-          const int col = forward ? q : 1 - q;
-          for (int u = tid; u < items; u += nth) {
-            const int p = u % np, rw = u / np;
-            rbgs_at<T, true>(L, col, A.w, xc[l], A.b[l], A.rho[l], p, rw % L.n[1], rw / L.n[1]);
-          }
-          cluster_barrier();
-        }
-      } else {
-        for (int u = tid; u < (int)L.nnode; u += nth) {
-          const int rw = u / L.nn[0];
-          fe_node_at<T, 0, true>(L, A.w, xc[l], xo[l], A.b[l], A.rho[l], u % L.nn[0], rw % L.nn[1], rw / L.nn[1]);
-        }
-        cluster_barrier();
-        T* t = xc[l];
-        xc[l] = xo[l];
-        xo[l] = t;
-      }
-    }
-  };
-  // down: smooth, then the residual's restriction (the coarse iterate zeroed)
-  for (int l = 0; l < last; l++) {
-    smooth(l, A.npre, true);
-    const Lv& F = A.lv[l];
-    const Lv& C = A.lv[l + 1];
-    if (kind == 0) {
-      for (int u = tid; u < (int)C.ncell; u += nth) {
-        const int rw = u / C.n[0];
-        resid_restrict_mac_at<T, true>(F, C, xc[l], A.b[l], A.rho[l], A.b[l + 1], xc[l + 1], u % C.n[0], rw % C.n[1],
-                                       rw / C.n[1]);
-      }
-    } else {
-      for (int u = tid; u < (int)F.nnode; u += nth) {
-        const int rw = u / F.nn[0];
-        fe_node_at<T, 1, true>(F, T(0), xc[l], A.r[l], A.b[l], A.rho[l], u % F.nn[0], rw % F.nn[1], rw / F.nn[1]);
-      }
-      cluster_barrier();
-      for (int u = tid; u < (int)C.nnode; u += nth) {
-        const int rw = u / C.nn[0];
-        restrict_at<T, true>(F, C, 1, A.r[l], A.b[l + 1], xc[l + 1], u % C.nn[0], rw % C.nn[1], rw / C.nn[1]);
-      }
-    }
-    cluster_barrier();
-  }
-  // coarsest: conjugate gradients in the first block's shared memory, as k_coarse_cg
-  if (rank == 0) {
-    const Lv& L = A.lv[last];
-    const long n = L.nunk;
-    T* x = (T*)tail_sm;
-    T* r = x + n;
-    T* p = r + n;
-    T* q = p + n;
-    T* c = q + n;
-    for (long u = threadIdx.x; u < n; u += TAIL_TPB) r[u] = __ldcg(A.b[last] + u);
-    for (long u = threadIdx.x; u < L.ncell; u += TAIL_TPB) c[u] = A.rho[last][u];
-    __syncthreads();
-    if (A.cg_warp) {
-      if (threadIdx.x < 32) {
-        cg_warp(L, kind, A.cg_max_it, A.cg_tol, x, r, p, q, c);
-        for (long u = threadIdx.x; u < n; u += 32) xc[last][u] = x[u];
-      }
-    } else {
-      cg_block(L, kind, A.cg_max_it, A.cg_tol, x, r, p, q, c, red);
-      for (long u = threadIdx.x; u < n; u += TAIL_TPB) xc[last][u] = x[u];
-    }
-  }
-  cluster_barrier();
-  // up: prolongation of the correction, then smoothing
-  for (int l = last - 1; l >= 0; l--) {
-    const Lv& F = A.lv[l];
-    const Lv& C = A.lv[l + 1];
-    const int ex = kind == 0 ? C.n[0] : C.nn[0], ey = kind == 0 ? C.n[1] : C.nn[1];
-    const int items = (int)(kind == 0 ? C.ncell : C.nnode);
-    for (int u = tid; u < items; u += nth) {
-      const int rw = u / ex;
-      if (kind == 0)
-        prolong_mac_at<T, true>(F, C, xc[l + 1], xc[l], u % ex, rw % ey, rw / ey);
-      else
-        prolong_fe_at<T, true>(F, C, xc[l + 1], xc[l], u % ex, rw % ey, rw / ey);
-    }
-    cluster_barrier();
-    smooth(l, A.npost, false);
-  }
 }
 
 }  // namespace
@@ -1692,8 +1474,6 @@ struct MGSolver {
   int* nonfinite = nullptr;  // device flag set when a mean or norm of a solve is not finite
   int zc0_auto = 0;          // z-chunk of the finest level's fused sweep from the wave heuristic
   int fe_zc0 = 0;            // z-chunk of the finest level's FE tiles (0: the heuristic)
-  int lt = 0;                // first level of the one-launch coarse tail (0: the hierarchy has none)
-  int tail = 0;              // run the coarse tail as one launch (0: level by level)
   size_t bytes = 0;          // device bytes requested
 };
 
@@ -1715,8 +1495,6 @@ void mg_set_inner(MGSolver* m, int inner) {
 }
 void mg_set_warm(MGSolver* m, int warm) { m->warm = warm != 0; }
 void mg_set_nonfinite_flag(MGSolver* m, int* flag) { m->nonfinite = flag; }
-void mg_set_tail(MGSolver* m, int on) { m->tail = on != 0; }
-int mg_tail_levels(const MGSolver* m) { return m->lt > 0 && m->tail ? m->nlev - m->lt : 0; }
 void mg_set_sweep(MGSolver* m, int fused) { m->sweep = fused < 0 ? 0 : (fused > 2 ? 2 : fused); }
 void mg_set_block(MGSolver* m, int by) {
   if (by == 1 || by == 2 || by == 4 || by == 8) m->by = by;
@@ -1810,13 +1588,6 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
   }
   alloc((void**)&m->part, (size_t)(nbr > RED_BLOCKS ? nbr : RED_BLOCKS) * sizeof(double));
   alloc((void**)&m->scal, 8 * sizeof(double));
-  // the coarse tail: from the first level below TAIL_MAX_UNK unknowns (never the finest) to the
-  // coarsest, when there are at least two such levels and the coarsest fits in shared memory
-  for (int l = 1; l < m->nlev; l++)
-    if (m->lv[l].nunk <= TAIL_MAX_UNK) {
-      if (m->nlev - l >= 2 && m->nlev - l <= TAIL_MAXL && coarse_smem(m->lv[m->nlev - 1], m->esz) > 0) m->lt = l;
-      break;
-    }
   if (!dry) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&m->hpin, 8 * sizeof(double));
     // the coarsest level lives in shared memory during its solve (when it fits): opt in to its
@@ -1833,14 +1604,7 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
         e = cudaFuncSetAttribute(k_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) opted[prec_fp32 ? 1 : 0] = smem;
     }
-    static size_t opted_tail[2] = {0, 0};
-    if (e == cudaSuccess && m->lt > 0 && smem > opted_tail[prec_fp32 ? 1 : 0]) {
-      if (prec_fp32)
-        e = cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      else
-        e = cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) opted_tail[prec_fp32 ? 1 : 0] = smem;
-    }
+
     // the fused sweep's staging ring (beyond the 48 KB default) with the largest shared-memory
     // carveout, so that three blocks fit on an SM; once per process
     static bool sweep_opted = false;
@@ -2023,44 +1787,9 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
   }
 }
 
-// the levels from m->lt down in one cluster launch (k_mg_tail); afterwards the FE levels' iterate
-// pointers are where the level-by-level sweeps would have left them
-template <typename T>
-void launch_tail(MGSolver* m, cudaStream_t s) {
-  TailArgs<T> A;
-  memset(&A, 0, sizeof A);
-  A.kind = m->kind;
-  A.nl = m->nlev - m->lt;
-  A.npre = m->cpre >= 0 ? m->cpre : m->pre;
-  A.npost = m->cpost >= 0 ? m->cpost : m->post;
-  A.w = T(m->omega);
-  const Lv& Lc = m->lv[m->nlev - 1];
-  const int nmax = std::max(Lc.n[0], std::max(Lc.n[1], Lc.n[2]));
-  A.cg_max_it = 8 * nmax + 64;  // as the level-by-level coarsest solve
-  A.cg_tol = sizeof(T) == 4 ? 1e-5 : 1e-10;
-  A.cg_warp = Lc.nunk <= 512;
-  for (int i = 0; i < A.nl; i++) {
-    const int l = m->lt + i;
-    A.lv[i] = m->lv[l];
-    A.x[i] = (T*)m->x[l];
-    A.xt[i] = (T*)m->xt[l];
-    A.b[i] = (T*)m->b[l];
-    A.r[i] = (T*)m->r[l];
-    A.rho[i] = (const T*)m->rho[l];
-  }
-  k_mg_tail<T><<<TAIL_CTAS, TAIL_TPB, coarse_smem(Lc, sizeof(T)), s>>>(A);
-  rmt_count_launches(1);
-  if (m->kind == 1 && ((A.npre + A.npost) & 1))
-    for (int i = 0; i + 1 < A.nl; i++) std::swap(m->x[m->lt + i], m->xt[m->lt + i]);
-}
-
 template <typename T>
 void vcycle(MGSolver* m, int l, cudaStream_t s) {
   const Lv& L = m->lv[l];
-  if (l > 0 && l == m->lt && m->tail) {
-    launch_tail<T>(m, s);
-    return;
-  }
   if (l == m->nlev - 1) {
     int nmax = L.n[0];
     if (L.n[1] > nmax) nmax = L.n[1];
@@ -2068,7 +1797,7 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
     // conjugate gradients converge in O(nmax) iterations on this level; the cap only bounds
     // the launch, the tolerance ends it
     const int max_it = 8 * nmax + 64;
-    const double tol = sizeof(T) == 4 ? 1e-5 : 1e-10;
+    const double tol = coarse_tol<T>();
     const size_t smem = coarse_smem(L, sizeof(T));  // opted in at creation
     // as many warps as the level has unknowns for, and a single warp (reductions by shuffles, no
     // block barriers) up to 512 unknowns: a small level's iterations are bound by the reductions
