@@ -535,7 +535,7 @@ rmt_status step_t(rmt_grid* g) {
   // 1. tau^n and its divergence
   pb(g, P_STRESS_N);
   CK(g, launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 0), nb, g->bb_all + 6 * cur, 12, g->t_d, 0.0,
-                              (T*)g->divn, g->slist, g->scount, s));
+                              (T*)g->divn, g->slist, g->scount, slopes, s));
   pe(g, P_STRESS_N);
   // 2. Godunov face states of u (transverse bar states first)
   pb(g, P_GODUNOV);
@@ -595,7 +595,7 @@ rmt_status step_t(rmt_grid* g) {
   // 8. tau^{n+1/2}; 9. rho^{n+1/2}; 10. u*
   pb(g, P_STRESS_H);
   CK(g, launch_stress_div<T>(G, u, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, g->t_d,
-                              0.5 * G.dt, (T*)g->divh, g->slist, g->scount, s));
+                              0.5 * G.dt, (T*)g->divh, g->slist, g->scount, slopes, s));
   pe(g, P_STRESS_H);
   pb(g, P_USTAR);
   launch_density<T>(G, g->bodies_d, views<T>(g, cur, 1), nb, g->bb_all + 6 * nxt, 12, (T*)g->rho_h, s);

@@ -301,32 +301,59 @@ __global__ void k_mac_rhs(Geo g, FacePtrs3 un, MGVec b) {
   }
 }
 
-template <typename T, int d>
-__global__ void k_mac_correct(Geo g, const T* __restrict__ un, const T* __restrict__ rho, MGVec q,
-                              T* __restrict__ umac) {
-  const int ex = g.n[0] + (d == 0), ey = g.n[1] + (d == 1);
+// The three directions' corrections in one pass: one thread per point (i, j, k) of the
+// (n0+1) x (n1+1) x (n2+1) lattice of face corners handles the x-, y- and z-faces with that
+// index (those that exist), so the cell above the three faces, (i, j, k), has its q and rho read
+// once for all of them.  Face coefficient 1/rho_face with rho_face the mean of the two cells.
+struct Umac3 {
+  const void* un[3];
+  void* um[3];
+};
+template <typename T>
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_mac_correct3(Geo g, Umac3 F, const T* __restrict__ rho, MGVec q) {
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y, k = blockIdx.z;
+  if (i > g.n[0] || j > g.n[1] || k > g.n[2]) return;
   const T fac = cv<T>(g.hdt_h, g.f.hdt_h);
-  GRID_LOOP(f, nfaces(g, d)) {
-    int i, j, k;
-    decode(f, ex, ey, i, j, k);
-    const int fi = d == 0 ? i : (d == 1 ? j : k);
-    if (is_wall_face(g, d, fi)) {
-      umac[f] = un[f];
+  const bool bin = i < g.n[0] && j < g.n[1] && k < g.n[2];  // the cell above the faces exists
+  long cb = 0;
+  T rb = T(0), qbh = T(0), qbl = T(0);
+  if (bin) {
+    cb = cidx(g, i, j, k);
+    rb = rho[cb];
+    if constexpr (sizeof(T) == 8)
+      qbh = q.d[cb];
+    else {
+      qbh = q.h[cb];
+      qbl = q.l[cb];
+    }
+  }
+  const int ii[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    // the d-face (i, j, k) exists where the other two indices are cells
+    if (ii[(d + 1) % 3] >= g.n[(d + 1) % 3] || ii[(d + 2) % 3] >= g.n[(d + 2) % 3]) continue;
+    const long f = fidx(g, d, i, j, k);
+    const T* un = (const T*)F.un[d];
+    T* um = (T*)F.um[d];
+    if (is_wall_face(g, d, ii[d])) {
+      um[f] = un[f];
       continue;
     }
-    int a[3] = {i, j, k};
+    int a[3] = {i, j, k}, b[3] = {i, j, k};
     a[d] -= 1;
-    long ca, cb;
+    long ca, cbb;
     cell_at(g, a[0], a[1], a[2], ca);
-    cell_at(g, i, j, k, cb);
-    // face coefficient 1/rho_face, rho_face the mean of the two cells
-    const T beta = T(2) / (rho[ca] + rho[cb]);
+    const bool own = bin;  // the upper cell is (i, j, k) itself unless the face is the periodic end
+    if (!own) cell_at(g, b[0], b[1], b[2], cbb);
+    else cbb = cb;
+    const T ra = rho[ca], rbb = own ? rb : rho[cbb];
+    const T beta = T(2) / (ra + rbb);
     T dq;
     if constexpr (sizeof(T) == 8)
-      dq = q.d[cb] - q.d[ca];
+      dq = (own ? qbh : q.d[cbb]) - q.d[ca];
     else
-      dq = ff_diff(q.h[cb], q.l[cb], q.h[ca], q.l[ca]);
-    umac[f] = un[f] - fac * beta * dq;
+      dq = own ? ff_diff(qbh, qbl, q.h[ca], q.l[ca]) : ff_diff(q.h[cbb], q.l[cbb], q.h[ca], q.l[ca]);
+    um[f] = un[f] - fac * beta * dq;
   }
 }
 
@@ -576,11 +603,14 @@ void launch_mac_setup(const Geo& g, T* const uf[3][3], MGVec b64, cudaStream_t s
 template <typename T>
 void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, MGVec q, T* const umac[3],
                         cudaStream_t s) {
+  Umac3 F;
   for (int d = 0; d < 3; d++) {
-    auto kc = d == 0 ? k_mac_correct<T, 0> : (d == 1 ? k_mac_correct<T, 1> : k_mac_correct<T, 2>);
-    kc<<<nblocks(nfaces(g, d)), TPB, 0, s>>>(g, uf[d][d], rho, q, umac[d]);
-    rmt_count_launches(1);
+    F.un[d] = uf[d][d];
+    F.um[d] = umac[d];
   }
+  const dim3 gr((g.n[0] + 1 + TILE_X - 1) / TILE_X, (g.n[1] + 1 + TILE_Y - 1) / TILE_Y, g.n[2] + 1);
+  k_mac_correct3<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, F, rho, q);
+  rmt_count_launches(1);
 }
 template <typename T>
 void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cudaStream_t s) {

@@ -26,12 +26,13 @@ struct Faces3 {
 
 // ---- flow (rmt_flow.cu) -------------------------------------------------------------
 // bbs: band boxes of the bodies (6 ints each, stride ints apart) of the time level of views;
-// list (N ints) and count: scratch for the cells a band reaches
+// list (N ints) and count: scratch for the cells a band reaches; rows: nine cell arrays of
+// scratch for the face rows of those cells (the Godunov slope arrays, free at both stress passes)
 // t: device pointer to the simulated time; the stress is evaluated at *t + toff
 template <typename T>
 cudaError_t launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
                               const int* bbs, int bstride, const double* t, double toff, T* out, int* list,
-                              int* count, cudaStream_t s);
+                              int* count, T* const rows[9], cudaStream_t s);
 void launch_tick(double* t, double dt, cudaStream_t s);
 // slopes: nine cell arrays, written by launch_bar_states (limited slope of u_a along d at 3d+a)
 // and read by launch_face_states

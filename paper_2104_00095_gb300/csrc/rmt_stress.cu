@@ -1,8 +1,9 @@
 // Stress kernel of the RMT per-step update (arXiv 2104.00095, SI "Stress calculations",
 // eq. mixed_stresses and the multi-body rule; main text "Swimming" for the active stress).
-// Two passes: every cell that no body's band reaches takes the pure-fluid divergence at once
+// Three passes: every cell that no body's band reaches takes the pure-fluid divergence at once
 // and the rest are listed; then one thread per listed cell computes the face-normal rows of the
-// blended stress at its six faces and their divergence.  Templated on T.
+// blended stress at its three lower faces, and one per listed cell their divergence.  Templated
+// on T.
 //
 // FP32 storage holds S = xi - x0 (rmt_common.cuh): the stencil differences give grad S =
 // grad xi - I, and the neo-Hookean stress is formed from it without cancellation: with
@@ -283,15 +284,50 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T*
   }
 }
 
-// Pass 2, the listed cells (a body's band reaches them): blended face rows at the six faces,
-// one thread per cell, so every lane of a warp takes the same long path.
+// Pass 2, the listed cells (a body's band reaches them): the blended face row of each listed
+// cell's three lower faces (the face below the cell along d), one thread per cell, into rows
+// (nine cell arrays, row component a of the d-face at 3d+a).  A face row depends only on the face:
+// a body contributes where it holds both cells of the face, and every such body is in the mask of
+// either cell, so each face is computed once.
+struct Rows9 {
+  void* r[9];
+};
+template <typename T>
+__global__ void __launch_bounds__(128) k_stress_rows(Geo g, const T* __restrict__ u, const Body* __restrict__ bodies,
+                                                      const BodyView<T>* __restrict__ views, int nb,
+                                                      const int* __restrict__ bbs, int bstride,
+                                                      const double* __restrict__ t, double toff,
+                                                      const int* __restrict__ list, const int* __restrict__ count,
+                                                      Rows9 R) {
+  __shared__ int sbb[6 * RMT_MAX_BODIES];
+  stage_boxes(bbs, bstride, nb, sbb);
+  const int n = *count;
+  const T tt = (T)(*t + toff);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const long c = list[e];
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
+    const uint64_t bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      T rm[3];
+      face_row(g, u, bodies, views, bm, d, i, j, k, tt, rm);
+#pragma unroll
+      for (int a = 0; a < 3; a++) ((T*)R.r[3 * d + a])[c] = rm[a];
+    }
+  }
+}
+
+// Pass 3, the listed cells: divergence of the face rows.  The upper face along d is the lower
+// face of the neighbour above: its row is read from rows where that neighbour is listed, and
+// computed here otherwise (the band region's outer faces and the faces on a wall).
 template <typename T>
 __global__ void __launch_bounds__(128) k_stress_band(Geo g, const T* __restrict__ u, const Body* __restrict__ bodies,
                                                       const BodyView<T>* __restrict__ views, int nb,
                                                       const int* __restrict__ bbs, int bstride,
                                                       const double* __restrict__ t, double toff,
                                                       const int* __restrict__ list, const int* __restrict__ count,
-                                                      T* __restrict__ out) {
+                                                      Rows9 R, T* __restrict__ out) {
   __shared__ int sbb[6 * RMT_MAX_BODIES];
   stage_boxes(bbs, bstride, nb, sbb);
   const int n = *count;
@@ -301,17 +337,27 @@ __global__ void __launch_bounds__(128) k_stress_band(Geo g, const T* __restrict_
     const long c = list[e];
     int i, j, k;
     decode(c, g.n[0], g.n[1], i, j, k);
-    const uint64_t bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+    uint64_t bm = 0;
+    bool have_bm = false;
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       int ip[3] = {i, j, k};
       ip[d] += 1;
-      T rp[3], rm[3];
-      face_row(g, u, bodies, views, bm, d, ip[0], ip[1], ip[2], tt, rp);
-      face_row(g, u, bodies, views, bm, d, i, j, k, tt, rm);
+      T rp[3];
+      long cn;
+      if (cell_at(g, ip[0], ip[1], ip[2], cn) && cell_bodies(g, views, nb, sbb, ip[0], ip[1], ip[2], cn) != 0) {
 #pragma unroll
-      for (int a = 0; a < 3; a++) acc[a] += (rp[a] - rm[a]) * ih;
+        for (int a = 0; a < 3; a++) rp[a] = ((const T*)R.r[3 * d + a])[cn];
+      } else {
+        if (!have_bm) {
+          bm = cell_bodies(g, views, nb, sbb, i, j, k, c);
+          have_bm = true;
+        }
+        face_row(g, u, bodies, views, bm, d, ip[0], ip[1], ip[2], tt, rp);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; a++) acc[a] += (rp[a] - ((const T*)R.r[3 * d + a])[c]) * ih;
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) out[a * g.N + c] = acc[a];
@@ -323,23 +369,29 @@ __global__ void __launch_bounds__(128) k_stress_band(Geo g, const T* __restrict_
 template <typename T>
 cudaError_t launch_stress_div(const Geo& g, const T* u, const Body* bodies, const BodyView<T>* views, int nb,
                               const int* bbs, int bstride, const double* t, double toff, T* out, int* list,
-                              int* count, cudaStream_t s) {
+                              int* count, T* const rows[9], cudaStream_t s) {
   const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + SFZ - 1) / SFZ);
   const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_stress_fluid<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, views, nb, bbs, bstride, out, list, count);
   rmt_count_launches(1);
   if (nb == 0) return cudaSuccess;
-  k_stress_band<T><<<sm_count() * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, out);
+  Rows9 R;
+  for (int q = 0; q < 9; q++) R.r[q] = rows[q];
+  k_stress_rows<T><<<sm_count() * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, R);
+  rmt_count_launches(1);
+  k_stress_band<T><<<sm_count() * 8, 128, 0, s>>>(g, u, bodies, views, nb, bbs, bstride, t, toff, list, count, R,
+                                                  out);
   rmt_count_launches(1);
   return cudaSuccess;
 }
 
 template cudaError_t launch_stress_div<float>(const Geo&, const float*, const Body*, const BodyView<float>*, int,
-                                              const int*, int, const double*, double, float*, int*, int*, cudaStream_t);
+                                              const int*, int, const double*, double, float*, int*, int*,
+                                              float* const[9], cudaStream_t);
 template cudaError_t launch_stress_div<double>(const Geo&, const double*, const Body*, const BodyView<double>*, int,
                                                const int*, int, const double*, double, double*, int*, int*,
-                                               cudaStream_t);
+                                               double* const[9], cudaStream_t);
 
 // simulated time on the device: t += dt after each step (read by the stress kernels, so that a
 // captured step graph needs no per-step parameter)
