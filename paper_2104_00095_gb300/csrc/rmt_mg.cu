@@ -540,6 +540,28 @@ __global__ void __launch_bounds__(BX* BYMAX) k_rbgs(Lv L, int colour, T w, T* __
   rbgs_at(L, colour, w, x, b, rho, p, j, (int)blockIdx.z);
 }
 
+// weighted Jacobi sweep of the 7-point operator, out of place (x -> xo): the smoother of MAC
+// levels with an odd periodic side, where a red-black colouring is not consistent across the wrap
+// (two neighbours of one colour would update in the same pass)
+constexpr double MAC_JACOBI_W = 6.0 / 7.0;
+template <typename T>
+__global__ void __launch_bounds__(BX* BYMAX) k_jacobi_mac(Lv L, T w, const T* __restrict__ x, T* __restrict__ xo,
+                                                        const T* __restrict__ b, const T* __restrict__ rho) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  T dg;
+  const T ax = mac_op<T, true>(L, x, rho, i, j, k, dg);
+  const long c = cix(L, i, j, k);
+  T v = x[c];
+  if (dg > T(0)) {
+    if constexpr (sizeof(T) == 4) v = v + w * ((b[c] - ax) * rcp_approx(dg));
+    else v = v + w * ((b[c] - ax) / dg);
+  }
+  xo[c] = v;
+}
+
 // Asynchronous global -> shared copies (cp.async, 4 or 8 bytes; size 0 fills zeros), so that
 // several planes of a stencil tile are in flight while one is computed.
 template <typename T>
@@ -1468,6 +1490,7 @@ struct MGSolver {
   int sweep = 1;
   int zc[16] = {};      // z-chunk of k_rbgs_sweep per level (0: the level's layout does not allow it)
   bool big[16] = {};    // level large enough for the fused sweep to pay
+  bool jac[16] = {};    // MAC level with an odd periodic side: Jacobi sweeps instead of red-black
   double omega = 0.9;
   mg_hook_fn hook = nullptr;
   void* hook_ctx = nullptr;
@@ -1560,17 +1583,20 @@ MGSolver* mg_build(const Geo& g, int kind, int prec_fp32, bool dry, cudaError_t*
     L.f_s12_lo = (float)(L.s12 - (double)L.f_s12);
     m->lv[l] = L;
     m->nlev = l + 1;
+    for (int d = 0; d < 3; d++)
+      if (kind == 0 && L.per[d] && (L.n[d] & 1)) m->jac[l] = true;
     const size_t vb = (size_t)L.nunk * m->esz;
     alloc(&m->x[l], vb);
     alloc(&m->xt[l], vb);
     alloc(&m->b[l], vb);
     alloc(&m->r[l], vb);
     if (l > 0 || kind == 1) alloc(&m->rho[l], (size_t)L.ncell * m->esz);
-    // coarsen while every axis halves to an even-enough size
+    // coarsen while every axis is even and halves to at least 3 (a MAC level with an odd periodic
+    // side is smoothed by Jacobi sweeps, see jac)
     bool can = true;
     for (int d = 0; d < 3; d++) {
       const int h2 = L.n[d] / 2;
-      if ((L.n[d] & 1) || h2 < 3 || (L.per[d] && (h2 & 1))) can = false;
+      if ((L.n[d] & 1) || h2 < 3) can = false;
     }
     if (!can || l == 15) break;
     for (int d = 0; d < 3; d++) L.n[d] /= 2;
@@ -1760,7 +1786,16 @@ void smooth(MGSolver* m, int l, int sweeps, bool forward, cudaStream_t s) {
         continue;
       }
     }
-    if (m->kind == 0) {
+    if (m->kind == 0 && m->jac[l]) {
+      hk(m, l, 0, 1, s);
+      k_jacobi_mac<T><<<grid3(L.n[0], L.n[1], L.n[2], m->by), dim3(BX, m->by), 0, s>>>(
+          L, T(MAC_JACOBI_W), (const T*)m->x[l], (T*)m->xt[l], b, rho);
+      rmt_count_launches(1);
+      hk(m, l, 0, 0, s);
+      void* t = m->x[l];
+      m->x[l] = m->xt[l];
+      m->xt[l] = t;
+    } else if (m->kind == 0) {
       const dim3 gr(((L.n[0] + 1) / 2 + BX - 1) / BX, (L.n[1] + m->by - 1) / m->by, L.n[2]);
       for (int q = 0; q < 2; q++) {
         const int col = forward ? q : 1 - q;

@@ -327,8 +327,10 @@ def test_full_size_properties(cfg):
 
 @pytest.mark.parametrize("n,prec", [(44, "fp64"), (112, "fp32")])
 def test_uneven_multigrid_hierarchies(n, prec):
-    """Periodic sizes whose coarsening stops early: 44 -> 22 (the coarsest level of the FP64
-    path does not fit in shared memory) and 112 -> 14 (a large shared-memory coarse level)."""
+    """Periodic sizes whose hierarchy reaches odd levels: 44 -> 22 -> 11 and 112 -> 56 -> 28 ->
+    14 -> 7, where the MAC smoother switches to Jacobi sweeps (an odd periodic side has no
+    consistent red-black colouring; the finest level itself must have even periodic sides, which
+    rmt_create_grid checks)."""
     sc = S.swimmers(n=n, nbodies=1, seed=21, precision=prec)
     g = rmt.Grid(sc)
     if prec == "fp64":
