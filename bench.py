@@ -303,7 +303,7 @@ def batched_leg(args, stream) -> dict:
             tuned[n] = g.autotune(1e-6)
     tune_s = time.perf_counter() - t0
     keys = ("mac_pre", "mac_post", "mac_inner", "mac_block", "mac_cycles", "fe_pre", "fe_post", "fe_inner",
-            "fe_block", "fe_omega", "fe_cycles", "mac_zchunk", "fe_zchunk")
+            "fe_block", "fe_omega", "fe_cycles", "mac_zchunk", "fe_zchunk", "mac_omega")
     for g, sc in zip(grids, scenes):
         for k in keys:
             g.set_option(k, tuned[sc["n"][0]][k])

@@ -204,8 +204,9 @@ rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]);
 /* Autotuner of the two multigrid solves (no paper counterpart: the paper's multigrid library
  * is not described).  On the right-hand sides of the grid's last step (RMT_ESTATE before the
  * first step) it tries, per solver, smoother sweeps before/after the coarse correction (1..4
- * for the 7-point solve, 1..3 for the nodal one), the Jacobi weight of the nodal smoother (0.8,
- * 0.9, 1.0) and 1, 2 or 4 V-cycles per high-precision residual: for each, it counts the V-cycles
+ * for the 7-point solve, 1..3 for the nodal one), the relaxation factor of the red-black sweeps
+ * (1.0, 1.15), the Jacobi weight of the nodal smoother (0.8, 0.9, 1.0) and 1, 2 or 4 V-cycles per
+ * high-precision residual: for each, it counts the V-cycles
  * needed to reach the relative residual rtol and times that many with CUDA events.  It then
  * times the block height of the level kernels (1, 2, 4, 8 rows of 32 threads) for the fastest
  * schedule, and the z-chunk length of the finest level's plane-marching stencil tiles (the fused
@@ -223,6 +224,7 @@ typedef struct {
   double mac_ms, fe_ms; /* time of one solve with the chosen settings */
   int trials;           /* schedules and shapes tried */
   int mac_zchunk, fe_zchunk; /* z-chunk of the finest level's plane-marching tiles (0: default) */
+  double mac_omega;          /* relaxation factor of the red-black sweeps */
 } rmt_tune_result;
 rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* out);
 

@@ -48,15 +48,16 @@ void apply(MGSolver* m, const Sched& c) {
 int tune_one(MGSolver* m, int kind, double rtol, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, Sched& best,
              double& best_ms, int& trials, int& zchunk) {
   const int nsw = kind == 0 ? 4 : 3;
-  const double omegas_fe[3] = {0.8, 0.9, 1.0};
-  const int nom = kind == 0 ? 1 : 3;
+  // relaxation factors: red-black sweeps (1 and an over-relaxed 1.15), Jacobi weights
+  const double omegas[2][3] = {{1.0, 1.15, 0.0}, {0.8, 0.9, 1.0}};
+  const int nom = kind == 0 ? 2 : 3;
   int best_cyc = -1;
   best_ms = 1e300;
   for (int pre = 1; pre <= nsw; pre++)
     for (int post = 1; post <= nsw; post++)
       for (int io = 0; io < nom; io++)
         for (int inner : {1, 2, 4}) {
-          const Sched c{pre, post, inner, 4, kind == 0 ? 1.0 : omegas_fe[io]};
+          const Sched c{pre, post, inner, 4, omegas[kind][io]};
           apply(m, c);
           cudaError_t e = cudaSuccess;
           const int cyc = mg_solve(m, rtol, 40, 0, s, &e);
@@ -131,7 +132,7 @@ extern "C" rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* ou
               {"mac_block", (double)bm.block}, {"mac_cycles", (double)cm}, {"fe_pre", (double)bf.pre},
               {"fe_post", (double)bf.post}, {"fe_inner", (double)bf.inner}, {"fe_block", (double)bf.block},
               {"fe_omega", bf.omega}, {"fe_cycles", (double)cf}, {"mac_zchunk", (double)zm},
-              {"fe_zchunk", (double)zf}};
+              {"fe_zchunk", (double)zf}, {"mac_omega", bm.omega}};
   for (const auto& o : opts)
     if ((st = rmt_set_option(g, o.name, o.v)) != RMT_OK) return st;
   if (out) {
@@ -151,6 +152,7 @@ extern "C" rmt_status rmt_autotune(rmt_grid* g, double rtol, rmt_tune_result* ou
     out->trials = trials;
     out->mac_zchunk = zm;
     out->fe_zchunk = zf;
+    out->mac_omega = bm.omega;
   }
   return RMT_OK;
 }

@@ -68,6 +68,7 @@ class rmt_tune_result(C.Structure):
         ("mac_cycles", C.c_int), ("fe_pre", C.c_int), ("fe_post", C.c_int), ("fe_inner", C.c_int),
         ("fe_block", C.c_int), ("fe_cycles", C.c_int), ("fe_omega", C.c_double), ("mac_ms", C.c_double),
         ("fe_ms", C.c_double), ("trials", C.c_int), ("mac_zchunk", C.c_int), ("fe_zchunk", C.c_int),
+        ("mac_omega", C.c_double),
     ]
 
 
