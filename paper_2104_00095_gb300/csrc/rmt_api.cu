@@ -104,6 +104,7 @@ struct rmt_grid {
   void* xscr_s[9] = {};
   void* xscr_b[9] = {};
   int8_t* xscr_ok[3] = {};
+  int8_t* xscr_ok2[3] = {};  // the second predictor scratch set's flags (its arrays: slopes, wcell)
   void* vadv[3] = {};
   void* ub[3][3] = {};
   void* slopes[9] = {};
@@ -393,6 +394,8 @@ rmt_status alloc_t(rmt_grid* g) {
       AL(g->xscr_b[q], N * e);
     }
     for (int q = 0; q < 3; q++) AL(g->xscr_ok[q], N);
+    if (g->bodies.size() > 1)
+      for (int q = 0; q < 3; q++) AL(g->xscr_ok2[q], N);
   }
   for (int d = 0; d < 3; d++) {
     const long nf = nfaces(G, d);
@@ -566,12 +569,25 @@ rmt_status step_t(rmt_grid* g) {
   // 4. advective term
   launch_advect<T>(G, uf, umac, (T*)g->adv, s);
   pe(g, P_MAC_CORR_ADV);
-  // 5. predictor of every body (they share the predictor's scratch, so one after another)
+  // 5. predictor of every body.  Two scratch sets: the predictor's own and the Godunov slope and
+  // cell-state arrays (free from the Godunov stage until the half-step stress), so the even
+  // bodies run one after another on the step's stream and the odd ones on a second stream
   pb(g, P_XI_PRED);
+  cudaStream_t s2 = nb > 1 ? g->body_s[1] : s;
+  if (nb > 1) {
+    CK(g, cudaEventRecord(g->ev_fork, s));
+    CK(g, cudaStreamWaitEvent(s2, g->ev_fork, 0));
+  }
   for (int m = 0; m < nb; m++) {
     BodyMem& b = g->bm[m];
+    const bool odd = (m & 1) != 0;
     launch_xi_predict<T>(G, u, vadv, uf, umac, b.bb + 6 * cur, b.blocks, (const T*)b.X[cur], b.LAY[cur],
-                         (T* const*)g->xscr_s, (T* const*)g->xscr_b, g->xscr_ok, (T*)b.X[nxt], s);
+                         odd ? slopes : (T* const*)g->xscr_s, odd ? wcell : (T* const*)g->xscr_b,
+                         odd ? g->xscr_ok2 : g->xscr_ok, (T*)b.X[nxt], odd ? s2 : s);
+  }
+  if (nb > 1) {
+    CK(g, cudaEventRecord(g->ev_join[1], s2));
+    CK(g, cudaStreamWaitEvent(s, g->ev_join[1], 0));
   }
   pe(g, P_XI_PRED);
   // 6.-7. re-extrapolation and corrector: the bodies are independent, so each runs on its own
