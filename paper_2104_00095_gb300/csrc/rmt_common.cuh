@@ -444,14 +444,33 @@ __device__ __forceinline__ Win make_win(const Geo& g, const int* bb, int dil) {
   }
   return w;
 }
+// (a, b, c) of the linear index t on an n0 x n1 x .. box, a fastest.  32-bit arithmetic while t
+// fits: a 64-bit integer division is a long emulated instruction sequence on the GPU, which
+// dominated the grid-stride kernels that decoded every index with it.
+__device__ __forceinline__ void split3(long t, int n0, int n1, int& a, int& b, int& c) {
+  if (t <= 0x7fffffffL) {
+    const unsigned tu = (unsigned)t, r = tu / (unsigned)n0, q = r / (unsigned)n1;
+    a = (int)(tu - r * (unsigned)n0);
+    b = (int)(r - q * (unsigned)n1);
+    c = (int)q;
+  } else {
+    const long r = t / n0, q = r / n1;
+    a = (int)(t - r * n0);
+    b = (int)(r - q * n1);
+    c = (int)q;
+  }
+}
+// cell or node coordinates of a linear index on an nx x ny x .. grid
+__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) { split3(c, nx, ny, i, j, k); }
+
 // t-th cell of a window: unwrapped coordinates u[] and the wrapped cell index c
 __device__ __forceinline__ void win_cell(const Geo& g, const Win& w, long t, int u[3], int& i, int& j, int& k,
                                          long& c) {
-  const int a = (int)(t % w.ext[0]);
-  const long r = t / w.ext[0];
+  int a, b, cc;
+  split3(t, w.ext[0], w.ext[1], a, b, cc);
   u[0] = w.lo[0] + a;
-  u[1] = w.lo[1] + (int)(r % w.ext[1]);
-  u[2] = w.lo[2] + (int)(r / w.ext[1]);
+  u[1] = w.lo[1] + b;
+  u[2] = w.lo[2] + cc;
   int v[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) {

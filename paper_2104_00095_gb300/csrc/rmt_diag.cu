@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(DTPB) k_body_stats(Geo g, const T* __restrict_
     if (!(w > 0.0)) continue;
     for (int a = 0; a < 3; a++) acc[a] += w * (double)u[a * g.N + c];
     acc[3] += w;
-    const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
     const int ii[3] = {i, j, k};
     double A[9];
     bool ok = true;

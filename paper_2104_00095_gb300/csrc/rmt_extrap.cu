@@ -21,13 +21,6 @@ inline int nblocks(long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(c % nx);
-  long r = c / nx;
-  j = (int)(r % ny);
-  k = (int)(r / ny);
-}
-
 // xi^0 = x at every cell; on a periodic axis the image of x nearest the body centre (FP32
 // storage: the displacement from the cell's image, zero)
 template <typename T>
@@ -343,7 +336,8 @@ __global__ void __launch_bounds__(TPB, WLS_MINB(T, REDO)) k_wls(Geo g, Body b, i
   for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
     const long c = src[e];
     if (REDO && lay[c] != l) continue;  // listed by an earlier layer's pass
-    const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
     double out[3];
     const int r = wls_cell_warp<AT>(g, b, x, lay, i, j, k, l, out);
     __syncwarp();
@@ -422,7 +416,8 @@ __global__ void __launch_bounds__(TPB, WLS_MINB(T, REDO)) k_wls_half(Geo g, Body
   for (int e = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < n; e += (gridDim.x * blockDim.x) >> 5) {
     const long c = src[e];
     if (layn[c] != l || lay[c] >= 0) continue;
-    const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long)g.n[0] * g.n[1]));
+    int i, j, k;
+    decode(c, g.n[0], g.n[1], i, j, k);
     double out[3];
     const int r = wls_cell_warp<AT>(g, b, xh, layn, i, j, k, l, out);
     __syncwarp();

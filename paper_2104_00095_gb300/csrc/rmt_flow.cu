@@ -14,14 +14,6 @@ inline int nblocks(long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(c % nx);
-  long r = c / nx;
-  j = (int)(r % ny);
-  k = (int)(r / ny);
-}
-
-
 template <typename T>
 __device__ __forceinline__ void cell_faces(const Geo& g, int e, int i, int j, int k, long& lo, long& hi) {
   lo = fidx(g, e, i, j, k);

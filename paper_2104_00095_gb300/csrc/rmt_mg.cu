@@ -1408,7 +1408,8 @@ __device__ void cg_block(const Lv& L, int kind, int max_it, double rtol, T* x, T
     __syncthreads();  // p complete
     loc = T(0);
     for (long u = threadIdx.x; u < n; u += blockDim.x) {
-      const int i = (int)(u % ex), j = (int)((u / ex) % ey), k = (int)(u / ((long)ex * ey));
+      int i, j, k;
+      decode(u, ex, ey, i, j, k);
       T dg;
       const T ap = kind == 0 ? mac_op<T>(L, p, rho, i, j, k, dg) : fe_op<T>(L, p, rho, i, j, k, dg);
       q[u] = ap;

@@ -21,13 +21,6 @@ inline int nblocks(long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-__device__ __forceinline__ void decode(long c, int nx, int ny, int& i, int& j, int& k) {
-  i = (int)(c % nx);
-  long r = c / nx;
-  j = (int)(r % ny);
-  k = (int)(r / ny);
-}
-
 // ---------------------------------------------------------------------------------
 // stress: face-normal row of the blended deviatoric stress, then its divergence
 
