@@ -90,7 +90,9 @@ typedef struct {
 } rmt_solid_desc;
 
 /* Creates a grid.  Validates the descriptor; allocates the device state lazily on the first
- * step/read/write.  out receives the handle (caller destroys it).  Errors: RMT_EINVAL. */
+ * step/read/write.  out receives the handle (caller destroys it).  Errors: RMT_EINVAL, also
+ * for (n_x + 1)(n_y + 1)(n_z + 1) >= 2^31 (cell, node and face indices are 32-bit; such a grid
+ * would need more than 400 GB of device memory). */
 rmt_status rmt_create_grid(const rmt_grid_desc* desc, rmt_grid** out);
 
 /* Registers a body before the first step (SI "Initialization": xi^0 = x where

@@ -872,6 +872,8 @@ rmt_status rmt_create_grid(const rmt_grid_desc* d, rmt_grid** out) {
     if (p0 && (d->n[a] & 1)) return RMT_EINVAL;  // red-black colouring needs an even period
     if (d->wall_u[2 * a][a] != 0.0 || d->wall_u[2 * a + 1][a] != 0.0) return RMT_EINVAL;
   }
+  // cell, node and face indices are formed in 32-bit arithmetic
+  if ((long)(d->n[0] + 1) * (d->n[1] + 1) * (d->n[2] + 1) >= (1L << 31)) return RMT_EINVAL;
   const double h = (d->hi[0] - d->lo[0]) / d->n[0];
   for (int a = 1; a < 3; a++)
     if (fabs((d->hi[a] - d->lo[a]) / d->n[a] - h) > 1e-12 * h) return RMT_EINVAL;

@@ -126,16 +126,19 @@ struct BodyView {
   const int8_t* lay; // [N], -1 = absent
 };
 
+// Linear indices of cells, nodes and faces are formed in 32-bit arithmetic (a 64-bit product is
+// several instructions on the GPU): grid creation refuses grids of 2^31 or more nodes, so none of
+// them overflows an int.
 __host__ __device__ __forceinline__ long cidx(const Geo& g, int i, int j, int k) {
-  return i + (long)g.n[0] * (j + (long)g.n[1] * (long)k);
+  return (long)(i + g.n[0] * (j + g.n[1] * k));
 }
 __host__ __device__ __forceinline__ long nidx(const Geo& g, int i, int j, int k) {
-  return i + (long)g.nn[0] * (j + (long)g.nn[1] * (long)k);
+  return (long)(i + g.nn[0] * (j + g.nn[1] * k));
 }
 // d-face whose d-index is the face index f in [0, n_d] (between cells f-1 and f)
 __host__ __device__ __forceinline__ long fidx(const Geo& g, int d, int i, int j, int k) {
-  long e0 = g.n[0] + (d == 0), e1 = g.n[1] + (d == 1);
-  return i + e0 * (j + e1 * (long)k);
+  const int e0 = g.n[0] + (d == 0), e1 = g.n[1] + (d == 1);
+  return (long)(i + e0 * (j + e1 * k));
 }
 __host__ __device__ __forceinline__ long nfaces(const Geo& g, int d) {
   return g.N / g.n[d] * (g.n[d] + 1);

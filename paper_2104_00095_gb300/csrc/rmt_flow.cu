@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_bar(Geo g, const T* __restri
   T* ub[3] = {ub0, ub1, ub2};
   THREAD_XYZ(i, j, k);
   if (i >= ex || j >= ey || k >= ez) return;
-  const long f = i + (long)ex * (j + (long)ey * k);
+  const long f = (long)(i + ex * (j + ey * k));
   const int fi = e == 0 ? i : (e == 1 ? j : k);
   if (is_wall_face(g, e, fi)) {
     const int face = fi == 0 ? 2 * e : 2 * e + 1;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_face(Geo g, const T* __restr
   T* uf[3] = {(T*)bp.uf[0], (T*)bp.uf[1], (T*)bp.uf[2]};
   THREAD_XYZ(i, j, k);
   if (i >= ex || j >= ey || k >= ez) return;
-  const long f = i + (long)ex * (j + (long)ey * k);
+  const long f = (long)(i + ex * (j + ey * k));
   const int fi = d == 0 ? i : (d == 1 ? j : k);
   if (is_wall_face(g, d, fi)) {
     const int face = fi == 0 ? 2 * d : 2 * d + 1;

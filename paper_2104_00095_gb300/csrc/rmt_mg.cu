@@ -56,8 +56,9 @@ struct Lv {
 
 inline dim3 grid3(int nx, int ny, int nz, int by) { return dim3((nx + BX - 1) / BX, (ny + by - 1) / by, nz); }
 
-__device__ __forceinline__ long cix(const Lv& L, int i, int j, int k) { return i + (long)L.n[0] * (j + (long)L.n[1] * k); }
-__device__ __forceinline__ long nix(const Lv& L, int i, int j, int k) { return i + (long)L.nn[0] * (j + (long)L.nn[1] * k); }
+// 32-bit index arithmetic: every level is at most the finest grid, below 2^31 nodes
+__device__ __forceinline__ long cix(const Lv& L, int i, int j, int k) { return (long)(i + L.n[0] * (j + L.n[1] * k)); }
+__device__ __forceinline__ long nix(const Lv& L, int i, int j, int k) { return (long)(i + L.nn[0] * (j + L.nn[1] * k)); }
 // neighbour cell index along d: wrap on periodic axes; -1 outside a wall
 __device__ __forceinline__ int cnb(const Lv& L, int d, int v) {
   if (v < 0) return L.per[d] ? L.n[d] - 1 : -1;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid64(Lv L, int kind, const dou
   if (thread_cell(ext, i, j, k)) {
     double dg;
     const double ax = kind == 0 ? mac_op<double>(L, x, rho, i, j, k, dg) : fe_op<double>(L, x, rho, i, j, k, dg);
-    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const long u = (long)(i + ext[0] * (j + ext[1] * k));
     const double r = b[u] - ax;
     rT[u] = r;
     loc = r * r;
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(BX* BYMAX) k_first_resid64(Lv L, int kind, dou
   int i, j, k;
   double loc = 0.0;
   if (thread_cell(ext, i, j, k)) {
-    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const long u = (long)(i + ext[0] * (j + ext[1] * k));
     const double v = b[u] - *mean;
     b[u] = v;
     rT[u] = v;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(BX* BYMAX) k_first_resid_ff(Lv L, int kind, fl
   int i, j, k;
   float loc = 0.0f;
   if (thread_cell(ext, i, j, k)) {
-    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const long u = (long)(i + ext[0] * (j + ext[1] * k));
     float h = bh[u], l = bl[u];
     ff_sub_pair(h, l, mean);
     bh[u] = h;
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid_ff(Lv L, int kind, const fl
   float loc = 0.0f;
   if (thread_cell(ext, i, j, k)) {
     const F2 ax = kind == 0 ? mac_op_ff(L, xh, xl, rho, i, j, k) : fe_op_ff(L, xh, xl, rho, i, j, k);
-    const long u = i + (long)ext[0] * (j + (long)ext[1] * k);
+    const long u = (long)(i + ext[0] * (j + ext[1] * k));
     const F2 t = two_sum(bh[u], -ax.h);
     const float r = __fadd_rn(t.h, __fadd_rn(t.l, __fsub_rn(bl[u], ax.l)));
     rT[u] = r;
@@ -1173,17 +1174,16 @@ __device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T
   for (int qz = 0; qz < 3; qz++)
 #pragma unroll
     for (int qy = 0; qy < 3; qy++) {
-      const long row = (long)C.n[0] * (ny[qy] + (long)C.n[1] * nz[qz]);
+      const long row = (long)(C.n[0] * (ny[qy] + C.n[1] * nz[qz]));
       const T xm = xc[row + nx[0]], x0 = xc[row + nx[1]], xp = xc[row + nx[2]];
       rx[qz][qy][0] = w0 * x0 + w1 * xm;
       rx[qz][qy][1] = w0 * x0 + w1 * xp;
     }
-  const long sy = F.n[0], sz = (long)F.n[0] * F.n[1];
 #pragma unroll
   for (int cz = 0; cz < 2; cz++)
 #pragma unroll
     for (int cy = 0; cy < 2; cy++) {
-      const long base = (long)(2 * I) + (long)(2 * J + cy) * sy + (long)(2 * K + cz) * sz;
+      const long base = (long)(2 * I + (2 * J + cy) * F.n[0] + (2 * K + cz) * (F.n[0] * F.n[1]));
 #pragma unroll
       for (int cx = 0; cx < 2; cx++) {
         // along y, then z

@@ -39,6 +39,7 @@ def _desc(**kw):
     dict(bc=[1, 0, 0, 0, 0, 0]),                           # periodic on one face only
     dict(eps_h=0.0),
     dict(band_layers=0),
+    dict(n=(1290, 1290, 1290)),                            # 2^31 nodes or more: 32-bit indices
 ])
 def test_create_grid_rejects_bad_descriptors(bad):
     L = rmt.load()
