@@ -557,13 +557,12 @@ __device__ __forceinline__ bool rep_accel(const Geo& g, const Body* __restrict__
   return true;
 }
 
-// Bodies whose band box meets the block's tile (TILE_X x TILE_Y cells of plane blockIdx.z, the
-// THREAD_XYZ layout): only they need a per-cell test.  All threads of the block call it; warp 0
-// writes the mask to *slot.
-__device__ __forceinline__ unsigned long long tile_body_mask(const Geo& g, const int* sbb, int nb,
+// Bodies whose band box meets the block's tile (TILE_X x TILE_Y cells of planes k0..k1): only
+// they need a per-cell test.  All threads of the block call it; warp 0 writes the mask to *slot.
+__device__ __forceinline__ unsigned long long tile_body_mask(const Geo& g, const int* sbb, int nb, int k0, int k1,
                                                              unsigned long long* slot) {
   if (threadIdx.y == 0) {
-    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y, kk = blockIdx.z;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
     const int i1 = min(i0 + TILE_X, g.n[0]) - 1, j1 = min(j0 + TILE_Y, g.n[1]) - 1;
     unsigned long long mk = 0;
     for (int base = 0; base < nb; base += 32) {
@@ -571,7 +570,7 @@ __device__ __forceinline__ unsigned long long tile_body_mask(const Geo& g, const
       bool hit = false;
       if (m < nb) {
         const int* b = sbb + 6 * m;
-        hit = tile_meets_box(g, b, 0, i0, i1) && tile_meets_box(g, b, 1, j0, j1) && tile_meets_box(g, b, 2, kk, kk);
+        hit = tile_meets_box(g, b, 0, i0, i1) && tile_meets_box(g, b, 1, j0, j1) && tile_meets_box(g, b, 2, k0, k1);
       }
       mk |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << base;
     }

@@ -382,6 +382,9 @@ __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
 // ---------------------------------------------------------------------------------
 // density by mixing (eq. mod_heaviside) and u*
 
+// A block marches over DZ planes of a TILE_X x TILE_Y column, so the body boxes and the tile's
+// body mask are set up once per column.
+constexpr int DZ = 8;
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_density(Geo g, const Body* __restrict__ bodies,
                                                              const BodyView<T>* __restrict__ views, int nb,
@@ -390,22 +393,26 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_density(Geo g, const Body* _
   __shared__ int sbb[6 * RMT_MAX_BODIES];
   __shared__ unsigned long long tile_mask;
   stage_boxes(bbs, bstride, nb, sbb);
-  const unsigned long long tm = tile_body_mask(g, sbb, nb, &tile_mask);
+  const int k0 = blockIdx.z * DZ, k1 = min(k0 + DZ, g.n[2]);
+  const unsigned long long tm = tile_body_mask(g, sbb, nb, k0, k1 - 1, &tile_mask);
   const T eps = cv<T>(g.eps, g.f.eps);
-  THREAD_XYZ(i, j, k);
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  const long c = cidx(g, i, j, k);
-  T wsum = T(0), acc = T(0);
-  for (unsigned long long r = tm; r; r &= r - 1) {
-    const int m = __ffsll((long long)r) - 1;
-    if (!in_box(g, sbb + 6 * m, i, j, k) || views[m].lay[c] < 0) continue;
-    const T w = T(1) - heavi(views[m].phi[c], eps);
-    acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
-    wsum += w;
+  const T rf = cv<T>(g.rho_f, g.f.rho_f);
+  for (int k = k0; k < k1; k++) {
+    const long c = cidx(g, i, j, k);
+    T wsum = T(0), acc = T(0);
+    for (unsigned long long r = tm; r; r &= r - 1) {
+      const int m = __ffsll((long long)r) - 1;
+      if (!in_box(g, sbb + 6 * m, i, j, k) || views[m].lay[c] < 0) continue;
+      const T w = T(1) - heavi(views[m].phi[c], eps);
+      acc += w * cv<T>(bodies[m].rho_s, bodies[m].f.rho_s);
+      wsum += w;
+    }
+    const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
+    const T sc = wsum > T(1) ? T(1) / wsum : T(1);
+    rho[c] = Hf * rf + acc * sc;
   }
-  const T Hf = wsum < T(1) ? T(1) - wsum : T(0);
-  const T sc = wsum > T(1) ? T(1) / wsum : T(1);
-  rho[c] = Hf * cv<T>(g.rho_f, g.f.rho_f) + acc * sc;
 }
 
 template <typename T>
@@ -442,44 +449,121 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
 // approximate FE projection glue
 
 // weak divergence of V = (u* - u^n)/dt at every node: sum over adjacent cells of
-// (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d
+// (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d.
+// A thread marches up a column of FEZ nodes; the four cells of the plane below a node are the
+// ones above the previous node, so each cell plane is loaded once per column (the eight cells'
+// contributions are still summed in the order sx, sy, sz).
+constexpr int FEZ = 16;
 template <typename T>
-__global__ void k_fe_rhs(Geo g, const T* __restrict__ u, const T* __restrict__ ustar, MGVec b) {
-  GRID_LOOP(nd, g.NN) {
-    int i, j, k;
-    decode(nd, g.nn[0], g.nn[1], i, j, k);
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_fe_rhs(Geo g, const T* __restrict__ u,
+                                                           const T* __restrict__ ustar, MGVec b) {
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+  if (i >= g.nn[0] || j >= g.nn[1]) return;
+  const int k0 = blockIdx.z * FEZ, k1 = min(k0 + FEZ, g.nn[2]);
+  // the 2 x 2 cell columns around the node column (sx + 2 sy), -1 outside a wall
+  int col[4];
+  {
+    int cx[2] = {i - 1, i}, cy[2] = {j - 1, j};
+    const bool okx0 = wrap_axis(g, 0, cx[0]), okx1 = wrap_axis(g, 0, cx[1]);
+    const bool oky0 = wrap_axis(g, 1, cy[0]), oky1 = wrap_axis(g, 1, cy[1]);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int sx = q & 1, sy = q >> 1;
+      const bool ok = (sx ? okx1 : okx0) && (sy ? oky1 : oky0);
+      col[q] = ok ? cx[sx] + g.n[0] * cy[sy] : -1;
+    }
+  }
+  const int plane = g.n[0] * g.n[1];
+  const T* const u1 = u + g.N;
+  const T* const u2 = u + 2 * g.N;
+  const T* const s1 = ustar + g.N;
+  const T* const s2 = ustar + 2 * g.N;
+  // V of the four cells of cell plane kc (wrapped; skipped outside a wall)
+  auto load = [&](int kc, T (&V)[4][3], bool (&ok)[4]) {
+    const bool okz = wrap_axis(g, 2, kc);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      ok[q] = okz && col[q] >= 0;
+      const int c = ok[q] ? col[q] + plane * kc : 0;
+      V[q][0] = ustar[c] - u[c];
+      V[q][1] = s1[c] - u1[c];
+      V[q][2] = s2[c] - u2[c];
+    }
+  };
+  T lo[4][3], hi[4][3];
+  bool oklo[4], okhi[4];
+  load(k0 - 1, lo, oklo);
+  for (int k = k0; k < k1; k++) {
+    load(k, hi, okhi);
     T acc = T(0);
 #pragma unroll
     for (int q = 0; q < 8; q++) {
       const int sx = q & 1, sy = (q >> 1) & 1, sz = (q >> 2) & 1;
-      long c;
-      if (!cell_at(g, i - 1 + sx, j - 1 + sy, k - 1 + sz, c)) continue;
-      const T v0 = ustar[c] - u[c], v1 = ustar[g.N + c] - u[g.N + c], v2 = ustar[2 * g.N + c] - u[2 * g.N + c];
+      if (!(sz ? okhi[q & 3] : oklo[q & 3])) continue;
+      const T v0 = sz ? hi[q & 3][0] : lo[q & 3][0], v1 = sz ? hi[q & 3][1] : lo[q & 3][1],
+              v2 = sz ? hi[q & 3][2] : lo[q & 3][2];
       acc += (sx ? -v0 : v0) + (sy ? -v1 : v1) + (sz ? -v2 : v2);
     }
+    const long nd = nidx(g, i, j, k);
     if constexpr (sizeof(T) == 8)
       b.d[nd] = (double)acc * g.fe_rhs;
     else
       store_prod(b, nd, acc, g.f.fe_rhs, g.f.fe_rhs_lo);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      oklo[q] = okhi[q];
+#pragma unroll
+      for (int a = 0; a < 3; a++) lo[q][a] = hi[q][a];
+    }
   }
 }
 
+// u^{n+1} = u* - dt/rho grad psi with the cell gradient of the nodal psi.  A thread marches up
+// a column of FEZ cells; the four nodes below a cell are the ones above the previous cell, so
+// each node plane is loaded once per column.
 template <typename T>
-__global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __restrict__ rho_h, MGVec psi,
-                              T* __restrict__ u) {
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_fe_update_u(Geo g, const T* __restrict__ ustar,
+                                                                const T* __restrict__ rho_h, MGVec psi,
+                                                                T* __restrict__ u) {
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const int k0 = blockIdx.z * FEZ, k1 = min(k0 + FEZ, g.n[2]);
   const T dt = cv<T>(g.dt, g.f.dt);
-  GRID_LOOP(c, g.N) {
-    int i, j, k;
-    decode(c, g.n[0], g.n[1], i, j, k);
-    long nd[8];
+  // the 2 x 2 node columns of the cell column (sx + 2 sy), wrapped on a periodic axis
+  int col[4];
 #pragma unroll
-    for (int q = 0; q < 8; q++) nd[q] = node_at(g, i + (q & 1), j + ((q >> 1) & 1), k + ((q >> 2) & 1));
+  for (int q = 0; q < 4; q++) {
+    int x = i + (q & 1), y = j + (q >> 1);
+    if (g.per[0] && x >= g.nn[0]) x -= g.nn[0];
+    if (g.per[1] && y >= g.nn[1]) y -= g.nn[1];
+    col[q] = x + g.nn[0] * y;
+  }
+  const int plane = g.nn[0] * g.nn[1];
+  auto node_plane = [&](int kn) { return g.per[2] && kn >= g.nn[2] ? kn - g.nn[2] : kn; };
+  // psi at the four nodes of node plane kn (FP64: v[q][0]; FP32: the pair h, l)
+  auto load = [&](int kn, T (&v)[4][2]) {
+    const int base = plane * node_plane(kn);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if constexpr (sizeof(T) == 8) {
+        v[q][0] = psi.d[col[q] + base];
+        v[q][1] = 0.0;
+      } else {
+        v[q][0] = psi.h[col[q] + base];
+        v[q][1] = psi.l[col[q] + base];
+      }
+    }
+  };
+  T lo[4][2], hi[4][2];
+  load(k0, lo);
+  for (int k = k0; k < k1; k++) {
+    load(k + 1, hi);
     T gp[3];
     if constexpr (sizeof(T) == 8) {
       double s[3] = {0, 0, 0};
 #pragma unroll
       for (int q = 0; q < 8; q++) {
-        const double pv = psi.d[nd[q]];
+        const double pv = q & 4 ? hi[q & 3][0] : lo[q & 3][0];
         s[0] += (q & 1) ? pv : -pv;
         s[1] += ((q >> 1) & 1) ? pv : -pv;
         s[2] += ((q >> 2) & 1) ? pv : -pv;
@@ -490,8 +574,8 @@ __global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __res
       float v[8][2];
 #pragma unroll
       for (int q = 0; q < 8; q++) {
-        v[q][0] = psi.h[nd[q]];
-        v[q][1] = psi.l[nd[q]];
+        v[q][0] = q & 4 ? hi[q & 3][0] : lo[q & 3][0];
+        v[q][1] = q & 4 ? hi[q & 3][1] : lo[q & 3][1];
       }
 #pragma unroll
       for (int a = 0; a < 3; a++) {
@@ -503,9 +587,15 @@ __global__ void k_fe_update_u(Geo g, const T* __restrict__ ustar, const T* __res
         gp[a] = s * g.f.q4;
       }
     }
+    const long c = cidx(g, i, j, k);
     const T r = rho_h[c];
 #pragma unroll
     for (int a = 0; a < 3; a++) u[a * g.N + c] = ustar[a * g.N + c] - dt / r * gp[a];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      lo[q][0] = hi[q][0];
+      lo[q][1] = hi[q][1];
+    }
   }
 }
 
@@ -616,7 +706,7 @@ void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cu
 template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
                     T* rho, cudaStream_t s) {
-  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, g.n[2]);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + DZ - 1) / DZ);
   k_density<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, bodies, views, nb, bbs, bstride, rho);
   rmt_count_launches(1);
 }
@@ -633,13 +723,15 @@ void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* r
 }
 template <typename T>
 void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b64, cudaStream_t s) {
-  k_fe_rhs<T><<<nblocks(g.NN), TPB, 0, s>>>(g, u, ustar, b64);
+  const dim3 gr((g.nn[0] + TILE_X - 1) / TILE_X, (g.nn[1] + TILE_Y - 1) / TILE_Y, (g.nn[2] + FEZ - 1) / FEZ);
+  k_fe_rhs<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, ustar, b64);
   rmt_count_launches(1);
 }
 template <typename T>
 void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, MGVec psi, T* u, T* p, T* psi_out,
                       cudaStream_t s) {
-  k_fe_update_u<T><<<nblocks(g.N), TPB, 0, s>>>(g, ustar, rho_h, psi, u); rmt_count_launches(1);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + FEZ - 1) / FEZ);
+  k_fe_update_u<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, ustar, rho_h, psi, u); rmt_count_launches(1);
   k_fe_update_p<T><<<nblocks(g.NN), TPB, 0, s>>>(g.NN, psi, p, psi_out); rmt_count_launches(1);
 }
 template <typename T>

@@ -175,7 +175,7 @@ __device__ __forceinline__ uint64_t cell_bodies(const Geo& g, const BodyView<T>*
 // wall), so no warp takes a separate path at the domain's edges.
 constexpr int SFZ = 8;
 template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T* __restrict__ u,
+__global__ void __launch_bounds__(TILE_X* TILE_Y, 8) k_stress_fluid(Geo g, const T* __restrict__ u,
                                                                   const BodyView<T>* __restrict__ views, int nb,
                                                                   const int* __restrict__ bbs, int bstride,
                                                                   T* __restrict__ out, int* __restrict__ list,
@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T*
     return (long)kk * sz;
   };
   const long cij = i + (long)j * sy;
-  T win[3][3];  // win[a][0..2] = u_a at planes k-1, k, k+1
+  // win[a][0..2] = u_a at planes k-1, k, k+1; pre[a] = the value stored at plane k+2 (the cell's
+  // own plane beyond a wall), loaded one iteration ahead so that two planes of loads are in flight
+  T win[3][3], pre[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     const T* ua = u + (long)a * g.N + cij;
@@ -228,15 +230,18 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_stress_fluid(Geo g, const T*
     const T vl = ua[ol >= 0 ? ol : (long)k0 * sz];
     win[a][0] = ol >= 0 ? vl : T(2) * cv<T>(g.wall[4][a], g.f.wall[4][a]) - uk;
     win[a][1] = uk;
+    const long o1 = zoff(k0 + 1);
+    pre[a] = ua[o1 >= 0 ? o1 : (long)k0 * sz];
   }
   for (int k = k0; k < k1; k++) {
     const long c = cij + (long)k * sz;
     const long oh = zoff(k + 1);
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const T* ua = u + (long)a * g.N + cij;
-      const T vh = ua[oh >= 0 ? oh : (long)k * sz];
-      win[a][2] = oh >= 0 ? vh : T(2) * cv<T>(g.wall[5][a], g.f.wall[5][a]) - win[a][1];
+    for (int a = 0; a < 3; a++) win[a][2] = oh >= 0 ? pre[a] : T(2) * cv<T>(g.wall[5][a], g.f.wall[5][a]) - win[a][1];
+    if (k + 1 < k1) {
+      const long o2 = zoff(k + 2);
+#pragma unroll
+      for (int a = 0; a < 3; a++) pre[a] = u[(long)a * g.N + cij + (o2 >= 0 ? o2 : (long)(k + 1) * sz)];
     }
     uint64_t bm = 0;
     for (unsigned long long r = tm; r; r &= r - 1) {
