@@ -301,51 +301,108 @@ struct Umac3 {
   const void* un[3];
   void* um[3];
 };
+// A thread marches up to MCZ lattice points of its (i, j) column: the cell below a z-face is the
+// cell above the previous point's faces, so its q and rho come from registers; the column's
+// neighbour columns and wall tests are set up once.
+constexpr int MCZ = 8;
 template <typename T>
-__global__ void __launch_bounds__(TILE_X* TILE_Y) k_mac_correct3(Geo g, Umac3 F, const T* __restrict__ rho, MGVec q) {
-  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y, k = blockIdx.z;
-  if (i > g.n[0] || j > g.n[1] || k > g.n[2]) return;
+__global__ void __launch_bounds__(TILE_X* TILE_Y) k_mac_correct3(Geo g, Umac3 F, const T* __restrict__ rho, MGVec q,
+                                                                 int zc) {
+  const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
+  if (i > g.n[0] || j > g.n[1]) return;
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, g.n[2] + 1);
   const T fac = cv<T>(g.hdt_h, g.f.hdt_h);
-  const bool bin = i < g.n[0] && j < g.n[1] && k < g.n[2];  // the cell above the faces exists
-  long cb = 0;
-  T rb = T(0), qbh = T(0), qbl = T(0);
-  if (bin) {
-    cb = cidx(g, i, j, k);
-    rb = rho[cb];
-    if constexpr (sizeof(T) == 8)
-      qbh = q.d[cb];
-    else {
-      qbh = q.h[cb];
-      qbl = q.l[cb];
-    }
-  }
-  const int ii[3] = {i, j, k};
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long plane = (long)n0 * n1;
+  const bool cij = i < n0 && j < n1;  // (i, j) is a cell column
+  // per direction d < 2: the face (i, j, k) exists (other index a cell), is a wall face, and the
+  // columns of its lower and upper cells (the upper one wraps at the periodic end)
+  bool has[2], wall[2];
+  int colA[2], colB[2];
 #pragma unroll
-  for (int d = 0; d < 3; d++) {
-    // the d-face (i, j, k) exists where the other two indices are cells
-    if (ii[(d + 1) % 3] >= g.n[(d + 1) % 3] || ii[(d + 2) % 3] >= g.n[(d + 2) % 3]) continue;
-    const long f = fidx(g, d, i, j, k);
-    const T* un = (const T*)F.un[d];
-    T* um = (T*)F.um[d];
-    if (is_wall_face(g, d, ii[d])) {
-      um[f] = un[f];
-      continue;
+  for (int d = 0; d < 2; d++) {
+    const int fi = d == 0 ? i : j;
+    has[d] = d == 0 ? j < n1 : i < n0;
+    wall[d] = is_wall_face(g, d, fi);
+    int lo = fi - 1, up = fi;  // both exist (wrapped) unless the face is a wall face
+    wrap_axis(g, d, lo);
+    wrap_axis(g, d, up);
+    colA[d] = d == 0 ? lo + n0 * j : i + n0 * lo;
+    colB[d] = d == 0 ? up + n0 * j : i + n0 * up;
+  }
+  const int col = i + n0 * j;
+  T pr = T(0), ph = T(0), pl = T(0);  // rho and q of cell (i, j, k-1), once loaded
+  bool have_prev = false;
+  for (int k = k0; k < k1; k++) {
+    const bool kin = k < n2;
+    const bool bin = cij && kin;  // the cell above the faces exists
+    const long cb = col + plane * k;
+    T rb = T(0), qbh = T(0), qbl = T(0);
+    if (bin) {
+      rb = rho[cb];
+      if constexpr (sizeof(T) == 8)
+        qbh = q.d[cb];
+      else {
+        qbh = q.h[cb];
+        qbl = q.l[cb];
+      }
     }
-    int a[3] = {i, j, k}, b[3] = {i, j, k};
-    a[d] -= 1;
-    long ca, cbb;
-    cell_at(g, a[0], a[1], a[2], ca);
-    const bool own = bin;  // the upper cell is (i, j, k) itself unless the face is the periodic end
-    if (!own) cell_at(g, b[0], b[1], b[2], cbb);
-    else cbb = cb;
-    const T ra = rho[ca], rbb = own ? rb : rho[cbb];
-    const T beta = T(2) / (ra + rbb);
-    T dq;
-    if constexpr (sizeof(T) == 8)
-      dq = (own ? qbh : q.d[cbb]) - q.d[ca];
-    else
-      dq = own ? ff_diff(qbh, qbl, q.h[ca], q.l[ca]) : ff_diff(q.h[cbb], q.l[cbb], q.h[ca], q.l[ca]);
-    um[f] = un[f] - fac * beta * dq;
+    if (kin) {
+#pragma unroll
+      for (int d = 0; d < 2; d++) {
+        if (!has[d]) continue;
+        const long f = fidx(g, d, i, j, k);
+        const T* un = (const T*)F.un[d];
+        T* um = (T*)F.um[d];
+        if (wall[d]) {
+          um[f] = un[f];
+          continue;
+        }
+        const long ca = colA[d] + plane * k;
+        const long cbb = bin ? cb : colB[d] + plane * k;
+        const T ra = rho[ca], rbb = bin ? rb : rho[cbb];
+        const T beta = T(2) / (ra + rbb);
+        T dq;
+        if constexpr (sizeof(T) == 8)
+          dq = (bin ? qbh : q.d[cbb]) - q.d[ca];
+        else
+          dq = bin ? ff_diff(qbh, qbl, q.h[ca], q.l[ca]) : ff_diff(q.h[cbb], q.l[cbb], q.h[ca], q.l[ca]);
+        um[f] = un[f] - fac * beta * dq;
+      }
+    }
+    if (cij) {
+      // the z-face (i, j, k)
+      const long f = fidx(g, 2, i, j, k);
+      const T* un = (const T*)F.un[2];
+      T* um = (T*)F.um[2];
+      if (is_wall_face(g, 2, k)) {
+        um[f] = un[f];
+      } else {
+        if (!have_prev) {  // cell (i, j, k-1), wrapped at the periodic start
+          const long ca = col + plane * (k > 0 ? k - 1 : n2 - 1);
+          pr = rho[ca];
+          if constexpr (sizeof(T) == 8)
+            ph = q.d[ca];
+          else {
+            ph = q.h[ca];
+            pl = q.l[ca];
+          }
+        }
+        const long cbb = bin ? cb : col;  // the periodic end: cell (i, j, 0)
+        const T rbb = bin ? rb : rho[cbb];
+        const T beta = T(2) / (pr + rbb);
+        T dq;
+        if constexpr (sizeof(T) == 8)
+          dq = (bin ? qbh : q.d[cbb]) - ph;
+        else
+          dq = bin ? ff_diff(qbh, qbl, ph, pl) : ff_diff(q.h[cbb], q.l[cbb], ph, pl);
+        um[f] = un[f] - fac * beta * dq;
+      }
+    }
+    pr = rb;
+    ph = qbh;
+    pl = qbl;
+    have_prev = bin;
   }
 }
 
@@ -382,18 +439,18 @@ __global__ void k_adv(Geo g, AdvPtrs ap, T* __restrict__ adv) {
 // ---------------------------------------------------------------------------------
 // density by mixing (eq. mod_heaviside) and u*
 
-// A block marches over DZ planes of a TILE_X x TILE_Y column, so the body boxes and the tile's
-// body mask are set up once per column.
+// A block marches over up to DZ planes of a TILE_X x TILE_Y column, so the body boxes and the
+// tile's body mask are set up once per column.
 constexpr int DZ = 8;
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_density(Geo g, const Body* __restrict__ bodies,
                                                              const BodyView<T>* __restrict__ views, int nb,
                                                              const int* __restrict__ bbs, int bstride,
-                                                             T* __restrict__ rho) {
+                                                             T* __restrict__ rho, int zc) {
   __shared__ int sbb[6 * RMT_MAX_BODIES];
   __shared__ unsigned long long tile_mask;
   stage_boxes(bbs, bstride, nb, sbb);
-  const int k0 = blockIdx.z * DZ, k1 = min(k0 + DZ, g.n[2]);
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, g.n[2]);
   const unsigned long long tm = tile_body_mask(g, sbb, nb, k0, k1 - 1, &tile_mask);
   const T eps = cv<T>(g.eps, g.f.eps);
   const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
@@ -450,16 +507,16 @@ __global__ void k_ustar(Geo g, const T* __restrict__ u, const T* __restrict__ ad
 
 // weak divergence of V = (u* - u^n)/dt at every node: sum over adjacent cells of
 // (h^2/4) sum_d sigma_d V_d, sigma_d = +1 when the node is the cell's high corner along d.
-// A thread marches up a column of FEZ nodes; the four cells of the plane below a node are the
-// ones above the previous node, so each cell plane is loaded once per column (the eight cells'
+// A thread marches up a column of up to FEZ nodes; the four cells of the plane below a node are
+// the ones above the previous node, so each cell plane is loaded once per column (the eight cells'
 // contributions are still summed in the order sx, sy, sz).
 constexpr int FEZ = 16;
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_fe_rhs(Geo g, const T* __restrict__ u,
-                                                           const T* __restrict__ ustar, MGVec b) {
+                                                           const T* __restrict__ ustar, MGVec b, int zc) {
   const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
   if (i >= g.nn[0] || j >= g.nn[1]) return;
-  const int k0 = blockIdx.z * FEZ, k1 = min(k0 + FEZ, g.nn[2]);
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, g.nn[2]);
   // the 2 x 2 cell columns around the node column (sx + 2 sy), -1 outside a wall
   int col[4];
   {
@@ -519,15 +576,15 @@ __global__ void __launch_bounds__(TILE_X* TILE_Y) k_fe_rhs(Geo g, const T* __res
 }
 
 // u^{n+1} = u* - dt/rho grad psi with the cell gradient of the nodal psi.  A thread marches up
-// a column of FEZ cells; the four nodes below a cell are the ones above the previous cell, so
+// a column of up to FEZ cells; the four nodes below a cell are the ones above the previous cell, so
 // each node plane is loaded once per column.
 template <typename T>
 __global__ void __launch_bounds__(TILE_X* TILE_Y) k_fe_update_u(Geo g, const T* __restrict__ ustar,
                                                                 const T* __restrict__ rho_h, MGVec psi,
-                                                                T* __restrict__ u) {
+                                                                T* __restrict__ u, int zc) {
   const int i = blockIdx.x * TILE_X + threadIdx.x, j = blockIdx.y * TILE_Y + threadIdx.y;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  const int k0 = blockIdx.z * FEZ, k1 = min(k0 + FEZ, g.n[2]);
+  const int k0 = blockIdx.z * zc, k1 = min(k0 + zc, g.n[2]);
   const T dt = cv<T>(g.dt, g.f.dt);
   // the 2 x 2 node columns of the cell column (sx + 2 sy), wrapped on a periodic axis
   int col[4];
@@ -690,8 +747,9 @@ void launch_mac_correct(const Geo& g, T* const uf[3][3], const T* rho, MGVec q, 
     F.un[d] = uf[d][d];
     F.um[d] = umac[d];
   }
-  const dim3 gr((g.n[0] + 1 + TILE_X - 1) / TILE_X, (g.n[1] + 1 + TILE_Y - 1) / TILE_Y, g.n[2] + 1);
-  k_mac_correct3<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, F, rho, q);
+  const int zc = column_chunk(g.N, MCZ);
+  const dim3 gr((g.n[0] + 1 + TILE_X - 1) / TILE_X, (g.n[1] + 1 + TILE_Y - 1) / TILE_Y, (g.n[2] + 1 + zc - 1) / zc);
+  k_mac_correct3<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, F, rho, q, zc);
   rmt_count_launches(1);
 }
 template <typename T>
@@ -706,8 +764,9 @@ void launch_advect(const Geo& g, T* const uf[3][3], T* const umac[3], T* adv, cu
 template <typename T>
 void launch_density(const Geo& g, const Body* bodies, const BodyView<T>* views, int nb, const int* bbs, int bstride,
                     T* rho, cudaStream_t s) {
-  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + DZ - 1) / DZ);
-  k_density<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, bodies, views, nb, bbs, bstride, rho);
+  const int zc = column_chunk(g.N, DZ);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + zc - 1) / zc);
+  k_density<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, bodies, views, nb, bbs, bstride, rho, zc);
   rmt_count_launches(1);
 }
 template <typename T>
@@ -723,15 +782,17 @@ void launch_ustar(const Geo& g, const T* u, const T* adv, const T* p, const T* r
 }
 template <typename T>
 void launch_fe_setup(const Geo& g, const T* u, const T* ustar, MGVec b64, cudaStream_t s) {
-  const dim3 gr((g.nn[0] + TILE_X - 1) / TILE_X, (g.nn[1] + TILE_Y - 1) / TILE_Y, (g.nn[2] + FEZ - 1) / FEZ);
-  k_fe_rhs<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, ustar, b64);
+  const int zc = column_chunk(g.NN, FEZ);
+  const dim3 gr((g.nn[0] + TILE_X - 1) / TILE_X, (g.nn[1] + TILE_Y - 1) / TILE_Y, (g.nn[2] + zc - 1) / zc);
+  k_fe_rhs<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, u, ustar, b64, zc);
   rmt_count_launches(1);
 }
 template <typename T>
 void launch_fe_update(const Geo& g, const T* ustar, const T* rho_h, MGVec psi, T* u, T* p, T* psi_out,
                       cudaStream_t s) {
-  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + FEZ - 1) / FEZ);
-  k_fe_update_u<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, ustar, rho_h, psi, u); rmt_count_launches(1);
+  const int zc = column_chunk(g.N, FEZ);
+  const dim3 gr((g.n[0] + TILE_X - 1) / TILE_X, (g.n[1] + TILE_Y - 1) / TILE_Y, (g.n[2] + zc - 1) / zc);
+  k_fe_update_u<T><<<gr, dim3(TILE_X, TILE_Y), 0, s>>>(g, ustar, rho_h, psi, u, zc); rmt_count_launches(1);
   k_fe_update_p<T><<<nblocks(g.NN), TPB, 0, s>>>(g.NN, psi, p, psi_out); rmt_count_launches(1);
 }
 template <typename T>

@@ -9,6 +9,14 @@
 // widths are multiples of it
 int sm_count();
 
+// Planes per thread column of a column-marching kernel over `units` points (cap at most): one
+// plane on small grids, where a column's planes would only follow one another, and more once
+// the columns alone give every SM a full set of resident threads.
+inline int column_chunk(long units, int cap) {
+  const long c = units / ((long)sm_count() * 2048);
+  return c < 1 ? 1 : (c > cap ? cap : (int)c);
+}
+
 // A multigrid right-hand side or solution as the step kernels see it.  FP64 mode: the FP64
 // array d.  FP32 mode: two-float pairs, value = h + l (d is null), so that no FP64 arithmetic
 // runs in the FP32 step.

@@ -1108,98 +1108,150 @@ __global__ void __launch_bounds__(BX* BYMAX) k_resid_restrict_mac(Lv F, Lv C, co
 
 // restriction of the residual to the coarse right-hand side at coarse unknown (I, J, K) (coarse
 // x zeroed): MAC the 8-cell mean, FE full weighting
-template <typename T>
-__device__ __forceinline__ void restrict_at(const Lv& F, const Lv& C, int kind, const T* __restrict__ rf,
-                                            T* __restrict__ bc, T* __restrict__ xc, int I, int J, int K) {
-  T s = T(0);
-  if (kind == 0) {
-#pragma unroll
-    for (int q = 0; q < 8; q++) s += rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
-    s *= T(0.125);
-  } else {
-    for (int oz = -1; oz <= 1; oz++)
-      for (int oy = -1; oy <= 1; oy++)
-        for (int ox = -1; ox <= 1; ox++) {
-          int ff[3] = {2 * I + ox, 2 * J + oy, 2 * K + oz};
-          bool in = true;
-#pragma unroll
-          for (int d = 0; d < 3; d++) {
-            if (ff[d] < 0 || ff[d] >= F.nn[d]) {
-              if (F.per[d]) ff[d] = ff[d] < 0 ? ff[d] + F.nn[d] : ff[d] - F.nn[d];
-              else in = false;
-            }
-          }
-          if (!in) continue;
-          const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
-          s += w * rf[nix(F, ff[0], ff[1], ff[2])];
-        }
-  }
-  const long u = kind == 0 ? cix(C, I, J, K) : nix(C, I, J, K);
-  bc[u] = s;
-  xc[u] = T(0);
-}
+// Restriction of the fine residual to the coarse right-hand side (and a zero coarse iterate).
+// Cell-centred: the mean of the 8 children.  Nodal: full weighting, weight 1/2 per axis on which
+// the fine node lies between coarse nodes, summed plane by plane (fine planes 2K-1, 2K, 2K+1).
+// One thread marches up to RZ coarse unknowns of its (I, J) column; in the nodal case the fine
+// plane 2K+1 is kept in registers as the next unknown's plane 2K'-1.
+constexpr int RZ = 8;
 template <typename T>
 __global__ void __launch_bounds__(BX* BYMAX) k_restrict(Lv F, Lv C, int kind, const T* __restrict__ rf,
-                                                      T* __restrict__ bc, T* __restrict__ xc) {
+                                                      T* __restrict__ bc, T* __restrict__ xc, int zc) {
   const int ext[3] = {kind == 0 ? C.n[0] : C.nn[0], kind == 0 ? C.n[1] : C.nn[1], kind == 0 ? C.n[2] : C.nn[2]};
-  int I, J, K;
-  if (!thread_cell(ext, I, J, K)) return;
-  restrict_at(F, C, kind, rf, bc, xc, I, J, K);
-}
-
-// Trilinear prolongation of the coarse correction, added to the fine iterate; one thread per
-// coarse unknown writes its 2 x 2 x 2 fine children.
-// Cell-centred: along each axis a child takes 3/4 of its parent and 1/4 of the parent's
-// neighbour on the child's side (the parent itself beyond a wall: Neumann mirror), applied
-// axis by axis.
-template <typename T>
-__device__ __forceinline__ void prolong_mac_at(const Lv& F, const Lv& C, const T* __restrict__ xc, T* __restrict__ xf,
-                                               int I, int J, int K) {
-  int nx[3], ny[3], nz[3];  // coarse indices of I-1, I, I+1 (and for J, K)
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= ext[0] || J >= ext[1]) return;
+  const int K0 = blockIdx.z * zc, K1 = min(K0 + zc, ext[2]);
+  if (kind == 0) {
+    for (int K = K0; K < K1; K++) {
+      T s = T(0);
 #pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const int di = q - 1;
-    int a = I + di, b = J + di, c = K + di;
-    if (a < 0 || a >= C.n[0]) a = C.per[0] ? (a < 0 ? a + C.n[0] : a - C.n[0]) : I;
-    if (b < 0 || b >= C.n[1]) b = C.per[1] ? (b < 0 ? b + C.n[1] : b - C.n[1]) : J;
-    if (c < 0 || c >= C.n[2]) c = C.per[2] ? (c < 0 ? c + C.n[2] : c - C.n[2]) : K;
-    nx[q] = a;
-    ny[q] = b;
-    nz[q] = c;
-  }
-  const T w0 = T(0.75), w1 = T(0.25);
-  // along x: rx[z][y][child] for the 3 x 3 coarse rows around (J, K)
-  T rx[3][3][2];
-#pragma unroll
-  for (int qz = 0; qz < 3; qz++)
-#pragma unroll
-    for (int qy = 0; qy < 3; qy++) {
-      const long row = (long)(C.n[0] * (ny[qy] + C.n[1] * nz[qz]));
-      const T xm = xc[row + nx[0]], x0 = xc[row + nx[1]], xp = xc[row + nx[2]];
-      rx[qz][qy][0] = w0 * x0 + w1 * xm;
-      rx[qz][qy][1] = w0 * x0 + w1 * xp;
+      for (int q = 0; q < 8; q++) s += rf[cix(F, 2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + ((q >> 2) & 1))];
+      s *= T(0.125);
+      const long u = cix(C, I, J, K);
+      bc[u] = s;
+      xc[u] = T(0);
     }
+    return;
+  }
+  // the fine x and y node indices 2I-1, 2I, 2I+1 (wrapped; -1 outside a wall) and the columns
+  int fx[3], fy[3];
 #pragma unroll
-  for (int cz = 0; cz < 2; cz++)
+  for (int o = 0; o < 3; o++) {
+    int v = 2 * I + o - 1, w = 2 * J + o - 1;
+    if (v < 0 || v >= F.nn[0]) v = F.per[0] ? (v < 0 ? v + F.nn[0] : v - F.nn[0]) : -1;
+    if (w < 0 || w >= F.nn[1]) w = F.per[1] ? (w < 0 ? w + F.nn[1] : w - F.nn[1]) : -1;
+    fx[o] = v;
+    fy[o] = w;
+  }
+  const int fplane = F.nn[0] * F.nn[1];
+  // the 3 x 3 values of fine plane p (zero where a node lies outside a wall: skipped in the sum)
+  auto load = [&](int p, T (&v)[3][3]) {
+    if (p < 0 || p >= F.nn[2]) p = F.per[2] ? (p < 0 ? p + F.nn[2] : p - F.nn[2]) : -1;
 #pragma unroll
-    for (int cy = 0; cy < 2; cy++) {
-      const long base = (long)(2 * I + (2 * J + cy) * F.n[0] + (2 * K + cz) * (F.n[0] * F.n[1]));
+    for (int oy = 0; oy < 3; oy++)
 #pragma unroll
-      for (int cx = 0; cx < 2; cx++) {
-        // along y, then z
-        const T y0 = w0 * rx[1][1][cx] + w1 * rx[1][2 * cy][cx];
-        const T ym = w0 * rx[0][1][cx] + w1 * rx[0][2 * cy][cx];
-        const T yp = w0 * rx[2][1][cx] + w1 * rx[2][2 * cy][cx];
-        const T v = w0 * y0 + w1 * (cz ? yp : ym);
-        xf[base + cx] += v;
+      for (int ox = 0; ox < 3; ox++) {
+        const bool in = p >= 0 && fy[oy] >= 0 && fx[ox] >= 0;
+        v[oy][ox] = in ? rf[fx[ox] + F.nn[0] * fy[oy] + (long)fplane * p] : T(0);
+      }
+  };
+  // whether each fine plane and row/column exists (a node outside a wall adds nothing)
+  auto zin = [&](int p) { return F.per[2] || (p >= 0 && p < F.nn[2]); };
+  T lo[3][3], mid[3][3], hi[3][3];
+  load(2 * K0 - 1, lo);
+  for (int K = K0; K < K1; K++) {
+    load(2 * K, mid);
+    load(2 * K + 1, hi);
+    T s = T(0);
+#pragma unroll
+    for (int oz = 0; oz < 3; oz++) {
+      if (!zin(2 * K + oz - 1)) continue;
+#pragma unroll
+      for (int oy = 0; oy < 3; oy++) {
+        if (fy[oy] < 0) continue;
+#pragma unroll
+        for (int ox = 0; ox < 3; ox++) {
+          if (fx[ox] < 0) continue;
+          const T w = (ox != 1 ? T(0.5) : T(1)) * (oy != 1 ? T(0.5) : T(1)) * (oz != 1 ? T(0.5) : T(1));
+          const T v = oz == 0 ? lo[oy][ox] : (oz == 1 ? mid[oy][ox] : hi[oy][ox]);
+          s += w * v;
+        }
       }
     }
+    const long u = nix(C, I, J, K);
+    bc[u] = s;
+    xc[u] = T(0);
+#pragma unroll
+    for (int oy = 0; oy < 3; oy++)
+#pragma unroll
+      for (int ox = 0; ox < 3; ox++) lo[oy][ox] = hi[oy][ox];
+  }
 }
+
+// Trilinear prolongation of the coarse correction, added to the fine iterate; a thread marches up
+// to PZ coarse cells of its (I, J) column and writes each one's 2 x 2 x 2 fine children.
+// Cell-centred: along each axis a child takes 3/4 of its parent and 1/4 of the parent's
+// neighbour on the child's side (the parent itself beyond a wall: Neumann mirror), applied
+// axis by axis; the x- and y-interpolated coarse planes below and above stay in registers.
+constexpr int PZ = 8;  // coarse planes per thread column
 template <typename T>
-__global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf) {
-  int I, J, K;
-  if (!thread_cell(C.n, I, J, K)) return;
-  prolong_mac_at(F, C, xc, xf, I, J, K);
+__global__ void __launch_bounds__(BX* BYMAX) k_prolong_mac(Lv F, Lv C, const T* __restrict__ xc, T* __restrict__ xf,
+                                                         int zc) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.n[0] || J >= C.n[1]) return;
+  const int K0 = blockIdx.z * zc, K1 = min(K0 + zc, C.n[2]);
+  int nx[3], ny[3];  // coarse indices of I-1, I, I+1 and J-1, J, J+1
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    int a = I + q - 1, b = J + q - 1;
+    if (a < 0 || a >= C.n[0]) a = C.per[0] ? (a < 0 ? a + C.n[0] : a - C.n[0]) : I;
+    if (b < 0 || b >= C.n[1]) b = C.per[1] ? (b < 0 ? b + C.n[1] : b - C.n[1]) : J;
+    nx[q] = a;
+    ny[q] = b;
+  }
+  const T w0 = T(0.75), w1 = T(0.25);
+  // coarse plane of K + dk (wrapped, or K itself beyond a wall)
+  auto zp = [&](int K, int dk) {
+    const int c = K + dk;
+    if (c >= 0 && c < C.n[2]) return c;
+    return C.per[2] ? (c < 0 ? c + C.n[2] : c - C.n[2]) : K;
+  };
+  // one coarse plane interpolated along x (child side cx), then along y (child side cy): Y[cy][cx]
+  auto plane_y = [&](int Kp, T (&Y)[2][2]) {
+    T rx[3][2];
+#pragma unroll
+    for (int qy = 0; qy < 3; qy++) {
+      const long row = (long)(C.n[0] * (ny[qy] + C.n[1] * Kp));
+      const T xm = xc[row + nx[0]], x0 = xc[row + nx[1]], xp = xc[row + nx[2]];
+      rx[qy][0] = w0 * x0 + w1 * xm;
+      rx[qy][1] = w0 * x0 + w1 * xp;
+    }
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++)
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) Y[cy][cx] = w0 * rx[1][cx] + w1 * rx[2 * cy][cx];
+  };
+  T Ym[2][2], Y0[2][2], Yp[2][2];
+  plane_y(zp(K0, -1), Ym);
+  plane_y(K0, Y0);
+  for (int K = K0; K < K1; K++) {
+    plane_y(zp(K, 1), Yp);
+#pragma unroll
+    for (int cz = 0; cz < 2; cz++)
+#pragma unroll
+      for (int cy = 0; cy < 2; cy++) {
+        const long base = (long)(2 * I + (2 * J + cy) * F.n[0] + (2 * K + cz) * (F.n[0] * F.n[1]));
+#pragma unroll
+        for (int cx = 0; cx < 2; cx++) xf[base + cx] += w0 * Y0[cy][cx] + w1 * (cz ? Yp[cy][cx] : Ym[cy][cx]);
+      }
+#pragma unroll
+    for (int cy = 0; cy < 2; cy++)
+#pragma unroll
+      for (int cx = 0; cx < 2; cx++) {
+        Ym[cy][cx] = Y0[cy][cx];
+        Y0[cy][cx] = Yp[cy][cx];
+      }
+  }
 }
 
 // Nodal: a fine node on a coarse node takes its value, one between two coarse nodes their mean
@@ -1305,8 +1357,8 @@ __global__ void __launch_bounds__(1024) k_final(const double* __restrict__ part,
   }
 }
 
-// per-block partial sums of the two-float array h + l: two-float accumulation per thread, FP64
-// across threads
+// per-block partial sums of the two-float array h + l (l null: all zero): two-float
+// accumulation per thread, FP64 across threads
 __global__ void k_partial_ff(const float* __restrict__ h, const float* __restrict__ l, long n,
                              double* __restrict__ part) {
   __shared__ double sh[TPB / 32];
@@ -1314,7 +1366,7 @@ __global__ void k_partial_ff(const float* __restrict__ h, const float* __restric
   GRID_LOOP(i, n) {
     const F2 t = two_sum(ah, h[i]);
     ah = t.h;
-    al = __fadd_rn(al, __fadd_rn(t.l, l[i]));
+    al = __fadd_rn(al, __fadd_rn(t.l, l ? l[i] : 0.0f));
   }
   double loc = (double)ah + (double)al;
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
@@ -1324,6 +1376,17 @@ __global__ void k_partial_ff(const float* __restrict__ h, const float* __restric
     double s = 0.0;
     for (int w = 0; w < TPB / 32; w++) s += sh[w];
     part[blockIdx.x] = s;
+  }
+}
+
+// (h, l) = (e, 0) - m: the two-float solution from a single FP32 solve, mean-free
+__global__ void k_set_ff_sub_mean(const float* __restrict__ e, float* __restrict__ h, float* __restrict__ l, long n,
+                                  const float* __restrict__ m) {
+  GRID_LOOP(i, n) {
+    float a = e[i], b = 0.0f;
+    ff_sub_pair(a, b, m);
+    h[i] = a;
+    l[i] = b;
   }
 }
 
@@ -1921,15 +1984,17 @@ void vcycle(MGSolver* m, int l, cudaStream_t s) {
       k_fe_tile<T, 1><<<fg, dim3(FX, FY), 0, s>>>(L, T(0), (const T*)m->x[l], (T*)m->r[l], (const T*)m->b[l],
                                                          (const T*)m->rho[l]);
     rmt_count_launches(1);
-    k_restrict<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(
-        L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1], (T*)m->x[l + 1]);
+    const int zc = column_chunk(C.nnode, RZ);
+    k_restrict<T><<<grid3(C.nn[0], C.nn[1], (C.nn[2] + zc - 1) / zc, m->by), dim3(BX, m->by), 0, s>>>(
+        L, C, m->kind, (const T*)m->r[l], (T*)m->b[l + 1], (T*)m->x[l + 1], zc);
     rmt_count_launches(1);
   }
   vcycle<T>(m, l + 1, s);
-  if (m->kind == 0)
-    k_prolong_mac<T><<<grid3(C.n[0], C.n[1], C.n[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
-                                                                                      (T*)m->x[l]);
-  else
+  if (m->kind == 0) {
+    const int zc = column_chunk(C.ncell, PZ);
+    k_prolong_mac<T><<<grid3(C.n[0], C.n[1], (C.n[2] + zc - 1) / zc, m->by), dim3(BX, m->by), 0, s>>>(
+        L, C, (const T*)m->x[l + 1], (T*)m->x[l], zc);
+  } else
     k_prolong_fe<T><<<grid3(C.nn[0], C.nn[1], C.nn[2], m->by), dim3(BX, m->by), 0, s>>>(L, C, (const T*)m->x[l + 1],
                                                                                         (T*)m->x[l]);
   rmt_count_launches(1);
@@ -1966,6 +2031,7 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
   int cycles = 0;
   int ok = 1;
   bool have_x = false;  // false: the iterate is still zero
+  bool single = false;  // FP32: one solve from zero, its result still in x[0]
   double bn2 = -1.0;
   if (m->warm) {
     // warm start from the last solution (mean-free; zero before the first solve): remove the
@@ -2031,6 +2097,11 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
       vcycle<T>(m, 0, s);
       cycles++;
     }
+    if (ff && !have_x && fixed_cycles > 0 && cycles >= fixed_cycles) {
+      single = true;  // x[0] is the whole solution: converted below with its mean removed
+      have_x = true;
+      break;
+    }
     if constexpr (ff)
       k_add_ff<<<nblocks(n), TPB, 0, s>>>((const float*)m->x[0], m->xh, m->xl, n, have_x ? 0 : 1);
     else
@@ -2045,6 +2116,11 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
       k_zero<float><<<nblocks(n), TPB, 0, s>>>(m->xh, n);
       k_zero<float><<<nblocks(n), TPB, 0, s>>>(m->xl, n);
       rmt_count_launches(2);
+    } else if (single) {
+      // the same values as setting (x, 0) and removing the two-float mean, in one pass
+      sum_ff(m, (const float*)m->x[0], nullptr, n, 1.0 / (double)n, m->scal + 3, fm + 2, s);
+      k_set_ff_sub_mean<<<nblocks(n), TPB, 0, s>>>((const float*)m->x[0], m->xh, m->xl, n, fm + 2);
+      rmt_count_launches(1);
     } else {
       sum_ff(m, m->xh, m->xl, n, 1.0 / (double)n, m->scal + 3, fm + 2, s);
       k_ff_sub_mean<<<nblocks(n), TPB, 0, s>>>(m->xh, m->xl, n, fm + 2);
