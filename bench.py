@@ -572,26 +572,38 @@ def main():
                      "unit": "GB/s", "frac": step_achieved / peak, "peak_source": peak_kind}
 
     # end to end through the C ABI with host buffers: every step uploads u from pinned host
-    # memory, advances one step and reads u back
+    # memory, advances one step and reads u back, in the grid's storage precision (the float
+    # calls for an FP32 grid, whose u they copy without conversion; the FP64 calls otherwise)
     e2e = None
     if not args.no_e2e:
-        host_in = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
-        host_out = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
-        g.read(rmt.RMT_F_U, out=host_in.numpy())
+        f32 = cfg["precision"] == "fp32"
+        hd = torch.float32 if f32 else torch.float64
+        esz = 4 if f32 else 8
+        host_in = torch.empty(3 * N, dtype=hd, pin_memory=True)
+        host_out = torch.empty(3 * N, dtype=hd, pin_memory=True)
+        if f32:
+            g.read_float(rmt.RMT_F_U, out=host_in.numpy())
+        else:
+            g.read(rmt.RMT_F_U, out=host_in.numpy())
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            g.write_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * 8, 0)
-            g.step(1)
-            g.read(rmt.RMT_F_U, out=host_out.numpy())
+            if f32:
+                g.write_float_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * esz, 0)
+                g.step(1)
+                g.read_float_ptr(rmt.RMT_F_U, host_out.data_ptr(), host_out.numel() * esz, 0)
+            else:
+                g.write_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * esz, 0)
+                g.step(1)
+                g.read(rmt.RMT_F_U, out=host_out.numpy())
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         et = t1 - t0
         et = max_over_ranks(et, world)
         e2e = {"value": job_rate(world, N, args.steps, et), "unit": "cell-updates/s",
-               "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
-               "ms_per_step": 1e3 * et / args.steps}
+               "h2d_bytes_per_step": 3 * N * esz, "d2h_bytes_per_step": 3 * N * esz,
+               "host_dtype": "f32" if f32 else "f64", "ms_per_step": 1e3 * et / args.steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -145,6 +145,16 @@ rmt_status rmt_read_fields(rmt_grid* g, int field, int solid_id, void* dst, size
 rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* src,
                             size_t src_bytes, int src_is_device);
 
+/* The same two calls with FP32 host or device buffers (dst_bytes / src_bytes >= 4 *
+ * rmt_field_len): the FP64 values rounded to float, or converted from float.  For U and P of an
+ * RMT_PREC_FP32_REFINE grid these are the stored values themselves, copied without conversion
+ * (half the bytes of the FP64 calls, and no rounding either way).  Same synchronisation and
+ * errors as rmt_read_fields / rmt_write_fields. */
+rmt_status rmt_read_fields_float(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes,
+                                 int dst_is_device);
+rmt_status rmt_write_fields_float(rmt_grid* g, int field, int solid_id, const void* src,
+                                  size_t src_bytes, int src_is_device);
+
 /* Multigrid cycles used by the last step's MAC (which = 0) and FE (which = 1) solves. */
 int rmt_last_cycles(rmt_grid* g, int which);
 /* The time step in use (after initialisation). */

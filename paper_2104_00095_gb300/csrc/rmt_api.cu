@@ -119,6 +119,7 @@ struct rmt_grid {
   int* err_d = nullptr;
   int* err_h = nullptr;
   double* stage = nullptr;
+  float* stage_f = nullptr;  // FP32 field I/O of fields without FP32 storage (first use)
   long stage_len = 0;
   int cycles[2] = {0, 0};
   double t = 0.0;
@@ -442,6 +443,9 @@ rmt_status alloc_t(rmt_grid* g) {
     return RMT_OK;
   }
   CK(g, cudaMallocHost((void**)&g->err_h, 16));
+  // no step has copied its error words yet: a step polls them before its first copy lands, and
+  // pinned memory may come back from an earlier grid with that grid's words in it
+  memset(g->err_h, 0, 16);
   cudaError_t ce = cudaSuccess;
   g->mac = mg_create(G, 0, g->fp32, &ce);
   if (ce != cudaSuccess) return fail(g, RMT_ENOMEM, "multigrid (MAC) allocation: %s", cudaGetErrorString(ce));
@@ -857,6 +861,79 @@ rmt_status scatter_t(rmt_grid* g, int field, int sid) {
   CK(g, cudaGetLastError());
   return RMT_OK;
 }
+// the body of rmt_read_fields (FP64 dst) and rmt_read_fields_float (FP32 dst)
+rmt_status read_field(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes, int dst_is_device, bool f32) {
+  if (!g || !dst) return RMT_EINVAL;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  const long n = rmt_field_len(g, field);
+  if (n < 0) return fail(g, RMT_EINVAL, "unknown field %d", field);
+  if (dst_bytes < (size_t)n * (f32 ? sizeof(float) : sizeof(double))) return fail(g, RMT_EINVAL, "destination too small");
+  if ((field == RMT_F_XI || field == RMT_F_PHI || field == RMT_F_LAYER || field == RMT_F_XI_HALF) &&
+      (solid_id < 0 || solid_id >= (int)g->bodies.size()))
+    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  if (g->in_batch && g->batch_s != g->s) CK(g, cudaStreamSynchronize(g->batch_s));  // the batch's steps first
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (f32 && g->fp32 && (field == RMT_F_U || field == RMT_F_P)) {
+    // stored in this layout: one copy, no conversion
+    CK(g, cudaMemcpyAsync(dst, field == RMT_F_U ? g->u : g->p, (size_t)n * sizeof(float), kind, g->s));
+  } else if (f32) {
+    st = g->fp32 ? gather_t<float>(g, field, solid_id, g->stage) : gather_t<double>(g, field, solid_id, g->stage);
+    if (st != RMT_OK) return st;
+    if (!g->stage_f) CK(g, cudaMalloc((void**)&g->stage_f, (size_t)g->stage_len * sizeof(float)));
+    k_cvt_back<float><<<nbk(n), 256, 0, g->s>>>(g->stage, g->stage_f, n);
+    rmt_count_launches(1);
+    CK(g, cudaMemcpyAsync(dst, g->stage_f, (size_t)n * sizeof(float), kind, g->s));
+  } else {
+    double* out = dst_is_device ? (double*)dst : g->stage;
+    st = g->fp32 ? gather_t<float>(g, field, solid_id, out) : gather_t<double>(g, field, solid_id, out);
+    if (st != RMT_OK) return st;
+    if (!dst_is_device) CK(g, cudaMemcpyAsync(dst, g->stage, (size_t)n * sizeof(double), kind, g->s));
+  }
+  CK(g, cudaStreamSynchronize(g->s));
+  return RMT_OK;
+}
+
+// the body of rmt_write_fields (FP64 src) and rmt_write_fields_float (FP32 src)
+rmt_status write_field(rmt_grid* g, int field, int solid_id, const void* src, size_t src_bytes, int src_is_device,
+                       bool f32) {
+  if (!g || !src) return RMT_EINVAL;
+  if (g->sticky != RMT_OK) return RMT_ESTATE;
+  rmt_status st = ensure_init(g);
+  if (st != RMT_OK) return st;
+  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
+  if (field != RMT_F_U && field != RMT_F_P && field != RMT_F_XI) return fail(g, RMT_EINVAL, "field %d is not writable", field);
+  if (field == RMT_F_XI && (solid_id < 0 || solid_id >= (int)g->bodies.size()))
+    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
+  const long n = rmt_field_len(g, field);
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
+  if (src_bytes < (size_t)n * esz) return fail(g, RMT_EINVAL, "source too small");
+  const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (f32 && g->fp32 && field != RMT_F_XI) {
+    // U and P of an FP32 grid are stored in this layout: one copy, no conversion
+    CK(g, cudaMemcpyAsync(field == RMT_F_U ? g->u : g->p, src, (size_t)n * sizeof(float), kind, g->s));
+    if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
+    return RMT_OK;
+  }
+  if (f32) {
+    if (!g->stage_f) CK(g, cudaMalloc((void**)&g->stage_f, (size_t)g->stage_len * sizeof(float)));
+    CK(g, cudaMemcpyAsync(g->stage_f, src, (size_t)n * sizeof(float), kind, g->s));
+    k_cvt<float><<<nbk(n), 256, 0, g->s>>>(g->stage_f, g->stage, n);
+    rmt_count_launches(1);
+  } else {
+    CK(g, cudaMemcpyAsync(g->stage, src, (size_t)n * sizeof(double), kind, g->s));
+  }
+  if (field == RMT_F_XI) drop_graphs(g);  // re-extrapolation resizes the body's launch windows
+  st = g->fp32 ? scatter_t<float>(g, field, solid_id) : scatter_t<double>(g, field, solid_id);
+  if (st != RMT_OK) return st;
+  if (field == RMT_F_XI) {
+    if ((st = check_err(g)) != RMT_OK) return st;
+    return size_windows(g);
+  }
+  if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
+  return RMT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1032,23 +1109,12 @@ long rmt_field_len(rmt_grid* g, int field) {
 
 
 rmt_status rmt_read_fields(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes, int dst_is_device) {
-  if (!g || !dst) return RMT_EINVAL;
-  rmt_status st = ensure_init(g);
-  if (st != RMT_OK) return st;
-  const long n = rmt_field_len(g, field);
-  if (n < 0) return fail(g, RMT_EINVAL, "unknown field %d", field);
-  if (dst_bytes < (size_t)n * sizeof(double)) return fail(g, RMT_EINVAL, "destination too small");
-  if ((field == RMT_F_XI || field == RMT_F_PHI || field == RMT_F_LAYER || field == RMT_F_XI_HALF) &&
-      (solid_id < 0 || solid_id >= (int)g->bodies.size()))
-    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
-  if (g->in_batch && g->batch_s != g->s) CK(g, cudaStreamSynchronize(g->batch_s));  // the batch's steps first
-  double* out = dst_is_device ? (double*)dst : g->stage;
-  st = g->fp32 ? gather_t<float>(g, field, solid_id, out) : gather_t<double>(g, field, solid_id, out);
-  if (st != RMT_OK) return st;
-  if (!dst_is_device)
-    CK(g, cudaMemcpyAsync(dst, g->stage, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, g->s));
-  CK(g, cudaStreamSynchronize(g->s));
-  return RMT_OK;
+  return read_field(g, field, solid_id, dst, dst_bytes, dst_is_device, false);
+}
+
+rmt_status rmt_read_fields_float(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes,
+                                 int dst_is_device) {
+  return read_field(g, field, solid_id, dst, dst_bytes, dst_is_device, true);
 }
 
 rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]) {
@@ -1091,27 +1157,12 @@ rmt_status rmt_body_stats(rmt_grid* g, int solid_id, double out[7]) {
 }
 
 rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* src, size_t src_bytes, int src_is_device) {
-  if (!g || !src) return RMT_EINVAL;
-  if (g->sticky != RMT_OK) return RMT_ESTATE;
-  rmt_status st = ensure_init(g);
-  if (st != RMT_OK) return st;
-  if (g->in_batch) return refuse(g, "the grid is stepped by its batch");
-  if (field != RMT_F_U && field != RMT_F_P && field != RMT_F_XI) return fail(g, RMT_EINVAL, "field %d is not writable", field);
-  if (field == RMT_F_XI && (solid_id < 0 || solid_id >= (int)g->bodies.size()))
-    return fail(g, RMT_EINVAL, "bad solid id %d", solid_id);
-  const long n = rmt_field_len(g, field);
-  if (src_bytes < (size_t)n * sizeof(double)) return fail(g, RMT_EINVAL, "source too small");
-  CK(g, cudaMemcpyAsync(g->stage, src, (size_t)n * sizeof(double),
-                        src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s));
-  if (field == RMT_F_XI) drop_graphs(g);  // re-extrapolation resizes the body's launch windows
-  st = g->fp32 ? scatter_t<float>(g, field, solid_id) : scatter_t<double>(g, field, solid_id);
-  if (st != RMT_OK) return st;
-  if (field == RMT_F_XI) {
-    if ((st = check_err(g)) != RMT_OK) return st;
-    return size_windows(g);
-  }
-  if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
-  return RMT_OK;
+  return write_field(g, field, solid_id, src, src_bytes, src_is_device, false);
+}
+
+rmt_status rmt_write_fields_float(rmt_grid* g, int field, int solid_id, const void* src, size_t src_bytes,
+                                  int src_is_device) {
+  return write_field(g, field, solid_id, src, src_bytes, src_is_device, true);
 }
 
 int rmt_last_cycles(rmt_grid* g, int which) { return g ? g->cycles[which ? 1 : 0] : -1; }
@@ -1130,6 +1181,7 @@ rmt_status rmt_destroy_grid(rmt_grid* g) {
     if (e) cudaEventDestroy(e);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   for (void* p : g->allocs) cudaFree(p);
+  if (g->stage_f) cudaFree(g->stage_f);
   if (g->err_h) cudaFreeHost(g->err_h);
   mg_destroy(g->mac);
   mg_destroy(g->fe);

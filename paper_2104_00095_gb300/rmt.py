@@ -26,7 +26,7 @@ RMT_F_REPULSION = 34
 RMT_JOB_QUEUED, RMT_JOB_RUNNING, RMT_JOB_DONE, RMT_JOB_FAILED = 0, 1, 2, 3
 
 EXPORTS = ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_field_len", "rmt_read_fields",
-           "rmt_write_fields", "rmt_last_cycles", "rmt_dt", "rmt_set_option", "rmt_kernel_launches", "rmt_profile",
+           "rmt_write_fields", "rmt_read_fields_float", "rmt_write_fields_float", "rmt_last_cycles", "rmt_dt", "rmt_set_option", "rmt_kernel_launches", "rmt_profile",
            "rmt_profile_entries", "rmt_profile_name", "rmt_profile_read", "rmt_extrapolate_noalloc", "rmt_destroy_grid",
            "rmt_last_error", "rmt_grid_footprint", "rmt_grid_device_bytes", "rmt_batch_create", "rmt_batch_add",
            "rmt_batch_remove", "rmt_batch_step", "rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy",
@@ -101,6 +101,8 @@ def load(build: bool = True):
     L.rmt_field_len.restype = C.c_long
     L.rmt_read_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
     L.rmt_write_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+    L.rmt_read_fields_float.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+    L.rmt_write_fields_float.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
     L.rmt_last_cycles.argtypes = [vp, C.c_int]
     L.rmt_dt.argtypes = [vp]
     L.rmt_dt.restype = C.c_double
@@ -160,7 +162,7 @@ def load(build: bool = True):
     L.rmt_wall_repulsion.argtypes = [C.c_double] * 8
     L.rmt_wall_repulsion.restype = C.c_double
     for f in ("rmt_create_grid", "rmt_add_solid", "rmt_step", "rmt_read_fields", "rmt_write_fields",
-              "rmt_destroy_grid", "rmt_batch_create", "rmt_batch_add", "rmt_batch_remove", "rmt_batch_step",
+              "rmt_read_fields_float", "rmt_write_fields_float", "rmt_destroy_grid", "rmt_batch_create", "rmt_batch_add", "rmt_batch_remove", "rmt_batch_step",
               "rmt_batch_sync", "rmt_batch_size", "rmt_batch_destroy", "rmt_server_create", "rmt_server_set_option",
               "rmt_server_submit", "rmt_server_poll", "rmt_server_job", "rmt_server_release", "rmt_server_destroy",
               "rmt_autotune"):
@@ -282,6 +284,27 @@ class Grid:
 
     def read_device(self, field: int, ptr: int, nbytes: int, solid: int = 0):
         self._check("rmt_read_fields", self._L.rmt_read_fields(self._g, field, solid, C.c_void_p(ptr), nbytes, 1))
+
+    def read_float(self, field: int, solid: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        n = self.field_len(field)
+        if out is None:
+            out = np.empty(n, dtype=np.float32)
+        self._check("rmt_read_fields_float",
+                    self._L.rmt_read_fields_float(self._g, field, solid, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def read_float_ptr(self, field: int, ptr: int, nbytes: int, is_device: int, solid: int = 0):
+        self._check("rmt_read_fields_float",
+                    self._L.rmt_read_fields_float(self._g, field, solid, C.c_void_p(ptr), nbytes, is_device))
+
+    def write_float(self, field: int, data: np.ndarray, solid: int = 0):
+        a = np.ascontiguousarray(data, dtype=np.float32).reshape(-1)
+        self._check("rmt_write_fields_float",
+                    self._L.rmt_write_fields_float(self._g, field, solid, a.ctypes.data, a.nbytes, 0))
+
+    def write_float_ptr(self, field: int, ptr: int, nbytes: int, is_device: int, solid: int = 0):
+        self._check("rmt_write_fields_float",
+                    self._L.rmt_write_fields_float(self._g, field, solid, C.c_void_p(ptr), nbytes, is_device))
 
     def write(self, field: int, data: np.ndarray, solid: int = 0):
         a = np.ascontiguousarray(data, dtype=np.float64).reshape(-1)

@@ -49,6 +49,24 @@ def test_nan_in_the_velocity_is_reported_at_once_in_adaptive_mode():
     g.close()
 
 
+def test_a_new_grid_starts_with_clean_error_words():
+    """The host copy of a grid's error words starts at zero.  A grid whose steps diverged leaves
+    non-zero words in its pinned buffer when it is destroyed; a new grid initialised by a read
+    polls its words at its first step, before a copy of its own has landed, and must not see the
+    old grid's words if the pinned block comes back to it."""
+    for _ in range(3):
+        bad = rmt.Grid(_fixed(S.cavity_sphere(24, precision="fp32")))
+        bad.set_option("inject_nan_step", 1)
+        bad.step(3)
+        bad.read(rmt.RMT_F_U)  # the diverged words have landed in the pinned buffer
+        bad.close()
+        g = rmt.Grid(_fixed(S.cavity_sphere(24, precision="fp32")))
+        g.read(rmt.RMT_F_LAYER, 0)  # initialises the grid (allocates its pinned words)
+        g.step(2)
+        assert np.all(np.isfinite(g.read(rmt.RMT_F_U)))
+        g.close()
+
+
 def test_a_clean_run_reports_nothing():
     g = rmt.Grid(_fixed(S.cavity_sphere(24, precision="fp32")))
     g.step(6)

@@ -11,8 +11,7 @@ import oracle as O
 from paper_2104_00095_gb300 import rmt, scenes as S
 from parity_util import compare_state, needs_gpu, pair, rel_l2
 
-# the multigrid schedule bench.py times (with 5 MAC and 4 FE V-cycles per solve)
-# the multigrid schedule bench.py times (fixed cycle counts)
+# the multigrid schedule bench.py times (5 MAC and 4 FE V-cycles per solve)
 BENCH_OPTIONS = {"fe_inner": 4, "mac_inner": 5, "mac_pre": 2, "mac_post": 2, "mac_omega": 1.15, "mac_coarse_pre": 2,
                  "mac_coarse_post": 2, "graph": 1}
 BENCH_CYCLES = {"mg_fixed_cycles": 5, "mg_fixed_cycles_fe": 4}
@@ -446,3 +445,47 @@ def test_body_stats_parity(prec):
             assert abs(a[5] - b[5]) <= 2e-2 * b[5]
     # deterministic: the same call twice gives the same bits
     assert np.array_equal(g.body_stats(0), g.body_stats(0))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_float_field_io_matches_the_fp64_calls(precision):
+    """rmt_read_fields_float / rmt_write_fields_float against the FP64 calls: reads are the FP64
+    values rounded to float (exact for u and p of an FP32 grid, which are stored as floats; xi of
+    a body goes through the conversion path), and a step after writing u as floats equals the
+    step after writing the same values through the FP64 call, bit for bit."""
+    import torch
+
+    sc = S.swimmers(n=32, nbodies=2, seed=5, precision=precision)
+    a, b = rmt.Grid(sc), rmt.Grid(sc)
+    a.step(2)
+    b.step(2)
+    for f in (rmt.RMT_F_U, rmt.RMT_F_P, rmt.RMT_F_RHO):
+        ref = a.read(f)
+        got = a.read_float(f)
+        assert got.dtype == np.float32 and np.array_equal(got, ref.astype(np.float32)), f
+        if precision == "fp32" and f != rmt.RMT_F_RHO:
+            assert np.array_equal(got.astype(np.float64), ref), f  # stored as floats: no rounding
+    xi = a.read(rmt.RMT_F_XI, 1)
+    xf = a.read_float(rmt.RMT_F_XI, 1)
+    assert np.array_equal(np.isnan(xf), np.isnan(xi))
+    ok = ~np.isnan(xi)
+    assert np.array_equal(xf[ok], xi[ok].astype(np.float32))
+    # device destination
+    d = torch.empty(a.field_len(rmt.RMT_F_U), dtype=torch.float32, device="cuda")
+    a.read_float_ptr(rmt.RMT_F_U, d.data_ptr(), d.numel() * 4, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), a.read_float(rmt.RMT_F_U))
+    # the same new velocity written both ways
+    u = (a.read(rmt.RMT_F_U) * 0.9).astype(np.float32)
+    a.write_float(rmt.RMT_F_U, u)
+    b.write(rmt.RMT_F_U, u.astype(np.float64))
+    assert np.array_equal(a.read(rmt.RMT_F_U), b.read(rmt.RMT_F_U))
+    a.step(1)
+    b.step(1)
+    for f in (rmt.RMT_F_U, rmt.RMT_F_P):
+        assert np.array_equal(a.read(f), b.read(f)), f
+    with pytest.raises(rmt.RMTError):
+        a.write_float(rmt.RMT_F_U, u[:-1])
+    a.close()
+    b.close()
+
