@@ -587,18 +587,26 @@ def main():
             g.read(rmt.RMT_F_U, out=host_in.numpy())
         barrier()
         torch.cuda.synchronize()
+        calls = np.zeros(3)  # host seconds in the write, step and read calls
         t0 = time.perf_counter()
         for _ in range(args.steps):
+            c0 = time.perf_counter()
             if f32:
                 g.write_float_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * esz, 0)
-                g.step(1)
-                g.read_float_ptr(rmt.RMT_F_U, host_out.data_ptr(), host_out.numel() * esz, 0)
             else:
                 g.write_ptr(rmt.RMT_F_U, host_in.data_ptr(), host_in.numel() * esz, 0)
-                g.step(1)
+            c1 = time.perf_counter()
+            g.step(1)
+            c2 = time.perf_counter()
+            if f32:
+                g.read_float_ptr(rmt.RMT_F_U, host_out.data_ptr(), host_out.numel() * esz, 0)
+            else:
                 g.read(rmt.RMT_F_U, out=host_out.numpy())
+            calls += (c1 - c0, c2 - c1, time.perf_counter() - c2)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        print("e2e host ms per step in write / step / read calls: " +
+              " / ".join(f"{1e3 * v / args.steps:.2f}" for v in calls), file=sys.stderr)
         et = t1 - t0
         et = max_over_ranks(et, world)
         e2e = {"value": job_rate(world, N, args.steps, et), "unit": "cell-updates/s",

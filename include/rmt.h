@@ -149,7 +149,10 @@ rmt_status rmt_write_fields(rmt_grid* g, int field, int solid_id, const void* sr
  * rmt_field_len): the FP64 values rounded to float, or converted from float.  For U and P of an
  * RMT_PREC_FP32_REFINE grid these are the stored values themselves, copied without conversion
  * (half the bytes of the FP64 calls, and no rounding either way).  Same synchronisation and
- * errors as rmt_read_fields / rmt_write_fields. */
+ * errors as rmt_read_fields / rmt_write_fields, except that writing U or P of such a grid from
+ * page-locked host memory (cudaHostAlloc / cudaMallocHost / registered) leaves the copy
+ * asynchronous on the grid's stream: the caller must not modify src until a call that
+ * synchronises the grid (a read, for one) has returned. */
 rmt_status rmt_read_fields_float(rmt_grid* g, int field, int solid_id, void* dst, size_t dst_bytes,
                                  int dst_is_device);
 rmt_status rmt_write_fields_float(rmt_grid* g, int field, int solid_id, const void* src,

@@ -910,9 +910,18 @@ rmt_status write_field(rmt_grid* g, int field, int solid_id, const void* src, si
   if (src_bytes < (size_t)n * esz) return fail(g, RMT_EINVAL, "source too small");
   const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (f32 && g->fp32 && field != RMT_F_XI) {
-    // U and P of an FP32 grid are stored in this layout: one copy, no conversion
+    // U and P of an FP32 grid are stored in this layout: one copy, no conversion.  From
+    // page-locked host memory the copy stays asynchronous (the host can launch the next step
+    // while it runs; the caller keeps src until a synchronising call), from pageable memory the
+    // call waits so that the caller may reuse src at once.
     CK(g, cudaMemcpyAsync(field == RMT_F_U ? g->u : g->p, src, (size_t)n * sizeof(float), kind, g->s));
-    if (!src_is_device) CK(g, cudaStreamSynchronize(g->s));  // the caller may reuse src
+    if (!src_is_device) {
+      cudaPointerAttributes at;
+      const cudaError_t pe = cudaPointerGetAttributes(&at, src);
+      if (pe != cudaSuccess) cudaGetLastError();  // not a pointer the runtime knows: pageable
+      const bool pinned = pe == cudaSuccess && at.type == cudaMemoryTypeHost;
+      if (!pinned) CK(g, cudaStreamSynchronize(g->s));
+    }
     return RMT_OK;
   }
   if (f32) {

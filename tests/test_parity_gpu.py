@@ -484,6 +484,14 @@ def test_float_field_io_matches_the_fp64_calls(precision):
     b.step(1)
     for f in (rmt.RMT_F_U, rmt.RMT_F_P):
         assert np.array_equal(a.read(f), b.read(f)), f
+    # from page-locked memory the write stays asynchronous; the next step is ordered after it
+    pin = torch.from_numpy(u * np.float32(1.1)).pin_memory()
+    a.write_float_ptr(rmt.RMT_F_U, pin.data_ptr(), pin.numel() * 4, 0)
+    b.write(rmt.RMT_F_U, pin.numpy().astype(np.float64))
+    a.step(1)
+    b.step(1)
+    for f in (rmt.RMT_F_U, rmt.RMT_F_P):
+        assert np.array_equal(a.read(f), b.read(f)), f
     with pytest.raises(rmt.RMTError):
         a.write_float(rmt.RMT_F_U, u[:-1])
     a.close()
