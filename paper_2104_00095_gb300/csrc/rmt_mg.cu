@@ -454,10 +454,14 @@ __global__ void __launch_bounds__(BX* BYMAX) k_first_resid64(Lv L, int kind, dou
   block_partial(loc, part);
 }
 
-// the same for the two-float right-hand side (FP32 mode; mean given as a two-float pair)
+// the same for the two-float right-hand side (FP32 mode; mean given as a two-float pair).
+// once: the solve is a single pass from zero (fixed cycles, no later residual), so the
+// mean-free right-hand side is not stored back, no norm is needed, and the storage-precision
+// iterate x is zeroed here instead of by a separate launch.
 __global__ void __launch_bounds__(BX* BYMAX) k_first_resid_ff(Lv L, int kind, float* __restrict__ bh,
                                                             float* __restrict__ bl, const float* __restrict__ mean,
-                                                            float* __restrict__ rT, double* __restrict__ part) {
+                                                            float* __restrict__ rT, double* __restrict__ part,
+                                                            int once, float* __restrict__ x) {
   const int ext[3] = {kind == 0 ? L.n[0] : L.nn[0], kind == 0 ? L.n[1] : L.nn[1], kind == 0 ? L.n[2] : L.nn[2]};
   int i, j, k;
   float loc = 0.0f;
@@ -465,13 +469,17 @@ __global__ void __launch_bounds__(BX* BYMAX) k_first_resid_ff(Lv L, int kind, fl
     const long u = (long)(i + ext[0] * (j + ext[1] * k));
     float h = bh[u], l = bl[u];
     ff_sub_pair(h, l, mean);
-    bh[u] = h;
-    bl[u] = l;
     const float r = __fadd_rn(h, l);
     rT[u] = r;
-    loc = r * r;
+    if (once) {
+      x[u] = 0.0f;
+    } else {
+      bh[u] = h;
+      bl[u] = l;
+      loc = r * r;
+    }
   }
-  block_partial_f(loc, part);
+  if (!once) block_partial_f(loc, part);
 }
 
 // residual r = b - A x of the two-float iterate (xh + xl) against the two-float right-hand
@@ -2053,12 +2061,17 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
       bn2 = m->hpin[0];
     }
   }
+  // a single FP32 pass from zero: fixed cycles that one round of inner V-cycles covers
+  const bool once = ff && !have_x && fixed_cycles > 0 && m->inner >= fixed_cycles;
+  bool x_zeroed = false;
   for (;;) {
     if (!have_x) {
       // the residual of the zero iterate is b itself: remove its mean, no operator
-      if constexpr (ff)
-        k_first_resid_ff<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->bh, m->bl, fm, (float*)m->b[0], m->part);
-      else
+      if constexpr (ff) {
+        k_first_resid_ff<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->bh, m->bl, fm, (float*)m->b[0], m->part,
+                                                        once ? 1 : 0, (float*)m->x[0]);
+        x_zeroed = once;
+      } else
         k_first_resid64<<<g0, dim3(BX, m->by), 0, s>>>(L0, m->kind, m->b64, m->scal, (double*)m->b[0], m->part);
       rmt_count_launches(1);
     } else {
@@ -2090,8 +2103,11 @@ int solve_t(MGSolver* m, double rtol, int max_cycles, int fixed_cycles, cudaStre
       if (fixed_cycles <= 0) ok = 0;
       break;
     }
-    k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
-    rmt_count_launches(1);
+    if (!x_zeroed) {
+      k_zero<T><<<nblocks(n), TPB, 0, s>>>((T*)m->x[0], n);
+      rmt_count_launches(1);
+    }
+    x_zeroed = false;
     // inner V-cycles on A e = r in the storage type (the high-precision residual is re-formed after them)
     for (int q = 0; q < m->inner && cycles < cap; q++) {
       vcycle<T>(m, 0, s);
