@@ -54,3 +54,27 @@ def test_replicas_max_over_ranks_and_job_rate():
         assert res[r][1] == pytest.approx(2 * 256**3 * 10 / 30.25e-3)
     assert res[0][2] == 1 and '"impl": "reference"' in res[0][3]
     assert res[1][2] == 0 and res[1][3] == ""
+
+
+def test_dram_traffic_record_follows_its_source_file(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed small-case ncu record, scaled by the cell count,
+    and only while the kernel's source file still hashes to the record's prefix."""
+    import hashlib
+
+    import bench
+
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    rec = tmp_path / "profiles" / "dram_traffic_small_case.txt"
+    rec.write_text(f"# comment\nk_x    1000    10    k.cu    {sha}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.dram_traffic("k_x", 40) == pytest.approx(4000.0)
+    assert bench.dram_traffic("k_other", 40) is None
+    src.write_text("kernel source, changed\n")
+    assert bench.dram_traffic("k_x", 40) is None
+    # the committed record parses; it counts while the sweep kernel's file is the one captured
+    monkeypatch.setattr(bench, "ROOT", ROOT)
+    t = bench.dram_traffic("k_rbgs_sweep(mac,level0)", 256**3)
+    assert t is None or 0.5 * 16 * 256**3 < t < 1.5 * 16 * 256**3
