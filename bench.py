@@ -235,7 +235,8 @@ def solver_options(args, graph: bool = True) -> dict:
     """The multigrid schedule of the timed configuration (rmt_set_option names)."""
     o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm, "fe_warm": args.fe_warm,
          "mac_pre": args.mac_sweeps, "mac_post": args.mac_sweeps, "mac_omega": args.mac_omega,
-         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse}
+         "mac_coarse_pre": args.mac_coarse, "mac_coarse_post": args.mac_coarse,
+         "fe_pre": args.fe_pre, "fe_post": args.fe_post, "fe_omega": args.fe_omega}
     if graph:
         o["graph"] = args.graph
     return o
@@ -466,6 +467,9 @@ def main():
                     help="over-relaxation factor of the MAC red-black sweeps")
     ap.add_argument("--mac-coarse", type=int, default=2,
                     help="red-black sweeps before and after the coarse correction on the MAC levels below the finest")
+    ap.add_argument("--fe-pre", type=int, default=2, help="weighted Jacobi sweeps before the coarse correction (FE)")
+    ap.add_argument("--fe-post", type=int, default=1, help="weighted Jacobi sweeps after the coarse correction (FE)")
+    ap.add_argument("--fe-omega", type=float, default=1.0, help="weight of the FE Jacobi sweeps")
     ap.add_argument("--graph", type=int, default=1, help="replay each step as one captured CUDA graph")
     ap.add_argument("--nbodies", type=int, default=None,
                     help="override the body count (profiling captures only; changes the workload)")
@@ -566,7 +570,11 @@ def main():
     # for the stages outside the projections plus 24 per V-cycle (six finest-level passes over x,
     # b and rho and one write), k_MAC + k_FE cycles, and 1/7 more for the coarse levels
     word = 4 if cfg["precision"] == "fp32" else 8
-    model_words = 55 + 24 * (args.mg_cycles_mac + args.mg_cycles_fe) * 8.0 / 7.0
+    # about 24 words per V-cycle for 6 fine-level passes (2 + 2 sweeps, the residual and the
+    # transfers), scaled by the passes the schedule makes
+    mac_passes = 2 * args.mac_sweeps + 2
+    fe_passes = args.fe_pre + args.fe_post + 2
+    model_words = 55 + 24 * (args.mg_cycles_mac * mac_passes / 6.0 + args.mg_cycles_fe * fe_passes / 6.0) * 8.0 / 7.0
     step_achieved = model_words * word * N / (ms / args.steps / 1e3) / 1e9
     step_roofline = {"model_bytes_per_cell_step": model_words * word, "achieved": step_achieved, "peak": peak,
                      "unit": "GB/s", "frac": step_achieved / peak, "peak_source": peak_kind}
@@ -642,6 +650,8 @@ def main():
                                                    "mac_inner": args.mac_inner, "fe_inner": args.fe_inner,
                                                    "mac_sweeps": args.mac_sweeps, "mac_omega": args.mac_omega,
                                                    "mac_coarse_sweeps": args.mac_coarse,
+                                                   "fe_sweeps": [args.fe_pre, args.fe_post],
+                                                   "fe_omega": args.fe_omega,
                                                    "mac_warm_start": bool(args.mac_warm),
                                                    "fe_warm_start": bool(args.fe_warm)},
                            "step_graph": bool(args.graph),

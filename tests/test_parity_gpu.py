@@ -13,7 +13,7 @@ from parity_util import compare_state, needs_gpu, pair, rel_l2
 
 # the multigrid schedule bench.py times (5 MAC and 4 FE V-cycles per solve)
 BENCH_OPTIONS = {"fe_inner": 4, "mac_inner": 5, "mac_pre": 2, "mac_post": 2, "mac_omega": 1.15, "mac_coarse_pre": 2,
-                 "mac_coarse_post": 2, "graph": 1}
+                 "mac_coarse_post": 2, "fe_pre": 2, "fe_post": 1, "fe_omega": 1.0, "graph": 1}
 BENCH_CYCLES = {"mg_fixed_cycles": 5, "mg_fixed_cycles_fe": 4}
 
 pytestmark = [pytest.mark.gpu, needs_gpu]
@@ -350,7 +350,8 @@ def test_uneven_multigrid_hierarchies(n, prec):
 def test_bench_cycle_counts_stay_close_to_the_converged_solve(scene):
     """The fixed-cycle configuration that bench.py times (5 MAC cycles after one two-float
     residual, 2 red-black sweeps each way over-relaxed by 1.15 on the finest level and 2 on the
-    others, 4 FE cycles after one two-float residual) against adaptive solves to 1e-9, after 6 and 12 steps in FP32:
+    others, 4 FE cycles after one two-float residual with 2 + 1 Jacobi sweeps of weight 1) against
+    adaptive solves to 1e-9, after 6 and 12 steps in FP32:
     the swimmer scene on a small copy and on the benchmark's own 256^3 grid (an FP32 V-cycle's
     accuracy on smooth modes falls with n, so the small case alone does not cover the
     benchmark), and the settling mixture between no-slip walls."""
