@@ -231,6 +231,15 @@ def timed_steps(g, steps: int, stream) -> float:
     return a.elapsed_time(b) / steps
 
 
+def step_model_words(args) -> float:
+    """Words moved per cell-step by the whole-step byte model: 55 outside the projections, and
+    about 24 per V-cycle for 6 fine-level passes (2 + 2 sweeps, the residual and the transfers),
+    scaled by the passes the schedule makes; 8/7 for the coarser levels."""
+    mac_passes = 2 * args.mac_sweeps + 2
+    fe_passes = args.fe_pre + args.fe_post + 2
+    return 55 + 24 * (args.mg_cycles_mac * mac_passes / 6.0 + args.mg_cycles_fe * fe_passes / 6.0) * 8.0 / 7.0
+
+
 def solver_options(args, graph: bool = True) -> dict:
     """The multigrid schedule of the timed configuration (rmt_set_option names)."""
     o = {"fe_inner": args.fe_inner, "mac_inner": args.mac_inner, "mac_warm": args.mac_warm, "fe_warm": args.fe_warm,
@@ -570,11 +579,7 @@ def main():
     # for the stages outside the projections plus 24 per V-cycle (six finest-level passes over x,
     # b and rho and one write), k_MAC + k_FE cycles, and 1/7 more for the coarse levels
     word = 4 if cfg["precision"] == "fp32" else 8
-    # about 24 words per V-cycle for 6 fine-level passes (2 + 2 sweeps, the residual and the
-    # transfers), scaled by the passes the schedule makes
-    mac_passes = 2 * args.mac_sweeps + 2
-    fe_passes = args.fe_pre + args.fe_post + 2
-    model_words = 55 + 24 * (args.mg_cycles_mac * mac_passes / 6.0 + args.mg_cycles_fe * fe_passes / 6.0) * 8.0 / 7.0
+    model_words = step_model_words(args)
     step_achieved = model_words * word * N / (ms / args.steps / 1e3) / 1e9
     step_roofline = {"model_bytes_per_cell_step": model_words * word, "achieved": step_achieved, "peak": peak,
                      "unit": "GB/s", "frac": step_achieved / peak, "peak_source": peak_kind}

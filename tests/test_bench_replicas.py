@@ -78,3 +78,15 @@ def test_dram_traffic_record_follows_its_source_file(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", ROOT)
     t = bench.dram_traffic("k_rbgs_sweep(mac,level0)", 256**3)
     assert t is None or 0.5 * 16 * 256**3 < t < 1.5 * 16 * 256**3
+
+
+def test_step_byte_model_counts_the_schedule():
+    """The whole-step byte model: 24 words per V-cycle of 6 passes, scaled by the passes the
+    schedule makes (2 + 2 MAC sweeps and 2 + 1 FE sweeps: 6 and 5 passes)."""
+    import bench
+
+    A = type("A", (), dict(mac_sweeps=2, fe_pre=2, fe_post=2, mg_cycles_mac=5, mg_cycles_fe=4))
+    assert bench.step_model_words(A()) == pytest.approx(55 + 24 * 9 * 8 / 7)
+    A.fe_post = 1
+    assert bench.step_model_words(A()) == pytest.approx(55 + 24 * (5 + 4 * 5 / 6) * 8 / 7)
+    assert bench.step_model_words(A()) * 4 == pytest.approx(1134.2857, rel=1e-6)
